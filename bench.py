@@ -1,0 +1,379 @@
+#!/usr/bin/env python3
+"""Benchmark: local ROI reconstructions per second on one GB300 (or N, one rank each).
+
+One step = one pass of the whole local pipeline on one region of the 1024 x 1024
+workload (256 angles, 1024 bins, 50 ellipses + fine texture, I0 = 5e3, ROI radius
+64 px + margin 32 px, Chambolle-Pock TV lambda = 0.01, 500 iterations, FP32):
+copy the resident sinogram into the handle, Ram-Lak FBP, ROI plan, exterior
+reprojection and subtraction, 500 CP iterations on the 192 x 192 box, crop.
+Steps cycle over 8 seeded regions so each plans a new box.
+
+Timing: W warm-up steps; then K steps between a barrier + synchronize on both
+sides; each step is bracketed by CUDA events on the library's stream and a
+256 MB write flushes L2 between steps (outside the events).  ``value`` is
+(steps x ranks) / max over ranks of the summed step time.  ``e2e`` repeats the
+step through the C ABI with host buffers: pinned host sinogram in, host image out.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead (rank 0
+only): each step is FBP + exterior + a bounded number of CP iterations, scaled to
+a whole solve.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1604_02292_gb300 import workloads as WL  # noqa: E402
+
+WORKLOAD = "roi_cptv_1024"
+N_REGIONS = 8
+FLUSH_BYTES = 256 << 20
+# lerps one SM can retire per clock: a Joseph interpolation needs two shared/L1 loads
+# (32 lanes per clock per SM) and ~8 FP32-pipe instructions (128 lanes per clock per SM),
+# both giving 16 lerps per clock per SM
+LERPS_PER_CLK_SM = 16
+N_SM = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WL.WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        smi = shutil.which("nvidia-smi")
+        if smi:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen([smi, f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def lerps_per_launch(pl, w):
+    """Algorithmic work of the two projector kernels for one box: forward = window rays x
+    samples (the box side along the stepping axis); back = pixels x angles."""
+    nx, ny = pl.box[2], pl.box[3]
+    th = np.arange(w.n_angles) * math.pi / w.n_angles
+    row = np.abs(np.cos(th)) >= np.abs(np.sin(th)) - 1e-12
+    steps = np.where(row, ny, nx)
+    fwd = int(np.sum(np.asarray(pl.width) * steps))
+    back = int(nx * ny * w.n_angles)
+    return fwd, back
+
+
+def bytes_per_launch(pl, w):
+    """Algorithmic DRAM-level bytes (each operand once) of the CP projector kernels."""
+    n = pl.box[2] * pl.box[3]
+    win = int(np.sum(pl.width))
+    fwd = 4 * (n + 4 * win)          # read xbar; read p', sigma, u; write u
+    back = 4 * (win + 4 * n + 3 * n)  # read u; read x, tau, vx, vy; write x, xbar, xbar^T
+    return fwd, back
+
+
+# --------------------------------------------------------------------------- oracle arm
+
+def oracle_sample(w, p, region, cp_iters):
+    """Time the FP64 oracle: FBP + exterior + cp_iters CP iterations; returns seconds per
+    whole solve (CP time scaled to w.iters) and the parts."""
+    import oracle
+    g = oracle.Geometry(*w.geometry())
+    box = oracle.roi_box(w.N, *region)
+    t0 = time.perf_counter()
+    xf = oracle.fbp(g, p.astype(np.float64))
+    t1 = time.perf_counter()
+    pp = oracle.exterior(g, box, p.astype(np.float64), xf)
+    t2 = time.perf_counter()
+    if w.reg == "sirt":
+        oracle.sirt(g, box, pp, cp_iters)
+    else:
+        oracle.cp_tv(g, box, pp, cp_iters, w.lam, precond=1)
+    t3 = time.perf_counter()
+    per_solve = (t1 - t0) + (t2 - t1) + (t3 - t2) * (w.iters / cp_iters)
+    return per_solve, (t1 - t0, t2 - t1, t3 - t2)
+
+
+def omp_threads():
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = WL.WORKLOADS[args.workload]
+    p = WL.sinogram(w, 0)
+    regions = [WL.region(w, seed=s) for s in range(N_REGIONS)]
+    cp_iters = 25
+    for k in range(args.warmup):
+        oracle_sample(w, p, regions[k % N_REGIONS], 2)
+    times = []
+    for k in range(args.steps):
+        t, _ = oracle_sample(w, p, regions[k % N_REGIONS], cp_iters)
+        times.append(t)
+    total = sum(times)
+    value = args.steps / total
+    sample = (f"each step: oracle FBP + exterior + {cp_iters} of {w.iters} CP iterations on one region, "
+              f"CP time scaled by {w.iters}/{cp_iters}")
+    line = {
+        "impl": "reference", "metric": "roi_solves_per_s", "value": value, "unit": "solves/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "N": w.N, "n_angles": w.n_angles, "n_det": w.n_det,
+                   "roi_radius": w.radius, "roi_margin": w.margin, "solver": w.reg, "iters": w.iters,
+                   "lambda": w.lam},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": omp_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------ our arm
+
+def run_ours(args):
+    import torch
+
+    import paper_1604_02292_gb300 as R
+
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = WL.WORKLOADS[args.workload]
+    p_host = WL.sinogram(w, seed=rank)
+    regions = [WL.region(w, seed=rank * 1000 + s) for s in range(N_REGIONS)]
+    reg = R.ROI_TV_CP if w.reg == "tv" else R.ROI_SIRT_NONNEG
+    stream = torch.cuda.Stream()
+    rr = R.RoiRecon(*w.geometry(), stream=stream)
+    plans = [rr.plan(r) for r in regions]
+    p_dev = torch.from_numpy(p_host).cuda()
+    outs = [torch.empty((pl.box[3], pl.box[2]), dtype=torch.float32, device="cuda") for pl in plans]
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+
+    def step(k):
+        j = k % N_REGIONS
+        rr.set_sinogram(p_dev)
+        rr.fbp()
+        rr.solve_local(regions[j], reg, iters=w.iters, lam=w.lam, out=outs[j])
+
+    with torch.cuda.stream(stream):
+        for k in range(args.warmup):
+            step(k)
+    torch.cuda.synchronize()
+
+    # ---- timed region
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    n0 = R.roi_recon_launch_count()
+    t_wall0 = time.perf_counter()
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                flush.fill_(float(k))          # evict L2 between steps (outside the events)
+                ev[k][0].record(stream)
+                step(k)
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    if dist:
+        dist.barrier()
+    launches = R.roi_recon_launch_count() - n0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    tmax = total_s
+    if dist:
+        t = torch.tensor([total_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tmax = float(t.item())
+    value = ws * args.steps / tmax
+
+    # ---- projector kernels: per-launch device time from events inside the solve loop
+    rr.set_timing(True)
+    with torch.cuda.stream(stream):
+        step(0)
+    nf, msf = rr.kernel_times(0)
+    nb, msb = rr.kernel_times(1)
+    rr.set_timing(False)
+    lf, lb = lerps_per_launch(plans[0], w)
+    bf, bb = bytes_per_launch(plans[0], w)
+    avg_f, avg_b = msf / max(nf, 1), msb / max(nb, 1)
+    dominant = "back" if msb >= msf else "forward"
+    lerps, avg_ms, alg_bytes = (lb, avg_b, bb) if dominant == "back" else (lf, avg_f, bf)
+    pk, pk_src = peaks()
+    clocks = clk.summary()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    peak_glerps = N_SM * LERPS_PER_CLK_SM * sm_max * 1e6 / 1e9
+    achieved = lerps / (avg_ms * 1e-3) / 1e9
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        p_pin = torch.from_numpy(p_host).pin_memory()
+        outs_h = [torch.empty((pl.box[3], pl.box[2]), dtype=torch.float32).pin_memory().numpy() for pl in plans]
+        with torch.cuda.stream(stream):
+            for k in range(2):
+                rr.set_sinogram(p_pin.numpy())
+                rr.fbp()
+                rr.solve_local(regions[k % N_REGIONS], reg, iters=w.iters, lam=w.lam, out=outs_h[k % N_REGIONS])
+            torch.cuda.synchronize()
+            ke = max(3, args.steps // 2)
+            t0 = time.perf_counter()
+            for k in range(ke):
+                j = k % N_REGIONS
+                rr.set_sinogram(p_pin.numpy())
+                rr.fbp()
+                rr.solve_local(regions[j], reg, iters=w.iters, lam=w.lam, out=outs_h[j])  # synchronizes
+            te = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([te], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": ws * ke / te, "unit": "solves/s", "h2d_bytes_per_step": int(p_host.nbytes),
+               "d2h_bytes_per_step": int(outs_h[0].nbytes), "steps": ke}
+
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, one GPU only)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cp_iters = 50
+        per_solve, parts = oracle_sample(w, p_host, regions[0], cp_iters)
+        cpu = {"value": 1.0 / per_solve, "unit": "solves/s", "cores": omp_threads(), "kind": "oracle",
+               "sample": (f"one region: FP64 oracle FBP ({parts[0]:.2f} s) + exterior ({parts[1]:.2f} s) + "
+                          f"{cp_iters} of {w.iters} CP iterations ({parts[2]:.2f} s), CP time scaled by "
+                          f"{w.iters}/{cp_iters}")}
+
+    if rank == 0:
+        sm = sorted(step_ms)
+        line = {
+            "metric": "roi_solves_per_s", "value": value, "unit": "solves/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": w.name, "N": w.N, "n_angles": w.n_angles, "n_det": w.n_det,
+                       "roi_radius": w.radius, "roi_margin": w.margin, "box": plans[0].box[2],
+                       "solver": w.reg, "iters": w.iters, "lambda": w.lam, "regions": N_REGIONS,
+                       "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}"},
+            "latency_ms": {"p50": sm[len(sm) // 2], "p99": sm[min(len(sm) - 1, int(math.ceil(0.99 * len(sm))) - 1)],
+                           "min": sm[0], "max": sm[-1]},
+            "wall_s_timed_region": t_wall,
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "alu", "kernel": f"k_{dominant} (CP)", "achieved": achieved,
+                         "peak": peak_glerps, "unit": "Glerp/s", "frac": achieved / peak_glerps,
+                         "traffic": None, "peak_source": f"derived: {N_SM} SMs x {LERPS_PER_CLK_SM} lerp/clk x "
+                                                         f"{sm_max:.0f} MHz ({pk_src} sm_max_mhz)",
+                         "launch_ms": avg_ms, "lerps_per_launch": lerps,
+                         "algorithmic_GBps": alg_bytes / (avg_ms * 1e-3) / 1e9,
+                         "hbm_peak_GBps": pk.get("hbm_gbs")},
+            "projectors": {"forward_ms": avg_f, "back_ms": avg_b, "forward_lerps": lf, "back_lerps": lb,
+                           "launches": [nf, nb]},
+            "clocks": clocks,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    rr.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,198 @@
+/*
+ * roi_recon.h -- C ABI of the GB300 local region-of-interest reconstruction library.
+ *
+ * Method: Pelt & Batenburg, "A method for locally approximating regularized
+ * iterative tomographic reconstruction methods" (arXiv 1604.02292).
+ *
+ * The library reconstructs a square local part L (an "extended ROI box") of an
+ * N x N image from a 2D parallel-beam sinogram.  It follows the
+ * exterior-subtraction scheme the paper describes in Sec. 1: a global Ram-Lak
+ * FBP (Eq. fbp), reprojection of that image outside L and subtraction from the
+ * data (W = W_L + W_F, Eq. locouter), then a regularized iterative solve on L
+ * only -- nonnegative SIRT (Eq. sirtit, Eq. sirtbox) or total variation
+ * (Eq. priorsys with g = ||grad x||_1) by Chambolle-Pock.
+ *
+ * Conventions (every entry point):
+ *   - Geometry (Sec. 2.1): pixel (i, j) = (row from the top, column) has centre
+ *     (j - (N-1)/2, (N-1)/2 - i); bin d has centre t_d = d - (n_det-1)/2; a ray is
+ *     x cos(theta) + y sin(theta) = t.  Sinograms are row-major [n_angles][n_det],
+ *     images row-major [rows][columns], float32 unless stated.
+ *   - Projector: Joseph's method, one ray per bin centre, sampled per row when
+ *     |cos| >= |sin| (per column otherwise) with linear interpolation; the
+ *     backprojector is its exact transpose.
+ *   - Regions are given in pixel-index units: centre (cx = column, cy = row),
+ *     radius r and margin m.  The extended box is the 2R x 2R pixels,
+ *     R = ceil(r + m), whose centre indices are nearest to [c - R, c + R),
+ *     clipped to the grid (Sec. 3.3 pads the local part and crops afterwards).
+ *   - Streams: all device work of a handle is ordered on the CUDA stream given
+ *     to roi_recon_create and is asynchronous with respect to the host, unless
+ *     an entry point says it synchronizes.  Device pointers passed in must stay
+ *     valid until that work completes.
+ *   - Ownership: the handle owns its device copy of the sinogram, the cached
+ *     FBP image and all scratch.  The caller owns every buffer it passes.
+ *   - Errors: every entry point returns a roi_status and never throws or aborts.
+ *     ROI_EINVAL for bad arguments, ROI_ESTATE for calls out of order,
+ *     ROI_ENOMEM when a device allocation fails, ROI_ECUDA for other CUDA errors,
+ *     ROI_ETIMEOUT when a bounded device-side wait gives up.  A message is kept
+ *     per handle (roi_recon_last_error).
+ *   - Threads: a handle may be used by one host thread at a time.
+ */
+#ifndef ROI_RECON_H
+#define ROI_RECON_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct roi_recon* roi_recon_t;
+
+typedef enum {
+    ROI_OK = 0,
+    ROI_EINVAL = 1,
+    ROI_ENOMEM = 2,
+    ROI_ESTATE = 3,
+    ROI_ECUDA = 4,
+    ROI_ETIMEOUT = 5,
+    ROI_EBUSY = 6
+} roi_status;
+
+typedef enum { ROI_F32 = 0, ROI_BF16 = 1, ROI_F16 = 2 } roi_dtype;
+
+typedef enum { ROI_SIRT_NONNEG = 0, ROI_TV_CP = 1 } roi_regularizer;
+
+/* Acquisition geometry (Sec. 2.1: N x N grid, N_d detectors, N_theta angles). */
+typedef struct {
+    int n_pix;             /* N >= 1                                                   */
+    int n_angles;          /* N_theta >= 1                                             */
+    int n_det;             /* N_d >= 1                                                 */
+    const double* angles;  /* host array of n_angles radians, copied; NULL: a*pi/N_theta */
+    roi_dtype storage;     /* storage type of the resident sinogram: ROI_F32 only       */
+} roi_geometry;
+
+/* Region of interest in pixel-index units (see Conventions). */
+typedef struct {
+    double cx, cy;   /* centre: column, row            */
+    double radius;   /* r > 0                           */
+    double margin;   /* m >= 0, padding around the disk */
+} roi_region;
+
+typedef struct {
+    roi_regularizer reg;   /* ROI_SIRT_NONNEG or ROI_TV_CP                                  */
+    double lambda;         /* TV weight (CP); the data term is ||p' - W_L x||^2, no 1/2     */
+    int iters;             /* iterations >= 0 (200 SIRT / 500 CP in the reference workloads) */
+    int weighting;         /* SIRT: 0 = scalar alpha = 1/(N_theta N_d) (Sec. 3.1),
+                              1 = row/column-sum weights x += C W_L^T R (p' - W_L x)          */
+    int precond;           /* CP: 1 = diagonal steps (Pock & Chambolle 2011), 0 = 0.99/||K||  */
+    int crop_disk;         /* 1: set output pixels outside the disk of radius r to 0          */
+    int eval_objective;    /* 1: fill info->objective (the call then synchronizes)            */
+} roi_solve_params;
+
+/* Plan and result description of one local solve. */
+typedef struct {
+    int box_x0, box_y0, box_w, box_h;  /* extended box: columns [x0, x0+w), rows [y0, y0+h) */
+    int window_max;                    /* max over angles of the number of bins reaching the box */
+    int window_stride;                 /* row stride of window buffers (multiple of 4, >= max) */
+    int iters_done;
+    double step_L;                     /* CP with precond = 0: the ||K|| used; 0 otherwise      */
+    double objective;                  /* eval_objective: ||W_L x - p'||^2 + lambda TV(x)        */
+} roi_solve_info;
+
+/* --------------------------------------------------------------------------
+ * Handle life cycle and data
+ * ------------------------------------------------------------------------ */
+
+/* Create a handle for geometry *geom, ordering all work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream) of the current device.
+ * Allocates the sinogram, filter and FBP buffers (4 (2 N_theta N_d + 2 N^2) bytes).
+ * ROI_EINVAL for non-positive sizes or storage != ROI_F32, ROI_ENOMEM if the
+ * device allocation fails.  *out is NULL on failure. */
+roi_status roi_recon_create(const roi_geometry* geom, void* cuda_stream, roi_recon_t* out);
+
+/* Release every resource of the handle (waits for its stream first).  NULL is ignored. */
+void roi_recon_destroy(roi_recon_t h);
+
+/* Message of the last failed call on this handle ("" if none).  Valid until the next call. */
+const char* roi_recon_last_error(roi_recon_t h);
+
+/* Copy the measured sinogram p (Sec. 2.1), [n_angles][n_det] float32, into the handle.
+ * on_device = 1: p is a device pointer (device-to-device copy, asynchronous);
+ * on_device = 0: p is host memory, copied with cudaMemcpyAsync semantics: pageable
+ * memory is consumed before the call returns, page-locked memory must stay unchanged
+ * until the handle's stream has passed the copy.  dt must be ROI_F32.
+ * Invalidates the cached FBP image. */
+roi_status roi_recon_set_sinogram(roi_recon_t h, const void* p, roi_dtype dt, int on_device);
+
+/* Global filtered backprojection FBP(p, h) = W^T C_h p (Eq. fbp), Ram-Lak filter
+ * scaled by pi/N_theta, on the whole N x N grid; the result is cached in the
+ * handle for the exterior step.  out_or_null: optional device [N][N] float32 copy.
+ * ROI_ESTATE before set_sinogram. */
+roi_status roi_recon_fbp(roi_recon_t h, float* out_or_null);
+
+/* Exterior subtraction (Sec. 1; Eq. locouter): p' = p - W M_F x_fbp on every ray that
+ * reaches the extended box of *region.  window_out_or_null: optional device buffer
+ * [n_angles][window_stride] float32 receiving p'; entry [a][k] belongs to bin
+ * d0[a] + k, entries past the angle's width are 0.  d0_out_or_null: optional host
+ * int[n_angles] receiving d0 (the call then synchronizes).  Sizes come from
+ * roi_recon_plan.  ROI_ESTATE before fbp. */
+roi_status roi_recon_reproject_exterior(roi_recon_t h, const roi_region* region,
+                                        float* window_out_or_null, int* d0_out_or_null);
+
+/* Local solve on the extended box of *region (Sec. 1 scheme; Eq. sirtit + Eq. sirtbox
+ * with l = 0, or Eq. priorsys with TV by Chambolle-Pock), starting from x = 0.
+ * Runs the exterior subtraction first.  out: [box_h][box_w] float32, a device
+ * pointer when out_on_device = 1, host memory otherwise (the call then
+ * synchronizes).  info (optional) receives the plan; its objective only when
+ * params->eval_objective.  ROI_ESTATE before fbp, ROI_EINVAL for bad params or a
+ * region whose box misses the grid. */
+roi_status roi_recon_solve_local(roi_recon_t h, const roi_region* region, const roi_solve_params* params,
+                                 float* out, int out_on_device, roi_solve_info* info);
+
+/* --------------------------------------------------------------------------
+ * Planning and single operators (for custom solvers and for verification)
+ * ------------------------------------------------------------------------ */
+
+/* Host-only ROI plan (no GPU needed): box and per-angle detector windows of the
+ * rays that reach the box (rows of W_L that are not zero, Sec. 2.1).  info receives
+ * box_* , window_max and window_stride; d0 and width (optional host int[n_angles])
+ * receive each angle's first bin and bin count. */
+roi_status roi_recon_plan(const roi_geometry* geom, const roi_region* region, roi_solve_info* info,
+                          int* d0, int* width);
+
+/* y = W_L x (Sec. 2.1): x device [box_h][box_w], y device [n_angles][window_stride]
+ * (window layout as in roi_recon_reproject_exterior).  Needs only create. */
+roi_status roi_recon_forward_local(roi_recon_t h, const roi_region* region, const float* x, float* y);
+
+/* x = W_L^T y = M_L W^T y restricted to the box (Sec. 2.1), the exact transpose of
+ * roi_recon_forward_local: y device window [n_angles][window_stride], x device
+ * [box_h][box_w].  Needs only create. */
+roi_status roi_recon_back_local(roi_recon_t h, const roi_region* region, const float* y, float* x);
+
+/* q = C_h p: the resident sinogram filtered by the Ram-Lak filter scaled by pi/N_theta
+ * (linear convolution, Eq. fbp), into device q [n_angles][n_det].  ROI_ESTATE before
+ * set_sinogram. */
+roi_status roi_recon_ramp_filter(roi_recon_t h, float* q);
+
+
+/* --------------------------------------------------------------------------
+ * Measurement
+ * ------------------------------------------------------------------------ */
+
+/* Kernel timing for profiling.  enable = 1 starts recording CUDA events around every
+ * launch of the two projector kernels made by roi_recon_solve_local (and clears
+ * earlier records); enable = 0 stops.  Recording adds host work per launch, so
+ * time whole steps with it off. */
+roi_status roi_recon_set_timing(roi_recon_t h, int enable);
+
+/* Launch count and summed device time (milliseconds, from the recorded events) of
+ * kernel class `kernel` since timing was enabled: 0 = forward projector W_L
+ * (ray-driven, fused dual/residual update), 1 = backprojector W_L^T (pixel gather,
+ * fused primal update).  Synchronizes the handle's stream. */
+roi_status roi_recon_kernel_times(roi_recon_t h, int kernel, int* launches, double* total_ms);
+
+/* Number of CUDA kernels this library has launched in this process (all handles). */
+unsigned long long roi_recon_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ROI_RECON_H */

@@ -1,0 +1,353 @@
+"""GB300-native local region-of-interest tomographic reconstruction.
+
+Python binding of the C ABI declared in ``include/roi_recon.h`` (Pelt & Batenburg,
+arXiv 1604.02292: global FBP, exterior reprojection and subtraction, then a local
+nonnegative-SIRT or Chambolle-Pock TV solve on the extended ROI).  Every step of
+the pipeline runs in the CUDA library ``_lib/libroi_recon.so``; this module only
+marshals arguments.  There is no CPU fallback: importing the library raises if
+it cannot be built or loaded.
+
+Functions ``roi_recon_*`` mirror the C entry points one to one and take raw
+pointers (ints).  ``RoiRecon`` is a convenience wrapper taking torch tensors,
+which supply device memory and the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+from . import build as _build
+
+__all__ = [
+    "ROI_OK", "ROI_EINVAL", "ROI_ENOMEM", "ROI_ESTATE", "ROI_ECUDA", "ROI_ETIMEOUT", "ROI_EBUSY",
+    "ROI_F32", "ROI_BF16", "ROI_F16", "ROI_SIRT_NONNEG", "ROI_TV_CP",
+    "Geometry", "Region", "SolveParams", "SolveInfo", "RoiError", "lib", "EXPORTS",
+    "roi_recon_create", "roi_recon_destroy", "roi_recon_last_error", "roi_recon_set_sinogram",
+    "roi_recon_fbp", "roi_recon_reproject_exterior", "roi_recon_solve_local", "roi_recon_plan",
+    "roi_recon_forward_local", "roi_recon_back_local", "roi_recon_ramp_filter", "roi_recon_set_timing",
+    "roi_recon_kernel_times", "roi_recon_launch_count", "RoiRecon", "plan",
+]
+
+ROI_OK, ROI_EINVAL, ROI_ENOMEM, ROI_ESTATE, ROI_ECUDA, ROI_ETIMEOUT, ROI_EBUSY = range(7)
+ROI_F32, ROI_BF16, ROI_F16 = range(3)
+ROI_SIRT_NONNEG, ROI_TV_CP = range(2)
+
+_STATUS = {0: "ROI_OK", 1: "ROI_EINVAL", 2: "ROI_ENOMEM", 3: "ROI_ESTATE", 4: "ROI_ECUDA",
+           5: "ROI_ETIMEOUT", 6: "ROI_EBUSY"}
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("n_pix", ctypes.c_int), ("n_angles", ctypes.c_int), ("n_det", ctypes.c_int),
+                ("angles", ctypes.POINTER(ctypes.c_double)), ("storage", ctypes.c_int)]
+
+
+class Region(ctypes.Structure):
+    _fields_ = [("cx", ctypes.c_double), ("cy", ctypes.c_double), ("radius", ctypes.c_double),
+                ("margin", ctypes.c_double)]
+
+
+class SolveParams(ctypes.Structure):
+    _fields_ = [("reg", ctypes.c_int), ("lam", ctypes.c_double), ("iters", ctypes.c_int),
+                ("weighting", ctypes.c_int), ("precond", ctypes.c_int), ("crop_disk", ctypes.c_int),
+                ("eval_objective", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("box_x0", ctypes.c_int), ("box_y0", ctypes.c_int), ("box_w", ctypes.c_int),
+                ("box_h", ctypes.c_int), ("window_max", ctypes.c_int), ("window_stride", ctypes.c_int),
+                ("iters_done", ctypes.c_int), ("step_L", ctypes.c_double), ("objective", ctypes.c_double)]
+
+
+# every symbol declared in include/roi_recon.h
+EXPORTS = [
+    "roi_recon_create", "roi_recon_destroy", "roi_recon_last_error", "roi_recon_set_sinogram",
+    "roi_recon_fbp", "roi_recon_reproject_exterior", "roi_recon_solve_local", "roi_recon_plan",
+    "roi_recon_forward_local", "roi_recon_back_local", "roi_recon_ramp_filter",
+    "roi_recon_set_timing", "roi_recon_kernel_times", "roi_recon_launch_count",
+]
+
+_lib = None
+_lock = threading.Lock()
+_P = ctypes.c_void_p
+_H = ctypes.c_void_p
+
+
+def lib() -> ctypes.CDLL:
+    """Build (if needed) and load the CUDA library; raises on failure (no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            st = ctypes.c_int
+            L.roi_recon_create.argtypes = [ctypes.POINTER(Geometry), _P, ctypes.POINTER(_H)]
+            L.roi_recon_create.restype = st
+            L.roi_recon_destroy.argtypes = [_H]
+            L.roi_recon_destroy.restype = None
+            L.roi_recon_last_error.argtypes = [_H]
+            L.roi_recon_last_error.restype = ctypes.c_char_p
+            L.roi_recon_set_sinogram.argtypes = [_H, _P, ctypes.c_int, ctypes.c_int]
+            L.roi_recon_set_sinogram.restype = st
+            L.roi_recon_fbp.argtypes = [_H, _P]
+            L.roi_recon_fbp.restype = st
+            L.roi_recon_reproject_exterior.argtypes = [_H, ctypes.POINTER(Region), _P, _P]
+            L.roi_recon_reproject_exterior.restype = st
+            L.roi_recon_solve_local.argtypes = [_H, ctypes.POINTER(Region), ctypes.POINTER(SolveParams), _P,
+                                                ctypes.c_int, ctypes.POINTER(SolveInfo)]
+            L.roi_recon_solve_local.restype = st
+            L.roi_recon_plan.argtypes = [ctypes.POINTER(Geometry), ctypes.POINTER(Region),
+                                         ctypes.POINTER(SolveInfo), _P, _P]
+            L.roi_recon_plan.restype = st
+            L.roi_recon_forward_local.argtypes = [_H, ctypes.POINTER(Region), _P, _P]
+            L.roi_recon_forward_local.restype = st
+            L.roi_recon_back_local.argtypes = [_H, ctypes.POINTER(Region), _P, _P]
+            L.roi_recon_back_local.restype = st
+            L.roi_recon_ramp_filter.argtypes = [_H, _P]
+            L.roi_recon_ramp_filter.restype = st
+            L.roi_recon_set_timing.argtypes = [_H, ctypes.c_int]
+            L.roi_recon_set_timing.restype = st
+            L.roi_recon_kernel_times.argtypes = [_H, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                                 ctypes.POINTER(ctypes.c_double)]
+            L.roi_recon_kernel_times.restype = st
+            L.roi_recon_launch_count.argtypes = []
+            L.roi_recon_launch_count.restype = ctypes.c_ulonglong
+            _lib = L
+    return _lib
+
+
+# ---- one-to-one wrappers of the C entry points (raw pointers as ints) ----------------
+
+def roi_recon_create(geom: Geometry, stream: int):
+    h = _H()
+    s = lib().roi_recon_create(ctypes.byref(geom), stream or None, ctypes.byref(h))
+    return s, h.value
+
+
+def roi_recon_destroy(h) -> None:
+    lib().roi_recon_destroy(h)
+
+
+def roi_recon_last_error(h) -> str:
+    return lib().roi_recon_last_error(h).decode()
+
+
+def roi_recon_set_sinogram(h, p: int, dtype: int, on_device: int) -> int:
+    return lib().roi_recon_set_sinogram(h, p, dtype, on_device)
+
+
+def roi_recon_fbp(h, out: int | None) -> int:
+    return lib().roi_recon_fbp(h, out or None)
+
+
+def roi_recon_reproject_exterior(h, region: Region, window_out: int | None, d0_out: int | None) -> int:
+    return lib().roi_recon_reproject_exterior(h, ctypes.byref(region), window_out or None, d0_out or None)
+
+
+def roi_recon_solve_local(h, region: Region, params: SolveParams, out: int, out_on_device: int,
+                          info: SolveInfo | None) -> int:
+    return lib().roi_recon_solve_local(h, ctypes.byref(region), ctypes.byref(params), out, out_on_device,
+                                       ctypes.byref(info) if info is not None else None)
+
+
+def roi_recon_plan(geom: Geometry, region: Region, info: SolveInfo, d0: int | None, width: int | None) -> int:
+    return lib().roi_recon_plan(ctypes.byref(geom), ctypes.byref(region), ctypes.byref(info), d0 or None,
+                                width or None)
+
+
+def roi_recon_forward_local(h, region: Region, x: int, y: int) -> int:
+    return lib().roi_recon_forward_local(h, ctypes.byref(region), x, y)
+
+
+def roi_recon_back_local(h, region: Region, y: int, x: int) -> int:
+    return lib().roi_recon_back_local(h, ctypes.byref(region), y, x)
+
+
+def roi_recon_ramp_filter(h, q: int) -> int:
+    return lib().roi_recon_ramp_filter(h, q)
+
+
+def roi_recon_set_timing(h, enable: int) -> int:
+    return lib().roi_recon_set_timing(h, int(enable))
+
+
+def roi_recon_kernel_times(h, kernel: int):
+    n = ctypes.c_int()
+    ms = ctypes.c_double()
+    s = lib().roi_recon_kernel_times(h, int(kernel), ctypes.byref(n), ctypes.byref(ms))
+    return s, n.value, ms.value
+
+
+def roi_recon_launch_count() -> int:
+    return int(lib().roi_recon_launch_count())
+
+
+# ---- convenience layer -----------------------------------------------------------------
+
+class RoiError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _geometry(N, n_angles, n_det, angles=None):
+    g = Geometry(int(N), int(n_angles), int(n_det), None, ROI_F32)
+    keep = None
+    if angles is not None:
+        import numpy as np
+        keep = np.ascontiguousarray(angles, dtype=np.float64)
+        assert keep.shape == (int(n_angles),)
+        g.angles = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return g, keep
+
+
+@dataclass
+class Plan:
+    box: tuple          # (x0, y0, w, h)
+    window_max: int
+    window_stride: int
+    d0: list
+    width: list
+
+
+def plan(N, n_angles, n_det, region, angles=None) -> Plan:
+    """Host-only ROI plan (box and per-angle detector windows); needs no GPU."""
+    import numpy as np
+    g, _keep = _geometry(N, n_angles, n_det, angles)
+    info = SolveInfo()
+    d0 = np.zeros(int(n_angles), np.int32)
+    wd = np.zeros(int(n_angles), np.int32)
+    s = roi_recon_plan(g, Region(*map(float, region)), info, d0.ctypes.data, wd.ctypes.data)
+    if s != ROI_OK:
+        raise RoiError(s, "roi_recon_plan failed")
+    return Plan((info.box_x0, info.box_y0, info.box_w, info.box_h), info.window_max, info.window_stride,
+                d0.tolist(), wd.tolist())
+
+
+class RoiRecon:
+    """Handle over one geometry, with device memory and the stream taken from torch.
+
+    ``region`` arguments are ``(cx, cy, radius, margin)`` in pixel-index units.
+    Tensors must be contiguous float32 CUDA tensors on the current device.
+    """
+
+    def __init__(self, N, n_angles, n_det, angles=None, stream=None):
+        import torch
+        self._torch = torch
+        self.N, self.n_angles, self.n_det = int(N), int(n_angles), int(n_det)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        g, self._angles_keep = _geometry(N, n_angles, n_det, angles)
+        s, h = roi_recon_create(g, self.stream.cuda_stream)
+        if s != ROI_OK:
+            raise RoiError(s, "roi_recon_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            roi_recon_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, s):
+        if s != ROI_OK:
+            raise RoiError(s, roi_recon_last_error(self.h))
+
+    def _dev(self, t, shape=None):
+        torch = self._torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise TypeError("expected a contiguous float32 CUDA tensor")
+        if shape is not None and tuple(t.shape) != tuple(shape):
+            raise ValueError(f"expected shape {tuple(shape)}, got {tuple(t.shape)}")
+        return t.data_ptr()
+
+    def plan(self, region) -> Plan:
+        return plan(self.N, self.n_angles, self.n_det, region,
+                    None if self._angles_keep is None else self._angles_keep)
+
+    def set_sinogram(self, p):
+        """p: float32 [n_angles][n_det], a CUDA tensor or host (numpy / CPU tensor) array."""
+        torch = self._torch
+        shape = (self.n_angles, self.n_det)
+        if isinstance(p, torch.Tensor) and p.is_cuda:
+            self._check(roi_recon_set_sinogram(self.h, self._dev(p, shape), ROI_F32, 1))
+            self._sino_keep = p
+        else:
+            import numpy as np
+            arr = p.numpy() if isinstance(p, torch.Tensor) else np.asarray(p)
+            if arr.dtype != np.float32 or not arr.flags["C_CONTIGUOUS"] or arr.shape != shape:
+                raise TypeError(f"host sinogram must be C-contiguous float32 of shape {shape}")
+            self._check(roi_recon_set_sinogram(self.h, arr.ctypes.data, ROI_F32, 0))
+            self._sino_keep = arr
+
+    def fbp(self, out=None):
+        self._check(roi_recon_fbp(self.h, self._dev(out, (self.N, self.N)) if out is not None else None))
+        return out
+
+    def reproject_exterior(self, region, window_out=None):
+        pl = self.plan(region)
+        d0 = None
+        import numpy as np
+        d0 = np.zeros(self.n_angles, np.int32)
+        ptr = self._dev(window_out, (self.n_angles, pl.window_stride)) if window_out is not None else None
+        self._check(roi_recon_reproject_exterior(self.h, Region(*map(float, region)), ptr, d0.ctypes.data))
+        return d0
+
+    def solve_local(self, region, reg=ROI_SIRT_NONNEG, iters=200, lam=0.0, weighting=0, precond=1,
+                    crop_disk=0, eval_objective=0, out=None):
+        """Returns (out, info); out is a CUDA tensor [box_h][box_w] or a host numpy array."""
+        torch = self._torch
+        pl = self.plan(region)
+        shape = (pl.box[3], pl.box[2])
+        prm = SolveParams(int(reg), float(lam), int(iters), int(weighting), int(precond), int(crop_disk),
+                          int(eval_objective))
+        info = SolveInfo()
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float32, device="cuda")
+        if isinstance(out, torch.Tensor) and out.is_cuda:
+            s = roi_recon_solve_local(self.h, Region(*map(float, region)), prm, self._dev(out, shape), 1, info)
+        else:
+            import numpy as np
+            if out.dtype != np.float32 or out.shape != shape or not out.flags["C_CONTIGUOUS"]:
+                raise TypeError(f"host output must be C-contiguous float32 of shape {shape}")
+            s = roi_recon_solve_local(self.h, Region(*map(float, region)), prm, out.ctypes.data, 0, info)
+        self._check(s)
+        return out, info
+
+    def forward_local(self, region, x, y=None):
+        pl = self.plan(region)
+        if y is None:
+            y = self._torch.zeros((self.n_angles, pl.window_stride), dtype=self._torch.float32, device="cuda")
+        self._check(roi_recon_forward_local(self.h, Region(*map(float, region)),
+                                            self._dev(x, (pl.box[3], pl.box[2])),
+                                            self._dev(y, (self.n_angles, pl.window_stride))))
+        return y
+
+    def back_local(self, region, y, x=None):
+        pl = self.plan(region)
+        if x is None:
+            x = self._torch.zeros((pl.box[3], pl.box[2]), dtype=self._torch.float32, device="cuda")
+        self._check(roi_recon_back_local(self.h, Region(*map(float, region)),
+                                         self._dev(y, (self.n_angles, pl.window_stride)),
+                                         self._dev(x, (pl.box[3], pl.box[2]))))
+        return x
+
+    def set_timing(self, enable: bool):
+        self._check(roi_recon_set_timing(self.h, int(enable)))
+
+    def kernel_times(self, kernel: int):
+        """(launches, total device ms) of kernel class 0 (forward) or 1 (back) while timing."""
+        s, n, ms = roi_recon_kernel_times(self.h, kernel)
+        self._check(s)
+        return n, ms
+
+    def ramp_filter(self, q=None):
+        if q is None:
+            q = self._torch.empty((self.n_angles, self.n_det), dtype=self._torch.float32, device="cuda")
+        self._check(roi_recon_ramp_filter(self.h, self._dev(q, (self.n_angles, self.n_det))))
+        return q

@@ -1,0 +1,653 @@
+// capi.cu -- the roi_recon C ABI: handle, resident data, ROI workspace and the local
+// pipeline (global FBP -> exterior subtraction -> local SIRT / Chambolle-Pock TV).
+//
+// Paper: Sec. 1 (exterior-subtraction ROI scheme), Sec. 2.1 (W, W_L, W_F, Eq. locouter),
+// Sec. 2.2 (Eq. fbp, Eq. sirtit), Sec. 2.3 (Eq. priorsys, Eq. sirtbox), Sec. 3.1 (alpha).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/roi_recon.h"
+#include "roi_internal.h"
+
+using roi::AngleRec;
+using roi::Rect;
+
+namespace roi {
+static std::atomic<unsigned long long> g_launches{0};
+void count_launches(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+unsigned long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace roi
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kRedScratch = 2 * 152;   // doubles of reduction scratch (152 block partials x 2)
+
+template <class T>
+cudaError_t dev_alloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void**)p, sizeof(T) * count);
+}
+
+// Grow-only device buffer.
+struct DevBuf {
+    float* p = nullptr;
+    size_t cap = 0;
+    cudaError_t ensure(size_t n) {
+        if (n <= cap) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        cudaError_t e = dev_alloc(&p, n);
+        if (e == cudaSuccess) cap = n;
+        return e;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+}  // namespace
+
+struct roi_recon {
+    int N = 0, na = 0, nd = 0;
+    std::vector<double> angles;
+    cudaStream_t st = nullptr;
+    std::string err;
+    // resident data
+    float* p = nullptr;      // [na][nd]
+    float* q = nullptr;      // [na][nd] filtered sinogram
+    float* xfbp = nullptr;   // [N][N]
+    float* xfbpT = nullptr;  // [N][N] transpose
+    float* hodd = nullptr;   // Ram-Lak odd taps scaled by pi/na, [nd/2 + 1]
+    AngleRec* rec_fbp = nullptr;  // frame = grid, window = whole detector
+    bool have_sino = false, have_fbp = false;
+    // ROI plan cache
+    bool plan_valid = false;
+    roi_region plan_region{};
+    Rect box{};
+    int wmax = 0, stride = 0;
+    std::vector<AngleRec> h_loc, h_ext;
+    AngleRec* rec_loc = nullptr;  // frame = box
+    AngleRec* rec_ext = nullptr;  // frame = grid, window of the box
+    // ROI workspace: window buffers [na][stride], image buffers [h][w]
+    DevBuf pp, u, sig, wtmp, wrow;
+    DevBuf x, xb, xT, vx, vy, tau, itmp, itmpT;
+    double* red = nullptr;   // kRedScratch partials + 4 results
+    int exterior_ready = 0;  // p' in `pp` matches the cached plan and FBP
+    // optional kernel timing: event pairs per kernel class (0 forward, 1 back)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spans[2];
+};
+
+namespace {
+
+roi_status fail(roi_recon* h, roi_status s, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
+roi_status fail(roi_recon* h, roi_status s, const char* fmt, ...) {
+    if (h) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        h->err = buf;
+    }
+    return s;
+}
+
+roi_status cuda_fail(roi_recon* h, cudaError_t e, const char* where) {
+    const roi_status s = (e == cudaErrorMemoryAllocation) ? ROI_ENOMEM : ROI_ECUDA;
+    return fail(h, s, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CU(h, call)                                        \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+    } while (0)
+
+#define LAUNCHED(h, what)                                         \
+    do {                                                          \
+        cudaError_t e_ = cudaGetLastError();                      \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, what);     \
+    } while (0)
+
+cudaEvent_t take_event(roi_recon* h) {
+    if (h->ev_used == h->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        h->ev_pool.push_back(e);
+    }
+    return h->ev_pool[h->ev_used++];
+}
+
+// RAII span: records an event pair around one kernel launch when timing is on
+struct Span {
+    roi_recon* h;
+    int cls;
+    cudaEvent_t a = nullptr;
+    Span(roi_recon* h_, int cls_) : h(h_), cls(cls_) {
+        if (h->timing && (a = take_event(h))) cudaEventRecord(a, h->st);
+    }
+    ~Span() {
+        if (a) {
+            cudaEvent_t b = take_event(h);
+            if (b) {
+                cudaEventRecord(b, h->st);
+                h->spans[cls].push_back({a, b});
+            }
+        }
+    }
+};
+
+bool finite_region(const roi_region* r) {
+    return std::isfinite(r->cx) && std::isfinite(r->cy) && std::isfinite(r->radius) && std::isfinite(r->margin) &&
+           r->radius > 0 && r->margin >= 0 && r->radius + r->margin < 1e7;
+}
+
+bool same_region(const roi_region& a, const roi_region& b) {
+    return a.cx == b.cx && a.cy == b.cy && a.radius == b.radius && a.margin == b.margin;
+}
+
+roi_status check_geometry(const roi_geometry* g) {
+    if (!g) return ROI_EINVAL;
+    if (g->n_pix < 1 || g->n_angles < 1 || g->n_det < 1) return ROI_EINVAL;
+    if (g->n_pix > 65536 || g->n_angles > 65536 || g->n_det > 8192) return ROI_EINVAL;
+    if (g->storage != ROI_F32) return ROI_EINVAL;
+    if (g->angles)
+        for (int a = 0; a < g->n_angles; ++a)
+            if (!std::isfinite(g->angles[a])) return ROI_EINVAL;
+    return ROI_OK;
+}
+
+std::vector<double> make_angles(const roi_geometry* g) {
+    std::vector<double> a(g->n_angles);
+    for (int i = 0; i < g->n_angles; ++i) a[i] = g->angles ? g->angles[i] : i * kPi / g->n_angles;
+    return a;
+}
+
+// Plan `region` (box, windows) and upload the per-angle tables; grows the workspace.
+roi_status ensure_plan(roi_recon* h, const roi_region* region) {
+    if (!finite_region(region)) return fail(h, ROI_EINVAL, "region: radius must be > 0, margin >= 0, all finite");
+    if (h->plan_valid && same_region(h->plan_region, *region)) return ROI_OK;
+    Rect box;
+    if (!roi::plan_box(h->N, region->cx, region->cy, region->radius, region->margin, &box))
+        return fail(h, ROI_EINVAL, "region: extended box does not intersect the %d x %d grid", h->N, h->N);
+    h->plan_valid = false;
+    h->exterior_ready = 0;
+    h->h_loc.resize(h->na);
+    h->h_ext.resize(h->na);
+    const Rect grid{0, 0, h->N, h->N};
+    const int wl = roi::plan_angles(h->N, h->na, h->nd, h->angles.data(), box, box, false, h->h_loc.data());
+    roi::plan_angles(h->N, h->na, h->nd, h->angles.data(), grid, box, false, h->h_ext.data());
+    const int stride = roi::round_stride(wl);
+    const size_t nwin = (size_t)h->na * stride, nimg = (size_t)box.w * box.h;
+    DevBuf* wins[] = {&h->pp, &h->u, &h->sig, &h->wtmp, &h->wrow};
+    for (DevBuf* b : wins) CU(h, b->ensure(nwin));
+    DevBuf* imgs[] = {&h->x, &h->xb, &h->xT, &h->vx, &h->vy, &h->tau, &h->itmp, &h->itmpT};
+    for (DevBuf* b : imgs) CU(h, b->ensure(nimg));
+    CU(h, cudaMemcpyAsync(h->rec_loc, h->h_loc.data(), sizeof(AngleRec) * h->na, cudaMemcpyHostToDevice, h->st));
+    CU(h, cudaMemcpyAsync(h->rec_ext, h->h_ext.data(), sizeof(AngleRec) * h->na, cudaMemcpyHostToDevice, h->st));
+    h->box = box;
+    h->wmax = wl;
+    h->stride = stride;
+    h->plan_region = *region;
+    h->plan_valid = true;
+    return ROI_OK;
+}
+
+void fill_info(const roi_recon* h, roi_solve_info* info) {
+    info->box_x0 = h->box.x0;
+    info->box_y0 = h->box.y0;
+    info->box_w = h->box.w;
+    info->box_h = h->box.h;
+    info->window_max = h->wmax;
+    info->window_stride = h->stride;
+}
+
+roi::FwdArgs fwd_local(roi_recon* h, const float* img, const float* imgT, float* out) {
+    roi::FwdArgs a{};
+    a.rec = h->rec_loc;
+    a.na = h->na;
+    a.stride = h->stride;
+    a.nx = h->box.w;
+    a.ny = h->box.h;
+    a.img = img;
+    a.imgT = imgT;
+    a.out = out;
+    a.nd = h->nd;
+    return a;
+}
+
+roi::BackArgs back_local(roi_recon* h, const float* win, float* out, float* outT) {
+    roi::BackArgs b{};
+    b.rec = h->rec_loc;
+    b.na = h->na;
+    b.stride = h->stride;
+    b.nx = h->box.w;
+    b.ny = h->box.h;
+    b.win = win;
+    b.out = out;
+    b.outT = outT;
+    return b;
+}
+
+// Row sums W_L 1 into h->wrow and column sums W_L^T 1 into `cols`.
+roi_status rowcol_sums(roi_recon* h, float* cols) {
+    const size_t nimg = (size_t)h->box.w * h->box.h;
+    roi::launch_fill(h->itmp.p, 1.f, nimg, h->st);
+    roi::launch_fill(h->itmpT.p, 1.f, nimg, h->st);
+    roi::launch_forward(roi::FWD_PLAIN, fwd_local(h, h->itmp.p, h->itmpT.p, h->wrow.p), h->st);
+    roi::launch_window_ones(h->wtmp.p, h->rec_loc, h->na, h->stride, h->st);
+    roi::launch_back(roi::BACK_PLAIN, back_local(h, h->wtmp.p, cols, nullptr), h->st);
+    LAUNCHED(h, "row/column sums");
+    return ROI_OK;
+}
+
+roi_status run_exterior(roi_recon* h) {
+    roi::FwdArgs a{};
+    a.rec = h->rec_ext;
+    a.na = h->na;
+    a.stride = h->stride;
+    a.nx = h->N;
+    a.ny = h->N;
+    a.img = h->xfbp;
+    a.imgT = h->xfbpT;
+    a.hole = h->box;
+    a.out = h->pp.p;
+    a.p = h->p;
+    a.nd = h->nd;
+    roi::launch_forward(roi::FWD_EXTERIOR, a, h->st);
+    LAUNCHED(h, "exterior reprojection");
+    h->exterior_ready = 1;
+    return ROI_OK;
+}
+
+roi_status solve_sirt(roi_recon* h, const roi_solve_params* prm) {
+    const int nx = h->box.w, ny = h->box.h;
+    const size_t nimg = (size_t)nx * ny, nwin = (size_t)h->na * h->stride;
+    roi::launch_fill(h->x.p, 0.f, nimg, h->st);
+    roi::launch_fill(h->xT.p, 0.f, nimg, h->st);
+    const float* R = nullptr;
+    const float* C = nullptr;
+    if (prm->weighting) {
+        roi_status s = rowcol_sums(h, h->tau.p);
+        if (s != ROI_OK) return s;
+        CU(h, cudaMemcpyAsync(h->sig.p, h->wrow.p, sizeof(float) * nwin, cudaMemcpyDeviceToDevice, h->st));
+        roi::launch_precond(h->sig.p, (int)nwin, h->tau.p, nx, ny, 0, h->st);
+        R = h->sig.p;
+        C = h->tau.p;
+    }
+    const float alpha = (float)(1.0 / ((double)h->na * h->nd));
+    roi::FwdArgs fa = fwd_local(h, h->x.p, h->xT.p, h->u.p);
+    fa.pp = h->pp.p;
+    fa.R = R;
+    roi::BackArgs ba = back_local(h, h->u.p, h->x.p, h->xT.p);
+    ba.C = C;
+    ba.step_scalar = alpha;
+    ba.nonneg = 1;
+    for (int it = 0; it < prm->iters; ++it) {
+        {
+            Span sp(h, 0);
+            roi::launch_forward(roi::FWD_SIRT, fa, h->st);
+        }
+        {
+            Span sp(h, 1);
+            roi::launch_back(roi::BACK_SIRT, ba, h->st);
+        }
+    }
+    LAUNCHED(h, "SIRT iterations");
+    return ROI_OK;
+}
+
+roi_status power_norm(roi_recon* h, int iters) {
+    // ||K||, K = [W_L; grad], by power iteration on K^T K from the normalised all-ones image
+    const int nx = h->box.w, ny = h->box.h;
+    const size_t nimg = (size_t)nx * ny;
+    const float v0 = (float)(1.0 / std::sqrt((double)nimg));
+    roi::launch_fill(h->itmp.p, v0, nimg, h->st);
+    roi::launch_fill(h->itmpT.p, v0, nimg, h->st);
+    double* n2 = h->red + kRedScratch;
+    for (int it = 0; it < iters; ++it) {
+        roi::launch_forward(roi::FWD_PLAIN, fwd_local(h, h->itmp.p, h->itmpT.p, h->wtmp.p), h->st);
+        roi::launch_back(roi::BACK_PLAIN, back_local(h, h->wtmp.p, h->x.p, nullptr), h->st);
+        roi::launch_power_ktk_grad(h->x.p, h->itmp.p, nx, ny, h->st);
+        roi::launch_sumsq(h->x.p, (int)nimg, h->red, kRedScratch, n2, h->st);
+        roi::launch_normalize(h->x.p, h->itmp.p, h->itmpT.p, nx, ny, n2, h->st);
+    }
+    LAUNCHED(h, "power iteration");
+    return ROI_OK;
+}
+
+roi_status solve_cp(roi_recon* h, const roi_solve_params* prm, double* L_out) {
+    const int nx = h->box.w, ny = h->box.h;
+    const size_t nimg = (size_t)nx * ny, nwin = (size_t)h->na * h->stride;
+    const float* sigma_v_dev = nullptr;
+    float sigma_v = 0.5f;
+    if (prm->precond) {
+        roi_status s = rowcol_sums(h, h->tau.p);
+        if (s != ROI_OK) return s;
+        CU(h, cudaMemcpyAsync(h->sig.p, h->wrow.p, sizeof(float) * nwin, cudaMemcpyDeviceToDevice, h->st));
+        roi::launch_precond(h->sig.p, (int)nwin, h->tau.p, nx, ny, 1, h->st);
+    } else {
+        roi_status s = power_norm(h, 100);
+        if (s != ROI_OK) return s;
+        double* n2 = h->red + kRedScratch;
+        roi::launch_fill_step(h->sig.p, nwin, n2, h->red + kRedScratch + 1, h->st);
+        roi::launch_fill_step(h->tau.p, nimg, n2, nullptr, h->st);
+        sigma_v_dev = h->sig.p;  // same scalar step
+        *L_out = 1.0;            // marker: read back later
+    }
+    for (DevBuf* b : {&h->x, &h->xb, &h->xT, &h->vx, &h->vy}) roi::launch_fill(b->p, 0.f, nimg, h->st);
+    roi::launch_fill(h->u.p, 0.f, nwin, h->st);
+    roi::FwdArgs fa = fwd_local(h, h->xb.p, h->xT.p, h->u.p);
+    fa.pp = h->pp.p;
+    fa.R = h->sig.p;
+    roi::BackArgs ba = back_local(h, h->u.p, h->x.p, h->xT.p);
+    ba.C = h->tau.p;
+    ba.vx = h->vx.p;
+    ba.vy = h->vy.p;
+    ba.xbar = h->xb.p;
+    const float lam = (float)prm->lambda;
+    for (int it = 0; it < prm->iters; ++it) {
+        {
+            Span sp(h, 0);
+            roi::launch_forward(roi::FWD_CP, fa, h->st);
+        }
+        if (sigma_v_dev)
+            roi::launch_cp_dual_grad_dev(h->xb.p, h->vx.p, h->vy.p, nx, ny, sigma_v_dev, lam, h->st);
+        else
+            roi::launch_cp_dual_grad(h->xb.p, h->vx.p, h->vy.p, nx, ny, sigma_v, lam, h->st);
+        {
+            Span sp(h, 1);
+            roi::launch_back(roi::BACK_CP, ba, h->st);
+        }
+    }
+    LAUNCHED(h, "Chambolle-Pock iterations");
+    return ROI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+roi_status roi_recon_create(const roi_geometry* geom, void* cuda_stream, roi_recon_t* out) {
+    if (!out) return ROI_EINVAL;
+    *out = nullptr;
+    if (check_geometry(geom) != ROI_OK) return ROI_EINVAL;
+    roi_recon* h = new (std::nothrow) roi_recon;
+    if (!h) return ROI_ENOMEM;
+    h->N = geom->n_pix;
+    h->na = geom->n_angles;
+    h->nd = geom->n_det;
+    h->angles = make_angles(geom);
+    h->st = (cudaStream_t)cuda_stream;
+    const size_t ns = (size_t)h->na * h->nd, nimg = (size_t)h->N * h->N;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = dev_alloc(&h->p, ns);
+    if (e == cudaSuccess) e = dev_alloc(&h->q, ns);
+    if (e == cudaSuccess) e = dev_alloc(&h->xfbp, nimg);
+    if (e == cudaSuccess) e = dev_alloc(&h->xfbpT, nimg);
+    if (e == cudaSuccess) e = dev_alloc(&h->hodd, (size_t)h->nd / 2 + 1);
+    if (e == cudaSuccess) e = dev_alloc(&h->rec_fbp, (size_t)h->na);
+    if (e == cudaSuccess) e = dev_alloc(&h->rec_loc, (size_t)h->na);
+    if (e == cudaSuccess) e = dev_alloc(&h->rec_ext, (size_t)h->na);
+    if (e == cudaSuccess) e = dev_alloc(&h->red, (size_t)kRedScratch + 4);
+    if (e == cudaSuccess) {
+        // Ram-Lak odd taps h_m = -1/(pi m)^2, m = 2t + 1, scaled by pi / N_theta (Eq. fbp)
+        std::vector<float> ho((size_t)h->nd / 2 + 1);
+        const double scale = kPi / h->na;
+        for (size_t t = 0; t < ho.size(); ++t) {
+            const double m = 2.0 * t + 1.0;
+            ho[t] = (float)(-scale / (kPi * kPi * m * m));
+        }
+        std::vector<AngleRec> rf(h->na);
+        const Rect grid{0, 0, h->N, h->N};
+        roi::plan_angles(h->N, h->na, h->nd, h->angles.data(), grid, grid, true, rf.data());
+        e = cudaMemcpy(h->hodd, ho.data(), sizeof(float) * ho.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(h->rec_fbp, rf.data(), sizeof(AngleRec) * h->na, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        roi_recon_destroy(h);
+        return e == cudaErrorMemoryAllocation ? ROI_ENOMEM : ROI_ECUDA;
+    }
+    *out = h;
+    return ROI_OK;
+}
+
+void roi_recon_destroy(roi_recon_t h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->st);
+    for (float* b : {h->p, h->q, h->xfbp, h->xfbpT, h->hodd})
+        if (b) cudaFree(b);
+    for (AngleRec* b : {h->rec_fbp, h->rec_loc, h->rec_ext})
+        if (b) cudaFree(b);
+    if (h->red) cudaFree(h->red);
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    for (DevBuf* b : {&h->pp, &h->u, &h->sig, &h->wtmp, &h->wrow, &h->x, &h->xb, &h->xT, &h->vx, &h->vy, &h->tau,
+                      &h->itmp, &h->itmpT})
+        b->release();
+    delete h;
+}
+
+const char* roi_recon_last_error(roi_recon_t h) { return h ? h->err.c_str() : "null handle"; }
+
+roi_status roi_recon_set_sinogram(roi_recon_t h, const void* p, roi_dtype dt, int on_device) {
+    if (!h) return ROI_EINVAL;
+    h->err.clear();
+    if (!p) return fail(h, ROI_EINVAL, "set_sinogram: null pointer");
+    if (dt != ROI_F32) return fail(h, ROI_EINVAL, "set_sinogram: only ROI_F32 input is supported");
+    CU(h, cudaMemcpyAsync(h->p, p, sizeof(float) * (size_t)h->na * h->nd,
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+    h->have_sino = true;
+    h->have_fbp = false;
+    h->exterior_ready = 0;
+    return ROI_OK;
+}
+
+roi_status roi_recon_ramp_filter(roi_recon_t h, float* q) {
+    if (!h) return ROI_EINVAL;
+    h->err.clear();
+    if (!q) return fail(h, ROI_EINVAL, "ramp_filter: null output");
+    if (!h->have_sino) return fail(h, ROI_ESTATE, "ramp_filter: no sinogram (call set_sinogram first)");
+    roi::launch_ramp(h->p, h->hodd, q, h->na, h->nd, (float)(kPi / h->na), h->st);
+    LAUNCHED(h, "ramp filter");
+    return ROI_OK;
+}
+
+roi_status roi_recon_fbp(roi_recon_t h, float* out_or_null) {
+    if (!h) return ROI_EINVAL;
+    h->err.clear();
+    if (!h->have_sino) return fail(h, ROI_ESTATE, "fbp: no sinogram (call set_sinogram first)");
+    roi::launch_ramp(h->p, h->hodd, h->q, h->na, h->nd, (float)(kPi / h->na), h->st);
+    roi::BackArgs b{};
+    b.rec = h->rec_fbp;
+    b.na = h->na;
+    b.stride = h->nd;
+    b.nx = h->N;
+    b.ny = h->N;
+    b.win = h->q;
+    b.out = h->xfbp;
+    b.outT = h->xfbpT;
+    roi::launch_back(roi::BACK_PLAIN, b, h->st);
+    LAUNCHED(h, "fbp");
+    if (out_or_null)
+        CU(h, cudaMemcpyAsync(out_or_null, h->xfbp, sizeof(float) * (size_t)h->N * h->N, cudaMemcpyDeviceToDevice,
+                              h->st));
+    h->have_fbp = true;
+    h->exterior_ready = 0;
+    return ROI_OK;
+}
+
+roi_status roi_recon_plan(const roi_geometry* geom, const roi_region* region, roi_solve_info* info, int* d0,
+                          int* width) {
+    if (check_geometry(geom) != ROI_OK || !region || !info) return ROI_EINVAL;
+    if (!finite_region(region)) return ROI_EINVAL;
+    Rect box;
+    if (!roi::plan_box(geom->n_pix, region->cx, region->cy, region->radius, region->margin, &box)) return ROI_EINVAL;
+    std::vector<double> ang = make_angles(geom);
+    std::vector<AngleRec> rec(geom->n_angles);
+    const int wl = roi::plan_angles(geom->n_pix, geom->n_angles, geom->n_det, ang.data(), box, box, false, rec.data());
+    std::memset(info, 0, sizeof *info);
+    info->box_x0 = box.x0;
+    info->box_y0 = box.y0;
+    info->box_w = box.w;
+    info->box_h = box.h;
+    info->window_max = wl;
+    info->window_stride = roi::round_stride(wl);
+    for (int a = 0; a < geom->n_angles; ++a) {
+        if (d0) d0[a] = rec[a].d0;
+        if (width) width[a] = rec[a].width;
+    }
+    return ROI_OK;
+}
+
+roi_status roi_recon_reproject_exterior(roi_recon_t h, const roi_region* region, float* window_out_or_null,
+                                        int* d0_out_or_null) {
+    if (!h || !region) return ROI_EINVAL;
+    h->err.clear();
+    if (!h->have_fbp) return fail(h, ROI_ESTATE, "reproject_exterior: no FBP image (call fbp first)");
+    roi_status s = ensure_plan(h, region);
+    if (s != ROI_OK) return s;
+    s = run_exterior(h);
+    if (s != ROI_OK) return s;
+    if (window_out_or_null)
+        CU(h, cudaMemcpyAsync(window_out_or_null, h->pp.p, sizeof(float) * (size_t)h->na * h->stride,
+                              cudaMemcpyDeviceToDevice, h->st));
+    if (d0_out_or_null) {
+        for (int a = 0; a < h->na; ++a) d0_out_or_null[a] = h->h_loc[a].d0;
+        CU(h, cudaStreamSynchronize(h->st));
+    }
+    return ROI_OK;
+}
+
+roi_status roi_recon_forward_local(roi_recon_t h, const roi_region* region, const float* x, float* y) {
+    if (!h || !region) return ROI_EINVAL;
+    h->err.clear();
+    if (!x || !y) return fail(h, ROI_EINVAL, "forward_local: null pointer");
+    roi_status s = ensure_plan(h, region);
+    if (s != ROI_OK) return s;
+    roi::launch_transpose(x, h->itmpT.p, h->box.h, h->box.w, h->st);
+    roi::launch_forward(roi::FWD_PLAIN, fwd_local(h, x, h->itmpT.p, y), h->st);
+    LAUNCHED(h, "forward_local");
+    return ROI_OK;
+}
+
+roi_status roi_recon_back_local(roi_recon_t h, const roi_region* region, const float* y, float* x) {
+    if (!h || !region) return ROI_EINVAL;
+    h->err.clear();
+    if (!x || !y) return fail(h, ROI_EINVAL, "back_local: null pointer");
+    roi_status s = ensure_plan(h, region);
+    if (s != ROI_OK) return s;
+    roi::launch_back(roi::BACK_PLAIN, back_local(h, y, x, nullptr), h->st);
+    LAUNCHED(h, "back_local");
+    return ROI_OK;
+}
+
+roi_status roi_recon_solve_local(roi_recon_t h, const roi_region* region, const roi_solve_params* params, float* out,
+                                 int out_on_device, roi_solve_info* info) {
+    if (!h || !region || !params) return ROI_EINVAL;
+    h->err.clear();
+    if (!out) return fail(h, ROI_EINVAL, "solve_local: null output");
+    if (params->reg != ROI_SIRT_NONNEG && params->reg != ROI_TV_CP)
+        return fail(h, ROI_EINVAL, "solve_local: unknown regularizer %d", (int)params->reg);
+    if (params->iters < 0 || params->iters > 1000000) return fail(h, ROI_EINVAL, "solve_local: iters out of range");
+    if (!std::isfinite(params->lambda) || params->lambda < 0)
+        return fail(h, ROI_EINVAL, "solve_local: lambda must be finite and >= 0");
+    if (!h->have_fbp) return fail(h, ROI_ESTATE, "solve_local: no FBP image (call fbp first)");
+    roi_status s = ensure_plan(h, region);
+    if (s != ROI_OK) return s;
+    s = run_exterior(h);
+    if (s != ROI_OK) return s;
+    double L_flag = 0.0;
+    if (params->reg == ROI_SIRT_NONNEG)
+        s = solve_sirt(h, params);
+    else
+        s = solve_cp(h, params, &L_flag);
+    if (s != ROI_OK) return s;
+    const int nx = h->box.w, ny = h->box.h;
+    const size_t nimg = (size_t)nx * ny;
+    const double cxl = region->cx - h->box.x0, cyl = region->cy - h->box.y0;
+    float* dst = out_on_device ? out : h->itmp.p;
+    roi::launch_crop(h->x.p, dst, nx, ny, cxl, cyl, region->radius, params->crop_disk, h->st);
+    LAUNCHED(h, "crop");
+    double objective = 0.0, L = 0.0;
+    if (params->eval_objective) {
+        // ||W_L x - p'||^2 over rays that reach the box + lambda TV(x)
+        roi::launch_transpose(h->x.p, h->itmpT.p, ny, nx, h->st);
+        roi::launch_forward(roi::FWD_PLAIN, fwd_local(h, h->x.p, h->itmpT.p, h->wtmp.p), h->st);
+        if (params->reg == ROI_SIRT_NONNEG || !params->precond) {
+            // row sums were not computed by the solver: W_L 1 into wrow (vx, vy are free scratch now)
+            roi::launch_fill(h->vx.p, 1.f, nimg, h->st);
+            roi::launch_fill(h->vy.p, 1.f, nimg, h->st);
+            roi::launch_forward(roi::FWD_PLAIN, fwd_local(h, h->vx.p, h->vy.p, h->wrow.p), h->st);
+        }
+        roi::launch_objective(h->wtmp.p, h->pp.p, h->wrow.p, h->na * h->stride, h->x.p, nx, ny, h->red, kRedScratch,
+                              h->red + kRedScratch + 2, h->st);
+        LAUNCHED(h, "objective");
+        double r2[2];
+        CU(h, cudaMemcpyAsync(r2, h->red + kRedScratch + 2, sizeof r2, cudaMemcpyDeviceToHost, h->st));
+        CU(h, cudaStreamSynchronize(h->st));
+        objective = r2[0] + params->lambda * r2[1];
+    }
+    if (L_flag != 0.0 && info) {
+        CU(h, cudaMemcpyAsync(&L, h->red + kRedScratch + 1, sizeof L, cudaMemcpyDeviceToHost, h->st));
+        CU(h, cudaStreamSynchronize(h->st));
+    }
+    if (!out_on_device) {
+        CU(h, cudaMemcpyAsync(out, h->itmp.p, sizeof(float) * nimg, cudaMemcpyDeviceToHost, h->st));
+        CU(h, cudaStreamSynchronize(h->st));
+    }
+    if (info) {
+        fill_info(h, info);
+        info->iters_done = params->iters;
+        info->step_L = L;
+        info->objective = objective;
+    }
+    return ROI_OK;
+}
+
+roi_status roi_recon_set_timing(roi_recon_t h, int enable) {
+    if (!h) return ROI_EINVAL;
+    h->err.clear();
+    CU(h, cudaStreamSynchronize(h->st));
+    h->timing = enable != 0;
+    h->spans[0].clear();
+    h->spans[1].clear();
+    h->ev_used = 0;
+    return ROI_OK;
+}
+
+roi_status roi_recon_kernel_times(roi_recon_t h, int kernel, int* launches, double* total_ms) {
+    if (!h || kernel < 0 || kernel > 1 || !launches || !total_ms) return ROI_EINVAL;
+    h->err.clear();
+    CU(h, cudaStreamSynchronize(h->st));
+    double ms = 0.0;
+    for (auto& pr : h->spans[kernel]) {
+        float t = 0.f;
+        CU(h, cudaEventElapsedTime(&t, pr.first, pr.second));
+        ms += t;
+    }
+    *launches = (int)h->spans[kernel].size();
+    *total_ms = ms;
+    return ROI_OK;
+}
+
+unsigned long long roi_recon_launch_count(void) { return roi::launches_total(); }
+
+}  // extern "C"

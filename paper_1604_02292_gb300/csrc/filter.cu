@@ -1,0 +1,79 @@
+// filter.cu -- Ram-Lak row convolution C_h (paper Eq. fbp), the first step of FBP.
+//
+// q[a][d] = s * ( h0 p[a][d] + sum_{odd m} h_m (p[a][d-m] + p[a][d+m]) ),  s = pi/N_theta,
+// with the spatial Ram-Lak taps h0 = 1/4, h_m = -1/(pi m)^2 (odd m), 0 for even m != 0,
+// applied as a linear (zero-padded) convolution of length 2 N_d - 1.
+//
+// One block per angle.  The row is staged in shared memory between N_d + 8 zeros
+// on each side; each thread produces 8 consecutive outputs and keeps a sliding
+// register window of the left (d - m) and right (d + m) samples, so each step
+// m -> m + 2 costs 4 shared loads for 16 multiply-adds.
+#include <cuda_runtime.h>
+
+#include "roi_internal.h"
+
+namespace roi {
+
+namespace {
+
+constexpr int OUT_PER_THREAD = 8;
+
+__global__ void k_ramp(const float* __restrict__ p, const float* __restrict__ hodd, float* __restrict__ q, int nd,
+                       float h0) {
+    extern __shared__ float sm[];
+    const int pad = nd + 8;
+    float* P = sm + pad;  // P[-pad .. nd + pad)
+    const int a = blockIdx.x;
+    const float* prow = p + (size_t)a * nd;
+    for (int i = threadIdx.x; i < nd + 2 * pad; i += blockDim.x) {
+        const int d = i - pad;
+        sm[i] = (d >= 0 && d < nd) ? prow[d] : 0.f;
+    }
+    __syncthreads();
+    const int d0 = threadIdx.x * OUT_PER_THREAD;
+    if (d0 >= nd) return;
+    float acc[OUT_PER_THREAD], L[OUT_PER_THREAD], R[OUT_PER_THREAD];
+#pragma unroll
+    for (int j = 0; j < OUT_PER_THREAD; ++j) {
+        acc[j] = h0 * P[d0 + j];
+        L[j] = P[d0 + j - 1];
+        R[j] = P[d0 + j + 1];
+    }
+    // m = 2t + 1; the last odd offset that can reach inside the row is < nd
+    for (int m = 1; m < nd; m += 2) {
+        const float h = hodd[m >> 1];
+#pragma unroll
+        for (int j = 0; j < OUT_PER_THREAD; ++j) acc[j] = fmaf(h, L[j] + R[j], acc[j]);
+        // slide to m + 2: L_j <- P[d0 + j - m - 2] = L_{j-2}, R_j <- P[d0 + j + m + 2] = R_{j+2}
+#pragma unroll
+        for (int j = OUT_PER_THREAD - 1; j >= 2; --j) L[j] = L[j - 2];
+        L[0] = P[d0 - m - 2];
+        L[1] = P[d0 - m - 1];
+#pragma unroll
+        for (int j = 0; j < OUT_PER_THREAD - 2; ++j) R[j] = R[j + 2];
+        R[OUT_PER_THREAD - 2] = P[d0 + OUT_PER_THREAD - 2 + m + 2];
+        R[OUT_PER_THREAD - 1] = P[d0 + OUT_PER_THREAD - 1 + m + 2];
+    }
+    float* qrow = q + (size_t)a * nd;
+#pragma unroll
+    for (int j = 0; j < OUT_PER_THREAD; ++j)
+        if (d0 + j < nd) qrow[d0 + j] = acc[j];
+}
+
+}  // namespace
+
+// Index bounds (P spans [-(nd + 8), 2 nd + 8)): with d0 <= nd - 1 and odd m <= nd - 1
+// the loads reach down to P[d0 - m - 2] >= P[-(nd + 1)] and up to
+// P[d0 + 7 + m + 2] <= P[2 nd + 7].  hodd needs nd / 2 + 1 entries (index m >> 1).
+void launch_ramp(const float* p, const float* hodd, float* q, int na, int nd, float scale, cudaStream_t st) {
+    if (na <= 0 || nd <= 0) return;
+    int threads = (nd + OUT_PER_THREAD - 1) / OUT_PER_THREAD;
+    threads = (threads + 31) / 32 * 32;
+    if (threads > 1024) threads = 1024;  // nd <= 8192 is checked by the caller
+    const size_t smem = sizeof(float) * (size_t)(nd + 2 * (nd + 8));
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_ramp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    count_launches(1);
+    k_ramp<<<na, threads, smem, st>>>(p, hodd, q, nd, 0.25f * scale);
+}
+
+}  // namespace roi

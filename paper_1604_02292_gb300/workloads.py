@@ -1,0 +1,65 @@
+"""Named synthetic workloads shaped like the paper's experiments (sizes only).
+
+Each workload fixes the geometry, the phantom recipe, the noise level, the region
+and the solver settings.  Inputs are drawn by ``synth`` from fixed seeds; the
+paper's own phantoms and its experimental data are not used (they stand in for
+them with the same grid sizes, detector counts, angle counts and noise model).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+from . import synth
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    name: str
+    N: int
+    n_angles: int
+    n_det: int
+    n_ellipses: int
+    texture: bool
+    I0: float
+    radius: float
+    margin: float
+    reg: str            # "sirt" or "tv"
+    iters: int
+    lam: float = 0.0
+
+    def geometry(self):
+        return self.N, self.n_angles, self.n_det
+
+
+WORKLOADS = {
+    # 128 x 128, 64 angles in [0, pi), 128 unit bins, 10 ellipses, I0 = 1e4,
+    # ROI radius 16 px + margin 8 px, Ram-Lak FBP then 200 nonnegative SIRT iterations
+    "roi_sirt_128": Workload("roi_sirt_128", 128, 64, 128, 10, False, 1e4, 16.0, 8.0, "sirt", 200),
+    # 1024 x 1024, 256 angles, 1024 bins, 50 ellipses + fine texture, I0 = 5e3,
+    # ROI radius 64 px + margin 32 px, Chambolle-Pock TV lambda = 0.01, 500 iterations
+    "roi_cptv_1024": Workload("roi_cptv_1024", 1024, 256, 1024, 50, True, 5e3, 64.0, 32.0, "tv", 500, 0.01),
+}
+
+
+def sinogram(w: Workload, seed: int = 0) -> np.ndarray:
+    """Noisy analytic sinogram of the seeded phantom, float32 [n_angles][n_det]."""
+    ph = synth.random_phantom(w.N, w.n_ellipses, texture=w.texture, seed=seed)
+    p = synth.analytic_sinogram(ph, w.n_angles, w.n_det)
+    p = synth.poisson_noise(p, w.I0, seed=seed + 1000)
+    return p.astype(np.float32)
+
+
+def region(w: Workload, seed: int = 0, centred: bool = False):
+    """(cx, cy, radius, margin); the extended box lies inside the grid."""
+    if centred:
+        c = (w.N - 1) / 2.0
+        return (c, c, w.radius, w.margin)
+    cx, cy = synth.random_roi_centre(w.N, w.radius, w.margin, seed=seed + 2000)
+    return (cx, cy, w.radius, w.margin)
+
+
+def box_side(w: Workload) -> int:
+    return 2 * math.ceil(w.radius + w.margin)
