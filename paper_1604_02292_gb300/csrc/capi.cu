@@ -72,6 +72,7 @@ struct roi_recon {
     float* xfbp = nullptr;   // [N][N]
     float* xfbpT = nullptr;  // [N][N] transpose
     float* hodd = nullptr;   // Ram-Lak odd taps scaled by pi/na, [nd/2 + 1]
+    float ctail = 0.f;       // (pi/na) (h0 + 2 sum_{odd m < nd} h_m)
     AngleRec* rec_fbp = nullptr;  // frame = grid, window = whole detector
     bool have_sino = false, have_fbp = false;
     // ROI plan cache
@@ -411,10 +412,14 @@ roi_status roi_recon_create(const roi_geometry* geom, void* cuda_stream, roi_rec
         // Ram-Lak odd taps h_m = -1/(pi m)^2, m = 2t + 1, scaled by pi / N_theta (Eq. fbp)
         std::vector<float> ho((size_t)h->nd / 2 + 1);
         const double scale = kPi / h->na;
+        double tail = 0.25;  // h0 + 2 sum over the odd offsets the convolution reaches (m < nd)
         for (size_t t = 0; t < ho.size(); ++t) {
             const double m = 2.0 * t + 1.0;
-            ho[t] = (float)(-scale / (kPi * kPi * m * m));
+            const double hm = -1.0 / (kPi * kPi * m * m);
+            ho[t] = (float)(scale * hm);
+            if (m < h->nd) tail += 2.0 * hm;
         }
+        h->ctail = (float)(scale * tail);
         std::vector<AngleRec> rf(h->na);
         const Rect grid{0, 0, h->N, h->N};
         roi::plan_angles(h->N, h->na, h->nd, h->angles.data(), grid, grid, true, rf.data());
@@ -465,7 +470,7 @@ roi_status roi_recon_ramp_filter(roi_recon_t h, float* q) {
     h->err.clear();
     if (!q) return fail(h, ROI_EINVAL, "ramp_filter: null output");
     if (!h->have_sino) return fail(h, ROI_ESTATE, "ramp_filter: no sinogram (call set_sinogram first)");
-    roi::launch_ramp(h->p, h->hodd, q, h->na, h->nd, (float)(kPi / h->na), h->st);
+    roi::launch_ramp(h->p, h->hodd, q, h->na, h->nd, h->ctail, h->st);
     LAUNCHED(h, "ramp filter");
     return ROI_OK;
 }
@@ -474,7 +479,7 @@ roi_status roi_recon_fbp(roi_recon_t h, float* out_or_null) {
     if (!h) return ROI_EINVAL;
     h->err.clear();
     if (!h->have_sino) return fail(h, ROI_ESTATE, "fbp: no sinogram (call set_sinogram first)");
-    roi::launch_ramp(h->p, h->hodd, h->q, h->na, h->nd, (float)(kPi / h->na), h->st);
+    roi::launch_ramp(h->p, h->hodd, h->q, h->na, h->nd, h->ctail, h->st);
     roi::BackArgs b{};
     b.rec = h->rec_fbp;
     b.na = h->na;

@@ -13,7 +13,10 @@
 // Precision: coordinates are anchored in double precision (per 32-sample segment
 // of a ray, per 32 x 32 tile and angle of the gather) and only short offsets
 // (|offset| <= 16 samples) are formed in float, so interpolation positions carry
-// an error of about 1e-6 pixel whatever the size of the grid.
+// an error of about 1e-6 pixel whatever the size of the grid.  Sums are formed in
+// float over at most 32 terms (one ray segment, one chunk of 32 angles) and carried
+// across segments and chunks in double, so a 4096-sample ray or a 1024-angle
+// backprojection rounds like a 32-term float sum.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -53,8 +56,9 @@ __global__ void __launch_bounds__(FWD_THREADS) k_forward(FwdArgs A) {
     const double Ak = r.A0 + (double)k * r.a_scale;
     const float slope = (float)r.slope;
     const double halfM = 0.5 * (M - 1);
-    float acc = 0.f;
+    double accd = 0.0;
     for (int m0 = 0; m0 < M; m0 += SEG) {
+        float acc = 0.f;
         // minor coordinate at the segment's centre sample m0 + 15.5, in double, split
         // into an integer part and a fraction so that float offsets stay small
         const double bd = Ak + ((double)m0 + 0.5 * (SEG - 1) - halfM) * r.slope;
@@ -80,12 +84,15 @@ __global__ void __launch_bounds__(FWD_THREADS) k_forward(FwdArgs A) {
             const float v1 = ok1 ? __ldg(rp + j0 + 1) : 0.f;
             acc += fmaf(f, v1 - v0, v0);
         }
+        accd += (double)acc;
     }
-    acc *= r.inv_w;
+    if (MODE == FWD_EXTERIOR) {
+        *out = (float)((double)A.p[(size_t)a * A.nd + r.d0 + k] - accd * (double)r.inv_w);
+        return;
+    }
+    const float acc = (float)(accd * (double)r.inv_w);
     if (MODE == FWD_PLAIN) {
         *out = acc;
-    } else if (MODE == FWD_EXTERIOR) {
-        *out = A.p[(size_t)a * A.nd + r.d0 + k] - acc;
     } else if (MODE == FWD_SIRT) {
         const size_t o = (size_t)a * A.stride + k;
         float res = A.pp[o] - acc;
@@ -121,9 +128,9 @@ __global__ void __launch_bounds__(BT_X* BT_Y) k_back(BackArgs A) {
     const double xi_t = tile_x0 + 0.5 * (TILE - 1) - 0.5 * (A.nx - 1);
     const double eta_t = 0.5 * (A.ny - 1) - (tile_y0 + 0.5 * (TILE - 1));
     const float dlj = (float)tx - 0.5f * (TILE - 1);
-    float acc[PPT];
+    double accd[PPT];
 #pragma unroll
-    for (int p = 0; p < PPT; ++p) acc[p] = 0.f;
+    for (int p = 0; p < PPT; ++p) accd[p] = 0.0;
 
     for (int a0 = 0; a0 < A.na; a0 += CH) {
         const int nch = min(CH, A.na - a0);
@@ -143,6 +150,9 @@ __global__ void __launch_bounds__(BT_X* BT_Y) k_back(BackArgs A) {
             stage[al][b] = (kk >= 0 && kk < wdt) ? __ldg(A.win + (size_t)(a0 + al) * A.stride + kk) : 0.f;
         }
         __syncthreads();
+        float acc[PPT];
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) acc[p] = 0.f;
         for (int al = 0; al < nch; ++al) {
             const float4 cc = cst[al];
             const float iw = cc.z, iw2 = cc.z * cc.z;
@@ -160,7 +170,12 @@ __global__ void __launch_bounds__(BT_X* BT_Y) k_back(BackArgs A) {
                 acc[p] = fmaf(w0, srow[kl], fmaf(w1, srow[kl + 1], acc[p]));
             }
         }
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) accd[p] += (double)acc[p];
     }
+    float acc[PPT];
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) acc[p] = (float)accd[p];
 
     // epilogue
 #pragma unroll

@@ -99,7 +99,8 @@ struct BackArgs {
 
 void launch_forward(FwdMode mode, const FwdArgs& a, cudaStream_t st);
 void launch_back(BackMode mode, const BackArgs& a, cudaStream_t st);
-void launch_ramp(const float* p, const float* hodd, float* q, int na, int nd, float scale, cudaStream_t st);
+// hodd[t] = s h_{2t+1}; ctail = s (h0 + 2 sum_{odd m < nd} h_m), s = pi / N_theta
+void launch_ramp(const float* p, const float* hodd, float* q, int na, int nd, float ctail, cudaStream_t st);
 void launch_transpose(const float* in, float* out, int rows, int cols, cudaStream_t st);
 void launch_fill(float* p, float v, size_t n, cudaStream_t st);
 void launch_window_ones(float* win, const AngleRec* rec, int na, int stride, cudaStream_t st);

@@ -3,7 +3,7 @@
 Tolerances (relative L2 over all compared values):
   * single operators (W_L, W_L^T, ramp filter, FBP, exterior subtraction): 1e-5,
     the FP32 projector bar; observed values are a few 1e-7;
-  * adjoint identity of the GPU pair: 1e-5 relative to |<W x, y>|;
+  * adjoint identity of the GPU pair: 1e-6 of ||W x|| ||y||, the scale of <W x, y>;
   * whole local solves (SIRT 200, CP-TV up to 500 iterations): 1e-4.  Each
     iteration adds FP32 rounding of about 1e-7 relative and the iterations are
     non-expansive, so after k iterations the error stays below k * 1e-7 plus the
@@ -11,7 +11,9 @@ Tolerances (relative L2 over all compared values):
 Every input is drawn from fixed seeds and rounded to float32 before it is given
 to both sides, so both see identical data.
 """
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -32,7 +34,18 @@ def rel_l2(a, b):
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
     nb = np.linalg.norm(b)
-    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+    err = float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+    _record(err)
+    return err
+
+
+def _record(err):
+    """Append the measured error to $PARITY_LOG (JSON lines) when set."""
+    path = os.environ.get("PARITY_LOG")
+    if path:
+        test = os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0]
+        with open(path, "a") as f:
+            f.write(json.dumps({"test": test, "rel_l2": err}) + "\n")
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -119,7 +132,10 @@ def test_gpu_pair_is_adjoint(N, na, nd, region):
     wty = rr.back_local(region, torch.from_numpy(win).cuda()).cpu().numpy().astype(np.float64)
     lhs = float((wx * win).sum())
     rhs = float((x.astype(np.float64) * wty).sum())
-    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+    # zero-mean data make <Wx, y> a sum with cancellation: compare against its scale
+    # |<Wx, y>| <= ||Wx|| ||y|| (Cauchy-Schwarz)
+    scale = float(np.linalg.norm(wx) * np.linalg.norm(win))
+    assert abs(lhs - rhs) <= 1e-6 * scale
 
 
 def _workload_data(name, seed=0):
