@@ -192,6 +192,33 @@ roi_status roi_recon_kernel_times(roi_recon_t h, int kernel, int* launches, doub
 /* Number of CUDA kernels this library has launched in this process (all handles). */
 unsigned long long roi_recon_launch_count(void);
 
+/* --------------------------------------------------------------------------
+ * Allocation-free variant
+ * ------------------------------------------------------------------------ */
+
+/* y = W_L x, the same operator as roi_recon_forward_local, without a handle and
+ * without allocating device memory.  The paper has no counterpart: this entry point
+ * serves callers that cannot allocate -- code whose device memory belongs to someone
+ * else's fixed budget (a framework's caching allocator, a server that reserves HBM up
+ * front) and loops that cannot take the implicit device synchronisation of
+ * cudaMalloc / cudaFree.  It calls neither, nor anything that allocates.
+ *   geom:    as for roi_recon_create; angles must be NULL (a*pi/N_theta), storage ROI_F32.
+ *   x:       device [box_h][box_w] float32; y: device [n_angles][window_stride] float32,
+ *            sizes from roi_recon_plan; work is ordered on cuda_stream (NULL = legacy
+ *            default stream) of the current device.
+ *   err:     optional buffer of err_len bytes receiving a message on failure.
+ * Scratch: a fixed 16 MiB device array inside the library holds the per-angle ray
+ * table and the transposed box image.  Calls needing more (table 64 bytes per angle,
+ * rounded up to 256, plus 4 box_w box_h bytes) fail with ROI_EINVAL and say so in err.
+ * Every GPU that loads the library keeps this array until the process exits.  The
+ * first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.  All
+ * calls share the array and it keeps the last call's contents; each call rewrites
+ * what it reads, but calls that overlap on the GPU race on it, so serialise them. */
+roi_status roi_recon_forward_local_noalloc(const roi_geometry* geom, const roi_region* region,
+                                           const float* x, float* y, void* cuda_stream,
+                                           char* err, int err_len);
+
 #ifdef __cplusplus
 }
 #endif

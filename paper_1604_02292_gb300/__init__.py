@@ -27,7 +27,7 @@ __all__ = [
     "roi_recon_create", "roi_recon_destroy", "roi_recon_last_error", "roi_recon_set_sinogram",
     "roi_recon_fbp", "roi_recon_reproject_exterior", "roi_recon_solve_local", "roi_recon_plan",
     "roi_recon_forward_local", "roi_recon_back_local", "roi_recon_ramp_filter", "roi_recon_set_timing",
-    "roi_recon_kernel_times", "roi_recon_launch_count", "RoiRecon", "plan",
+    "roi_recon_kernel_times", "roi_recon_launch_count", "roi_recon_forward_local_noalloc", "RoiRecon", "plan",
 ]
 
 ROI_OK, ROI_EINVAL, ROI_ENOMEM, ROI_ESTATE, ROI_ECUDA, ROI_ETIMEOUT, ROI_EBUSY = range(7)
@@ -66,6 +66,7 @@ EXPORTS = [
     "roi_recon_fbp", "roi_recon_reproject_exterior", "roi_recon_solve_local", "roi_recon_plan",
     "roi_recon_forward_local", "roi_recon_back_local", "roi_recon_ramp_filter",
     "roi_recon_set_timing", "roi_recon_kernel_times", "roi_recon_launch_count",
+    "roi_recon_forward_local_noalloc",
 ]
 
 _lib = None
@@ -113,6 +114,9 @@ def lib() -> ctypes.CDLL:
             L.roi_recon_kernel_times.restype = st
             L.roi_recon_launch_count.argtypes = []
             L.roi_recon_launch_count.restype = ctypes.c_ulonglong
+            L.roi_recon_forward_local_noalloc.argtypes = [ctypes.POINTER(Geometry), ctypes.POINTER(Region), _P, _P,
+                                                          _P, ctypes.c_char_p, ctypes.c_int]
+            L.roi_recon_forward_local_noalloc.restype = st
             _lib = L
     return _lib
 
@@ -181,6 +185,14 @@ def roi_recon_kernel_times(h, kernel: int):
 
 def roi_recon_launch_count() -> int:
     return int(lib().roi_recon_launch_count())
+
+
+def roi_recon_forward_local_noalloc(geom: Geometry, region: Region, x: int, y: int, stream: int):
+    """Allocation-free W_L x (see the header); returns (status, message)."""
+    buf = ctypes.create_string_buffer(256)
+    s = lib().roi_recon_forward_local_noalloc(ctypes.byref(geom), ctypes.byref(region), x, y, stream or None,
+                                              buf, len(buf))
+    return s, buf.value.decode()
 
 
 # ---- convenience layer -----------------------------------------------------------------
