@@ -208,8 +208,9 @@ unsigned long long roi_recon_launch_count(void);
  *            default stream) of the current device.
  *   err:     optional buffer of err_len bytes receiving a message on failure.
  * Scratch: a fixed 16 MiB device array inside the library holds the per-angle ray
- * table and the transposed box image.  Calls needing more (table 64 bytes per angle,
- * rounded up to 256, plus 4 box_w box_h bytes) fail with ROI_EINVAL and say so in err.
+ * table and two zero-padded copies of the box image (by rows and by columns).  Calls
+ * needing more (64 bytes per angle plus 4 (2 box_w box_h + 4 box_w + 4 box_h) bytes,
+ * each part rounded up to 256) fail with ROI_EINVAL and say so in err.
  * Every GPU that loads the library keeps this array until the process exits.  The
  * first call on a device looks up the array's device address (cudaGetSymbolAddress)
  * with that device current; make that first call before any stream capture.  All

@@ -40,8 +40,9 @@ cudaError_t dev_alloc(T** p, size_t count) {
 }
 
 // Grow-only device buffer.
-struct DevBuf {
-    float* p = nullptr;
+template <class T>
+struct DevBufT {
+    T* p = nullptr;
     size_t cap = 0;
     cudaError_t ensure(size_t n) {
         if (n <= cap) return cudaSuccess;
@@ -58,6 +59,7 @@ struct DevBuf {
         cap = 0;
     }
 };
+using DevBuf = DevBufT<float>;
 
 }  // namespace
 
@@ -69,8 +71,10 @@ struct roi_recon {
     // resident data
     float* p = nullptr;      // [na][nd]
     float* q = nullptr;      // [na][nd] filtered sinogram
-    float* xfbp = nullptr;   // [N][N]
-    float* xfbpT = nullptr;  // [N][N] transpose
+    float* xfbp = nullptr;   // [N][N] padded (row stride N + 4), element (0,0)
+    float* xfbpT = nullptr;  // its transpose, padded
+    float* xfbp_base = nullptr;
+    float* xfbpT_base = nullptr;
     float* hodd = nullptr;   // Ram-Lak odd taps scaled by pi/na, [nd/2 + 1]
     float ctail = 0.f;       // (pi/na) (h0 + 2 sum_{odd m < nd} h_m)
     AngleRec* rec_fbp = nullptr;  // frame = grid, window = whole detector
@@ -83,9 +87,12 @@ struct roi_recon {
     std::vector<AngleRec> h_loc, h_ext;
     AngleRec* rec_loc = nullptr;  // frame = box
     AngleRec* rec_ext = nullptr;  // frame = grid, window of the box
-    // ROI workspace: window buffers [na][stride], image buffers [h][w]
+    // ROI workspace: window buffers [na][stride]; box buffers [h][w]; the two images
+    // the forward projector reads (xa: row layout, xaT: transposed) are padded
     DevBuf pp, u, sig, wtmp, wrow;
-    DevBuf x, xb, xT, vx, vy, tau, itmp, itmpT;
+    DevBuf xc, vx, vy, tau, itmp;
+    DevBuf xa, xaT;
+    DevBuf part;             // angle-group partials of the gather
     double* red = nullptr;   // kRedScratch partials + 4 results
     int exterior_ready = 0;  // p' in `pp` matches the cached plan and FBP
     // optional kernel timing: event pairs per kernel class (0 forward, 1 back)
@@ -199,8 +206,12 @@ roi_status ensure_plan(roi_recon* h, const roi_region* region) {
     const size_t nwin = (size_t)h->na * stride, nimg = (size_t)box.w * box.h;
     DevBuf* wins[] = {&h->pp, &h->u, &h->sig, &h->wtmp, &h->wrow};
     for (DevBuf* b : wins) CU(h, b->ensure(nwin));
-    DevBuf* imgs[] = {&h->x, &h->xb, &h->xT, &h->vx, &h->vy, &h->tau, &h->itmp, &h->itmpT};
+    DevBuf* imgs[] = {&h->xc, &h->vx, &h->vy, &h->tau, &h->itmp};
     for (DevBuf* b : imgs) CU(h, b->ensure(nimg));
+    const size_t npad = std::max((size_t)box.h * roi::padded_ld(box.w), (size_t)box.w * roi::padded_ld(box.h));
+    CU(h, h->xa.ensure(npad));
+    CU(h, h->xaT.ensure(npad));
+    CU(h, h->part.ensure((size_t)roi::back_groups(h->na, box.w, box.h) * nimg));
     CU(h, cudaMemcpyAsync(h->rec_loc, h->h_loc.data(), sizeof(AngleRec) * h->na, cudaMemcpyHostToDevice, h->st));
     CU(h, cudaMemcpyAsync(h->rec_ext, h->h_ext.data(), sizeof(AngleRec) * h->na, cudaMemcpyHostToDevice, h->st));
     h->box = box;
@@ -208,6 +219,29 @@ roi_status ensure_plan(roi_recon* h, const roi_region* region) {
     h->stride = stride;
     h->plan_region = *region;
     h->plan_valid = true;
+    return ROI_OK;
+}
+
+// Padded box images: element (0,0) of xa ([h][w + 4]) and xaT ([w][h + 4]).
+int lda(const roi_recon* h) { return roi::padded_ld(h->box.w); }
+int ldaT(const roi_recon* h) { return roi::padded_ld(h->box.h); }
+float* xa0(roi_recon* h) { return h->xa.p + roi::kPad; }
+float* xaT0(roi_recon* h) { return h->xaT.p + roi::kPad; }
+
+// Zero both padded images (pads and interior).
+roi_status clear_padded(roi_recon* h) {
+    const size_t n1 = (size_t)h->box.h * lda(h), n2 = (size_t)h->box.w * ldaT(h);
+    CU(h, cudaMemsetAsync(h->xa.p, 0, sizeof(float) * n1, h->st));
+    CU(h, cudaMemsetAsync(h->xaT.p, 0, sizeof(float) * n2, h->st));
+    return ROI_OK;
+}
+
+// Load an unpadded [h][w] image (device) into xa / xaT.
+roi_status load_padded(roi_recon* h, const float* x) {
+    roi_status s = clear_padded(h);
+    if (s != ROI_OK) return s;
+    roi::launch_copy_pad(x, h->box.w, xa0(h), lda(h), h->box.h, h->box.w, h->st);
+    roi::launch_transpose(x, h->box.w, xaT0(h), ldaT(h), h->box.h, h->box.w, h->st);
     return ROI_OK;
 }
 
@@ -220,21 +254,25 @@ void fill_info(const roi_recon* h, roi_solve_info* info) {
     info->window_stride = h->stride;
 }
 
-roi::FwdArgs fwd_local(roi_recon* h, const float* img, const float* imgT, float* out) {
+// Forward over the box reading the padded images xa / xaT.
+roi::FwdArgs fwd_local(roi_recon* h, float* out) {
     roi::FwdArgs a{};
     a.rec = h->rec_loc;
     a.na = h->na;
     a.stride = h->stride;
     a.nx = h->box.w;
     a.ny = h->box.h;
-    a.img = img;
-    a.imgT = imgT;
+    a.img = xa0(h);
+    a.imgT = xaT0(h);
+    a.img_ld = lda(h);
+    a.imgT_ld = ldaT(h);
     a.out = out;
     a.nd = h->nd;
     return a;
 }
 
-roi::BackArgs back_local(roi_recon* h, const float* win, float* out, float* outT) {
+// Gather over the box into `out` (row stride out_ld), optionally its transpose.
+roi::BackArgs back_local(roi_recon* h, const float* win, float* out, int out_ld, float* outT, int outT_ld) {
     roi::BackArgs b{};
     b.rec = h->rec_loc;
     b.na = h->na;
@@ -243,18 +281,22 @@ roi::BackArgs back_local(roi_recon* h, const float* win, float* out, float* outT
     b.ny = h->box.h;
     b.win = win;
     b.out = out;
+    b.out_ld = out_ld;
     b.outT = outT;
+    b.outT_ld = outT_ld;
+    b.part = h->part.p;
     return b;
 }
 
-// Row sums W_L 1 into h->wrow and column sums W_L^T 1 into `cols`.
+// Row sums W_L 1 into h->wrow and column sums W_L^T 1 into `cols` (uses xa / xaT).
 roi_status rowcol_sums(roi_recon* h, float* cols) {
     const size_t nimg = (size_t)h->box.w * h->box.h;
     roi::launch_fill(h->itmp.p, 1.f, nimg, h->st);
-    roi::launch_fill(h->itmpT.p, 1.f, nimg, h->st);
-    roi::launch_forward(roi::FWD_PLAIN, fwd_local(h, h->itmp.p, h->itmpT.p, h->wrow.p), h->st);
+    roi_status s = load_padded(h, h->itmp.p);
+    if (s != ROI_OK) return s;
+    roi::launch_forward(roi::FWD_PLAIN, fwd_local(h, h->wrow.p), h->st);
     roi::launch_window_ones(h->wtmp.p, h->rec_loc, h->na, h->stride, h->st);
-    roi::launch_back(roi::BACK_PLAIN, back_local(h, h->wtmp.p, cols, nullptr), h->st);
+    roi::launch_back(roi::BACK_PLAIN, back_local(h, h->wtmp.p, cols, h->box.w, nullptr, 0), h->st);
     LAUNCHED(h, "row/column sums");
     return ROI_OK;
 }
@@ -268,6 +310,8 @@ roi_status run_exterior(roi_recon* h) {
     a.ny = h->N;
     a.img = h->xfbp;
     a.imgT = h->xfbpT;
+    a.img_ld = roi::padded_ld(h->N);
+    a.imgT_ld = roi::padded_ld(h->N);
     a.hole = h->box;
     a.out = h->pp.p;
     a.p = h->p;
@@ -278,11 +322,10 @@ roi_status run_exterior(roi_recon* h) {
     return ROI_OK;
 }
 
+// SIRT iterates x in the padded image xa (and its transpose xaT) that the forward reads.
 roi_status solve_sirt(roi_recon* h, const roi_solve_params* prm) {
     const int nx = h->box.w, ny = h->box.h;
-    const size_t nimg = (size_t)nx * ny, nwin = (size_t)h->na * h->stride;
-    roi::launch_fill(h->x.p, 0.f, nimg, h->st);
-    roi::launch_fill(h->xT.p, 0.f, nimg, h->st);
+    const size_t nwin = (size_t)h->na * h->stride;
     const float* R = nullptr;
     const float* C = nullptr;
     if (prm->weighting) {
@@ -293,11 +336,13 @@ roi_status solve_sirt(roi_recon* h, const roi_solve_params* prm) {
         R = h->sig.p;
         C = h->tau.p;
     }
+    roi_status s = clear_padded(h);  // x^0 = 0
+    if (s != ROI_OK) return s;
     const float alpha = (float)(1.0 / ((double)h->na * h->nd));
-    roi::FwdArgs fa = fwd_local(h, h->x.p, h->xT.p, h->u.p);
+    roi::FwdArgs fa = fwd_local(h, h->u.p);
     fa.pp = h->pp.p;
     fa.R = R;
-    roi::BackArgs ba = back_local(h, h->u.p, h->x.p, h->xT.p);
+    roi::BackArgs ba = back_local(h, h->u.p, xa0(h), lda(h), xaT0(h), ldaT(h));
     ba.C = C;
     ba.step_scalar = alpha;
     ba.nonneg = 1;
@@ -316,19 +361,21 @@ roi_status solve_sirt(roi_recon* h, const roi_solve_params* prm) {
 }
 
 roi_status power_norm(roi_recon* h, int iters) {
-    // ||K||, K = [W_L; grad], by power iteration on K^T K from the normalised all-ones image
+    // ||K||, K = [W_L; grad], by power iteration on K^T K from the normalised all-ones image;
+    // the iterate lives in xa / xaT, K^T K x in itmp
     const int nx = h->box.w, ny = h->box.h;
     const size_t nimg = (size_t)nx * ny;
     const float v0 = (float)(1.0 / std::sqrt((double)nimg));
     roi::launch_fill(h->itmp.p, v0, nimg, h->st);
-    roi::launch_fill(h->itmpT.p, v0, nimg, h->st);
+    roi_status s = load_padded(h, h->itmp.p);
+    if (s != ROI_OK) return s;
     double* n2 = h->red + kRedScratch;
     for (int it = 0; it < iters; ++it) {
-        roi::launch_forward(roi::FWD_PLAIN, fwd_local(h, h->itmp.p, h->itmpT.p, h->wtmp.p), h->st);
-        roi::launch_back(roi::BACK_PLAIN, back_local(h, h->wtmp.p, h->x.p, nullptr), h->st);
-        roi::launch_power_ktk_grad(h->x.p, h->itmp.p, nx, ny, h->st);
-        roi::launch_sumsq(h->x.p, (int)nimg, h->red, kRedScratch, n2, h->st);
-        roi::launch_normalize(h->x.p, h->itmp.p, h->itmpT.p, nx, ny, n2, h->st);
+        roi::launch_forward(roi::FWD_PLAIN, fwd_local(h, h->wtmp.p), h->st);
+        roi::launch_back(roi::BACK_PLAIN, back_local(h, h->wtmp.p, h->itmp.p, nx, nullptr, 0), h->st);
+        roi::launch_power_ktk_grad(h->itmp.p, xa0(h), lda(h), nx, ny, h->st);
+        roi::launch_sumsq(h->itmp.p, (int)nimg, h->red, kRedScratch, n2, h->st);
+        roi::launch_normalize(h->itmp.p, xa0(h), lda(h), xaT0(h), ldaT(h), nx, ny, n2, h->st);
     }
     LAUNCHED(h, "power iteration");
     return ROI_OK;
@@ -353,16 +400,20 @@ roi_status solve_cp(roi_recon* h, const roi_solve_params* prm, double* L_out) {
         sigma_v_dev = h->sig.p;  // same scalar step
         *L_out = 1.0;            // marker: read back later
     }
-    for (DevBuf* b : {&h->x, &h->xb, &h->xT, &h->vx, &h->vy}) roi::launch_fill(b->p, 0.f, nimg, h->st);
+    // x in xc; xbar in the padded xa (+ transpose xaT) that the forward reads
+    for (DevBuf* b : {&h->xc, &h->vx, &h->vy}) roi::launch_fill(b->p, 0.f, nimg, h->st);
     roi::launch_fill(h->u.p, 0.f, nwin, h->st);
-    roi::FwdArgs fa = fwd_local(h, h->xb.p, h->xT.p, h->u.p);
+    roi_status s0 = clear_padded(h);
+    if (s0 != ROI_OK) return s0;
+    roi::FwdArgs fa = fwd_local(h, h->u.p);
     fa.pp = h->pp.p;
     fa.R = h->sig.p;
-    roi::BackArgs ba = back_local(h, h->u.p, h->x.p, h->xT.p);
+    roi::BackArgs ba = back_local(h, h->u.p, h->xc.p, nx, xaT0(h), ldaT(h));
     ba.C = h->tau.p;
     ba.vx = h->vx.p;
     ba.vy = h->vy.p;
-    ba.xbar = h->xb.p;
+    ba.xbar = xa0(h);
+    ba.xbar_ld = lda(h);
     const float lam = (float)prm->lambda;
     for (int it = 0; it < prm->iters; ++it) {
         {
@@ -370,9 +421,9 @@ roi_status solve_cp(roi_recon* h, const roi_solve_params* prm, double* L_out) {
             roi::launch_forward(roi::FWD_CP, fa, h->st);
         }
         if (sigma_v_dev)
-            roi::launch_cp_dual_grad_dev(h->xb.p, h->vx.p, h->vy.p, nx, ny, sigma_v_dev, lam, h->st);
+            roi::launch_cp_dual_grad_dev(xa0(h), lda(h), h->vx.p, h->vy.p, nx, ny, sigma_v_dev, lam, h->st);
         else
-            roi::launch_cp_dual_grad(h->xb.p, h->vx.p, h->vy.p, nx, ny, sigma_v, lam, h->st);
+            roi::launch_cp_dual_grad(xa0(h), lda(h), h->vx.p, h->vy.p, nx, ny, sigma_v, lam, h->st);
         {
             Span sp(h, 1);
             roi::launch_back(roi::BACK_CP, ba, h->st);
@@ -397,12 +448,19 @@ roi_status roi_recon_create(const roi_geometry* geom, void* cuda_stream, roi_rec
     h->nd = geom->n_det;
     h->angles = make_angles(geom);
     h->st = (cudaStream_t)cuda_stream;
-    const size_t ns = (size_t)h->na * h->nd, nimg = (size_t)h->N * h->N;
+    const size_t ns = (size_t)h->na * h->nd;
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = dev_alloc(&h->p, ns);
     if (e == cudaSuccess) e = dev_alloc(&h->q, ns);
-    if (e == cudaSuccess) e = dev_alloc(&h->xfbp, nimg);
-    if (e == cudaSuccess) e = dev_alloc(&h->xfbpT, nimg);
+    const size_t npad = (size_t)h->N * roi::padded_ld(h->N);
+    if (e == cudaSuccess) e = dev_alloc(&h->xfbp_base, npad);
+    if (e == cudaSuccess) e = dev_alloc(&h->xfbpT_base, npad);
+    if (e == cudaSuccess) e = cudaMemset(h->xfbp_base, 0, sizeof(float) * npad);
+    if (e == cudaSuccess) e = cudaMemset(h->xfbpT_base, 0, sizeof(float) * npad);
+    if (e == cudaSuccess) {
+        h->xfbp = h->xfbp_base + roi::kPad;
+        h->xfbpT = h->xfbpT_base + roi::kPad;
+    }
     if (e == cudaSuccess) e = dev_alloc(&h->hodd, (size_t)h->nd / 2 + 1);
     if (e == cudaSuccess) e = dev_alloc(&h->rec_fbp, (size_t)h->na);
     if (e == cudaSuccess) e = dev_alloc(&h->rec_loc, (size_t)h->na);
@@ -438,15 +496,16 @@ roi_status roi_recon_create(const roi_geometry* geom, void* cuda_stream, roi_rec
 void roi_recon_destroy(roi_recon_t h) {
     if (!h) return;
     cudaStreamSynchronize(h->st);
-    for (float* b : {h->p, h->q, h->xfbp, h->xfbpT, h->hodd})
+    for (float* b : {h->p, h->q, h->xfbp_base, h->xfbpT_base, h->hodd})
         if (b) cudaFree(b);
     for (AngleRec* b : {h->rec_fbp, h->rec_loc, h->rec_ext})
         if (b) cudaFree(b);
     if (h->red) cudaFree(h->red);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
-    for (DevBuf* b : {&h->pp, &h->u, &h->sig, &h->wtmp, &h->wrow, &h->x, &h->xb, &h->xT, &h->vx, &h->vy, &h->tau,
-                      &h->itmp, &h->itmpT})
+    for (DevBuf* b : {&h->pp, &h->u, &h->sig, &h->wtmp, &h->wrow, &h->xc, &h->vx, &h->vy, &h->tau, &h->itmp, &h->xa,
+                      &h->xaT})
         b->release();
+    h->part.release();
     delete h;
 }
 
@@ -488,12 +547,15 @@ roi_status roi_recon_fbp(roi_recon_t h, float* out_or_null) {
     b.ny = h->N;
     b.win = h->q;
     b.out = h->xfbp;
+    b.out_ld = roi::padded_ld(h->N);
     b.outT = h->xfbpT;
+    b.outT_ld = roi::padded_ld(h->N);
+    b.part = nullptr;  // the whole grid has enough tiles for one angle group
     roi::launch_back(roi::BACK_PLAIN, b, h->st);
     LAUNCHED(h, "fbp");
     if (out_or_null)
-        CU(h, cudaMemcpyAsync(out_or_null, h->xfbp, sizeof(float) * (size_t)h->N * h->N, cudaMemcpyDeviceToDevice,
-                              h->st));
+        CU(h, cudaMemcpy2DAsync(out_or_null, sizeof(float) * h->N, h->xfbp, sizeof(float) * roi::padded_ld(h->N),
+                                sizeof(float) * h->N, h->N, cudaMemcpyDeviceToDevice, h->st));
     h->have_fbp = true;
     h->exterior_ready = 0;
     return ROI_OK;
@@ -547,8 +609,9 @@ roi_status roi_recon_forward_local(roi_recon_t h, const roi_region* region, cons
     if (!x || !y) return fail(h, ROI_EINVAL, "forward_local: null pointer");
     roi_status s = ensure_plan(h, region);
     if (s != ROI_OK) return s;
-    roi::launch_transpose(x, h->itmpT.p, h->box.h, h->box.w, h->st);
-    roi::launch_forward(roi::FWD_PLAIN, fwd_local(h, x, h->itmpT.p, y), h->st);
+    s = load_padded(h, x);
+    if (s != ROI_OK) return s;
+    roi::launch_forward(roi::FWD_PLAIN, fwd_local(h, y), h->st);
     LAUNCHED(h, "forward_local");
     return ROI_OK;
 }
@@ -559,7 +622,7 @@ roi_status roi_recon_back_local(roi_recon_t h, const roi_region* region, const f
     if (!x || !y) return fail(h, ROI_EINVAL, "back_local: null pointer");
     roi_status s = ensure_plan(h, region);
     if (s != ROI_OK) return s;
-    roi::launch_back(roi::BACK_PLAIN, back_local(h, y, x, nullptr), h->st);
+    roi::launch_back(roi::BACK_PLAIN, back_local(h, y, x, h->box.w, nullptr, 0), h->st);
     LAUNCHED(h, "back_local");
     return ROI_OK;
 }
@@ -588,22 +651,36 @@ roi_status roi_recon_solve_local(roi_recon_t h, const roi_region* region, const 
     const int nx = h->box.w, ny = h->box.h;
     const size_t nimg = (size_t)nx * ny;
     const double cxl = region->cx - h->box.x0, cyl = region->cy - h->box.y0;
+    // the solution: SIRT keeps x in the padded xa, CP in xc
+    const bool sirt = params->reg == ROI_SIRT_NONNEG;
+    const float* xs = sirt ? xa0(h) : h->xc.p;
+    const int xs_ld = sirt ? lda(h) : nx;
     float* dst = out_on_device ? out : h->itmp.p;
-    roi::launch_crop(h->x.p, dst, nx, ny, cxl, cyl, region->radius, params->crop_disk, h->st);
+    roi::launch_crop(xs, xs_ld, dst, nx, ny, cxl, cyl, region->radius, params->crop_disk, h->st);
     LAUNCHED(h, "crop");
     double objective = 0.0, L = 0.0;
     if (params->eval_objective) {
         // ||W_L x - p'||^2 over rays that reach the box + lambda TV(x)
-        roi::launch_transpose(h->x.p, h->itmpT.p, ny, nx, h->st);
-        roi::launch_forward(roi::FWD_PLAIN, fwd_local(h, h->x.p, h->itmpT.p, h->wtmp.p), h->st);
-        if (params->reg == ROI_SIRT_NONNEG || !params->precond) {
-            // row sums were not computed by the solver: W_L 1 into wrow (vx, vy are free scratch now)
+        if (sirt || !params->precond) {
+            // row sums were not computed by the solver: W_L 1 into wrow (vx, vy, xc are free now)
+            float* xkeep = sirt ? h->xc.p : h->vy.p;
+            roi::launch_copy_pad(xs, xs_ld, xkeep, nx, ny, nx, h->st);  // unpadded copy of x
             roi::launch_fill(h->vx.p, 1.f, nimg, h->st);
-            roi::launch_fill(h->vy.p, 1.f, nimg, h->st);
-            roi::launch_forward(roi::FWD_PLAIN, fwd_local(h, h->vx.p, h->vy.p, h->wrow.p), h->st);
+            s = load_padded(h, h->vx.p);
+            if (s != ROI_OK) return s;
+            roi::launch_forward(roi::FWD_PLAIN, fwd_local(h, h->wrow.p), h->st);
+            s = load_padded(h, xkeep);
+            if (s != ROI_OK) return s;
+            roi::launch_forward(roi::FWD_PLAIN, fwd_local(h, h->wtmp.p), h->st);
+            roi::launch_objective(h->wtmp.p, h->pp.p, h->wrow.p, h->na * h->stride, xkeep, nx, nx, ny, h->red,
+                                  kRedScratch, h->red + kRedScratch + 2, h->st);
+        } else {
+            s = load_padded(h, h->xc.p);
+            if (s != ROI_OK) return s;
+            roi::launch_forward(roi::FWD_PLAIN, fwd_local(h, h->wtmp.p), h->st);
+            roi::launch_objective(h->wtmp.p, h->pp.p, h->wrow.p, h->na * h->stride, h->xc.p, nx, nx, ny, h->red,
+                                  kRedScratch, h->red + kRedScratch + 2, h->st);
         }
-        roi::launch_objective(h->wtmp.p, h->pp.p, h->wrow.p, h->na * h->stride, h->x.p, nx, ny, h->red, kRedScratch,
-                              h->red + kRedScratch + 2, h->st);
         LAUNCHED(h, "objective");
         double r2[2];
         CU(h, cudaMemcpyAsync(r2, h->red + kRedScratch + 2, sizeof r2, cudaMemcpyDeviceToHost, h->st));

@@ -1,8 +1,8 @@
 // noalloc.cu -- a forward projector entry point that allocates no device memory.
 //
 // roi_recon_forward_local_noalloc computes the same y = W_L x as roi_recon_forward_local
-// but without a handle: its scratch (the per-angle ray table and the transposed box
-// image the projector reads for column-stepping angles) lives in one file-scope
+// but without a handle: its scratch (the per-angle ray table and the two zero-padded
+// copies of the box image the projector reads, by rows and by columns) lives in one file-scope
 // __device__ array of fixed size, so the call makes no cudaMalloc / cudaFree and
 // calls nothing that allocates.  It exists for callers that cannot allocate device
 // memory themselves: code whose device memory is owned by someone else's fixed
@@ -18,9 +18,10 @@
 //     with that device current.  That first call should come before any stream
 //     capture.
 //   * All calls share the array and it keeps the last call's contents.  Each call
-//     rewrites every scratch byte it reads before reading it, so nothing needs to
-//     start at zero; but calls whose work overlaps on the GPU (other streams, other
-//     host threads) race on the array and must be serialised by the caller.
+//     clears and rewrites every scratch byte it reads before reading it (the zero
+//     borders of the padded image copies included), so nothing carries over; but
+//     calls whose work overlaps on the GPU (other streams, other host threads) race
+//     on the array and must be serialised by the caller.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -66,17 +67,7 @@ __global__ void k_plan_box(roi::AngleRec* rec, int N, int na, int nd, roi::Rect 
     }
     if (width > stride) width = stride;  // the output row holds `stride` bins
     roi::AngleRec r;
-    r.c = c;
-    r.s = s;
-    r.row = row;
-    r.inv_w = (float)(1.0 / wd);
-    r.d0 = d0;
-    r.width = width;
-    r.phi = d0 - dhalf - Tb;
-    const int Mm = row ? box.w : box.h;
-    r.a_scale = row ? 1.0 / c : -1.0 / s;
-    r.slope = row ? s / c : c / s;
-    r.A0 = 0.5 * (Mm - 1) + r.a_scale * r.phi;
+    roi::angle_fill(r, c, s, row, wd, d0, width, d0 - dhalf - Tb, row ? box.w : box.h);
     rec[a] = r;
 }
 
@@ -118,7 +109,10 @@ extern "C" roi_status roi_recon_forward_local_noalloc(const roi_geometry* geom, 
     }
     const int na = geom->n_angles;
     const size_t table_bytes = ((sizeof(roi::AngleRec) * (size_t)na + 255) / 256) * 256;
-    const size_t image_bytes = sizeof(float) * (size_t)box.w * (size_t)box.h;
+    // the two padded copies of the box image the projector reads (rows and columns)
+    const size_t rows_bytes = ((sizeof(float) * (size_t)box.h * roi::padded_ld(box.w) + 255) / 256) * 256;
+    const size_t cols_bytes = sizeof(float) * (size_t)box.w * roi::padded_ld(box.h);
+    const size_t image_bytes = rows_bytes + cols_bytes;
     if (table_bytes + image_bytes > kNoallocScratchBytes) {
         char msg[256];
         std::snprintf(msg, sizeof msg,
@@ -151,18 +145,26 @@ extern "C" roi_status roi_recon_forward_local_noalloc(const roi_geometry* geom, 
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
     roi::AngleRec* rec = (roi::AngleRec*)base;
-    float* xT = (float*)((unsigned char*)base + table_bytes);
+    float* xr = (float*)((unsigned char*)base + table_bytes);               // [h][w + 4]
+    float* xc = (float*)((unsigned char*)base + table_bytes + rows_bytes);  // [w][h + 4]
+    if (cudaMemsetAsync(xr, 0, image_bytes, st) != cudaSuccess) {
+        put_err(err, err_len, "forward_local_noalloc: clearing the scratch failed");
+        return ROI_ECUDA;
+    }
     roi::count_launches(1);
     k_plan_box<<<(na + 127) / 128, 128, 0, st>>>(rec, geom->n_pix, na, geom->n_det, box, info.window_stride);
-    roi::launch_transpose(x, xT, box.h, box.w, st);
+    roi::launch_copy_pad(x, box.w, xr + roi::kPad, roi::padded_ld(box.w), box.h, box.w, st);
+    roi::launch_transpose(x, box.w, xc + roi::kPad, roi::padded_ld(box.h), box.h, box.w, st);
     roi::FwdArgs a{};
     a.rec = rec;
     a.na = na;
     a.stride = info.window_stride;
     a.nx = box.w;
     a.ny = box.h;
-    a.img = x;
-    a.imgT = xT;
+    a.img = xr + roi::kPad;
+    a.imgT = xc + roi::kPad;
+    a.img_ld = roi::padded_ld(box.w);
+    a.imgT_ld = roi::padded_ld(box.h);
     a.out = y;
     a.nd = geom->n_det;
     roi::launch_forward(roi::FWD_PLAIN, a, st);

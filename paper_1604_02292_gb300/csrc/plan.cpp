@@ -66,18 +66,8 @@ int plan_angles(int N, int na, int nd, const double* angles, Rect frame, Rect ta
             }
         }
         const double Tf = Xf * c + Yf * s;
-        AngleRec& r = rec[a];
-        r.c = c;
-        r.s = s;
-        r.row = row;
-        r.inv_w = (float)(1.0 / wd);
-        r.d0 = d0;
-        r.width = width;
-        r.phi = d0 - dhalf - Tf;
         const int Mm = row ? frame.w : frame.h;  // minor extent
-        r.a_scale = row ? 1.0 / c : -1.0 / s;
-        r.slope = row ? s / c : c / s;
-        r.A0 = 0.5 * (Mm - 1) + r.a_scale * r.phi;
+        angle_fill(rec[a], c, s, row, wd, d0, width, d0 - dhalf - Tf, Mm);
         wmax = std::max(wmax, width);
     }
     return wmax;

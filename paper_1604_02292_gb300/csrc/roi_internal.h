@@ -11,7 +11,52 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 namespace roi {
+
+// Float-float numbers (hi + lo, ~44 significant bits) built from error-free float
+// transformations, used where GB300's FP64 rate (1/64 of FP32) would dominate a kernel.
+struct ff {
+    float hi, lo;
+};
+#if defined(__CUDACC__)
+#define ROI_HD __host__ __device__ __forceinline__
+#else
+#define ROI_HD inline
+#endif
+ROI_HD ff ff_split(double v) {
+    ff r;
+    r.hi = (float)v;
+    r.lo = (float)(v - (double)r.hi);
+    return r;
+}
+// a + b exactly as hi + lo (Knuth's two-sum)
+ROI_HD ff two_sum(float a, float b) {
+    ff r;
+    r.hi = a + b;
+    const float bb = r.hi - a;
+    r.lo = (a - (r.hi - bb)) + (b - bb);
+    return r;
+}
+ROI_HD ff ff_add(ff a, ff b) {
+    ff s = two_sum(a.hi, b.hi);
+    s.lo += a.lo + b.lo;
+    return two_sum(s.hi, s.lo);
+}
+// a * b for float a (exact product via fma) times float-float b
+ROI_HD ff ff_mul_f(float a, ff b) {
+    ff p;
+    p.hi = a * b.hi;
+    p.lo = fmaf(a, b.hi, -p.hi) + a * b.lo;
+    return two_sum(p.hi, p.lo);
+}
+// Neumaier-compensated accumulation of v into (s, c)
+ROI_HD void neu_add(float& s, float& c, float v) {
+    const float t = s + v;
+    c += fabsf(s) >= fabsf(v) ? (s - t) + v : (v - t) + s;
+    s = t;
+}
 
 // Per-angle record of a ray set over a frame.  Frame-centre coordinates:
 //   pixel (li, lj) of the frame (row, column) sits at xi = lj - (nx-1)/2,
@@ -21,17 +66,38 @@ namespace roi {
 // column otherwise) has minor coordinate  A0 + k a_scale + (m - (M-1)/2) slope.
 // Back (pixel-driven): pixel (li, lj) sits at window coordinate
 //   kappa = xi c + eta s - phi.
+// The host computes every value in double and stores it as float-float.
 struct AngleRec {
-    double c, s;       // cos(theta), sin(theta)
-    double phi;        // d0 - (N_d-1)/2 - T_frame
-    double A0;         // (Mm-1)/2 + a_scale * phi
-    double a_scale;    // 1/c (row branch) or -1/s (column branch)
-    double slope;      // s/c (row branch) or c/s (column branch)
+    ff c, s;           // cos(theta), sin(theta)
+    ff phi;            // d0 - (N_d-1)/2 - T_frame
+    ff A0;             // (Mm-1)/2 + a_scale * phi
+    ff a_scale;        // 1/c (row branch) or -1/s (column branch)
+    ff slope;          // s/c (row branch) or c/s (column branch)
+    float inv_slope;   // 1/slope (unused when flat)
     float inv_w;       // 1 / |c| or 1 / |s|
     int row;           // 1: sample per row (|c| >= |s|), 0: per column
+    int flat;          // 1: |slope| < 1e-12 (rays parallel to the sampling axis)
     int d0;            // first bin of the window
     int width;         // bins in the window (0 if no ray reaches the frame)
 };
+
+// Fills the derived fields of `r` from doubles (host and device).
+ROI_HD void angle_fill(AngleRec& r, double c, double s, int row, double wd, int d0, int width, double phi, int Mm) {
+    r.c = ff_split(c);
+    r.s = ff_split(s);
+    r.row = row;
+    r.inv_w = (float)(1.0 / wd);
+    r.d0 = d0;
+    r.width = width;
+    r.phi = ff_split(phi);
+    const double as = row ? 1.0 / c : -1.0 / s;
+    const double sl = row ? s / c : c / s;
+    r.a_scale = ff_split(as);
+    r.slope = ff_split(sl);
+    r.flat = fabs(sl) < 1e-12;
+    r.inv_slope = r.flat ? 0.f : (float)(1.0 / sl);
+    r.A0 = ff_split(0.5 * (Mm - 1) + as * phi);
+}
 
 struct Rect {
     int x0, y0, w, h;
@@ -62,12 +128,20 @@ unsigned long long launches_total();
 enum FwdMode { FWD_PLAIN = 0, FWD_EXTERIOR = 1, FWD_SIRT = 2, FWD_CP = 3 };
 enum BackMode { BACK_PLAIN = 0, BACK_SIRT = 1, BACK_CP = 2 };
 
+// Images read by the forward projector are "padded": element (0, 0) sits at `img`,
+// rows have stride `img_ld` >= extent + 4, and the two columns on either side of each
+// row (indices -2, -1, extent, extent + 1) hold zeros.
+constexpr int kPad = 2;
+inline int padded_ld(int extent) { return extent + 2 * kPad; }
+
 struct FwdArgs {
     const AngleRec* rec;   // [na]
     int na, stride;        // window rows and their stride
     int nx, ny;            // frame size
-    const float* img;      // frame image [ny][nx]
-    const float* imgT;     // its transpose [nx][ny]
+    const float* img;      // frame image [ny][img_ld], padded
+    const float* imgT;     // its transpose [nx][imgT_ld], padded
+    int img_ld, imgT_ld;
+    int seg_len;           // set by launch_forward
     Rect hole;             // FWD_EXTERIOR: frame pixels treated as zero (w = 0: none)
     float* out;            // [na][stride]
     // FWD_EXTERIOR: out = p[a][d0 + k] - W_F x
@@ -85,44 +159,56 @@ struct BackArgs {
     int na, stride;
     int nx, ny;            // frame size
     const float* win;      // [na][stride] window values
-    float* out;            // BACK_PLAIN: [ny][nx]; else x (in/out)
-    float* outT;           // optional transpose of the written image ([nx][ny]) or null
+    float* out;            // BACK_PLAIN: result; else x (in/out); row stride out_ld
+    int out_ld;
+    float* outT;           // optional transpose of the written image, row stride outT_ld, or null
+    int outT_ld;
+    float* part;           // angle-group partials [G][ny][nx] (G = back_groups) or null (G = 1)
     // BACK_SIRT: x = max(0, x + step * acc) (nonneg) with step = C ? C[pix] : step_scalar
     // BACK_CP:   x+ = x - tau (acc - div v); xbar = 2 x+ - x  (tau = C ? C[pix] : step_scalar)
-    const float* C;
+    const float* C;        // [ny][nx]
     float step_scalar;
     int nonneg;
     const float* vx;       // BACK_CP: [ny][nx]
     const float* vy;
-    float* xbar;           // BACK_CP: [ny][nx] (its transpose goes to outT)
+    float* xbar;           // BACK_CP: row stride xbar_ld (its transpose goes to outT)
+    int xbar_ld;
 };
+
+// Work splits chosen from the sizes alone (results never depend on other work).
+int forward_segments(int na, int stride, int nx, int ny, int* seg_len);
+int back_groups(int na, int nx, int ny);
 
 void launch_forward(FwdMode mode, const FwdArgs& a, cudaStream_t st);
 void launch_back(BackMode mode, const BackArgs& a, cudaStream_t st);
 // hodd[t] = s h_{2t+1}; ctail = s (h0 + 2 sum_{odd m < nd} h_m), s = pi / N_theta
 void launch_ramp(const float* p, const float* hodd, float* q, int na, int nd, float ctail, cudaStream_t st);
-void launch_transpose(const float* in, float* out, int rows, int cols, cudaStream_t st);
+// out[c][r] = in[r][c] (row strides in_ld, out_ld)
+void launch_transpose(const float* in, int in_ld, float* out, int out_ld, int rows, int cols, cudaStream_t st);
+// out[r][c] = in[r][c] with row strides in_ld, out_ld (pads untouched)
+void launch_copy_pad(const float* in, int in_ld, float* out, int out_ld, int rows, int cols, cudaStream_t st);
 void launch_fill(float* p, float v, size_t n, cudaStream_t st);
 void launch_window_ones(float* win, const AngleRec* rec, int na, int stride, cudaStream_t st);
 // CP gradient dual: v = proj_{|v| <= lambda}(v + sigma_v grad xbar)
-void launch_cp_dual_grad(const float* xbar, float* vx, float* vy, int nx, int ny, float sigma_v, float lambda,
-                         cudaStream_t st);
-void launch_cp_dual_grad_dev(const float* xbar, float* vx, float* vy, int nx, int ny, const float* sigma_dev,
-                             float lambda, cudaStream_t st);
+void launch_cp_dual_grad(const float* xbar, int xbar_ld, float* vx, float* vy, int nx, int ny, float sigma_v,
+                         float lambda, cudaStream_t st);
+void launch_cp_dual_grad_dev(const float* xbar, int xbar_ld, float* vx, float* vy, int nx, int ny,
+                             const float* sigma_dev, float lambda, cudaStream_t st);
 // power iteration helpers for ||K||, K = [W_L; grad]
-void launch_power_ktk_grad(float* y, const float* x, int nx, int ny, cudaStream_t st);
+void launch_power_ktk_grad(float* y, const float* x, int x_ld, int nx, int ny, cudaStream_t st);
 void launch_sumsq(const float* v, int n, double* scratch, int nscratch, double* out2, cudaStream_t st);
-void launch_normalize(const float* y, float* x, float* xT, int nx, int ny, const double* n2, cudaStream_t st);
+void launch_normalize(const float* y, float* x, int x_ld, float* xT, int xT_ld, int nx, int ny, const double* n2,
+                      cudaStream_t st);
 void launch_fill_step(float* dst, size_t n, const double* n2, double* L_out, cudaStream_t st);
 // Preconditioners from row sums (window) and column sums (box):
 //   mode 0 (SIRT weights): R = s > 1e-3 ? 1/s : 0, C likewise
 //   mode 1 (CP diag):      sigma_u = s > 1e-6 ? 1/s : 0; tau = 1/(colsum + |grad| column count)
 void launch_precond(float* rows, int nrows_total, float* cols, int nx, int ny, int mode, cudaStream_t st);
 // out = x (box) with pixels outside the disk (cx, cy, r) in box-local coordinates set to 0 if crop
-void launch_crop(const float* x, float* out, int nx, int ny, double cxl, double cyl, double r, int crop,
+void launch_crop(const float* x, int x_ld, float* out, int nx, int ny, double cxl, double cyl, double r, int crop,
                  cudaStream_t st);
 // objective terms: part[0] = sum over rows with rowsum > 1e-6 of (wx - pp)^2, part[1] = sum |grad x|
-void launch_objective(const float* wx, const float* pp, const float* rowsum, int nwin, const float* x, int nx,
-                      int ny, double* scratch, int nscratch, double* out2, cudaStream_t st);
+void launch_objective(const float* wx, const float* pp, const float* rowsum, int nwin, const float* x, int x_ld,
+                      int nx, int ny, double* scratch, int nscratch, double* out2, cudaStream_t st);
 
 }  // namespace roi

@@ -13,16 +13,17 @@ namespace roi {
 
 namespace {
 
-__global__ void k_cp_dual_grad(const float* __restrict__ xb, float* vx, float* vy, int nx, int ny,
+__global__ void k_cp_dual_grad(const float* __restrict__ xb, int ld, float* vx, float* vy, int nx, int ny,
                                const float* sigma_dev, float sigma_v, float lambda) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= ny || j >= nx) return;
     const float sv = sigma_dev ? *sigma_dev : sigma_v;
     const size_t o = (size_t)i * nx + j;
-    const float x0 = xb[o];
-    const float gx = j < nx - 1 ? xb[o + 1] - x0 : 0.f;
-    const float gy = i < ny - 1 ? xb[o + nx] - x0 : 0.f;
+    const float* xp = xb + (size_t)i * ld + j;
+    const float x0 = xp[0];
+    const float gx = j < nx - 1 ? xp[1] - x0 : 0.f;
+    const float gy = i < ny - 1 ? xp[ld] - x0 : 0.f;
     const float ax = fmaf(sv, gx, vx[o]);
     const float ay = fmaf(sv, gy, vy[o]);
     const float m = sqrtf(ax * ax + ay * ay);
@@ -53,13 +54,13 @@ __global__ void k_precond_cols(float* cols, int nx, int ny, int mode) {
     }
 }
 
-__global__ void k_crop(const float* __restrict__ x, float* __restrict__ out, int nx, int ny, double cxl, double cyl,
-                       double r, int crop) {
+__global__ void k_crop(const float* __restrict__ x, int ld, float* __restrict__ out, int nx, int ny, double cxl,
+                       double cyl, double r, int crop) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= ny || j >= nx) return;
     const size_t o = (size_t)i * nx + j;
-    float v = x[o];
+    float v = x[(size_t)i * ld + j];
     if (crop) {
         const double dx = j - cxl, dy = i - cyl;
         if (dx * dx + dy * dy > r * r) v = 0.f;
@@ -94,8 +95,8 @@ __device__ inline double block_sum(double v, double* sh) {
 }
 
 __global__ void k_objective_partial(const float* __restrict__ wx, const float* __restrict__ pp,
-                                    const float* __restrict__ rowsum, int nwin, const float* __restrict__ x, int nx,
-                                    int ny, double* part) {
+                                    const float* __restrict__ rowsum, int nwin, const float* __restrict__ x, int ld,
+                                    int nx, int ny, double* part) {
     __shared__ double sh[RED_THREADS / 32];
     float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
     const int stride = gridDim.x * RED_THREADS;
@@ -108,8 +109,9 @@ __global__ void k_objective_partial(const float* __restrict__ wx, const float* _
     const int npx = nx * ny;
     for (int o = blockIdx.x * RED_THREADS + threadIdx.x; o < npx; o += stride) {
         const int i = o / nx, j = o - i * nx;
-        const float gx = j < nx - 1 ? x[o + 1] - x[o] : 0.f;
-        const float gy = i < ny - 1 ? x[o + nx] - x[o] : 0.f;
+        const float* xp = x + (size_t)i * ld + j;
+        const float gx = j < nx - 1 ? xp[1] - xp[0] : 0.f;
+        const float gy = i < ny - 1 ? xp[ld] - xp[0] : 0.f;
         neumaier_add(s1, c1, sqrtf(gx * gx + gy * gy));
     }
     const double d0 = block_sum((double)s0 + (double)c0, sh);
@@ -135,16 +137,17 @@ __global__ void k_sum_partials(const double* part, int nblocks, double* out2) {
 
 // ---- power iteration for ||K||, K = [W_L; grad] (scalar Chambolle-Pock steps)
 // y holds W^T W x on entry; adds grad^T grad x = -div(grad x).
-__global__ void k_ktk_grad(float* y, const float* __restrict__ x, int nx, int ny) {
+__global__ void k_ktk_grad(float* y, const float* __restrict__ x, int ld, int nx, int ny) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= ny || j >= nx) return;
     const size_t o = (size_t)i * nx + j;
+    const float* xp = x + (size_t)i * ld + j;
     // grad at (i,j) and at the left / upper neighbours
-    const float gx = j < nx - 1 ? x[o + 1] - x[o] : 0.f;
-    const float gy = i < ny - 1 ? x[o + nx] - x[o] : 0.f;
-    const float gxl = j > 0 ? x[o] - x[o - 1] : 0.f;
-    const float gyu = i > 0 ? x[o] - x[o - nx] : 0.f;
+    const float gx = j < nx - 1 ? xp[1] - xp[0] : 0.f;
+    const float gy = i < ny - 1 ? xp[ld] - xp[0] : 0.f;
+    const float gxl = j > 0 ? xp[0] - xp[-1] : 0.f;
+    const float gyu = i > 0 ? xp[0] - xp[-ld] : 0.f;
     float dv = 0.f;
     if (j < nx - 1) dv += gx;
     if (j > 0) dv -= gxl;
@@ -166,15 +169,16 @@ __global__ void k_sumsq_partial(const float* __restrict__ v, int n, double* part
 }
 
 // x = y / sqrt(n2[0]); xT = transpose (plain strided store: only used by the power iteration)
-__global__ void k_normalize(const float* __restrict__ y, float* x, float* xT, int nx, int ny, const double* n2) {
+__global__ void k_normalize(const float* __restrict__ y, float* x, int x_ld, float* xT, int xT_ld, int nx, int ny,
+                            const double* n2) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= ny || j >= nx) return;
     const size_t o = (size_t)i * nx + j;
     const double nrm = sqrt(n2[0]);
     const float v = nrm > 0.0 ? (float)(y[o] / nrm) : 0.f;
-    x[o] = v;
-    xT[(size_t)j * ny + i] = v;
+    x[(size_t)i * x_ld + j] = v;
+    xT[(size_t)j * xT_ld + i] = v;
 }
 
 // step = 0.99 / L with L = sqrt(||K^T K x||) = n2^(1/4); writes dst[0..n) and, if L_out, L
@@ -188,26 +192,26 @@ __global__ void k_fill_step(float* dst, size_t n, const double* n2, double* L_ou
 
 }  // namespace
 
-void launch_cp_dual_grad(const float* xbar, float* vx, float* vy, int nx, int ny, float sigma_v, float lambda,
-                         cudaStream_t st) {
+void launch_cp_dual_grad(const float* xbar, int xbar_ld, float* vx, float* vy, int nx, int ny, float sigma_v,
+                         float lambda, cudaStream_t st) {
     if (nx <= 0 || ny <= 0) return;
     dim3 block(32, 8), grid((nx + 31) / 32, (ny + 7) / 8);
     count_launches(1);
-    k_cp_dual_grad<<<grid, block, 0, st>>>(xbar, vx, vy, nx, ny, nullptr, sigma_v, lambda);
+    k_cp_dual_grad<<<grid, block, 0, st>>>(xbar, xbar_ld, vx, vy, nx, ny, nullptr, sigma_v, lambda);
 }
 
-void launch_cp_dual_grad_dev(const float* xbar, float* vx, float* vy, int nx, int ny, const float* sigma_dev,
-                             float lambda, cudaStream_t st) {
+void launch_cp_dual_grad_dev(const float* xbar, int xbar_ld, float* vx, float* vy, int nx, int ny,
+                             const float* sigma_dev, float lambda, cudaStream_t st) {
     if (nx <= 0 || ny <= 0) return;
     dim3 block(32, 8), grid((nx + 31) / 32, (ny + 7) / 8);
     count_launches(1);
-    k_cp_dual_grad<<<grid, block, 0, st>>>(xbar, vx, vy, nx, ny, sigma_dev, 0.f, lambda);
+    k_cp_dual_grad<<<grid, block, 0, st>>>(xbar, xbar_ld, vx, vy, nx, ny, sigma_dev, 0.f, lambda);
 }
 
-void launch_power_ktk_grad(float* y, const float* x, int nx, int ny, cudaStream_t st) {
+void launch_power_ktk_grad(float* y, const float* x, int x_ld, int nx, int ny, cudaStream_t st) {
     dim3 block(32, 8), grid((nx + 31) / 32, (ny + 7) / 8);
     count_launches(1);
-    k_ktk_grad<<<grid, block, 0, st>>>(y, x, nx, ny);
+    k_ktk_grad<<<grid, block, 0, st>>>(y, x, x_ld, nx, ny);
 }
 
 void launch_sumsq(const float* v, int n, double* scratch, int nscratch, double* out2, cudaStream_t st) {
@@ -218,10 +222,11 @@ void launch_sumsq(const float* v, int n, double* scratch, int nscratch, double* 
     k_sum_partials<<<1, 32, 0, st>>>(scratch, nblocks, out2);
 }
 
-void launch_normalize(const float* y, float* x, float* xT, int nx, int ny, const double* n2, cudaStream_t st) {
+void launch_normalize(const float* y, float* x, int x_ld, float* xT, int xT_ld, int nx, int ny, const double* n2,
+                      cudaStream_t st) {
     dim3 block(32, 8), grid((nx + 31) / 32, (ny + 7) / 8);
     count_launches(1);
-    k_normalize<<<grid, block, 0, st>>>(y, x, xT, nx, ny, n2);
+    k_normalize<<<grid, block, 0, st>>>(y, x, x_ld, xT, xT_ld, nx, ny, n2);
 }
 
 void launch_fill_step(float* dst, size_t n, const double* n2, double* L_out, cudaStream_t st) {
@@ -240,19 +245,19 @@ void launch_precond(float* rows, int nrows_total, float* cols, int nx, int ny, i
     }
 }
 
-void launch_crop(const float* x, float* out, int nx, int ny, double cxl, double cyl, double r, int crop,
+void launch_crop(const float* x, int x_ld, float* out, int nx, int ny, double cxl, double cyl, double r, int crop,
                  cudaStream_t st) {
     if (nx <= 0 || ny <= 0) return;
     dim3 block(32, 8), grid((nx + 31) / 32, (ny + 7) / 8);
     count_launches(1);
-    k_crop<<<grid, block, 0, st>>>(x, out, nx, ny, cxl, cyl, r, crop);
+    k_crop<<<grid, block, 0, st>>>(x, x_ld, out, nx, ny, cxl, cyl, r, crop);
 }
 
-void launch_objective(const float* wx, const float* pp, const float* rowsum, int nwin, const float* x, int nx,
-                      int ny, double* scratch, int nscratch, double* out2, cudaStream_t st) {
+void launch_objective(const float* wx, const float* pp, const float* rowsum, int nwin, const float* x, int x_ld,
+                      int nx, int ny, double* scratch, int nscratch, double* out2, cudaStream_t st) {
     const int nblocks = std::max(1, std::min(nscratch / 2, 152));
     count_launches(1);
-    k_objective_partial<<<nblocks, RED_THREADS, 0, st>>>(wx, pp, rowsum, nwin, x, nx, ny, scratch);
+    k_objective_partial<<<nblocks, RED_THREADS, 0, st>>>(wx, pp, rowsum, nwin, x, x_ld, nx, ny, scratch);
     count_launches(1);
     k_sum_partials<<<1, 32, 0, st>>>(scratch, nblocks, out2);
 }
