@@ -174,19 +174,45 @@ roi_status roi_recon_ramp_filter(roi_recon_t h, float* q);
 
 
 /* --------------------------------------------------------------------------
+ * Options and device-side status
+ * ------------------------------------------------------------------------ */
+
+typedef enum {
+    /* 1 (default): run each solve as one cooperative launch when the box's padded image
+     * fits in a block's shared memory (all iterations in one kernel, grid barriers
+     * between phases); 0: one launch per operator per iteration. */
+    ROI_OPT_SINGLE_LAUNCH = 0,
+    /* time limit of one grid-barrier wait in a single-launch solve, microseconds
+     * (default 1,000,000); a wait that runs out aborts the solve (see roi_recon_sync). */
+    ROI_OPT_WAIT_LIMIT_US = 1,
+    /* testing only: number of participants the grid barrier waits for beyond the blocks
+     * launched (default 0).  Any value > 0 makes every single-launch solve time out. */
+    ROI_OPT_TEST_ABSENT_BLOCKS = 2
+} roi_option;
+
+roi_status roi_recon_set_option(roi_recon_t h, roi_option opt, long long value);
+
+/* Wait for all work on the handle's stream, then report device-side failures: ROI_ETIMEOUT
+ * if a single-launch solve gave up at a grid barrier since the last report (its output is
+ * invalid; the context stays usable), ROI_ECUDA for a CUDA error.  solve_local calls this
+ * itself whenever it synchronizes (host output). */
+roi_status roi_recon_sync(roi_recon_t h);
+
+/* --------------------------------------------------------------------------
  * Measurement
  * ------------------------------------------------------------------------ */
 
 /* Kernel timing for profiling.  enable = 1 starts recording CUDA events around every
- * launch of the two projector kernels made by roi_recon_solve_local (and clears
- * earlier records); enable = 0 stops.  Recording adds host work per launch, so
+ * launch of the projector kernels and of the single-launch solver made by
+ * roi_recon_solve_local (and clears earlier records); enable = 0 stops.  Recording adds host work per launch, so
  * time whole steps with it off. */
 roi_status roi_recon_set_timing(roi_recon_t h, int enable);
 
 /* Launch count and summed device time (milliseconds, from the recorded events) of
  * kernel class `kernel` since timing was enabled: 0 = forward projector W_L
  * (ray-driven, fused dual/residual update), 1 = backprojector W_L^T (pixel gather,
- * fused primal update).  Synchronizes the handle's stream. */
+ * fused primal update), 2 = single-launch solve (all iterations of one solve).
+ * Synchronizes the handle's stream. */
 roi_status roi_recon_kernel_times(roi_recon_t h, int kernel, int* launches, double* total_ms);
 
 /* Number of CUDA kernels this library has launched in this process (all handles). */
@@ -208,9 +234,10 @@ unsigned long long roi_recon_launch_count(void);
  *            default stream) of the current device.
  *   err:     optional buffer of err_len bytes receiving a message on failure.
  * Scratch: a fixed 16 MiB device array inside the library holds the per-angle ray
- * table and two zero-padded copies of the box image (by rows and by columns).  Calls
- * needing more (64 bytes per angle plus 4 (2 box_w box_h + 4 box_w + 4 box_h) bytes,
- * each part rounded up to 256) fail with ROI_EINVAL and say so in err.
+ * table and two zero-padded copies of the box image (by rows and by columns, each row
+ * padded to its length + 4 rounded up to a multiple of 4 floats).  Calls needing more
+ * (about 80 bytes per angle plus 8 box_w box_h bytes for large boxes) fail with
+ * ROI_EINVAL and say so in err.
  * Every GPU that loads the library keeps this array until the process exits.  The
  * first call on a device looks up the array's device address (cudaGetSymbolAddress)
  * with that device current; make that first call before any stream capture.  All

@@ -27,12 +27,15 @@ __all__ = [
     "roi_recon_create", "roi_recon_destroy", "roi_recon_last_error", "roi_recon_set_sinogram",
     "roi_recon_fbp", "roi_recon_reproject_exterior", "roi_recon_solve_local", "roi_recon_plan",
     "roi_recon_forward_local", "roi_recon_back_local", "roi_recon_ramp_filter", "roi_recon_set_timing",
-    "roi_recon_kernel_times", "roi_recon_launch_count", "roi_recon_forward_local_noalloc", "RoiRecon", "plan",
+    "roi_recon_kernel_times", "roi_recon_launch_count", "roi_recon_forward_local_noalloc",
+    "roi_recon_set_option", "roi_recon_sync", "ROI_OPT_SINGLE_LAUNCH", "ROI_OPT_WAIT_LIMIT_US",
+    "ROI_OPT_TEST_ABSENT_BLOCKS", "RoiRecon", "plan",
 ]
 
 ROI_OK, ROI_EINVAL, ROI_ENOMEM, ROI_ESTATE, ROI_ECUDA, ROI_ETIMEOUT, ROI_EBUSY = range(7)
 ROI_F32, ROI_BF16, ROI_F16 = range(3)
 ROI_SIRT_NONNEG, ROI_TV_CP = range(2)
+ROI_OPT_SINGLE_LAUNCH, ROI_OPT_WAIT_LIMIT_US, ROI_OPT_TEST_ABSENT_BLOCKS = range(3)
 
 _STATUS = {0: "ROI_OK", 1: "ROI_EINVAL", 2: "ROI_ENOMEM", 3: "ROI_ESTATE", 4: "ROI_ECUDA",
            5: "ROI_ETIMEOUT", 6: "ROI_EBUSY"}
@@ -66,7 +69,7 @@ EXPORTS = [
     "roi_recon_fbp", "roi_recon_reproject_exterior", "roi_recon_solve_local", "roi_recon_plan",
     "roi_recon_forward_local", "roi_recon_back_local", "roi_recon_ramp_filter",
     "roi_recon_set_timing", "roi_recon_kernel_times", "roi_recon_launch_count",
-    "roi_recon_forward_local_noalloc",
+    "roi_recon_forward_local_noalloc", "roi_recon_set_option", "roi_recon_sync",
 ]
 
 _lib = None
@@ -117,6 +120,10 @@ def lib() -> ctypes.CDLL:
             L.roi_recon_forward_local_noalloc.argtypes = [ctypes.POINTER(Geometry), ctypes.POINTER(Region), _P, _P,
                                                           _P, ctypes.c_char_p, ctypes.c_int]
             L.roi_recon_forward_local_noalloc.restype = st
+            L.roi_recon_set_option.argtypes = [_H, ctypes.c_int, ctypes.c_longlong]
+            L.roi_recon_set_option.restype = st
+            L.roi_recon_sync.argtypes = [_H]
+            L.roi_recon_sync.restype = st
             _lib = L
     return _lib
 
@@ -193,6 +200,14 @@ def roi_recon_forward_local_noalloc(geom: Geometry, region: Region, x: int, y: i
     s = lib().roi_recon_forward_local_noalloc(ctypes.byref(geom), ctypes.byref(region), x, y, stream or None,
                                               buf, len(buf))
     return s, buf.value.decode()
+
+
+def roi_recon_set_option(h, opt: int, value: int) -> int:
+    return lib().roi_recon_set_option(h, int(opt), int(value))
+
+
+def roi_recon_sync(h) -> int:
+    return lib().roi_recon_sync(h)
 
 
 # ---- convenience layer -----------------------------------------------------------------
@@ -349,11 +364,18 @@ class RoiRecon:
                                          self._dev(x, (pl.box[3], pl.box[2]))))
         return x
 
+    def set_option(self, opt: int, value: int):
+        self._check(roi_recon_set_option(self.h, opt, value))
+
+    def sync(self):
+        """Wait for the handle's stream; raises RoiError(ROI_ETIMEOUT) if a device wait gave up."""
+        self._check(roi_recon_sync(self.h))
+
     def set_timing(self, enable: bool):
         self._check(roi_recon_set_timing(self.h, int(enable)))
 
     def kernel_times(self, kernel: int):
-        """(launches, total device ms) of kernel class 0 (forward) or 1 (back) while timing."""
+        """(launches, total device ms) of kernel class 0 (forward), 1 (back) or 2 (single-launch solve)."""
         s, n, ms = roi_recon_kernel_times(self.h, kernel)
         self._check(s)
         return n, ms

@@ -95,11 +95,19 @@ struct roi_recon {
     DevBuf part;             // angle-group partials of the gather
     double* red = nullptr;   // kRedScratch partials + 4 results
     int exterior_ready = 0;  // p' in `pp` matches the cached plan and FBP
-    // optional kernel timing: event pairs per kernel class (0 forward, 1 back)
+    // optional kernel timing: event pairs per kernel class (0 forward, 1 back, 2 single-launch solve)
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spans[2];
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spans[3];
+    // single-launch solver: barrier words, device error flag, options
+    unsigned* d_bar = nullptr;
+    int* d_err = nullptr;
+    int device = 0;
+    int opt_persistent = 1;
+    unsigned long long opt_wait_ns = 1000000000ull;
+    int opt_phantoms = 0;
+    size_t max_smem_optin = 0;
 };
 
 namespace {
@@ -323,6 +331,35 @@ roi_status run_exterior(roi_recon* h) {
 }
 
 // SIRT iterates x in the padded image xa (and its transpose xaT) that the forward reads.
+// Whether the single-launch solver can run this box; fills blocks.
+bool persist_ok(roi_recon* h, int* blocks) {
+    if (!h->opt_persistent) return false;
+    if (roi::persist_smem_bytes(h->na, h->box.w, h->box.h) > h->max_smem_optin) return false;
+    *blocks = roi::persist_max_blocks(h->na, h->box.w, h->box.h, h->device);
+    return *blocks > 0;
+}
+
+roi::PersistLaunch persist_base(roi_recon* h, int mode, int iters, int blocks) {
+    roi::PersistLaunch L{};
+    L.rec = h->rec_loc;
+    L.na = h->na;
+    L.stride = h->stride;
+    L.nx = h->box.w;
+    L.ny = h->box.h;
+    L.mode = mode;
+    L.iters = iters;
+    L.xa_base = h->xa.p;
+    L.xaT_base = h->xaT.p;
+    L.u = h->u.p;
+    L.pp = h->pp.p;
+    L.bar = h->d_bar;
+    L.err = h->d_err;
+    L.wait_ns = h->opt_wait_ns;
+    L.blocks = blocks;
+    L.phantoms = h->opt_phantoms;
+    return L;
+}
+
 roi_status solve_sirt(roi_recon* h, const roi_solve_params* prm) {
     const int nx = h->box.w, ny = h->box.h;
     const size_t nwin = (size_t)h->na * h->stride;
@@ -342,6 +379,21 @@ roi_status solve_sirt(roi_recon* h, const roi_solve_params* prm) {
     roi::FwdArgs fa = fwd_local(h, h->u.p);
     fa.pp = h->pp.p;
     fa.R = R;
+    int blocks = 0;
+    if (prm->iters > 0 && persist_ok(h, &blocks)) {
+        roi::PersistLaunch L = persist_base(h, 0, prm->iters, blocks);
+        L.R = R;
+        L.C = C;
+        L.step_scalar = alpha;
+        L.nonneg = 1;
+        cudaError_t e;
+        {
+            Span sp(h, 2);
+            e = roi::launch_persist(L, h->st);
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "single-launch SIRT solve");
+        return ROI_OK;
+    }
     roi::BackArgs ba = back_local(h, h->u.p, xa0(h), lda(h), xaT0(h), ldaT(h));
     ba.C = C;
     ba.step_scalar = alpha;
@@ -405,6 +457,26 @@ roi_status solve_cp(roi_recon* h, const roi_solve_params* prm, double* L_out) {
     roi::launch_fill(h->u.p, 0.f, nwin, h->st);
     roi_status s0 = clear_padded(h);
     if (s0 != ROI_OK) return s0;
+    const float lam = (float)prm->lambda;
+    int blocks = 0;
+    if (prm->iters > 0 && persist_ok(h, &blocks)) {
+        roi::PersistLaunch L = persist_base(h, 1, prm->iters, blocks);
+        L.R = h->sig.p;
+        L.C = h->tau.p;
+        L.x = h->xc.p;
+        L.vx = h->vx.p;
+        L.vy = h->vy.p;
+        L.sigma_v_dev = sigma_v_dev;
+        L.sigma_v = sigma_v;
+        L.lambda = lam;
+        cudaError_t e;
+        {
+            Span sp(h, 2);
+            e = roi::launch_persist(L, h->st);
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "single-launch Chambolle-Pock solve");
+        return ROI_OK;
+    }
     roi::FwdArgs fa = fwd_local(h, h->u.p);
     fa.pp = h->pp.p;
     fa.R = h->sig.p;
@@ -414,7 +486,6 @@ roi_status solve_cp(roi_recon* h, const roi_solve_params* prm, double* L_out) {
     ba.vy = h->vy.p;
     ba.xbar = xa0(h);
     ba.xbar_ld = lda(h);
-    const float lam = (float)prm->lambda;
     for (int it = 0; it < prm->iters; ++it) {
         {
             Span sp(h, 0);
@@ -466,6 +537,15 @@ roi_status roi_recon_create(const roi_geometry* geom, void* cuda_stream, roi_rec
     if (e == cudaSuccess) e = dev_alloc(&h->rec_loc, (size_t)h->na);
     if (e == cudaSuccess) e = dev_alloc(&h->rec_ext, (size_t)h->na);
     if (e == cudaSuccess) e = dev_alloc(&h->red, (size_t)kRedScratch + 4);
+    if (e == cudaSuccess) e = dev_alloc(&h->d_bar, 2);
+    if (e == cudaSuccess) e = dev_alloc(&h->d_err, 1);
+    if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) {
+        int v = 0;
+        e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+        h->max_smem_optin = (size_t)v;
+    }
     if (e == cudaSuccess) {
         // Ram-Lak odd taps h_m = -1/(pi m)^2, m = 2t + 1, scaled by pi / N_theta (Eq. fbp)
         std::vector<float> ho((size_t)h->nd / 2 + 1);
@@ -501,6 +581,8 @@ void roi_recon_destroy(roi_recon_t h) {
     for (AngleRec* b : {h->rec_fbp, h->rec_loc, h->rec_ext})
         if (b) cudaFree(b);
     if (h->red) cudaFree(h->red);
+    if (h->d_bar) cudaFree(h->d_bar);
+    if (h->d_err) cudaFree(h->d_err);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     for (DevBuf* b : {&h->pp, &h->u, &h->sig, &h->wtmp, &h->wrow, &h->xc, &h->vx, &h->vy, &h->tau, &h->itmp, &h->xa,
                       &h->xaT})
@@ -693,7 +775,8 @@ roi_status roi_recon_solve_local(roi_recon_t h, const roi_region* region, const 
     }
     if (!out_on_device) {
         CU(h, cudaMemcpyAsync(out, h->itmp.p, sizeof(float) * nimg, cudaMemcpyDeviceToHost, h->st));
-        CU(h, cudaStreamSynchronize(h->st));
+        s = roi_recon_sync(h);
+        if (s != ROI_OK) return s;
     }
     if (info) {
         fill_info(h, info);
@@ -709,14 +792,45 @@ roi_status roi_recon_set_timing(roi_recon_t h, int enable) {
     h->err.clear();
     CU(h, cudaStreamSynchronize(h->st));
     h->timing = enable != 0;
-    h->spans[0].clear();
-    h->spans[1].clear();
+    for (auto& s : h->spans) s.clear();
     h->ev_used = 0;
     return ROI_OK;
 }
 
+roi_status roi_recon_set_option(roi_recon_t h, roi_option opt, long long value) {
+    if (!h) return ROI_EINVAL;
+    h->err.clear();
+    switch (opt) {
+        case ROI_OPT_SINGLE_LAUNCH:
+            h->opt_persistent = value != 0;
+            return ROI_OK;
+        case ROI_OPT_WAIT_LIMIT_US:
+            if (value < 1 || value > 600000000LL) return fail(h, ROI_EINVAL, "set_option: wait limit out of range");
+            h->opt_wait_ns = (unsigned long long)value * 1000ull;
+            return ROI_OK;
+        case ROI_OPT_TEST_ABSENT_BLOCKS:
+            if (value < 0 || value > 1024) return fail(h, ROI_EINVAL, "set_option: absent blocks out of range");
+            h->opt_phantoms = (int)value;
+            return ROI_OK;
+    }
+    return fail(h, ROI_EINVAL, "set_option: unknown option %d", (int)opt);
+}
+
+roi_status roi_recon_sync(roi_recon_t h) {
+    if (!h) return ROI_EINVAL;
+    h->err.clear();
+    CU(h, cudaStreamSynchronize(h->st));
+    int flag = 0;
+    CU(h, cudaMemcpy(&flag, h->d_err, sizeof flag, cudaMemcpyDeviceToHost));
+    if (flag) {
+        CU(h, cudaMemset(h->d_err, 0, sizeof(int)));
+        return fail(h, ROI_ETIMEOUT, "a device-side wait of a single-launch solve gave up; its result is invalid");
+    }
+    return ROI_OK;
+}
+
 roi_status roi_recon_kernel_times(roi_recon_t h, int kernel, int* launches, double* total_ms) {
-    if (!h || kernel < 0 || kernel > 1 || !launches || !total_ms) return ROI_EINVAL;
+    if (!h || kernel < 0 || kernel > 2 || !launches || !total_ms) return ROI_EINVAL;
     h->err.clear();
     CU(h, cudaStreamSynchronize(h->st));
     double ms = 0.0;

@@ -129,10 +129,11 @@ enum FwdMode { FWD_PLAIN = 0, FWD_EXTERIOR = 1, FWD_SIRT = 2, FWD_CP = 3 };
 enum BackMode { BACK_PLAIN = 0, BACK_SIRT = 1, BACK_CP = 2 };
 
 // Images read by the forward projector are "padded": element (0, 0) sits at `img`,
-// rows have stride `img_ld` >= extent + 4, and the two columns on either side of each
-// row (indices -2, -1, extent, extent + 1) hold zeros.
+// rows have stride `img_ld` = extent + 4 rounded up to a multiple of 4 (16-byte rows,
+// so whole images can be staged with 16-byte copies), and the columns left and right
+// of each row (indices -2, -1 and extent .. ld - 3) hold zeros.
 constexpr int kPad = 2;
-inline int padded_ld(int extent) { return extent + 2 * kPad; }
+inline int padded_ld(int extent) { return (extent + 2 * kPad + 3) / 4 * 4; }
 
 struct FwdArgs {
     const AngleRec* rec;   // [na]
@@ -210,5 +211,36 @@ void launch_crop(const float* x, int x_ld, float* out, int nx, int ny, double cx
 // objective terms: part[0] = sum over rows with rowsum > 1e-6 of (wx - pp)^2, part[1] = sum |grad x|
 void launch_objective(const float* wx, const float* pp, const float* rowsum, int nwin, const float* x, int x_ld,
                       int nx, int ny, double* scratch, int nscratch, double* out2, cudaStream_t st);
+
+// ---- single-launch (cooperative) solver for boxes whose padded image fits in shared memory
+struct PersistLaunch {
+    const AngleRec* rec;
+    int na, stride, nx, ny;
+    int mode;                 // 0 SIRT (nonneg, x in xa), 1 CP (x in x, xbar in xa)
+    int iters;
+    float* xa_base;           // padded row image buffer (row 0, column -2)
+    float* xaT_base;          // padded column image buffer
+    float* u;
+    const float* pp;
+    const float* R;
+    float sig_scalar;
+    float* x;
+    float* vx;
+    float* vy;
+    const float* C;
+    float step_scalar;
+    const float* sigma_v_dev;
+    float sigma_v;
+    float lambda;
+    int nonneg;
+    unsigned* bar;            // 2 unsigned, zeroed by the launcher
+    int* err;                 // set to 1 when a barrier wait gives up
+    unsigned long long wait_ns;
+    int blocks;               // <= persist_max_blocks
+    int phantoms;             // extra barrier participants that never arrive (testing only)
+};
+size_t persist_smem_bytes(int na, int nx, int ny);
+int persist_max_blocks(int na, int nx, int ny, int device);
+cudaError_t launch_persist(const PersistLaunch& L, cudaStream_t st);
 
 }  // namespace roi

@@ -186,12 +186,17 @@ def _oracle_pipeline(w, p, region, reg, iters, lam=0.0, weighting=0, precond=1):
                               weighting=weighting, precond=precond)
 
 
+PATHS = [1, 0]  # ROI_OPT_SINGLE_LAUNCH: one cooperative launch per solve, or one launch per operator
+
+
+@pytest.mark.parametrize("single", PATHS)
 @pytest.mark.parametrize("centred", [True, False])
-def test_sirt_pipeline_128(centred):
+def test_sirt_pipeline_128(centred, single):
     """The whole 128 x 128 workload: Ram-Lak FBP, exterior subtraction, 200 nonneg SIRT."""
     w, p = _workload_data("roi_sirt_128")
     region = WL.region(w, seed=0, centred=centred)
     rr = R.RoiRecon(*w.geometry())
+    rr.set_option(R.ROI_OPT_SINGLE_LAUNCH, single)
     rr.set_sinogram(torch.from_numpy(p).cuda())
     rr.fbp()
     out, info = rr.solve_local(region, R.ROI_SIRT_NONNEG, iters=w.iters)
@@ -202,10 +207,12 @@ def test_sirt_pipeline_128(centred):
     assert rel_l2(got, x) <= SOLVE_TOL
 
 
-def test_sirt_weighted_pipeline_128():
+@pytest.mark.parametrize("single", PATHS)
+def test_sirt_weighted_pipeline_128(single):
     w, p = _workload_data("roi_sirt_128", seed=1)
     region = WL.region(w, seed=1)
     rr = R.RoiRecon(*w.geometry())
+    rr.set_option(R.ROI_OPT_SINGLE_LAUNCH, single)
     rr.set_sinogram(torch.from_numpy(p).cuda())
     rr.fbp()
     out, _ = rr.solve_local(region, R.ROI_SIRT_NONNEG, iters=50, weighting=1)
@@ -213,11 +220,13 @@ def test_sirt_weighted_pipeline_128():
     assert rel_l2(out.cpu().numpy(), x) <= SOLVE_TOL
 
 
+@pytest.mark.parametrize("single", PATHS)
 @pytest.mark.parametrize("lam", [0.0, 0.01, 0.5])
-def test_cp_tv_pipeline_128(lam):
+def test_cp_tv_pipeline_128(lam, single):
     w, p = _workload_data("roi_sirt_128", seed=2)
     region = WL.region(w, seed=2)
     rr = R.RoiRecon(*w.geometry())
+    rr.set_option(R.ROI_OPT_SINGLE_LAUNCH, single)
     rr.set_sinogram(torch.from_numpy(p).cuda())
     rr.fbp()
     out, info = rr.solve_local(region, R.ROI_TV_CP, iters=150, lam=lam, eval_objective=1)
@@ -227,11 +236,13 @@ def test_cp_tv_pipeline_128(lam):
     assert abs(info.objective - fo) <= 1e-4 * abs(fo)
 
 
-def test_cp_tv_scalar_steps_128():
+@pytest.mark.parametrize("single", PATHS)
+def test_cp_tv_scalar_steps_128(single):
     """precond = 0: steps 0.99/||K|| from 100 power iterations on the device."""
     w, p = _workload_data("roi_sirt_128", seed=3)
     region = WL.region(w, seed=3)
     rr = R.RoiRecon(*w.geometry())
+    rr.set_option(R.ROI_OPT_SINGLE_LAUNCH, single)
     rr.set_sinogram(torch.from_numpy(p).cuda())
     rr.fbp()
     out, info = rr.solve_local(region, R.ROI_TV_CP, iters=100, lam=0.05, precond=0)
@@ -330,12 +341,14 @@ def test_fbp_full_size_1024(big):
     assert rel_l2(out.cpu().numpy(), xf) <= OP_TOL
 
 
-def test_cp_tv_full_size_1024(big):
+@pytest.mark.parametrize("single", PATHS)
+def test_cp_tv_full_size_1024(big, single):
     """The 1024 x 1024 workload as the benchmark runs it: FBP, exterior subtraction and
     500 preconditioned Chambolle-Pock iterations on the 192 x 192 box, all outputs compared."""
     w, p, g, xf = big
     region = WL.region(w, seed=0)
     rr = R.RoiRecon(*w.geometry())
+    rr.set_option(R.ROI_OPT_SINGLE_LAUNCH, single)
     rr.set_sinogram(torch.from_numpy(p).cuda())
     rr.fbp()
     pl = rr.plan(region)
@@ -348,3 +361,23 @@ def test_cp_tv_full_size_1024(big):
     assert rel_l2(out.cpu().numpy(), x) <= SOLVE_TOL
     fo = oracle.objective(g, pl.box, pp, x, w.lam)
     assert abs(info.objective - fo) <= 1e-4 * abs(fo)
+
+
+@pytest.mark.parametrize("reg,N,na,nd,region", [
+    (R.ROI_TV_CP, 256, 200, 256, (128.0, 100.0, 50.0, 20.0)),     # 140 x 140 box, ragged tiles
+    (R.ROI_SIRT_NONNEG, 96, 37, 150, (10.0, 50.0, 12.0, 4.0)),    # clipped box, odd angle count
+    (R.ROI_TV_CP, 192, 90, 200, (96.0, 96.0, 60.0, 30.0)),        # 180 x 180 box
+])
+def test_single_launch_matches_multi_launch(reg, N, na, nd, region):
+    """The cooperative single-launch solver and the per-operator launches agree to rounding."""
+    p = np.random.default_rng(9).random((na, nd)).astype(np.float32) * 50
+    outs = []
+    for single in (1, 0):
+        rr = R.RoiRecon(N, na, nd)
+        rr.set_option(R.ROI_OPT_SINGLE_LAUNCH, single)
+        rr.set_sinogram(torch.from_numpy(p).cuda())
+        rr.fbp()
+        out, _ = rr.solve_local(region, reg, iters=60, lam=0.02)
+        rr.sync()
+        outs.append(out.cpu().numpy())
+    assert rel_l2(outs[0], outs[1]) <= 1e-5
