@@ -15,7 +15,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/roi_recon.h"
+#include "roi_recon.h"
 #include "roi_internal.h"
 
 using roi::AngleRec;
@@ -334,8 +334,7 @@ roi_status run_exterior(roi_recon* h) {
 // Whether the single-launch solver can run this box; fills blocks.
 bool persist_ok(roi_recon* h, int* blocks) {
     if (!h->opt_persistent) return false;
-    if (roi::persist_smem_bytes(h->na, h->box.w, h->box.h) > h->max_smem_optin) return false;
-    *blocks = roi::persist_max_blocks(h->na, h->box.w, h->box.h, h->device);
+    *blocks = roi::persist_max_blocks(h->na, h->box.w, h->box.h, h->stride, h->device);
     return *blocks > 0;
 }
 

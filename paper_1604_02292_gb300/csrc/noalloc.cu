@@ -28,7 +28,7 @@
 #include <cstdio>
 #include <mutex>
 
-#include "../../include/roi_recon.h"
+#include "roi_recon.h"
 #include "roi_internal.h"
 
 namespace {

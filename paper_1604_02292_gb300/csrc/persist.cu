@@ -6,10 +6,11 @@
 // Chambolle-Pock; the operators W_L, W_L^T of Sec. 2.1):
 //   phase A  every block stages the whole padded image it projects (x for SIRT, xbar
 //            for CP; rows or columns by the branch of its angles) into shared memory
-//            and runs the ray-driven forward W_L on its share of (angle, 32-ray) units,
-//            fusing  r = p' - W_L x  (SIRT)  or  u <- (u + sigma (W_L xbar - p'))/(1 + sigma/2)
-//            and, for CP, the gradient dual  v <- proj_lambda(v + sigma_v grad xbar)
-//            on its share of pixels;
+//            with one TMA bulk copy and runs the ray-driven forward W_L on its share of
+//            (angle, 32-ray) units, fusing  r = p' - W_L x  (SIRT)  or
+//            u <- (u + sigma (W_L xbar - p'))/(1 + sigma/2)  (CP); for CP it also
+//            updates the gradient dual  v <- proj_lambda(v + sigma_v grad xbar)  on its
+//            share of pixels while the copy is in flight;
 //   barrier
 //   phase B  every block takes 16 x 16 pixel tiles, stages the window bins the tile's
 //            pixels reach for all angles, gathers W_L^T of r (or u) over all angles and
@@ -17,15 +18,22 @@
 //            x+ = x - tau (W_L^T u - div v), xbar = 2 x+ - x  (CP),
 //            writing the padded row and column copies the next phase A stages;
 //   barrier.
-// The arithmetic, the summation structure and the work split per ray / pixel are the
-// ones of the multi-kernel path (project.cu), so both paths agree to rounding.
 //
-// The grid barrier spins on a generation counter with a time limit (one second by
+// Inner loops run in fixed point, so they need no float-to-integer conversion (a
+// quarter-rate instruction on this GPU): along a ray the interpolation coordinate is
+// a Q.22 integer re-anchored from float-float every 16 samples and stepped by
+// round(slope 2^22); across a gather tile row the window coordinate is a Q.24 integer
+// stepped by round(cos 2^24).  The interpolation fraction is rebuilt from the low bits
+// as a float in [1, 2) minus one.  Position errors stay below 2e-6 pixel.
+//
+// The grid barrier polls a monotonic arrival counter with a time limit (one second by
 // default, wall clock from %globaltimer): a block that waits longer sets the error flag
-// and every block leaves at its next barrier; the host reports ROI_ETIMEOUT.  Blocks are co-resident by construction
-// (cooperative launch of at most one block per SM).  Data written by other blocks in
-// the previous phase are read with ld.global.cg (L2), never through L1.
+// and every block leaves at its next barrier; the host reports ROI_ETIMEOUT.  The TMA
+// wait has the same limit.  Blocks are co-resident by construction (cooperative launch
+// of at most one block per SM).  Data written by other blocks in the previous phase are
+// read with ld.global.cg (L2) or by TMA, never through L1.
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 #include <algorithm>
 
@@ -39,11 +47,15 @@ constexpr int PT = 1024;                 // threads per block
 constexpr int NWARP = PT / 32;
 constexpr int RAYS = 32;                 // rays per unit (one warp-wide ray group)
 constexpr int FSEG = 4;                  // segments per ray in phase A
-constexpr int UNITS_PER_PASS = NWARP / FSEG;
-constexpr int SEGA = 16;                 // samples per float-float anchor
+constexpr int CHUNK_UNITS = 16;          // phase A units whose partials are held at once
+constexpr int SEGA = 24;                 // samples per float-float anchor
+constexpr int MAXUNITS = 512;            // phase A units per block (checked by the host)
+constexpr int MAXPRE = 2;                // phase B tiles per block with precomputed constants
 constexpr int BT = 16;                   // phase B tile side
 constexpr int BPIX = BT * BT;
-constexpr int QUART = PT / BPIX;         // angle groups per pixel in phase B
+constexpr int RUN = 8;                   // pixels per gather thread (along a tile row)
+constexpr int RUNS = BPIX / RUN;         // 32 runs per tile
+constexpr int BGROUPS = PT / RUNS;       // 32 angle groups
 // tile pixels lie within 7.5 (|c| + |s|) <= 10.61 of the tile centre in window
 // coordinates and the hat reaches one bin further: with kbase = floor(kappa_c) - 12
 // every staged index touched is in [1, 24] < BSB
@@ -56,7 +68,7 @@ struct PArgs {
     int mode;               // 0 SIRT, 1 CP
     int iters;
     // padded images read by phase A: row layout [ny][lda], column layout [nx][ldaT];
-    // *_base is the start of the buffer (row 0, column -2), *0 element (0, 0)
+    // *_base is the start of the buffer (row 0, column -2)
     float* xa_base;
     float* xaT_base;
     int lda, ldaT;
@@ -76,14 +88,21 @@ struct PArgs {
     float lambda;
     int nonneg;
     // grid barrier
-    unsigned* bar;          // [0] arrivals, [1] generation
-    unsigned expect;        // participants: gridDim.x (+ phantoms when testing the time limit)
+    unsigned* bar;          // [0] arrivals (monotonic within a launch)
+    unsigned expect;        // participants: gridDim.x (+ absent ones when testing the time limit)
     int* err;
-    unsigned long long wait_ns;  // time limit of one barrier wait
+    unsigned long long wait_ns;  // time limit of one wait
     // phase A partition
     int nchunk;             // 32-ray chunks per angle
     int units;              // na * nchunk
-    int img_floats;         // floats of the larger padded image (smem region size)
+    int region_floats;      // floats of the shared region (image / phase B staging)
+    int pre_tiles;          // phase B tiles per block whose constants are precomputed (0: none)
+};
+
+struct PhaseBConst {
+    int base;   // Q.24 window coordinate of tile pixel (0, 0), relative to kb
+    int c, s;   // Q.24 steps per column / per row
+    float iw;   // 1 / w
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -92,33 +111,82 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Generation-counting grid barrier with a time limit.  Returns 0 (in every thread of
-// the block) when this or another block gave up; the caller then returns.
-__device__ __forceinline__ int grid_sync(const PArgs& A, int* s_flag) {
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// One thread: arm the barrier for `bytes` and start the bulk copy global -> shared.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile("fence.proxy.async;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits (bounded) for the bulk copy of phase `parity`.  On time-out sets the error flag,
+// waits once more (bounded) so no copy is left writing into shared memory, returns false.
+__device__ __forceinline__ bool mbar_wait(const PArgs& A, uint64_t* bar, unsigned parity) {
+    const unsigned long long t0 = global_ns();
+    while (!mbar_test(bar, parity)) {
+        if (global_ns() - t0 > A.wait_ns) {
+            atomicExch(A.err, 1);
+            const unsigned long long t1 = global_ns();
+            while (!mbar_test(bar, parity) && global_ns() - t1 < A.wait_ns) {
+            }
+            return false;
+        }
+    }
+    return true;
+}
+
+// Grid barrier on a monotonic arrival counter: barrier number n (1, 2, ...) is passed
+// when the counter reaches n * expect.  Thread 0 of each block releases the block's
+// writes, adds one, and polls the counter with acquire loads; every 256 polls it checks
+// the time limit and the error flag.  Returns 0 (in every thread of the block) when
+// this or another block gave up; the caller then returns.
+__device__ __forceinline__ int grid_sync(const PArgs& A, int* s_flag, unsigned& nbar) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        volatile unsigned* gen = A.bar + 1;
-        const unsigned g = *gen;
+        ++nbar;
+        const unsigned target = nbar * A.expect;
         __threadfence();
-        const unsigned arrived = atomicAdd(A.bar, 1u);
-        if (arrived == A.expect - 1) {
-            A.bar[0] = 0u;
-            __threadfence();
-            atomicAdd(A.bar + 1, 1u);
-        } else {
-            const unsigned long long t0 = global_ns();
-            while (*gen == g) {
-                if (*(volatile int*)A.err) {
-                    ok = 0;
-                    break;
-                }
-                if (global_ns() - t0 > A.wait_ns) {
+        atomicAdd(A.bar, 1u);
+        unsigned long long t0 = 0;
+        for (unsigned polls = 1;; ++polls) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(A.bar) : "memory");
+            if ((int)(v - target) >= 0) break;
+            if ((polls & 255u) == 0) {
+                const unsigned long long now = global_ns();
+                if (t0 == 0) {
+                    t0 = now;
+                } else if (now - t0 > A.wait_ns) {
                     atomicExch(A.err, 1);
                     ok = 0;
                     break;
                 }
-                __nanosleep(100);
+                if (*(volatile int*)A.err) {
+                    ok = 0;
+                    break;
+                }
             }
         }
         __threadfence();
@@ -128,14 +196,26 @@ __device__ __forceinline__ int grid_sync(const PArgs& A, int* s_flag) {
     return *s_flag;
 }
 
-__device__ __forceinline__ void stage_image(float* dst, const float* src, int nfloats) {
-    const float4* s4 = reinterpret_cast<const float4*>(src);
-    float4* d4 = reinterpret_cast<float4*>(dst);
-    for (int i = threadIdx.x; i < nfloats / 4; i += PT) d4[i] = __ldcg(s4 + i);
+// Float-float coordinate v in [-2^8, 2^8) to Q.F fixed point.
+template <int F>
+__device__ __forceinline__ int to_fixed(ff v) {
+    const float n = floorf(v.hi);
+    const float fr = (v.hi - n) + v.lo;
+    return ((int)n << F) + __float2int_rn(fr * (float)(1 << F));
 }
 
-// One (unit, segment) of phase A: partial Joseph sum of ray k of angle a over the
-// samples of segment `seg`, image in shared memory (element (0,0) at img, stride ld).
+// Fraction bits of a Q.F number as a float in [0, 1).
+template <int F>
+__device__ __forceinline__ float frac_of(int q) {
+    const unsigned m = (F >= 23) ? (((unsigned)q >> (F - 23)) & 0x7FFFFFu) : (((unsigned)q << (23 - F)) & 0x7FFFFFu);
+    return __uint_as_float(0x3F800000u | m) - 1.0f;
+}
+
+// Partial Joseph sum of ray k of angle r over the samples of segment `seg`, image in
+// shared memory (element (0,0) at img, row stride ld).  Samples whose exact minor
+// coordinate q lies in [-1.5, Mm + 0.5] are visited (range in float, error ~1e-4 <<
+// 0.5), so the taps stay in [-2, Mm + 1], inside the padded row; samples outside the
+// range have both taps outside [0, Mm) and contribute 0.
 __device__ __forceinline__ ff ray_segment(const AngleRec& r, int k, int seg, int seg_len, int M, int Mm,
                                           const float* img, int ld) {
     float sum = 0.f, cmp = 0.f;
@@ -154,21 +234,16 @@ __device__ __forceinline__ ff ray_segment(const AngleRec& r, int k, int seg, int
     const int s0 = seg * seg_len;
     mlo = max(mlo, s0);
     mhi = min(mhi, min(s0 + seg_len, M));
-    const float slope = r.slope.hi;
+    const int step = r.slope_q22;
     for (int m0 = mlo; m0 < mhi; m0 += SEGA) {
-        const ff bd = ff_add(Ak, ff_mul_f((float)m0 + 0.5f * (SEGA - 1) - halfM, r.slope));
-        const float bfl = floorf(bd.hi);
-        const int bi = (int)bfl;
-        const float bf = (bd.hi - bfl) + bd.lo;
+        int q = to_fixed<22>(ff_add(Ak, ff_mul_f((float)m0 - halfM, r.slope)));  // sample m0
         const int mend = min(m0 + SEGA, mhi);
         float acc = 0.f;
-        const float* rp = img + m0 * ld + bi;
+        const float* rp = img + m0 * ld;
 #pragma unroll 4
-        for (int m = m0; m < mend; ++m, rp += ld) {
-            const float q = fmaf((float)(m - m0) - 0.5f * (SEGA - 1), slope, bf);
-            const float fl = floorf(q);
-            const int j = (int)fl;
-            const float f = q - fl;
+        for (int m = m0; m < mend; ++m, rp += ld, q += step) {
+            const int j = q >> 22;
+            const float f = frac_of<22>(q);
             const float v0 = rp[j], v1 = rp[j + 1];
             acc += fmaf(f, v1 - v0, v0);
         }
@@ -177,31 +252,114 @@ __device__ __forceinline__ ff ray_segment(const AngleRec& r, int k, int seg, int
     return two_sum(sum, cmp);
 }
 
+// Phase B constants of tile t for angle a: kappa at the tile centre (xi_t c + eta_t s -
+// phi) in float-float, kbase = floor - BKOFF, and the Q.24 coordinate of tile pixel (0, 0)
+// (centre - 7.5 c + 7.5 s) relative to kbase.
+__device__ __forceinline__ void tile_consts(const PArgs& A, int t, int tiles_x, int a, PhaseBConst* bcp, int* kbp,
+                                            int* wdp) {
+    const int tile_x0 = (t % tiles_x) * BT, tile_y0 = (t / tiles_x) * BT;
+    const float xi_t = (float)tile_x0 + 0.5f * (BT - 1) - 0.5f * (float)(A.nx - 1);
+    const float eta_t = 0.5f * (float)(A.ny - 1) - ((float)tile_y0 + 0.5f * (BT - 1));
+    const AngleRec& r = A.rec[a];
+    ff kt = ff_add(ff_mul_f(xi_t, r.c), ff_mul_f(eta_t, r.s));
+    kt = ff_add(kt, ff{-r.phi.hi, -r.phi.lo});
+    const int kbase = (int)floorf(kt.hi) - BKOFF;
+    kt = ff_add(kt, ff{-(float)kbase, 0.f});
+    kt = ff_add(kt, ff_mul_f(-0.5f * (BT - 1), r.c));
+    kt = ff_add(kt, ff_mul_f(0.5f * (BT - 1), r.s));
+    PhaseBConst q;
+    q.base = to_fixed<24>(kt);
+    q.c = r.c_q24;
+    q.s = r.s_q24;
+    q.iw = r.inv_w;
+    *bcp = q;
+    *kbp = kbase;
+    *wdp = r.width;
+}
+
 __global__ void __launch_bounds__(PT, 1) k_persist(PArgs A) {
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
-    float* img = smem;                                        // phase A image / phase B staging
-    float* red_s = smem + A.img_floats;                       // [NWARP][32]
-    float* red_c = red_s + NWARP * 32;                        // [NWARP][32]
+    float* img = smem;                              // phase A image
+    float* red_s = smem + A.region_floats;          // [CHUNK_UNITS][FSEG][32] phase A partials
+    float* red_c = red_s + CHUNK_UNITS * FSEG * 32;
+    PhaseBConst* pbc = reinterpret_cast<PhaseBConst*>(red_c + CHUNK_UNITS * FSEG * 32);  // [pre_tiles][na]
+    int* pkb = reinterpret_cast<int*>(pbc + A.pre_tiles * A.na);
+    int* pwd = pkb + A.pre_tiles * A.na;
     __shared__ int s_flag;
+    __shared__ int s_nunits, s_row, s_next;
+    __shared__ int s_units[MAXUNITS];               // this block's phase A units (angle * nchunk + chunk)
+    __shared__ __align__(8) uint64_t s_mbar;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int G = gridDim.x, b = blockIdx.x;
     const int nx = A.nx, ny = A.ny;
-    const int u0 = (int)((long long)A.units * b / G), u1 = (int)((long long)A.units * (b + 1) / G);
     const int npix = nx * ny;
     const int p0 = (int)((long long)npix * b / G), p1 = (int)((long long)npix * (b + 1) / G);
     const int tiles_x = (nx + BT - 1) / BT, tiles = tiles_x * ((ny + BT - 1) / BT);
     const int t0 = (int)((long long)tiles * b / G), t1 = (int)((long long)tiles * (b + 1) / G);
     float* xa = A.xa_base + kPad;
     float* xaT = A.xaT_base + kPad;
-    // phase B shared layout: stage[na][BSB] | cst[na] float4 | kb[na] int
+    // phase B shared layout: stage[na][BSB] | consts[na] | kb[na] | width[na] | part[BGROUPS][BPIX]
     float* stage = smem;
-    float4* cst = reinterpret_cast<float4*>(smem + ((A.na * BSB + 3) & ~3));
-    int* kb = reinterpret_cast<int*>(cst + A.na);
+    PhaseBConst* bc = reinterpret_cast<PhaseBConst*>(smem + ((A.na * BSB + 3) & ~3));
+    int* kb = reinterpret_cast<int*>(bc + A.na);
+    int* wdt = kb + A.na;
+    float* bpart = reinterpret_cast<float*>(wdt + A.na);
+
+    // prologue 1: phase A work.  The blocks are split between the two branches in
+    // proportion to their units; within a branch, units are dealt round-robin, so each
+    // block stages one orientation and gets a mix of ray lengths.
+    int* rank_angle = reinterpret_cast<int*>(smem);  // scratch in the (not yet used) region
+    if (tid == 0) {
+        int nrow = 0, ncol = 0;
+        for (int a = 0; a < A.na; ++a) (A.rec[a].row ? nrow : ncol)++;
+        const long ur = (long)nrow * A.nchunk, uc = (long)ncol * A.nchunk;
+        int gr = (int)((ur * G + (ur + uc) / 2) / max(ur + uc, 1L));
+        if (ur > 0 && gr < 1) gr = 1;
+        if (uc > 0 && gr > G - 1) gr = G - 1;
+        if (uc == 0) gr = G;
+        if (ur == 0) gr = 0;
+        const int mine = b < gr;  // 1: this block takes row-branch units
+        const int gsize = mine ? gr : G - gr, bi = mine ? b : b - gr;
+        int nb = 0;
+        for (int a = 0; a < A.na; ++a)
+            if (A.rec[a].row == mine) rank_angle[nb++] = a;
+        int nu = 0;
+        if (gsize > 0)
+            for (long j = bi; j < (long)nb * A.nchunk; j += gsize) {
+                if (nu == MAXUNITS) {  // the host sizes MAXUNITS; never silently drop work
+                    atomicExch(A.err, 1);
+                    break;
+                }
+                s_units[nu++] = rank_angle[j / A.nchunk] * A.nchunk + (int)(j % A.nchunk);
+            }
+        s_nunits = nu;
+        s_row = mine;
+        mbar_init(&s_mbar, 1);
+    }
+    __syncthreads();
+    const int nunits = s_nunits, my_row = s_row;
+    // prologue 2: phase B constants of this block's tiles (they do not change)
+    const bool pre = A.pre_tiles > 0 && (t1 - t0) <= A.pre_tiles;
+    if (pre) {
+        for (int e = tid; e < (t1 - t0) * A.na; e += PT) {
+            const int tt = e / A.na, a = e - tt * A.na;
+            tile_consts(A, t0 + tt, tiles_x, a, pbc + e, pkb + e, pwd + e);
+        }
+    }
+    __syncthreads();
+    unsigned parity = 0;
+    unsigned nbar = 0;
 
     for (int it = 0; it < A.iters; ++it) {
         // ------------------------------------------------------------ phase A
-        if (A.mode == 1) {  // gradient dual on this block's pixels (reads xbar^k)
+        if (nunits > 0 && tid == 0) {
+            if (my_row)
+                bulk_load(img, A.xa_base, sizeof(float) * ny * A.lda, &s_mbar);
+            else
+                bulk_load(img, A.xaT_base, sizeof(float) * nx * A.ldaT, &s_mbar);
+        }
+        if (A.mode == 1) {  // gradient dual on this block's pixels (reads xbar^k), overlaps the copy
             const float sv = A.sigma_v_dev ? __ldg(A.sigma_v_dev) : A.sigma_v;
             for (int p = p0 + tid; p < p1; p += PT) {
                 const int i = p / nx, j = p - i * nx;
@@ -217,49 +375,44 @@ __global__ void __launch_bounds__(PT, 1) k_persist(PArgs A) {
                 A.vy[p] = ay * sc;
             }
         }
-        int staged_row = -1;  // orientation in shared memory
-        for (int ub = u0; ub < u1;) {
-            // a pass takes up to UNITS_PER_PASS units sharing one branch (orientation)
-            const int ua = ub;
-            const int row_a = A.rec[ua / A.nchunk].row;
-            int ue = min(ub + UNITS_PER_PASS, u1);
-            for (int uu = ua + 1; uu < ue; ++uu)
-                if (A.rec[uu / A.nchunk].row != row_a) {
-                    ue = uu;
-                    break;
-                }
-            if (row_a != staged_row) {
-                __syncthreads();
-                if (row_a)
-                    stage_image(img, A.xa_base, ny * A.lda);
-                else
-                    stage_image(img, A.xaT_base, nx * A.ldaT);
-                staged_row = row_a;
-                __syncthreads();
-            }
-            const int M = row_a ? ny : nx, Mm = row_a ? nx : ny, ld = row_a ? A.lda : A.ldaT;
+        if (nunits > 0) {
+            if (!mbar_wait(A, &s_mbar, parity)) return;
+            parity ^= 1u;
+        }
+        {
+            // Items (unit, segment) are taken dynamically by warps from a shared counter;
+            // each item's partial goes to its own slot, and the slots of a ray are added in
+            // segment order, so the result does not depend on which warp took what.
+            const int M = my_row ? ny : nx, Mm = my_row ? nx : ny, ld = my_row ? A.lda : A.ldaT;
             const int seg_len = ((M + FSEG - 1) / FSEG + SEGA - 1) / SEGA * SEGA;
-            const int unit = ua + warp / FSEG, seg = warp % FSEG;
-            ff part = {0.f, 0.f};
-            if (unit < ue) {
-                const int a = unit / A.nchunk;
-                const int k = (unit - a * A.nchunk) * RAYS + lane;
-                const AngleRec& r = A.rec[a];
-                if (k < r.width) part = ray_segment(r, k, seg, seg_len, M, Mm, img + kPad, ld);
-            }
-            red_s[warp * 32 + lane] = part.hi;
-            red_c[warp * 32 + lane] = part.lo;
-            __syncthreads();
-            if (warp < UNITS_PER_PASS) {  // finish ray (unit ub + warp, lane)
-                const int unit2 = ub + warp;
-                if (unit2 < ue) {
-                    const int a = unit2 / A.nchunk;
-                    const int k = (unit2 - a * A.nchunk) * RAYS + lane;
+            for (int cu = 0; cu < nunits; cu += CHUNK_UNITS) {
+                const int nu = min(CHUNK_UNITS, nunits - cu), nitems = nu * FSEG;
+                if (tid == 0) s_next = NWARP;
+                __syncthreads();
+                for (int item = warp; item < nitems;) {
+                    const int ul = item / FSEG, seg = item - ul * FSEG;
+                    const int unit = s_units[cu + ul];
+                    const int a = unit / A.nchunk;
+                    const int k = (unit - a * A.nchunk) * RAYS + lane;
+                    const AngleRec& r = A.rec[a];
+                    ff part = {0.f, 0.f};
+                    if (k < r.width) part = ray_segment(r, k, seg, seg_len, M, Mm, img + kPad, ld);
+                    red_s[item * 32 + lane] = part.hi;
+                    red_c[item * 32 + lane] = part.lo;
+                    int nxt = 0;
+                    if (lane == 0) nxt = atomicAdd(&s_next, 1);
+                    item = __shfl_sync(0xffffffffu, nxt, 0);
+                }
+                __syncthreads();
+                for (int ul = warp; ul < nu; ul += NWARP) {  // finish ray (unit cu + ul, lane)
+                    const int unit = s_units[cu + ul];
+                    const int a = unit / A.nchunk;
+                    const int k = (unit - a * A.nchunk) * RAYS + lane;
                     const AngleRec& r = A.rec[a];
                     if (k < r.width) {
-                        ff tot = {red_s[(warp * FSEG) * 32 + lane], red_c[(warp * FSEG) * 32 + lane]};
+                        ff tot = {red_s[(ul * FSEG) * 32 + lane], red_c[(ul * FSEG) * 32 + lane]};
                         for (int s = 1; s < FSEG; ++s) {
-                            const ff o = {red_s[(warp * FSEG + s) * 32 + lane], red_c[(warp * FSEG + s) * 32 + lane]};
+                            const ff o = {red_s[(ul * FSEG + s) * 32 + lane], red_c[(ul * FSEG + s) * 32 + lane]};
                             tot = ff_add(tot, o);
                         }
                         tot = ff_mul_f(r.inv_w, tot);
@@ -275,83 +428,104 @@ __global__ void __launch_bounds__(PT, 1) k_persist(PArgs A) {
                         }
                     }
                 }
+                __syncthreads();
             }
-            __syncthreads();
-            ub = ue;
         }
-        if (!grid_sync(A, &s_flag)) return;
+        if (!grid_sync(A, &s_flag, nbar)) return;
 
         // ------------------------------------------------------------ phase B
         for (int t = t0; t < t1; ++t) {
             const int tile_x0 = (t % tiles_x) * BT, tile_y0 = (t / tiles_x) * BT;
-            const float xi_t = (float)tile_x0 + 0.5f * (BT - 1) - 0.5f * (float)(nx - 1);
-            const float eta_t = 0.5f * (float)(ny - 1) - ((float)tile_y0 + 0.5f * (BT - 1));
+            const PhaseBConst* tbc = bc;
+            const int* tkb = kb;
+            const int* twd = wdt;
             __syncthreads();
-            for (int a = tid; a < A.na; a += PT) {
-                const AngleRec& r = A.rec[a];
-                ff kt = ff_add(ff_mul_f(xi_t, r.c), ff_mul_f(eta_t, r.s));
-                kt = ff_add(kt, ff{-r.phi.hi, -r.phi.lo});
-                const float fl = floorf(kt.hi);
-                kb[a] = (int)fl - BKOFF;
-                cst[a] = make_float4(r.c.hi, r.s.hi, r.inv_w, ((kt.hi - fl) + kt.lo) + (float)BKOFF);
+            if (pre) {
+                tbc = pbc + (t - t0) * A.na;
+                tkb = pkb + (t - t0) * A.na;
+                twd = pwd + (t - t0) * A.na;
+            } else {
+                for (int a = tid; a < A.na; a += PT) tile_consts(A, t, tiles_x, a, bc + a, kb + a, wdt + a);
+                __syncthreads();
             }
-            __syncthreads();
-            for (int e = tid; e < A.na * BSB; e += PT) {
-                const int a = e / BSB, bb = e - a * BSB;
-                const int kk = kb[a] + bb;
-                stage[e] = (kk >= 0 && kk < A.rec[a].width) ? __ldcg(A.u + (size_t)a * A.stride + kk) : 0.f;
-            }
-            __syncthreads();
-            const int pix = tid % BPIX, q = tid / BPIX;
-            const int lj = pix % BT, li = pix / BT;
-            const float dlj = (float)lj - 0.5f * (BT - 1), dli = (float)li - 0.5f * (BT - 1);
-            const int a_lo = (int)((long long)A.na * q / QUART), a_hi = (int)((long long)A.na * (q + 1) / QUART);
-            float sum = 0.f, cmp = 0.f;
-            for (int c0 = a_lo; c0 < a_hi; c0 += 32) {
-                const int c1 = min(c0 + 32, a_hi);
-                float acc = 0.f;
-                for (int a = c0; a < c1; ++a) {
-                    const float4 cc = cst[a];
-                    const float iw = cc.z, iw2 = cc.z * cc.z;
-                    const float kap = fmaf(dlj, cc.x, fmaf(-dli, cc.y, cc.w));
-                    const float fl = floorf(kap);
-                    const int kl = (int)fl;
-                    const float f = kap - fl;
-                    const float w0 = fmaxf(0.f, fmaf(-f, iw2, iw));
-                    const float w1 = fmaxf(0.f, fmaf(f, iw2, iw - iw2));
-                    const float* srow = stage + a * BSB;
-                    acc = fmaf(w0, srow[kl], fmaf(w1, srow[kl + 1], acc));
+            {
+                // stage the bins of every angle: loads first, then stores (many loads in flight)
+                constexpr int BATCH = 8;
+                const int ne = A.na * BSB;
+                for (int e0 = tid; e0 < ne; e0 += PT * BATCH) {
+                    float v[BATCH];
+#pragma unroll
+                    for (int q = 0; q < BATCH; ++q) {
+                        const int e = e0 + q * PT;
+                        v[q] = 0.f;
+                        if (e < ne) {
+                            const int a = e / BSB, kk = tkb[a] + (e - a * BSB);
+                            if (kk >= 0 && kk < twd[a]) v[q] = __ldcg(A.u + (size_t)a * A.stride + kk);
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < BATCH; ++q)
+                        if (e0 + q * PT < ne) stage[e0 + q * PT] = v[q];
                 }
-                neu_add(sum, cmp, acc);
             }
-            red_s[q * BPIX + pix] = sum;
-            red_c[q * BPIX + pix] = cmp;
+            __syncthreads();
+            {
+                // thread = (run of 8 pixels along a tile row, group of angles)
+                const int run = tid % RUNS, grp = tid / RUNS;
+                const int li = run >> 1, lj0 = (run & 1) * RUN;
+                const int a_lo = (int)((long long)A.na * grp / BGROUPS);
+                const int a_hi = (int)((long long)A.na * (grp + 1) / BGROUPS);
+                float acc[RUN];
+#pragma unroll
+                for (int p = 0; p < RUN; ++p) acc[p] = 0.f;
+                for (int a = a_lo; a < a_hi; ++a) {
+                    const PhaseBConst q = tbc[a];
+                    const float iw = q.iw, iw2 = iw * iw, iwm = iw - iw2;
+                    int K = q.base + lj0 * q.c - li * q.s;
+                    const float* srow = stage + a * BSB;
+#pragma unroll
+                    for (int p = 0; p < RUN; ++p) {
+                        const int kl = K >> 24;
+                        const float f = frac_of<24>(K);
+                        const float w0 = fmaxf(0.f, fmaf(-f, iw2, iw));
+                        const float w1 = fmaxf(0.f, fmaf(f, iw2, iwm));
+                        acc[p] = fmaf(w0, srow[kl], fmaf(w1, srow[kl + 1], acc[p]));
+                        K += q.c;
+                    }
+                }
+                // partials as [group][p][run]: consecutive lanes store consecutive words
+#pragma unroll
+                for (int p = 0; p < RUN; ++p) bpart[grp * BPIX + p * RUNS + run] = acc[p];
+            }
             __syncthreads();
             if (tid < BPIX) {
+                const int li = tid / BT, lj = tid % BT;
                 const int gi = tile_y0 + li, gj = tile_x0 + lj;
                 if (gi < ny && gj < nx) {
-                    float s = red_s[pix], c = red_c[pix];
-                    for (int qq = 1; qq < QUART; ++qq) {
-                        neu_add(s, c, red_s[qq * BPIX + pix]);
-                        neu_add(s, c, red_c[qq * BPIX + pix]);
-                    }
-                    const float acc = s + c;
                     const int o = gi * nx + gj;
+                    // operands of the update first, so their loads overlap the partial sums
+                    float xo, cw, dv = 0.f;
                     if (A.mode == 0) {
-                        const float step = A.C ? __ldg(A.C + o) : A.step_scalar;
-                        float xn = fmaf(step, acc, __ldcg(xa + gi * A.lda + gj));
-                        if (A.nonneg) xn = fmaxf(xn, 0.f);
-                        xa[gi * A.lda + gj] = xn;
-                        xaT[gj * A.ldaT + gi] = xn;
+                        xo = __ldcg(xa + gi * A.lda + gj);
                     } else {
-                        float dv = 0.f;
+                        xo = __ldcg(A.x + o);
                         if (gj < nx - 1) dv += __ldcg(A.vx + o);
                         if (gj > 0) dv -= __ldcg(A.vx + o - 1);
                         if (gi < ny - 1) dv += __ldcg(A.vy + o);
                         if (gi > 0) dv -= __ldcg(A.vy + o - nx);
-                        const float tau = A.C ? __ldg(A.C + o) : A.step_scalar;
-                        const float xo = __ldcg(A.x + o);
-                        const float xn = xo - tau * (acc - dv);
+                    }
+                    cw = A.C ? __ldg(A.C + o) : A.step_scalar;
+                    const int slot = (lj % RUN) * RUNS + li * 2 + lj / RUN;  // [p][run] of this pixel
+                    float s = bpart[slot], c = 0.f;
+                    for (int g = 1; g < BGROUPS; ++g) neu_add(s, c, bpart[g * BPIX + slot]);
+                    const float acc = s + c;
+                    if (A.mode == 0) {
+                        float xn = fmaf(cw, acc, xo);
+                        if (A.nonneg) xn = fmaxf(xn, 0.f);
+                        xa[gi * A.lda + gj] = xn;
+                        xaT[gj * A.ldaT + gi] = xn;
+                    } else {
+                        const float xn = xo - cw * (acc - dv);
                         A.x[o] = xn;
                         const float xb = 2.f * xn - xo;
                         xa[gi * A.lda + gj] = xb;
@@ -360,20 +534,43 @@ __global__ void __launch_bounds__(PT, 1) k_persist(PArgs A) {
                 }
             }
         }
-        if (!grid_sync(A, &s_flag)) return;
+        if (!grid_sync(A, &s_flag, nbar)) return;
     }
+}
+
+size_t region_floats(int na, int nx, int ny) {
+    const size_t img = std::max((size_t)ny * padded_ld(nx), (size_t)nx * padded_ld(ny));
+    const size_t stageB = (size_t)((na * BSB + 3) & ~3) + 4 * (size_t)na + 2 * (size_t)na + (size_t)BGROUPS * BPIX;
+    return (std::max(img, stageB) + 3) & ~(size_t)3;
 }
 
 }  // namespace
 
-size_t persist_smem_bytes(int na, int nx, int ny) {
-    const size_t img = std::max((size_t)ny * padded_ld(nx), (size_t)nx * padded_ld(ny));
-    const size_t stageB = (size_t)((na * BSB + 3) & ~3) + 4 * (size_t)na + (size_t)na;  // floats
-    const size_t region = std::max(img, stageB);
-    return sizeof(float) * (region + 2 * NWARP * 32);
+// Tiles per block of phase B and whether their constants fit the precomputed area.
+static int tiles_per_block(int nx, int ny, int blocks) {
+    const int tiles = ((nx + BT - 1) / BT) * ((ny + BT - 1) / BT);
+    return (tiles + blocks - 1) / std::max(blocks, 1);
+}
+
+static int pre_tiles(int nx, int ny, int blocks) {
+    const int tpb = tiles_per_block(nx, ny, blocks);
+    return tpb <= MAXPRE ? tpb : 0;
+}
+
+size_t persist_smem_bytes(int na, int nx, int ny, int blocks) {
+    const size_t pre = (size_t)pre_tiles(nx, ny, blocks) * na * (sizeof(PhaseBConst) + 2 * sizeof(int));
+    return sizeof(float) * (region_floats(na, nx, ny) + 2 * CHUNK_UNITS * FSEG * 32) + pre;
+}
+
+// Phase A units per block: each branch group gets at least one block per
+// units / (total units / blocks), rounded; bound it generously.
+static bool units_fit(int na, int stride, int blocks) {
+    const long units = (long)na * ((stride + RAYS - 1) / RAYS);
+    return (units + blocks - 1) / blocks * 2 + 2 <= MAXUNITS;
 }
 
 cudaError_t launch_persist(const PersistLaunch& L, cudaStream_t st) {
+    if (!units_fit(L.na, L.stride, L.blocks)) return cudaErrorInvalidConfiguration;
     PArgs A{};
     A.rec = L.rec;
     A.na = L.na;
@@ -405,8 +602,9 @@ cudaError_t launch_persist(const PersistLaunch& L, cudaStream_t st) {
     A.wait_ns = L.wait_ns;
     A.nchunk = (L.stride + RAYS - 1) / RAYS;
     A.units = L.na * A.nchunk;
-    A.img_floats = (int)((persist_smem_bytes(L.na, L.nx, L.ny) / sizeof(float)) - 2 * NWARP * 32);
-    const size_t smem = persist_smem_bytes(L.na, L.nx, L.ny);
+    A.region_floats = (int)region_floats(L.na, L.nx, L.ny);
+    A.pre_tiles = pre_tiles(L.nx, L.ny, L.blocks);
+    const size_t smem = persist_smem_bytes(L.na, L.nx, L.ny, L.blocks);
     cudaError_t e = cudaFuncSetAttribute(k_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(L.bar, 0, 2 * sizeof(unsigned), st);
@@ -416,15 +614,19 @@ cudaError_t launch_persist(const PersistLaunch& L, cudaStream_t st) {
     return cudaLaunchCooperativeKernel((const void*)k_persist, dim3(L.blocks), dim3(PT), args, smem, st);
 }
 
-int persist_max_blocks(int na, int nx, int ny, int device) {
-    const size_t smem = persist_smem_bytes(na, nx, ny);
+int persist_max_blocks(int na, int nx, int ny, int stride, int device) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) return 0;
+    const size_t smem = persist_smem_bytes(na, nx, ny, sms);
+    if (smem > (size_t)optin) return 0;
     if (cudaFuncSetAttribute(k_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist, PT, smem) != cudaSuccess) return 0;
-    int sms = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
-    return std::min(per_sm, 1) * sms;
+    const int blocks = std::min(per_sm, 1) * sms;
+    return units_fit(na, stride, blocks) ? blocks : 0;
 }
 
 }  // namespace roi

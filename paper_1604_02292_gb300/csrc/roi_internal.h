@@ -79,6 +79,8 @@ struct AngleRec {
     int flat;          // 1: |slope| < 1e-12 (rays parallel to the sampling axis)
     int d0;            // first bin of the window
     int width;         // bins in the window (0 if no ray reaches the frame)
+    int slope_q22;     // round(slope 2^22): per-sample step of the fixed-point ray coordinate
+    int c_q24, s_q24;  // round(c 2^24), round(s 2^24): per-pixel steps of the gather coordinate
 };
 
 // Fills the derived fields of `r` from doubles (host and device).
@@ -97,6 +99,9 @@ ROI_HD void angle_fill(AngleRec& r, double c, double s, int row, double wd, int 
     r.flat = fabs(sl) < 1e-12;
     r.inv_slope = r.flat ? 0.f : (float)(1.0 / sl);
     r.A0 = ff_split(0.5 * (Mm - 1) + as * phi);
+    r.slope_q22 = (int)llrint(sl * 4194304.0);
+    r.c_q24 = (int)llrint(c * 16777216.0);
+    r.s_q24 = (int)llrint(s * 16777216.0);
 }
 
 struct Rect {
@@ -239,8 +244,8 @@ struct PersistLaunch {
     int blocks;               // <= persist_max_blocks
     int phantoms;             // extra barrier participants that never arrive (testing only)
 };
-size_t persist_smem_bytes(int na, int nx, int ny);
-int persist_max_blocks(int na, int nx, int ny, int device);
+size_t persist_smem_bytes(int na, int nx, int ny, int blocks);
+int persist_max_blocks(int na, int nx, int ny, int stride, int device);
 cudaError_t launch_persist(const PersistLaunch& L, cudaStream_t st);
 
 }  // namespace roi
