@@ -449,32 +449,32 @@ __global__ void __launch_bounds__(PT, 1) k_persist(PArgs A) {
                 __syncthreads();
             }
             {
-                // stage the bins of every angle: loads first, then stores (many loads in flight)
-                constexpr int BATCH = 8;
-                const int ne = A.na * BSB;
-                for (int e0 = tid; e0 < ne; e0 += PT * BATCH) {
-                    float v[BATCH];
-#pragma unroll
-                    for (int q = 0; q < BATCH; ++q) {
-                        const int e = e0 + q * PT;
-                        v[q] = 0.f;
-                        if (e < ne) {
-                            const int a = e / BSB, kk = tkb[a] + (e - a * BSB);
-                            if (kk >= 0 && kk < twd[a]) v[q] = __ldcg(A.u + (size_t)a * A.stride + kk);
-                        }
-                    }
-#pragma unroll
-                    for (int q = 0; q < BATCH; ++q)
-                        if (e0 + q * PT < ne) stage[e0 + q * PT] = v[q];
-                }
-            }
-            __syncthreads();
-            {
-                // thread = (run of 8 pixels along a tile row, group of angles)
+                // thread = (run of 8 pixels along a tile row, group of angles); a warp is one
+                // angle group and stages that group's bins itself (no block-wide wait)
                 const int run = tid % RUNS, grp = tid / RUNS;
                 const int li = run >> 1, lj0 = (run & 1) * RUN;
                 const int a_lo = (int)((long long)A.na * grp / BGROUPS);
                 const int a_hi = (int)((long long)A.na * (grp + 1) / BGROUPS);
+                {
+                    const int e_lo = a_lo * BSB, e_hi = a_hi * BSB;
+                    constexpr int BATCH = 8;
+                    for (int e0 = e_lo + lane; e0 < e_hi; e0 += 32 * BATCH) {
+                        float v[BATCH];
+#pragma unroll
+                        for (int q = 0; q < BATCH; ++q) {
+                            const int e = e0 + q * 32;
+                            v[q] = 0.f;
+                            if (e < e_hi) {
+                                const int a = e / BSB, kk = tkb[a] + (e - a * BSB);
+                                if (kk >= 0 && kk < twd[a]) v[q] = __ldcg(A.u + (size_t)a * A.stride + kk);
+                            }
+                        }
+#pragma unroll
+                        for (int q = 0; q < BATCH; ++q)
+                            if (e0 + q * 32 < e_hi) stage[e0 + q * 32] = v[q];
+                    }
+                    __syncwarp();
+                }
                 float acc[RUN];
 #pragma unroll
                 for (int p = 0; p < RUN; ++p) acc[p] = 0.f;
