@@ -80,7 +80,7 @@ struct AngleRec {
     int d0;            // first bin of the window
     int width;         // bins in the window (0 if no ray reaches the frame)
     int slope_q22;     // round(slope 2^22): per-sample step of the fixed-point ray coordinate
-    int c_q24, s_q24;  // round(c 2^24), round(s 2^24): per-pixel steps of the gather coordinate
+    int c_q23, s_q23;  // round(c 2^23), round(s 2^23): per-pixel steps of the gather coordinate
 };
 
 // Fills the derived fields of `r` from doubles (host and device).
@@ -100,8 +100,8 @@ ROI_HD void angle_fill(AngleRec& r, double c, double s, int row, double wd, int 
     r.inv_slope = r.flat ? 0.f : (float)(1.0 / sl);
     r.A0 = ff_split(0.5 * (Mm - 1) + as * phi);
     r.slope_q22 = (int)llrint(sl * 4194304.0);
-    r.c_q24 = (int)llrint(c * 16777216.0);
-    r.s_q24 = (int)llrint(s * 16777216.0);
+    r.c_q23 = (int)llrint(c * 8388608.0);
+    r.s_q23 = (int)llrint(s * 8388608.0);
 }
 
 struct Rect {
