@@ -67,6 +67,24 @@ def dist_env():
     return ws, rank, local
 
 
+def profile_traffic(kernel_src, profile_md):
+    """DRAM bytes per launch from a committed ncu summary, only while the kernel source still
+    hashes to the value recorded with the counters (else None: the kernel has changed)."""
+    import hashlib
+    try:
+        text = open(os.path.join(ROOT, profile_md)).read()
+        src = open(os.path.join(ROOT, kernel_src), "rb").read()
+    except OSError:
+        return None
+    fields = dict(line.split(":", 1) for line in text.splitlines() if line.startswith(("source_sha256:", "dram_bytes_per_launch:")))
+    if fields.get("source_sha256", "").strip() != hashlib.sha256(src).hexdigest():
+        return None
+    try:
+        return int(fields["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -310,6 +328,8 @@ def run_ours(args):
         kernel = "k_back (CP)" if msb >= msf else "k_forward (CP)"
         lerps, avg_ms, alg_bytes = (lb, avg_b, bb) if msb >= msf else (lf, avg_f, bf)
     achieved = lerps / (avg_ms * 1e-3) / 1e9
+    traffic = profile_traffic("paper_1604_02292_gb300/csrc/persist.cu", "profiles/k_persist_cptv_1024.md") \
+        if n_single else None
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -364,7 +384,7 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved,
                          "peak": peak_glerps, "unit": "Glerp/s", "frac": achieved / peak_glerps,
-                         "traffic": None, "peak_source": f"derived: {N_SM} SMs x {LERPS_PER_CLK_SM} lerp/clk x "
+                         "traffic": traffic, "traffic_unit": "DRAM bytes per launch (ncu, profiles/)", "peak_source": f"derived: {N_SM} SMs x {LERPS_PER_CLK_SM} lerp/clk x "
                                                          f"{sm_max:.0f} MHz ({pk_src} sm_max_mhz)",
                          "launch_ms": avg_ms, "lerps_per_launch": lerps,
                          "algorithmic_GBps": alg_bytes / (avg_ms * 1e-3) / 1e9,
