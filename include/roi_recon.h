@@ -147,6 +147,20 @@ roi_status roi_recon_reproject_exterior(roi_recon_t h, const roi_region* region,
 roi_status roi_recon_solve_local(roi_recon_t h, const roi_region* region, const roi_solve_params* params,
                                  float* out, int out_on_device, roi_solve_info* info);
 
+/* Many local solves in one call (Sec. 4.4: local reconstructions are independent and can
+ * be computed in parallel; Sec. 1 scheme for each).  regions[n], params[n] (one per region;
+ * SIRT and CP may be mixed; CP must use precond = 1; eval_objective is ignored), outs[n]:
+ * [box_h][box_w] float32 each, device pointers when out_on_device = 1, host memory
+ * otherwise (the call then synchronizes).  infos (optional) [n] receive each plan.
+ * All exterior windows are computed by one batched projection and all solves by one
+ * persistent launch whose blocks each solve whole regions, largest first.  A region's
+ * result is bit-identical whatever else is in the batch; it agrees with
+ * roi_recon_solve_local to rounding (a different split of the same sums).  Device memory:
+ * the angle tables (144 N_theta bytes per region), all windows, and scratch per SM for
+ * the largest region.  ROI_ESTATE before fbp, ROI_EINVAL naming the offending region. */
+roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions, const roi_solve_params* params,
+                                 float* const* outs, int out_on_device, roi_solve_info* infos);
+
 /* --------------------------------------------------------------------------
  * Planning and single operators (for custom solvers and for verification)
  * ------------------------------------------------------------------------ */

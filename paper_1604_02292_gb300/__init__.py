@@ -69,7 +69,7 @@ EXPORTS = [
     "roi_recon_fbp", "roi_recon_reproject_exterior", "roi_recon_solve_local", "roi_recon_plan",
     "roi_recon_forward_local", "roi_recon_back_local", "roi_recon_ramp_filter",
     "roi_recon_set_timing", "roi_recon_kernel_times", "roi_recon_launch_count",
-    "roi_recon_forward_local_noalloc", "roi_recon_set_option", "roi_recon_sync",
+    "roi_recon_forward_local_noalloc", "roi_recon_set_option", "roi_recon_sync", "roi_recon_solve_batch",
 ]
 
 _lib = None
@@ -124,6 +124,10 @@ def lib() -> ctypes.CDLL:
             L.roi_recon_set_option.restype = st
             L.roi_recon_sync.argtypes = [_H]
             L.roi_recon_sync.restype = st
+            L.roi_recon_solve_batch.argtypes = [_H, ctypes.c_int, ctypes.POINTER(Region), ctypes.POINTER(SolveParams),
+                                                ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                                ctypes.POINTER(SolveInfo)]
+            L.roi_recon_solve_batch.restype = st
             _lib = L
     return _lib
 
@@ -208,6 +212,12 @@ def roi_recon_set_option(h, opt: int, value: int) -> int:
 
 def roi_recon_sync(h) -> int:
     return lib().roi_recon_sync(h)
+
+
+def roi_recon_solve_batch(h, regions, params, outs, out_on_device: int, infos=None) -> int:
+    """regions, params: ctypes arrays (Region * n, SolveParams * n); outs: (c_void_p * n) pointers."""
+    n = len(regions)
+    return lib().roi_recon_solve_batch(h, n, regions, params, outs, int(out_on_device), infos)
 
 
 # ---- convenience layer -----------------------------------------------------------------
@@ -345,6 +355,42 @@ class RoiRecon:
             s = roi_recon_solve_local(self.h, Region(*map(float, region)), prm, out.ctypes.data, 0, info)
         self._check(s)
         return out, info
+
+    def solve_batch(self, regions, params, outs=None):
+        """Solve many regions in one call.  regions: list of (cx, cy, r, m); params: list of dicts
+        (reg, iters, lam, weighting, crop_disk) or one dict for all.  Returns (outs, infos);
+        outs are CUDA tensors unless host numpy arrays are passed."""
+        torch = self._torch
+        n = len(regions)
+        if isinstance(params, dict):
+            params = [params] * n
+        regs = (Region * n)(*[Region(*map(float, r)) for r in regions])
+        prms = (SolveParams * n)()
+        for i, p in enumerate(params):
+            prms[i] = SolveParams(int(p.get("reg", ROI_SIRT_NONNEG)), float(p.get("lam", 0.0)),
+                                  int(p.get("iters", 200)), int(p.get("weighting", 0)), 1,
+                                  int(p.get("crop_disk", 0)), 0)
+        infos = (SolveInfo * n)()
+        on_device = 1
+        if outs is None:
+            outs = []
+            for i, r in enumerate(regions):
+                try:
+                    pl = self.plan(r)
+                except RoiError as e:
+                    raise RoiError(e.status, f"solve_batch: region {i}: extended box misses the grid or is invalid")
+                outs.append(torch.empty((pl.box[3], pl.box[2]), dtype=torch.float32, device="cuda"))
+        ptrs = (ctypes.c_void_p * n)()
+        for i, o in enumerate(outs):
+            if isinstance(o, torch.Tensor) and o.is_cuda:
+                ptrs[i] = o.data_ptr()
+            else:
+                on_device = 0
+                ptrs[i] = o.ctypes.data
+        if on_device == 0 and any(isinstance(o, torch.Tensor) and o.is_cuda for o in outs):
+            raise TypeError("outs must be all CUDA tensors or all host arrays")
+        self._check(roi_recon_solve_batch(self.h, regs, prms, ptrs, on_device, infos))
+        return outs, list(infos)
 
     def forward_local(self, region, x, y=None):
         pl = self.plan(region)

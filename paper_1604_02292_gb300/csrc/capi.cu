@@ -41,7 +41,7 @@ cudaError_t dev_alloc(T** p, size_t count) {
 
 // Grow-only device buffer.
 template <class T>
-struct DevBufT {
+struct DevBufT {  // grow-only device array of T
     T* p = nullptr;
     size_t cap = 0;
     cudaError_t ensure(size_t n) {
@@ -108,6 +108,18 @@ struct roi_recon {
     unsigned long long opt_wait_ns = 1000000000ull;
     int opt_phantoms = 0;
     size_t max_smem_optin = 0;
+    int sms = 0;
+    // batched solves: per-region tables / windows / descriptors, per-block slots, pinned staging
+    DevBufT<AngleRec> b_tab;
+    DevBuf b_win, b_out;
+    DevBufT<roi::BatchRoi> b_rois;
+    DevBufT<roi::ExtItem> b_items;
+    DevBufT<int> b_order;
+    DevBufT<int> b_queue;
+    DevBuf s_u, s_sig, s_x, s_vx, s_vy, s_tau, s_xa, s_xaT;
+    unsigned char* pin = nullptr;  // page-locked staging of the uploads
+    size_t pin_cap = 0;
+    cudaEvent_t pin_free = nullptr;  // recorded after the last upload from `pin`
 };
 
 namespace {
@@ -545,6 +557,8 @@ roi_status roi_recon_create(const roi_geometry* geom, void* cuda_stream, roi_rec
         e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
         h->max_smem_optin = (size_t)v;
     }
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->pin_free, cudaEventDisableTiming);
     if (e == cudaSuccess) {
         // Ram-Lak odd taps h_m = -1/(pi m)^2, m = 2t + 1, scaled by pi / N_theta (Eq. fbp)
         std::vector<float> ho((size_t)h->nd / 2 + 1);
@@ -582,6 +596,16 @@ void roi_recon_destroy(roi_recon_t h) {
     if (h->red) cudaFree(h->red);
     if (h->d_bar) cudaFree(h->d_bar);
     if (h->d_err) cudaFree(h->d_err);
+    h->b_tab.release();
+    h->b_rois.release();
+    h->b_items.release();
+    h->b_order.release();
+    h->b_queue.release();
+    for (DevBuf* b : {&h->b_win, &h->b_out, &h->s_u, &h->s_sig, &h->s_x, &h->s_vx, &h->s_vy, &h->s_tau, &h->s_xa,
+                      &h->s_xaT})
+        b->release();
+    if (h->pin) cudaFreeHost(h->pin);
+    if (h->pin_free) cudaEventDestroy(h->pin_free);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     for (DevBuf* b : {&h->pp, &h->u, &h->sig, &h->wtmp, &h->wrow, &h->xc, &h->vx, &h->vy, &h->tau, &h->itmp, &h->xa,
                       &h->xaT})
@@ -782,6 +806,200 @@ roi_status roi_recon_solve_local(roi_recon_t h, const roi_region* region, const 
         info->iters_done = params->iters;
         info->step_L = L;
         info->objective = objective;
+    }
+    return ROI_OK;
+}
+
+roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions, const roi_solve_params* params,
+                                 float* const* outs, int out_on_device, roi_solve_info* infos) {
+    if (!h) return ROI_EINVAL;
+    h->err.clear();
+    if (n < 0 || (n > 0 && (!regions || !params || !outs))) return fail(h, ROI_EINVAL, "solve_batch: bad arguments");
+    if (n == 0) return ROI_OK;
+    if (!h->have_fbp) return fail(h, ROI_ESTATE, "solve_batch: no FBP image (call fbp first)");
+    const int na = h->na;
+    const Rect grid{0, 0, h->N, h->N};
+    // ---- host plan of every region
+    std::vector<Rect> boxes(n);
+    std::vector<int> strides(n), nrows(n);
+    std::vector<AngleRec> loc(na), ext(na);
+    std::vector<int> perm(na);
+    size_t win_total = 0, out_total = 0, win_cap = 0, img_cap = 0, pad_cap = 0, max_smem_img = 0;
+    int stride_max = 0;
+    const size_t smem_img_limit = std::min<size_t>(200 * 1024, h->max_smem_optin > 4096 ? h->max_smem_optin - 4096 : 0);
+    std::vector<double> cost(n);
+    for (int i = 0; i < n; ++i) {
+        const roi_solve_params& P = params[i];
+        if (!finite_region(&regions[i]))
+            return fail(h, ROI_EINVAL, "solve_batch: region %d: radius must be > 0, margin >= 0, all finite", i);
+        if (P.reg != ROI_SIRT_NONNEG && P.reg != ROI_TV_CP)
+            return fail(h, ROI_EINVAL, "solve_batch: region %d: unknown regularizer", i);
+        if (P.iters < 0 || P.iters > 1000000) return fail(h, ROI_EINVAL, "solve_batch: region %d: iters out of range", i);
+        if (!std::isfinite(P.lambda) || P.lambda < 0) return fail(h, ROI_EINVAL, "solve_batch: region %d: bad lambda", i);
+        if (P.reg == ROI_TV_CP && !P.precond)
+            return fail(h, ROI_EINVAL, "solve_batch: region %d: batched CP uses the diagonal steps (precond = 1)", i);
+        if (!outs[i]) return fail(h, ROI_EINVAL, "solve_batch: region %d: null output", i);
+        Rect box;
+        if (!roi::plan_box(h->N, regions[i].cx, regions[i].cy, regions[i].radius, regions[i].margin, &box))
+            return fail(h, ROI_EINVAL, "solve_batch: region %d: extended box misses the grid", i);
+        const int wl = roi::plan_angles(h->N, na, h->nd, h->angles.data(), box, box, false, loc.data());
+        boxes[i] = box;
+        strides[i] = roi::round_stride(wl);
+        stride_max = std::max(stride_max, strides[i]);
+        win_total += (size_t)na * strides[i];
+        out_total += (size_t)box.w * box.h;
+        win_cap = std::max(win_cap, (size_t)na * strides[i]);
+        img_cap = std::max(img_cap, (size_t)box.w * box.h);
+        const size_t pr = (size_t)box.h * roi::padded_ld(box.w), pc = (size_t)box.w * roi::padded_ld(box.h);
+        pad_cap = std::max(pad_cap, std::max(pr, pc));
+        if (sizeof(float) * std::max(pr, pc) <= smem_img_limit) max_smem_img = std::max(max_smem_img, std::max(pr, pc));
+        cost[i] = (double)box.w * box.h * na * (double)std::max(P.iters, 1);
+    }
+    // ---- device storage
+    CU(h, h->b_tab.ensure((size_t)n * 2 * na));
+    CU(h, h->b_win.ensure(win_total));
+    CU(h, h->b_rois.ensure(n));
+    CU(h, h->b_items.ensure(n));
+    CU(h, h->b_order.ensure(n));
+    CU(h, h->b_queue.ensure(1));
+    if (!out_on_device) CU(h, h->b_out.ensure(out_total));
+    const int blocks = std::max(1, h->sms);
+    for (DevBuf* b : {&h->s_u, &h->s_sig}) CU(h, b->ensure(win_cap * blocks));
+    for (DevBuf* b : {&h->s_x, &h->s_vx, &h->s_vy, &h->s_tau}) CU(h, b->ensure(img_cap * blocks));
+    for (DevBuf* b : {&h->s_xa, &h->s_xaT}) CU(h, b->ensure(pad_cap * blocks));
+    // ---- page-locked staging: tables, descriptors, items, order
+    const size_t tab_bytes = sizeof(AngleRec) * (size_t)n * 2 * na;
+    const size_t roi_bytes = sizeof(roi::BatchRoi) * (size_t)n, item_bytes = sizeof(roi::ExtItem) * (size_t)n;
+    const size_t ord_bytes = sizeof(int) * (size_t)n;
+    const size_t pin_need = tab_bytes + roi_bytes + item_bytes + ord_bytes;
+    CU(h, cudaEventSynchronize(h->pin_free));  // the previous uploads have left the staging area
+    if (pin_need > h->pin_cap) {
+        if (h->pin) cudaFreeHost(h->pin);
+        h->pin = nullptr;
+        h->pin_cap = 0;
+        CU(h, cudaMallocHost((void**)&h->pin, pin_need));
+        h->pin_cap = pin_need;
+    }
+    AngleRec* ptab = reinterpret_cast<AngleRec*>(h->pin);
+    roi::BatchRoi* prois = reinterpret_cast<roi::BatchRoi*>(h->pin + tab_bytes);
+    roi::ExtItem* pitems = reinterpret_cast<roi::ExtItem*>(h->pin + tab_bytes + roi_bytes);
+    int* pord = reinterpret_cast<int*>(h->pin + tab_bytes + roi_bytes + item_bytes);
+    size_t woff = 0, ooff = 0;
+    for (int i = 0; i < n; ++i) {
+        const Rect box = boxes[i];
+        roi::plan_angles(h->N, na, h->nd, h->angles.data(), box, box, false, loc.data());
+        roi::plan_angles(h->N, na, h->nd, h->angles.data(), grid, box, false, ext.data());
+        // per-row-branch angles first (stable), the same order for both tables
+        int nr = 0;
+        for (int a = 0; a < na; ++a)
+            if (loc[a].row) perm[nr++] = a;
+        int k = nr;
+        for (int a = 0; a < na; ++a)
+            if (!loc[a].row) perm[k++] = a;
+        AngleRec* tl = ptab + (size_t)i * 2 * na;
+        AngleRec* te = tl + na;
+        for (int a = 0; a < na; ++a) {
+            tl[a] = loc[perm[a]];
+            te[a] = ext[perm[a]];
+        }
+        const roi_solve_params& P = params[i];
+        roi::BatchRoi& R = prois[i];
+        R.rec = h->b_tab.p + (size_t)i * 2 * na;
+        R.pp = h->b_win.p + woff;
+        R.out = out_on_device ? outs[i] : h->b_out.p + ooff;
+        R.na = na;
+        R.nrow = nr;
+        R.nx = box.w;
+        R.ny = box.h;
+        R.stride = strides[i];
+        R.reg = P.reg == ROI_TV_CP ? 1 : 0;
+        R.iters = P.iters;
+        R.weighting = P.reg == ROI_SIRT_NONNEG && P.weighting ? 1 : 0;
+        R.lambda = (float)P.lambda;
+        R.sigma_v = 0.5f;
+        R.crop = P.crop_disk ? 1 : 0;
+        R.cxl = (float)(regions[i].cx - box.x0);
+        R.cyl = (float)(regions[i].cy - box.y0);
+        R.r2 = (float)(regions[i].radius * regions[i].radius);
+        roi::ExtItem& it = pitems[i];
+        it.rec = h->b_tab.p + (size_t)i * 2 * na + na;
+        it.stride = strides[i];
+        it.hole = box;
+        it.out = h->b_win.p + woff;
+        woff += (size_t)na * strides[i];
+        ooff += (size_t)box.w * box.h;
+        pord[i] = i;
+        if (infos) {
+            infos[i].box_x0 = box.x0;
+            infos[i].box_y0 = box.y0;
+            infos[i].box_w = box.w;
+            infos[i].box_h = box.h;
+            infos[i].window_max = 0;
+            for (int a = 0; a < na; ++a) infos[i].window_max = std::max(infos[i].window_max, loc[a].width);
+            infos[i].window_stride = strides[i];
+            infos[i].iters_done = P.iters;
+            infos[i].step_L = 0.0;
+            infos[i].objective = 0.0;
+        }
+    }
+    std::stable_sort(pord, pord + n, [&](int a, int b) { return cost[a] > cost[b]; });
+    CU(h, cudaMemcpyAsync(h->b_tab.p, ptab, tab_bytes, cudaMemcpyHostToDevice, h->st));
+    CU(h, cudaMemcpyAsync(h->b_rois.p, prois, roi_bytes, cudaMemcpyHostToDevice, h->st));
+    CU(h, cudaMemcpyAsync(h->b_items.p, pitems, item_bytes, cudaMemcpyHostToDevice, h->st));
+    CU(h, cudaMemcpyAsync(h->b_order.p, pord, ord_bytes, cudaMemcpyHostToDevice, h->st));
+    CU(h, cudaEventRecord(h->pin_free, h->st));
+    // ---- exterior windows of every region
+    roi::FwdArgs fa{};
+    fa.na = na;
+    fa.nx = h->N;
+    fa.ny = h->N;
+    fa.img = h->xfbp;
+    fa.imgT = h->xfbpT;
+    fa.img_ld = roi::padded_ld(h->N);
+    fa.imgT_ld = roi::padded_ld(h->N);
+    fa.p = h->p;
+    fa.nd = h->nd;
+    roi::launch_forward_batch(fa, h->b_items.p, n, stride_max, h->st);
+    LAUNCHED(h, "batched exterior reprojection");
+    // ---- all solves in one persistent launch
+    roi::BatchArgs B{};
+    B.rois = h->b_rois.p;
+    B.order = h->b_order.p;
+    B.nroi = n;
+    B.queue = h->b_queue.p;
+    B.slot_u = h->s_u.p;
+    B.slot_sig = h->s_sig.p;
+    B.win_cap = win_cap;
+    B.slot_x = h->s_x.p;
+    B.slot_vx = h->s_vx.p;
+    B.slot_vy = h->s_vy.p;
+    B.slot_tau = h->s_tau.p;
+    B.img_cap = img_cap;
+    B.slot_xa = h->s_xa.p;
+    B.slot_xaT = h->s_xaT.p;
+    B.pad_cap = pad_cap;
+    B.alpha = (float)(1.0 / ((double)na * h->nd));
+    B.smem_img_bytes = (int)(sizeof(float) * max_smem_img);
+    B.err = h->d_err;
+    B.wait_ns = h->opt_wait_ns;
+    const size_t smem = roi::batch_smem_bytes(max_smem_img);
+    cudaError_t e;
+    {
+        Span sp(h, 2);
+        e = roi::launch_batch(B, blocks, smem, h->st);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "batched solve launch");
+    if (!out_on_device) {
+        std::vector<float> all(out_total);
+        CU(h, cudaMemcpyAsync(all.data(), h->b_out.p, sizeof(float) * out_total, cudaMemcpyDeviceToHost, h->st));
+        roi_status s = roi_recon_sync(h);
+        if (s != ROI_OK) return s;
+        size_t o = 0;
+        for (int i = 0; i < n; ++i) {
+            const size_t m = (size_t)boxes[i].w * boxes[i].h;
+            std::memcpy(outs[i], all.data() + o, sizeof(float) * m);
+            o += m;
+        }
     }
     return ROI_OK;
 }

@@ -1,0 +1,79 @@
+// dev_common.cuh -- device helpers shared by the solver kernels: wall-clock time,
+// TMA bulk copies with mbarrier completion and bounded waits, fixed-point conversions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "roi_internal.h"
+
+namespace roi {
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// One thread: arm the barrier for `bytes` and start the bulk copy global -> shared.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile("fence.proxy.async;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits (bounded) for the bulk copy of phase `parity`.  On time-out sets the error flag,
+// waits once more (bounded) so no copy is left writing into shared memory, returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned long long wait_ns, int* err) {
+    const unsigned long long t0 = global_ns();
+    while (!mbar_test(bar, parity)) {
+        if (global_ns() - t0 > wait_ns) {
+            atomicExch(err, 1);
+            const unsigned long long t1 = global_ns();
+            while (!mbar_test(bar, parity) && global_ns() - t1 < wait_ns) {
+            }
+            return false;
+        }
+    }
+    return true;
+}
+
+// Float-float coordinate v in [-2^8, 2^8) to Q.F fixed point.
+template <int F>
+__device__ __forceinline__ int to_fixed(ff v) {
+    const float n = floorf(v.hi);
+    const float fr = (v.hi - n) + v.lo;
+    return ((int)n << F) + __float2int_rn(fr * (float)(1 << F));
+}
+
+// The F <= 23 fraction bits of a Q.F number as an integer-valued float in [0, 2^F):
+// OR-ing them into the mantissa of 2^23 and subtracting 2^23 is exact (one logic op and
+// one add, no conversion instruction).
+template <int F>
+__device__ __forceinline__ float frac_int(int q) {
+    return __uint_as_float(0x4B000000u | ((unsigned)q & ((1u << F) - 1u))) - 8388608.0f;
+}
+
+}  // namespace roi

@@ -67,7 +67,7 @@ __global__ void k_plan_box(roi::AngleRec* rec, int N, int na, int nd, roi::Rect 
     }
     if (width > stride) width = stride;  // the output row holds `stride` bins
     roi::AngleRec r;
-    roi::angle_fill(r, c, s, row, wd, d0, width, d0 - dhalf - Tb, row ? box.w : box.h);
+    roi::angle_fill(r, a, c, s, row, wd, d0, width, d0 - dhalf - Tb, row ? box.w : box.h);
     rec[a] = r;
 }
 

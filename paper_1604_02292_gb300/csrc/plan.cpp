@@ -67,7 +67,7 @@ int plan_angles(int N, int na, int nd, const double* angles, Rect frame, Rect ta
         }
         const double Tf = Xf * c + Yf * s;
         const int Mm = row ? frame.w : frame.h;  // minor extent
-        angle_fill(rec[a], c, s, row, wd, d0, width, d0 - dhalf - Tf, Mm);
+        angle_fill(rec[a], a, c, s, row, wd, d0, width, d0 - dhalf - Tf, Mm);
         wmax = std::max(wmax, width);
     }
     return wmax;

@@ -79,12 +79,15 @@ struct AngleRec {
     int flat;          // 1: |slope| < 1e-12 (rays parallel to the sampling axis)
     int d0;            // first bin of the window
     int width;         // bins in the window (0 if no ray reaches the frame)
+    int aidx;          // index of the angle in the sinogram (tables may be reordered)
     int slope_q22;     // round(slope 2^22): per-sample step of the fixed-point ray coordinate
     int c_q23, s_q23;  // round(c 2^23), round(s 2^23): per-pixel steps of the gather coordinate
 };
 
 // Fills the derived fields of `r` from doubles (host and device).
-ROI_HD void angle_fill(AngleRec& r, double c, double s, int row, double wd, int d0, int width, double phi, int Mm) {
+ROI_HD void angle_fill(AngleRec& r, int aidx, double c, double s, int row, double wd, int d0, int width, double phi,
+                       int Mm) {
+    r.aidx = aidx;
     r.c = ff_split(c);
     r.s = ff_split(s);
     r.row = row;
@@ -138,9 +141,18 @@ enum BackMode { BACK_PLAIN = 0, BACK_SIRT = 1, BACK_CP = 2 };
 // so whole images can be staged with 16-byte copies), and the columns left and right
 // of each row (indices -2, -1 and extent .. ld - 3) hold zeros.
 constexpr int kPad = 2;
-inline int padded_ld(int extent) { return (extent + 2 * kPad + 3) / 4 * 4; }
+ROI_HD int padded_ld(int extent) { return (extent + 2 * kPad + 3) / 4 * 4; }
+
+// One region of a batched exterior projection (blockIdx.z of k_forward selects it).
+struct ExtItem {
+    const AngleRec* rec;   // grid-frame table of the region's windows
+    int stride;
+    Rect hole;             // the region's box
+    float* out;            // p' window [na][stride]
+};
 
 struct FwdArgs {
+    const ExtItem* items;  // FWD_EXTERIOR only: per-region overrides of rec/stride/hole/out, or null
     const AngleRec* rec;   // [na]
     int na, stride;        // window rows and their stride
     int nx, ny;            // frame size
@@ -247,5 +259,44 @@ struct PersistLaunch {
 size_t persist_smem_bytes(int na, int nx, int ny, int blocks);
 int persist_max_blocks(int na, int nx, int ny, int stride, int device);
 cudaError_t launch_persist(const PersistLaunch& L, cudaStream_t st);
+
+// ---- batched solves: one block per SM pulls regions and solves each one completely
+struct BatchRoi {
+    const AngleRec* rec;   // box-frame table, per-row-branch angles first
+    const float* pp;       // p' window [na][stride] (same angle order)
+    float* out;            // result [ny][nx], device
+    int na, nrow;          // angles; the first nrow sample per row
+    int nx, ny, stride;
+    int reg, iters, weighting;
+    float lambda, sigma_v;
+    int crop;
+    float cxl, cyl, r2;    // disk crop in box coordinates
+};
+
+struct BatchArgs {
+    const BatchRoi* rois;
+    const int* order;      // solve order (largest first)
+    int nroi;
+    int* queue;            // zeroed by the launcher
+    float* slot_u;         // per-block windows and box buffers
+    float* slot_sig;
+    size_t win_cap;
+    float* slot_x;
+    float* slot_vx;
+    float* slot_vy;
+    float* slot_tau;
+    size_t img_cap;
+    float* slot_xa;        // padded images (row / column), from row 0 column -2
+    float* slot_xaT;
+    size_t pad_cap;
+    float alpha;           // SIRT scalar step 1/(N_theta N_d)
+    int smem_img_bytes;    // boxes whose padded image fits here are staged in shared memory
+    int* err;
+    unsigned long long wait_ns;
+};
+size_t batch_smem_bytes(size_t max_img_floats);
+cudaError_t launch_batch(const BatchArgs& B, int blocks, size_t smem, cudaStream_t st);
+// Batched exterior projection: items[nroi], grid (ceil(stride_max / 32), na, nroi)
+void launch_forward_batch(const FwdArgs& a, const ExtItem* items, int nroi, int stride_max, cudaStream_t st);
 
 }  // namespace roi
