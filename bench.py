@@ -54,7 +54,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WL.WORKLOADS))
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WL.WORKLOADS) + sorted(WL.BATCHES))
+    ap.add_argument("--batch-count", type=int, default=None,
+                    help="batch workloads: solve this many of the regions per step (default: all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -403,10 +405,67 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """Batch workload: one step = roi_recon_solve_batch over the regions (one batched exterior
+    projection + one persistent launch); value = regions solved per second."""
+    import torch
+
+    import paper_1604_02292_gb300 as R
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    w = WL.BATCHES[args.workload]
+    p = WL.sinogram(w, seed=rank)
+    items = WL.batch_regions(w, seed=rank, count=args.batch_count)
+    regions = [r for r, _ in items]
+    params = [prm for _, prm in items]
+    stream = torch.cuda.Stream()
+    rr = R.RoiRecon(*w.geometry(), stream=stream)
+    outs = None
+    with torch.cuda.stream(stream):
+        rr.set_sinogram(torch.from_numpy(p).cuda())
+        rr.fbp()
+        for _ in range(args.warmup):
+            outs, _ = rr.solve_batch(regions, params, outs)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    n0 = R.roi_recon_launch_count()
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                ev[k][0].record(stream)
+                outs, _ = rr.solve_batch(regions, params, outs)
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    rr.sync()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    n_lerps = 0
+    for reg, prm in items:
+        pl = rr.plan(reg)
+        nx, ny = pl.box[2], pl.box[3]
+        n_lerps += prm["iters"] * (sum(pl.width) * max(nx, ny) + nx * ny * w.n_angles)
+    t = sum(ms) / 1e3
+    line = {
+        "metric": "roi_solves_per_s", "value": len(items) * args.steps / t, "unit": "solves/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(ms), "higher_is_better": True,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "N": w.N, "n_angles": w.n_angles, "n_det": w.n_det, "regions": len(items),
+                   "radius": [w.r_lo, w.r_hi], "iters": w.iters, "solvers": "SIRT/TV 50/50"},
+        "gpu_launches": int(R.roi_recon_launch_count() - n0),
+        "projector_Glerp_s": n_lerps * args.steps / t / 1e9,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    rr.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload in WL.BATCHES:
+        return run_batch(args)
     return run_ours(args)
 
 

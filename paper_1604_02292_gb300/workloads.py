@@ -44,9 +44,56 @@ WORKLOADS = {
 }
 
 
-def sinogram(w: Workload, seed: int = 0) -> np.ndarray:
+@dataclasses.dataclass(frozen=True)
+class BatchWorkload:
+    """Many regions over one sinogram: centres on a jittered grid of cells, radii uniform,
+    margin = radius / 2, SIRT or TV by a seeded coin."""
+    name: str
+    N: int
+    n_angles: int
+    n_det: int
+    n_ellipses: int
+    I0: float
+    grid: int             # cells per side
+    r_lo: float
+    r_hi: float
+    iters: int
+    lam: float
+
+    def geometry(self):
+        return self.N, self.n_angles, self.n_det
+
+
+BATCHES = {
+    # 2048 x 2048, 180 angles, 2048 bins, 50 ellipses (noise-free); 4096 regions with centres
+    # on a jittered 64 x 64 grid of 32 px cells, radius U[16, 128], margin r/2, SIRT/TV 50/50,
+    # 200 iterations
+    "roi_batch_2048": BatchWorkload("roi_batch_2048", 2048, 180, 2048, 50, 0.0, 64, 16.0, 128.0, 200, 0.01),
+}
+
+
+def batch_regions(w: BatchWorkload, seed: int = 0, count: int | None = None):
+    """[(region, params)] for the batch: params dicts as taken by RoiRecon.solve_batch."""
+    rng = np.random.default_rng(seed + 3000)
+    cell = w.N / w.grid
+    out = []
+    for i in range(w.grid):
+        for j in range(w.grid):
+            cx = (j + 0.5) * cell + rng.uniform(-cell / 4, cell / 4)
+            cy = (i + 0.5) * cell + rng.uniform(-cell / 4, cell / 4)
+            r = float(rng.uniform(w.r_lo, w.r_hi))
+            tv = bool(rng.integers(0, 2))
+            prm = dict(reg=1 if tv else 0, iters=w.iters, lam=w.lam if tv else 0.0)
+            out.append(((float(cx), float(cy), r, r / 2.0), prm))
+    if count is not None:
+        idx = rng.permutation(len(out))[:count]
+        out = [out[k] for k in sorted(idx)]
+    return out
+
+
+def sinogram(w, seed: int = 0) -> np.ndarray:
     """Noisy analytic sinogram of the seeded phantom, float32 [n_angles][n_det]."""
-    ph = synth.random_phantom(w.N, w.n_ellipses, texture=w.texture, seed=seed)
+    ph = synth.random_phantom(w.N, w.n_ellipses, texture=getattr(w, "texture", False), seed=seed)
     p = synth.analytic_sinogram(ph, w.n_angles, w.n_det)
     p = synth.poisson_noise(p, w.I0, seed=seed + 1000)
     return p.astype(np.float32)

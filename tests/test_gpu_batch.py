@@ -127,3 +127,37 @@ def test_batch_argument_errors(setup):
     with pytest.raises(R.RoiError) as e:
         fresh.solve_batch([(128.0, 128.0, 16.0, 8.0)], dict(iters=5))
     assert e.value.status == R.ROI_ESTATE
+
+
+def test_batch_full_geometry_2048_sampled():
+    """The 2048 x 2048 / 180-angle batching geometry: a seeded sample of its regions solved
+    in one batch; the two smallest regions compared with the oracle (10 iterations), every
+    region checked for finiteness and nonnegativity (SIRT)."""
+    from paper_1604_02292_gb300 import workloads as WL
+
+    w = WL.BATCHES["roi_batch_2048"]
+    items = WL.batch_regions(w, seed=0, count=6)
+    items = [(r, dict(prm, iters=10)) for r, prm in items]
+    p = WL.sinogram(w, 0)
+    rr = R.RoiRecon(*w.geometry())
+    rr.set_sinogram(torch.from_numpy(p).cuda())
+    rr.fbp()
+    outs, infos = rr.solve_batch([r for r, _ in items], [prm for _, prm in items])
+    rr.sync()
+    outs = [o.cpu().numpy() for o in outs]
+    for (r, prm), o in zip(items, outs):
+        assert np.isfinite(o).all()
+        if prm["reg"] == R.ROI_SIRT_NONNEG:
+            assert (o >= 0).all()
+    g = oracle.Geometry(*w.geometry())
+    xf = oracle.fbp(g, p.astype(np.float64))
+    smallest = sorted(range(len(items)), key=lambda k: items[k][0][2])[:2]
+    for k in smallest:
+        region, prm = items[k]
+        box = oracle.roi_box(w.N, *region)
+        pp = oracle.exterior(g, box, p.astype(np.float64), xf)
+        if prm["reg"] == R.ROI_SIRT_NONNEG:
+            x = oracle.sirt(g, box, pp, prm["iters"])
+        else:
+            x = oracle.cp_tv(g, box, pp, prm["iters"], prm["lam"], precond=1)
+        assert rel_l2(outs[k], x) <= SOLVE_TOL, k
