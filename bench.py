@@ -36,6 +36,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_1604_02292_gb300 import shard  # noqa: E402
 from paper_1604_02292_gb300 import workloads as WL  # noqa: E402
 
 WORKLOAD = "roi_cptv_1024"
@@ -292,12 +293,8 @@ def run_ours(args):
     launches = R.roi_recon_launch_count() - n0
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_s = sum(step_ms) / 1e3
-    tmax = total_s
-    if dist:
-        t = torch.tensor([total_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tmax = float(t.item())
-    value = ws * args.steps / tmax
+    tmax = shard.max_over_ranks(total_s, dist, device="cuda")
+    value = shard.throughput(args.steps, ws, tmax)
 
     # ---- kernels: per-launch device time from CUDA events recorded inside the solve
     pk, pk_src = peaks()
@@ -352,11 +349,8 @@ def run_ours(args):
                 rr.fbp()
                 rr.solve_local(regions[j], reg, iters=w.iters, lam=w.lam, out=outs_h[j])  # synchronizes
             te = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([te], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
-        e2e = {"value": ws * ke / te, "unit": "solves/s", "h2d_bytes_per_step": int(p_host.nbytes),
+        te = shard.max_over_ranks(te, dist, device="cuda")
+        e2e = {"value": shard.throughput(ke, ws, te), "unit": "solves/s", "h2d_bytes_per_step": int(p_host.nbytes),
                "d2h_bytes_per_step": int(outs_h[0].nbytes), "steps": ke}
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, one GPU only)
@@ -414,9 +408,15 @@ def run_batch(args):
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     w = WL.BATCHES[args.workload]
-    p = WL.sinogram(w, seed=rank)
-    items = WL.batch_regions(w, seed=rank, count=args.batch_count)
+    p = WL.sinogram(w, seed=0)
+    all_items = WL.batch_regions(w, seed=0, count=args.batch_count)
+    share = shard.assign([shard.region_cost(r, prm["iters"], w.n_angles) for r, prm in all_items], ws)[rank]
+    items = [all_items[i] for i in share]
     regions = [r for r, _ in items]
     params = [prm for _, prm in items]
     stream = torch.cuda.Stream()
@@ -439,24 +439,30 @@ def run_batch(args):
         torch.cuda.synchronize()
     rr.sync()
     ms = [a.elapsed_time(b) for a, b in ev]
+    if dist:
+        dist.barrier()
     n_lerps = 0
     for reg, prm in items:
         pl = rr.plan(reg)
         nx, ny = pl.box[2], pl.box[3]
         n_lerps += prm["iters"] * (sum(pl.width) * max(nx, ny) + nx * ny * w.n_angles)
-    t = sum(ms) / 1e3
+    t = shard.max_over_ranks(sum(ms) / 1e3, dist, device="cuda")
     line = {
-        "metric": "roi_solves_per_s", "value": len(items) * args.steps / t, "unit": "solves/s", "n_gpus": 1,
+        "metric": "roi_solves_per_s", "value": len(all_items) * args.steps / t, "unit": "solves/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(ms), "higher_is_better": True,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w.name, "N": w.N, "n_angles": w.n_angles, "n_det": w.n_det, "regions": len(items),
+        "scaling": "strong",
+        "config": {"workload": w.name, "N": w.N, "n_angles": w.n_angles, "n_det": w.n_det, "regions": len(all_items),
                    "radius": [w.r_lo, w.r_hi], "iters": w.iters, "solvers": "SIRT/TV 50/50"},
         "gpu_launches": int(R.roi_recon_launch_count() - n0),
-        "projector_Glerp_s": n_lerps * args.steps / t / 1e9,
+        "projector_Glerp_s_rank0": n_lerps * args.steps / t / 1e9,
         "clocks": clk.summary(),
     }
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     rr.close()
+    if dist:
+        dist.destroy_process_group()
     return 0
 
 
