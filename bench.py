@@ -55,9 +55,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WL.WORKLOADS) + sorted(WL.BATCHES))
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=sorted(WL.WORKLOADS) + sorted(WL.BATCHES) + sorted(WL.SERVING))
     ap.add_argument("--batch-count", type=int, default=None,
                     help="batch workloads: solve this many of the regions per step (default: all)")
+    ap.add_argument("--requests", type=int, default=256, help="serving workloads: requests in the run")
+    ap.add_argument("--rate", type=float, default=None, help="serving workloads: arrival rate (default: workload's)")
+    ap.add_argument("--team-blocks", type=int, default=0, help="serving: blocks per team (0: library default)")
+    ap.add_argument("--teams", type=int, default=-1, help="serving: teams (-1: library default)")
+    ap.add_argument("--large-side", type=int, default=0, help="serving: box side served by teams (0: default)")
+    ap.add_argument("--no-plain", action="store_true", help="serving: skip the one-at-a-time comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -466,12 +473,144 @@ def run_batch(args):
     return 0
 
 
+def _pct(v, q):
+    v = sorted(v)
+    if not v:
+        return None
+    k = min(len(v) - 1, max(0, int(math.ceil(q / 100.0 * len(v))) - 1))
+    return v[k]
+
+
+def run_serve(args):
+    """Serving workload: the requests arrive by a seeded Poisson process and are submitted
+    to the server (continuous batching over resident sinograms) at their arrival times;
+    latency = completion seen on the host - arrival.  The same requests are then solved
+    one at a time with roi_recon_solve_local (FP32, whole GPU per request, host output)
+    in arrival order ("plain"), each starting at max(arrival, previous completion).
+    Times are host monotonic clocks; results land in host memory in both arms."""
+    import torch
+
+    import paper_1604_02292_gb300 as R
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = WL.SERVING[args.workload]
+    count = args.requests
+    reqs = WL.serve_requests(w, seed=0, count=count)
+    arr = WL.arrivals(w, seed=0, count=count, rate=args.rate)
+    mine = [i for i in range(count) if i % ws == rank]
+    recons = []
+    for k in range(w.n_sinos):
+        rr = R.RoiRecon(*w.geometry())
+        rr.set_sinogram(torch.from_numpy(WL.sinogram(w, k)).cuda())
+        rr.fbp()
+        recons.append(rr)
+    torch.cuda.synchronize()
+    srv = R.Server(team_blocks=args.team_blocks, teams=args.teams, large_side=args.large_side)
+    for rr in recons:
+        srv.add(rr)
+    # warm-up: a few short requests through both paths (first launch, ring allocation)
+    for sino, reg, prm in WL.serve_requests(w, seed=99, count=max(args.warmup, 1)):
+        rid = srv.submit(sino, reg, dict(prm, iters=5))
+        recons[sino].solve_local(reg, reg=prm["reg"], iters=5, lam=prm["lam"])
+    srv.drain()
+    for c in srv.poll():
+        srv.take(c["id"], (c["box"][3], c["box"][2]))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    # ---- served
+    n0 = R.roi_recon_launch_count()
+    lat, done, who = [], {}, {}
+    nbytes = 0
+    with ClockSampler(local) as clk:
+        t0 = time.monotonic()
+        i = 0
+        while len(done) < len(mine):
+            now = time.monotonic()
+            while i < len(mine) and t0 + arr[mine[i]] <= now:
+                k = mine[i]
+                sino, reg, prm = reqs[k]
+                who[srv.submit(sino, reg, prm)] = k
+                i += 1
+            got = srv.poll()
+            for c in got:
+                if c["status"] != R.ROI_OK:
+                    raise R.RoiError(c["status"], "served request failed")
+                k = who[c["id"]]
+                x = srv.take(c["id"], (c["box"][3], c["box"][2]))
+                nbytes += x.nbytes
+                done[k] = c
+                lat.append(c["t_done_ms"] - (t0 + arr[k]) * 1e3)
+            if not got:
+                time.sleep(50e-6)
+        t_served = max(c["t_done_ms"] for c in done.values()) / 1e3 - t0
+    st = srv.stats()
+    srv.close()
+    launches = int(R.roi_recon_launch_count() - n0)
+    # ---- plain: one request at a time, whole GPU, in arrival order
+    plain = None
+    if not args.no_plain:
+        plat = []
+        t0 = time.monotonic()
+        for k in mine:
+            a = t0 + arr[k]
+            while time.monotonic() < a:
+                time.sleep(20e-6)
+            sino, reg, prm = reqs[k]
+            pl = recons[sino].plan(reg)
+            out = np.empty((pl.box[3], pl.box[2]), np.float32)
+            recons[sino].solve_local(reg, reg=prm["reg"], iters=prm["iters"], lam=prm["lam"], out=out)
+            plat.append((time.monotonic() - a) * 1e3)
+        t_plain = time.monotonic() - t0
+        t_plain = shard.max_over_ranks(t_plain, dist, device="cuda")
+        plain = {"value": count / t_plain, "unit": "solves/s", "p50_ms": _pct(plat, 50), "p99_ms": _pct(plat, 99),
+                 "mean_ms": statistics.mean(plat)}
+    t_served = shard.max_over_ranks(t_served, dist, device="cuda")
+    n_lerps = 0
+    for k in mine:
+        sino, reg, prm = reqs[k]
+        pl = recons[sino].plan(reg)
+        nx, ny = pl.box[2], pl.box[3]
+        n_lerps += prm["iters"] * (sum(pl.width) * max(nx, ny) + nx * ny * w.n_angles)
+    line = {
+        "metric": "roi_solves_per_s_served", "value": count / t_served, "unit": "solves/s", "n_gpus": ws,
+        "steps": 1, "warmup": args.warmup, "ms_per_step": t_served * 1e3, "higher_is_better": True,
+        "dtype": "f32", "data": "synthetic", "scaling": "strong",
+        "config": {"workload": w.name, "N": w.N, "n_angles": w.n_angles, "n_det": w.n_det, "sinograms": w.n_sinos,
+                   "requests": count, "rate_per_s": args.rate or w.rate, "radius": [w.r_lo, w.r_hi],
+                   "iters": w.iters, "solvers": "SIRT/TV 50/50", "timing": "host monotonic clock, arrival to result"},
+        "latency_ms": {"p50": _pct(lat, 50), "p99": _pct(lat, 99), "mean": statistics.mean(lat)},
+        "plain": plain,
+        "server": {k: st[k] for k in ("blocks", "single_units", "teams", "team_blocks", "kernel_launches",
+                                      "device_peak", "host_peak")},
+        "e2e": {"value": count / t_served, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": nbytes},
+        "gpu_launches": launches,
+        "projector_Glerp_s_rank0": n_lerps / t_served / 1e9,
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for rr in recons:
+        rr.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload in WL.BATCHES:
         return run_batch(args)
+    if args.workload in WL.SERVING:
+        return run_serve(args)
     return run_ours(args)
 
 

@@ -152,12 +152,15 @@ roi_status roi_recon_solve_local(roi_recon_t h, const roi_region* region, const 
  * SIRT and CP may be mixed; CP must use precond = 1; eval_objective is ignored), outs[n]:
  * [box_h][box_w] float32 each, device pointers when out_on_device = 1, host memory
  * otherwise (the call then synchronizes).  infos (optional) [n] receive each plan.
- * All exterior windows are computed by one batched projection and all solves by one
- * persistent launch whose blocks each solve whole regions, largest first.  A region's
- * result is bit-identical whatever else is in the batch; it agrees with
- * roi_recon_solve_local to rounding (a different split of the same sums).  Device memory:
- * the angle tables (144 N_theta bytes per region), all windows, and scratch per SM for
- * the largest region.  ROI_ESTATE before fbp, ROI_EINVAL naming the offending region. */
+ * One persistent launch solves everything: its blocks each take whole regions, largest
+ * first, exterior step included -- p' = (p - W x_fbp) + W_L x_fbp on the box, which is
+ * p - W_F x_fbp by Eq. locouter, with the residual p - W x_fbp of every ray computed once
+ * per FBP.  A region's result is bit-identical whatever else is in the batch and equals
+ * the serving path's (roi_server_*); it agrees with roi_recon_solve_local to rounding (a
+ * different split of the same sums).  Device memory: the residual (4 N_theta N_d bytes,
+ * kept with the FBP image), the angle tables (about 90 N_theta bytes per region), and
+ * scratch per SM for the largest region.  ROI_ESTATE before fbp, ROI_EINVAL naming the
+ * offending region. */
 roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions, const roi_solve_params* params,
                                  float* const* outs, int out_on_device, roi_solve_info* infos);
 
@@ -231,6 +234,105 @@ roi_status roi_recon_kernel_times(roi_recon_t h, int kernel, int* launches, doub
 
 /* Number of CUDA kernels this library has launched in this process (all handles). */
 unsigned long long roi_recon_launch_count(void);
+
+/* --------------------------------------------------------------------------
+ * Serving: continuous batching of ROI requests over resident sinograms
+ * ------------------------------------------------------------------------ */
+
+/* A server solves ROI requests (each the Sec. 1 scheme on one region of one resident
+ * sinogram, Sec. 4.4: regions are independent) while more keep arriving.  One
+ * cooperative kernel runs while there is work: its blocks form units -- single blocks
+ * for small boxes, teams of team_blocks blocks for boxes of side >= large_side -- that
+ * take requests from rings in page-locked host memory mapped into the device, so a
+ * request submitted while others are on the GPU starts as soon as a unit is free,
+ * without a launch.  The host side (a progress engine, run by a background thread after
+ * roi_server_start or by explicit roi_server_progress calls) admits requests in arrival
+ * order while their state fits the device budget and their results fit the page-locked
+ * result area, publishes them, polls completion words and recycles memory; the kernel
+ * leaves after idle_us without work and is relaunched when work arrives.
+ * A request's result is bit-identical whichever unit solves it and whatever runs beside
+ * it, and equals roi_recon_solve_batch's for the same region (same exterior form).
+ * Threads: submit / poll / take / stats may be called from any thread; the server
+ * serialises them internally. */
+typedef struct roi_server* roi_server_t;
+
+typedef struct {
+    size_t device_bytes;   /* HBM budget for the state of admitted requests (0: 4 GiB) */
+    size_t host_bytes;     /* page-locked result area (0: 512 MiB) */
+    int ring_slots;        /* request slots per unit pool (0: 1024) */
+    int team_blocks;       /* blocks per team of the large-box pool (0: 8) */
+    int teams;             /* teams (-1: about 3/4 of the blocks; 0: no team pool) */
+    int large_side;        /* box side from which a request goes to the team pool (0: 320) */
+    int idle_us;           /* the kernel leaves after this long without work (0: 2000) */
+} roi_server_config;
+
+typedef struct {
+    long long id;          /* as returned by roi_server_submit */
+    roi_status status;     /* ROI_OK, or ROI_ETIMEOUT when a device wait gave up */
+    int sino;
+    int box_x0, box_y0, box_w, box_h;
+    int pool;              /* 0: one block, 1: a team */
+    double t_submit_ms;    /* host monotonic clock (CLOCK_MONOTONIC), milliseconds */
+    double t_publish_ms;   /* admitted and published to the device */
+    double t_done_ms;      /* completion seen by the host */
+} roi_server_completion;
+
+typedef struct {
+    long long submitted, completed, failed, pending, in_flight;
+    long long kernel_launches;
+    size_t device_in_use, device_peak, host_in_use, host_peak;
+    int blocks, single_units, teams, team_blocks;
+} roi_server_stats;
+
+/* Creates a server on the current device (it owns a non-blocking stream).  cfg may be
+ * NULL (defaults).  ROI_EINVAL for bad sizes, ROI_ENOMEM when the budgets cannot be
+ * allocated. */
+roi_status roi_server_create(const roi_server_config* cfg, roi_server_t* out);
+
+/* Registers the resident sinogram and FBP image of handle h (fbp done; ROI_ESTATE
+ * otherwise) and computes its residual p - W x_fbp; *sino_id receives its index.  The
+ * handle must outlive the server and its sinogram must not change while registered.
+ * All sinograms must be added before the first submit. */
+roi_status roi_server_add_sinogram(roi_server_t s, roi_recon_t h, int* sino_id);
+
+/* Queues one request (params as for roi_recon_solve_batch: CP needs precond = 1).
+ * Plans it on the host; *id receives its id.  ROI_EINVAL for a bad sinogram id,
+ * region or params; ROI_ENOMEM when its state or result could never fit the budgets. */
+roi_status roi_server_submit(roi_server_t s, int sino_id, const roi_region* region, const roi_solve_params* params,
+                             long long* id);
+
+/* Starts / stops the background progress thread. */
+roi_status roi_server_start(roi_server_t s);
+roi_status roi_server_stop(roi_server_t s);
+
+/* One pass of the progress engine (admission, publication, completion, relaunch) for
+ * callers that do not start the thread. */
+roi_status roi_server_progress(roi_server_t s);
+
+/* Moves up to max completion records into out; returns how many (0 if none, -1 on a
+ * bad argument). */
+int roi_server_poll(roi_server_t s, roi_server_completion* out, int max);
+
+/* Copies the result of completed request id ([box_h][box_w] float32) into host memory
+ * dst (may be NULL to discard) and releases it.  ROI_EBUSY if not complete yet,
+ * ROI_EINVAL for an unknown id, the request's own status if it failed. */
+roi_status roi_server_take(roi_server_t s, long long id, float* dst);
+
+/* Waits (running progress itself when the thread is not started) until every submitted
+ * request has completed or timeout_ms has passed (ROI_EBUSY then). */
+roi_status roi_server_drain(roi_server_t s, double timeout_ms);
+
+roi_status roi_server_stats_get(roi_server_t s, roi_server_stats* out);
+const char* roi_server_last_error(roi_server_t s);
+
+/* Stops the thread, tells the kernel to leave once the requests it holds are done, waits
+ * for it and frees everything; results not taken are dropped. */
+void roi_server_destroy(roi_server_t s);
+
+/* Host only (no GPU): the device-state and result bytes the server budgets for a request
+ * on a sinogram of n_pix / n_angles / n_det, and its box side. */
+roi_status roi_server_footprint(int n_pix, int n_angles, int n_det, const roi_region* region,
+                                size_t* device_bytes, size_t* host_bytes, int* box_side);
 
 /* --------------------------------------------------------------------------
  * Allocation-free variant

@@ -30,6 +30,10 @@ __all__ = [
     "roi_recon_kernel_times", "roi_recon_launch_count", "roi_recon_forward_local_noalloc",
     "roi_recon_set_option", "roi_recon_sync", "ROI_OPT_SINGLE_LAUNCH", "ROI_OPT_WAIT_LIMIT_US",
     "ROI_OPT_TEST_ABSENT_BLOCKS", "RoiRecon", "plan",
+    "ServerConfig", "ServerCompletion", "ServerStats", "Server", "server_footprint",
+    "roi_server_create", "roi_server_destroy", "roi_server_add_sinogram", "roi_server_submit",
+    "roi_server_start", "roi_server_stop", "roi_server_progress", "roi_server_poll", "roi_server_take",
+    "roi_server_drain", "roi_server_stats_get", "roi_server_last_error", "roi_server_footprint",
 ]
 
 ROI_OK, ROI_EINVAL, ROI_ENOMEM, ROI_ESTATE, ROI_ECUDA, ROI_ETIMEOUT, ROI_EBUSY = range(7)
@@ -63,6 +67,28 @@ class SolveInfo(ctypes.Structure):
                 ("iters_done", ctypes.c_int), ("step_L", ctypes.c_double), ("objective", ctypes.c_double)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("device_bytes", ctypes.c_size_t), ("host_bytes", ctypes.c_size_t), ("ring_slots", ctypes.c_int),
+                ("team_blocks", ctypes.c_int), ("teams", ctypes.c_int), ("large_side", ctypes.c_int),
+                ("idle_us", ctypes.c_int)]
+
+
+class ServerCompletion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_longlong), ("status", ctypes.c_int), ("sino", ctypes.c_int),
+                ("box_x0", ctypes.c_int), ("box_y0", ctypes.c_int), ("box_w", ctypes.c_int),
+                ("box_h", ctypes.c_int), ("pool", ctypes.c_int), ("t_submit_ms", ctypes.c_double),
+                ("t_publish_ms", ctypes.c_double), ("t_done_ms", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong),
+                ("pending", ctypes.c_longlong), ("in_flight", ctypes.c_longlong),
+                ("kernel_launches", ctypes.c_longlong), ("device_in_use", ctypes.c_size_t),
+                ("device_peak", ctypes.c_size_t), ("host_in_use", ctypes.c_size_t), ("host_peak", ctypes.c_size_t),
+                ("blocks", ctypes.c_int), ("single_units", ctypes.c_int), ("teams", ctypes.c_int),
+                ("team_blocks", ctypes.c_int)]
+
+
 # every symbol declared in include/roi_recon.h
 EXPORTS = [
     "roi_recon_create", "roi_recon_destroy", "roi_recon_last_error", "roi_recon_set_sinogram",
@@ -70,6 +96,9 @@ EXPORTS = [
     "roi_recon_forward_local", "roi_recon_back_local", "roi_recon_ramp_filter",
     "roi_recon_set_timing", "roi_recon_kernel_times", "roi_recon_launch_count",
     "roi_recon_forward_local_noalloc", "roi_recon_set_option", "roi_recon_sync", "roi_recon_solve_batch",
+    "roi_server_create", "roi_server_add_sinogram", "roi_server_submit", "roi_server_start", "roi_server_stop",
+    "roi_server_progress", "roi_server_poll", "roi_server_take", "roi_server_drain", "roi_server_stats_get",
+    "roi_server_last_error", "roi_server_destroy", "roi_server_footprint",
 ]
 
 _lib = None
@@ -128,6 +157,32 @@ def lib() -> ctypes.CDLL:
                                                 ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
                                                 ctypes.POINTER(SolveInfo)]
             L.roi_recon_solve_batch.restype = st
+            L.roi_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(_H)]
+            L.roi_server_create.restype = st
+            L.roi_server_add_sinogram.argtypes = [_H, _H, ctypes.POINTER(ctypes.c_int)]
+            L.roi_server_add_sinogram.restype = st
+            L.roi_server_submit.argtypes = [_H, ctypes.c_int, ctypes.POINTER(Region), ctypes.POINTER(SolveParams),
+                                            ctypes.POINTER(ctypes.c_longlong)]
+            L.roi_server_submit.restype = st
+            for name in ("roi_server_start", "roi_server_stop", "roi_server_progress"):
+                getattr(L, name).argtypes = [_H]
+                getattr(L, name).restype = st
+            L.roi_server_poll.argtypes = [_H, ctypes.POINTER(ServerCompletion), ctypes.c_int]
+            L.roi_server_poll.restype = ctypes.c_int
+            L.roi_server_take.argtypes = [_H, ctypes.c_longlong, _P]
+            L.roi_server_take.restype = st
+            L.roi_server_drain.argtypes = [_H, ctypes.c_double]
+            L.roi_server_drain.restype = st
+            L.roi_server_stats_get.argtypes = [_H, ctypes.POINTER(ServerStats)]
+            L.roi_server_stats_get.restype = st
+            L.roi_server_last_error.argtypes = [_H]
+            L.roi_server_last_error.restype = ctypes.c_char_p
+            L.roi_server_destroy.argtypes = [_H]
+            L.roi_server_destroy.restype = None
+            L.roi_server_footprint.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Region),
+                                               ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
+                                               ctypes.POINTER(ctypes.c_int)]
+            L.roi_server_footprint.restype = st
             _lib = L
     return _lib
 
@@ -218,6 +273,68 @@ def roi_recon_solve_batch(h, regions, params, outs, out_on_device: int, infos=No
     """regions, params: ctypes arrays (Region * n, SolveParams * n); outs: (c_void_p * n) pointers."""
     n = len(regions)
     return lib().roi_recon_solve_batch(h, n, regions, params, outs, int(out_on_device), infos)
+
+
+def roi_server_create(cfg: ServerConfig | None):
+    h = _H()
+    s = lib().roi_server_create(ctypes.byref(cfg) if cfg is not None else None, ctypes.byref(h))
+    return s, h.value
+
+
+def roi_server_destroy(s) -> None:
+    lib().roi_server_destroy(s)
+
+
+def roi_server_add_sinogram(s, h):
+    i = ctypes.c_int(-1)
+    st = lib().roi_server_add_sinogram(s, h, ctypes.byref(i))
+    return st, i.value
+
+
+def roi_server_submit(s, sino: int, region: Region, params: SolveParams):
+    i = ctypes.c_longlong(0)
+    st = lib().roi_server_submit(s, int(sino), ctypes.byref(region), ctypes.byref(params), ctypes.byref(i))
+    return st, i.value
+
+
+def roi_server_start(s) -> int:
+    return lib().roi_server_start(s)
+
+
+def roi_server_stop(s) -> int:
+    return lib().roi_server_stop(s)
+
+
+def roi_server_progress(s) -> int:
+    return lib().roi_server_progress(s)
+
+
+def roi_server_poll(s, out, max_n: int) -> int:
+    """out: (ServerCompletion * k) array, k >= max_n."""
+    return lib().roi_server_poll(s, out, int(max_n))
+
+
+def roi_server_take(s, rid: int, dst: int | None) -> int:
+    return lib().roi_server_take(s, int(rid), dst or None)
+
+
+def roi_server_drain(s, timeout_ms: float) -> int:
+    return lib().roi_server_drain(s, float(timeout_ms))
+
+
+def roi_server_stats_get(s, out: ServerStats) -> int:
+    return lib().roi_server_stats_get(s, ctypes.byref(out))
+
+
+def roi_server_last_error(s) -> str:
+    return (lib().roi_server_last_error(s) or b"").decode()
+
+
+def roi_server_footprint(n_pix: int, n_angles: int, n_det: int, region: Region):
+    dev, host, side = ctypes.c_size_t(0), ctypes.c_size_t(0), ctypes.c_int(0)
+    st = lib().roi_server_footprint(int(n_pix), int(n_angles), int(n_det), ctypes.byref(region), ctypes.byref(dev),
+                                    ctypes.byref(host), ctypes.byref(side))
+    return st, dev.value, host.value, side.value
 
 
 # ---- convenience layer -----------------------------------------------------------------
@@ -431,3 +548,112 @@ class RoiRecon:
             q = self._torch.empty((self.n_angles, self.n_det), dtype=self._torch.float32, device="cuda")
         self._check(roi_recon_ramp_filter(self.h, self._dev(q, (self.n_angles, self.n_det))))
         return q
+
+
+def _params(p: dict) -> SolveParams:
+    return SolveParams(int(p.get("reg", ROI_SIRT_NONNEG)), float(p.get("lam", 0.0)), int(p.get("iters", 200)),
+                       int(p.get("weighting", 0)), 1, int(p.get("crop_disk", 0)), 0)
+
+
+def server_footprint(N, n_angles, n_det, region):
+    """(device_bytes, host_bytes, box_side) the server budgets for a request; host only."""
+    st, dev, host, side = roi_server_footprint(N, n_angles, n_det, Region(*map(float, region)))
+    if st != ROI_OK:
+        raise RoiError(st, "roi_server_footprint failed")
+    return dev, host, side
+
+
+class Server:
+    """ROI server over resident sinograms (continuous batching; see roi_server_* in the C header).
+
+    ``add(recon)`` registers a RoiRecon whose FBP is done; ``submit(sino, region, params)``
+    queues a request and returns its id; ``poll()`` returns completion records (dicts);
+    ``take(id)`` returns the result as a float32 numpy array [box_h][box_w].
+    """
+
+    def __init__(self, device_bytes=0, host_bytes=0, ring_slots=0, team_blocks=0, teams=-1, large_side=0,
+                 idle_us=0, start=True):
+        cfg = ServerConfig(int(device_bytes), int(host_bytes), int(ring_slots), int(team_blocks), int(teams),
+                           int(large_side), int(idle_us))
+        st, s = roi_server_create(cfg)
+        if st != ROI_OK:
+            raise RoiError(st, "roi_server_create failed")
+        self.s = s
+        self._recons = []
+        self._buf = (ServerCompletion * 256)()
+        self._start = bool(start)
+        self._started = False
+
+    def _check(self, st):
+        if st != ROI_OK:
+            raise RoiError(st, roi_server_last_error(self.s))
+
+    def add(self, recon) -> int:
+        st, i = roi_server_add_sinogram(self.s, recon.h)
+        self._check(st)
+        self._recons.append(recon)
+        return i
+
+    def start(self):
+        self._check(roi_server_start(self.s))
+        self._started = True
+
+    def stop(self):
+        self._check(roi_server_stop(self.s))
+        self._started = False
+
+    def progress(self):
+        self._check(roi_server_progress(self.s))
+
+    def submit(self, sino: int, region, params: dict | None = None) -> int:
+        st, rid = roi_server_submit(self.s, sino, Region(*map(float, region)), _params(params or {}))
+        self._check(st)
+        if self._start and not self._started:
+            self.start()
+        return rid
+
+    def poll(self):
+        out = []
+        while True:
+            n = roi_server_poll(self.s, self._buf, len(self._buf))
+            if n < 0:
+                raise RoiError(ROI_EINVAL, "roi_server_poll failed")
+            for c in self._buf[:n]:
+                out.append(dict(id=c.id, status=c.status, sino=c.sino, box=(c.box_x0, c.box_y0, c.box_w, c.box_h),
+                                pool=c.pool, t_submit_ms=c.t_submit_ms, t_publish_ms=c.t_publish_ms,
+                                t_done_ms=c.t_done_ms))
+            if n < len(self._buf):
+                return out
+
+    def take(self, rid: int, shape=None):
+        import numpy as np
+        if shape is None:
+            raise ValueError("take: pass the (box_h, box_w) shape from the completion record")
+        out = np.empty(shape, np.float32)
+        self._check(roi_server_take(self.s, rid, out.ctypes.data))
+        return out
+
+    def drain(self, timeout_ms: float = 600000.0):
+        self._check(roi_server_drain(self.s, timeout_ms))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        self._check(roi_server_stats_get(self.s, st))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "s", None):
+            roi_server_destroy(self.s)
+            self.s = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -111,12 +111,16 @@ struct roi_recon {
     int sms = 0;
     // batched solves: per-region tables / windows / descriptors, per-block slots, pinned staging
     DevBufT<AngleRec> b_tab;
-    DevBuf b_win, b_out;
+    DevBuf b_out;
     DevBufT<roi::BatchRoi> b_rois;
-    DevBufT<roi::ExtItem> b_items;
     DevBufT<int> b_order;
     DevBufT<int> b_queue;
-    DevBuf s_u, s_sig, s_x, s_vx, s_vy, s_tau, s_xa, s_xaT;
+    DevBuf s_pp, s_u, s_sig, s_x, s_vx, s_vy, s_tau, s_xa, s_xaT;
+    // residual p - W x_fbp over every ray, [na][resid_ld] (exterior step of the
+    // whole-region solvers, Eq. locouter); valid while resid_ready
+    DevBuf resid;
+    int resid_ld = 0;
+    int resid_ready = 0;
     unsigned char* pin = nullptr;  // page-locked staging of the uploads
     size_t pin_cap = 0;
     cudaEvent_t pin_free = nullptr;  // recorded after the last upload from `pin`
@@ -321,6 +325,43 @@ roi_status rowcol_sums(roi_recon* h, float* cols) {
     return ROI_OK;
 }
 
+// Residual p - W x_fbp of every ray (full detector, no hole), computed once per FBP.
+roi_status ensure_residual(roi_recon* h) {
+    if (h->resid_ready) return ROI_OK;
+    h->resid_ld = roi::round_stride(h->nd);
+    CU(h, h->resid.ensure((size_t)h->na * h->resid_ld));
+    roi::FwdArgs a{};
+    a.rec = h->rec_fbp;
+    a.na = h->na;
+    a.stride = h->resid_ld;
+    a.nx = h->N;
+    a.ny = h->N;
+    a.img = h->xfbp;
+    a.imgT = h->xfbpT;
+    a.img_ld = roi::padded_ld(h->N);
+    a.imgT_ld = roi::padded_ld(h->N);
+    a.hole = Rect{0, 0, 0, 0};
+    a.out = h->resid.p;
+    a.p = h->p;
+    a.nd = h->nd;
+    roi::launch_forward(roi::FWD_EXTERIOR, a, h->st);
+    LAUNCHED(h, "residual reprojection");
+    h->resid_ready = 1;
+    return ROI_OK;
+}
+
+// The exterior inputs of a whole-region solve (pointers into the handle).
+void exterior_inputs(const roi_recon* h, roi::BatchRoi& R, Rect box) {
+    R.resid = h->resid.p;
+    R.resid_ld = h->resid_ld;
+    R.xfbp = h->xfbp;
+    R.xfbpT = h->xfbpT;
+    R.xfbp_ld = roi::padded_ld(h->N);
+    R.box_x0 = box.x0;
+    R.box_y0 = box.y0;
+    R.alpha = (float)(1.0 / ((double)h->na * h->nd));
+}
+
 roi_status run_exterior(roi_recon* h) {
     roi::FwdArgs a{};
     a.rec = h->rec_ext;
@@ -517,6 +558,36 @@ roi_status solve_cp(roi_recon* h, const roi_solve_params* prm, double* L_out) {
 
 }  // namespace
 
+namespace roi {
+// The server's view of a handle's resident data; computes the residual and waits for
+// it (the server works on its own stream).  Returns a roi_status.
+int sino_view(roi_recon* h, SinoView* v, std::string* msg) {
+    if (!h->have_fbp) {
+        *msg = "no FBP image (call fbp first)";
+        return ROI_ESTATE;
+    }
+    roi_status s = ensure_residual(h);
+    if (s == ROI_OK) {
+        cudaError_t e = cudaStreamSynchronize(h->st);
+        if (e != cudaSuccess) s = cuda_fail(h, e, "residual reprojection");
+    }
+    if (s != ROI_OK) {
+        *msg = h->err;
+        return s;
+    }
+    v->N = h->N;
+    v->na = h->na;
+    v->nd = h->nd;
+    v->angles = h->angles.data();
+    v->xfbp = h->xfbp;
+    v->xfbpT = h->xfbpT;
+    v->xfbp_ld = roi::padded_ld(h->N);
+    v->resid = h->resid.p;
+    v->resid_ld = h->resid_ld;
+    return ROI_OK;
+}
+}  // namespace roi
+
 extern "C" {
 
 roi_status roi_recon_create(const roi_geometry* geom, void* cuda_stream, roi_recon_t* out) {
@@ -598,11 +669,10 @@ void roi_recon_destroy(roi_recon_t h) {
     if (h->d_err) cudaFree(h->d_err);
     h->b_tab.release();
     h->b_rois.release();
-    h->b_items.release();
     h->b_order.release();
     h->b_queue.release();
-    for (DevBuf* b : {&h->b_win, &h->b_out, &h->s_u, &h->s_sig, &h->s_x, &h->s_vx, &h->s_vy, &h->s_tau, &h->s_xa,
-                      &h->s_xaT})
+    for (DevBuf* b : {&h->b_out, &h->s_pp, &h->s_u, &h->s_sig, &h->s_x, &h->s_vx, &h->s_vy, &h->s_tau, &h->s_xa,
+                      &h->s_xaT, &h->resid})
         b->release();
     if (h->pin) cudaFreeHost(h->pin);
     if (h->pin_free) cudaEventDestroy(h->pin_free);
@@ -626,6 +696,7 @@ roi_status roi_recon_set_sinogram(roi_recon_t h, const void* p, roi_dtype dt, in
     h->have_sino = true;
     h->have_fbp = false;
     h->exterior_ready = 0;
+    h->resid_ready = 0;
     return ROI_OK;
 }
 
@@ -663,6 +734,7 @@ roi_status roi_recon_fbp(roi_recon_t h, float* out_or_null) {
                                 sizeof(float) * h->N, h->N, cudaMemcpyDeviceToDevice, h->st));
     h->have_fbp = true;
     h->exterior_ready = 0;
+    h->resid_ready = 0;
     return ROI_OK;
 }
 
@@ -818,16 +890,13 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
     if (n == 0) return ROI_OK;
     if (!h->have_fbp) return fail(h, ROI_ESTATE, "solve_batch: no FBP image (call fbp first)");
     const int na = h->na;
-    const Rect grid{0, 0, h->N, h->N};
     // ---- host plan of every region
     std::vector<Rect> boxes(n);
-    std::vector<int> strides(n), nrows(n);
-    std::vector<AngleRec> loc(na), ext(na);
-    std::vector<int> perm(na);
-    size_t win_total = 0, out_total = 0, win_cap = 0, img_cap = 0, pad_cap = 0, max_smem_img = 0;
-    int stride_max = 0;
+    std::vector<int> strides(n);
+    size_t out_total = 0, win_cap = 0, img_cap = 0, pad_cap = 0, max_smem_img = 0;
     const size_t smem_img_limit = std::min<size_t>(200 * 1024, h->max_smem_optin > 4096 ? h->max_smem_optin - 4096 : 0);
     std::vector<double> cost(n);
+    std::vector<AngleRec> loc(na);
     for (int i = 0; i < n; ++i) {
         const roi_solve_params& P = params[i];
         if (!finite_region(&regions[i]))
@@ -845,8 +914,6 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
         const int wl = roi::plan_angles(h->N, na, h->nd, h->angles.data(), box, box, false, loc.data());
         boxes[i] = box;
         strides[i] = roi::round_stride(wl);
-        stride_max = std::max(stride_max, strides[i]);
-        win_total += (size_t)na * strides[i];
         out_total += (size_t)box.w * box.h;
         win_cap = std::max(win_cap, (size_t)na * strides[i]);
         img_cap = std::max(img_cap, (size_t)box.w * box.h);
@@ -855,23 +922,23 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
         if (sizeof(float) * std::max(pr, pc) <= smem_img_limit) max_smem_img = std::max(max_smem_img, std::max(pr, pc));
         cost[i] = (double)box.w * box.h * na * (double)std::max(P.iters, 1);
     }
+    roi_status s0 = ensure_residual(h);
+    if (s0 != ROI_OK) return s0;
     // ---- device storage
-    CU(h, h->b_tab.ensure((size_t)n * 2 * na));
-    CU(h, h->b_win.ensure(win_total));
+    CU(h, h->b_tab.ensure((size_t)n * na));
     CU(h, h->b_rois.ensure(n));
-    CU(h, h->b_items.ensure(n));
     CU(h, h->b_order.ensure(n));
     CU(h, h->b_queue.ensure(1));
     if (!out_on_device) CU(h, h->b_out.ensure(out_total));
     const int blocks = std::max(1, h->sms);
-    for (DevBuf* b : {&h->s_u, &h->s_sig}) CU(h, b->ensure(win_cap * blocks));
+    for (DevBuf* b : {&h->s_pp, &h->s_u, &h->s_sig}) CU(h, b->ensure(win_cap * blocks));
     for (DevBuf* b : {&h->s_x, &h->s_vx, &h->s_vy, &h->s_tau}) CU(h, b->ensure(img_cap * blocks));
     for (DevBuf* b : {&h->s_xa, &h->s_xaT}) CU(h, b->ensure(pad_cap * blocks));
-    // ---- page-locked staging: tables, descriptors, items, order
-    const size_t tab_bytes = sizeof(AngleRec) * (size_t)n * 2 * na;
-    const size_t roi_bytes = sizeof(roi::BatchRoi) * (size_t)n, item_bytes = sizeof(roi::ExtItem) * (size_t)n;
+    // ---- page-locked staging: tables, descriptors, order
+    const size_t tab_bytes = sizeof(AngleRec) * (size_t)n * na;
+    const size_t roi_bytes = sizeof(roi::BatchRoi) * (size_t)n;
     const size_t ord_bytes = sizeof(int) * (size_t)n;
-    const size_t pin_need = tab_bytes + roi_bytes + item_bytes + ord_bytes;
+    const size_t pin_need = tab_bytes + roi_bytes + ord_bytes;
     CU(h, cudaEventSynchronize(h->pin_free));  // the previous uploads have left the staging area
     if (pin_need > h->pin_cap) {
         if (h->pin) cudaFreeHost(h->pin);
@@ -882,30 +949,16 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
     }
     AngleRec* ptab = reinterpret_cast<AngleRec*>(h->pin);
     roi::BatchRoi* prois = reinterpret_cast<roi::BatchRoi*>(h->pin + tab_bytes);
-    roi::ExtItem* pitems = reinterpret_cast<roi::ExtItem*>(h->pin + tab_bytes + roi_bytes);
-    int* pord = reinterpret_cast<int*>(h->pin + tab_bytes + roi_bytes + item_bytes);
-    size_t woff = 0, ooff = 0;
+    int* pord = reinterpret_cast<int*>(h->pin + tab_bytes + roi_bytes);
+    size_t ooff = 0;
     for (int i = 0; i < n; ++i) {
         const Rect box = boxes[i];
-        roi::plan_angles(h->N, na, h->nd, h->angles.data(), box, box, false, loc.data());
-        roi::plan_angles(h->N, na, h->nd, h->angles.data(), grid, box, false, ext.data());
-        // per-row-branch angles first (stable), the same order for both tables
         int nr = 0;
-        for (int a = 0; a < na; ++a)
-            if (loc[a].row) perm[nr++] = a;
-        int k = nr;
-        for (int a = 0; a < na; ++a)
-            if (!loc[a].row) perm[k++] = a;
-        AngleRec* tl = ptab + (size_t)i * 2 * na;
-        AngleRec* te = tl + na;
-        for (int a = 0; a < na; ++a) {
-            tl[a] = loc[perm[a]];
-            te[a] = ext[perm[a]];
-        }
+        const int wl = roi::plan_region_table(h->N, na, h->nd, h->angles.data(), box, ptab + (size_t)i * na, &nr);
         const roi_solve_params& P = params[i];
         roi::BatchRoi& R = prois[i];
-        R.rec = h->b_tab.p + (size_t)i * 2 * na;
-        R.pp = h->b_win.p + woff;
+        R = roi::BatchRoi{};
+        R.rec = h->b_tab.p + (size_t)i * na;
         R.out = out_on_device ? outs[i] : h->b_out.p + ooff;
         R.na = na;
         R.nrow = nr;
@@ -921,12 +974,7 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
         R.cxl = (float)(regions[i].cx - box.x0);
         R.cyl = (float)(regions[i].cy - box.y0);
         R.r2 = (float)(regions[i].radius * regions[i].radius);
-        roi::ExtItem& it = pitems[i];
-        it.rec = h->b_tab.p + (size_t)i * 2 * na + na;
-        it.stride = strides[i];
-        it.hole = box;
-        it.out = h->b_win.p + woff;
-        woff += (size_t)na * strides[i];
+        exterior_inputs(h, R, box);
         ooff += (size_t)box.w * box.h;
         pord[i] = i;
         if (infos) {
@@ -934,8 +982,7 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
             infos[i].box_y0 = box.y0;
             infos[i].box_w = box.w;
             infos[i].box_h = box.h;
-            infos[i].window_max = 0;
-            for (int a = 0; a < na; ++a) infos[i].window_max = std::max(infos[i].window_max, loc[a].width);
+            infos[i].window_max = wl;
             infos[i].window_stride = strides[i];
             infos[i].iters_done = P.iters;
             infos[i].step_L = 0.0;
@@ -945,28 +992,15 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
     std::stable_sort(pord, pord + n, [&](int a, int b) { return cost[a] > cost[b]; });
     CU(h, cudaMemcpyAsync(h->b_tab.p, ptab, tab_bytes, cudaMemcpyHostToDevice, h->st));
     CU(h, cudaMemcpyAsync(h->b_rois.p, prois, roi_bytes, cudaMemcpyHostToDevice, h->st));
-    CU(h, cudaMemcpyAsync(h->b_items.p, pitems, item_bytes, cudaMemcpyHostToDevice, h->st));
     CU(h, cudaMemcpyAsync(h->b_order.p, pord, ord_bytes, cudaMemcpyHostToDevice, h->st));
     CU(h, cudaEventRecord(h->pin_free, h->st));
-    // ---- exterior windows of every region
-    roi::FwdArgs fa{};
-    fa.na = na;
-    fa.nx = h->N;
-    fa.ny = h->N;
-    fa.img = h->xfbp;
-    fa.imgT = h->xfbpT;
-    fa.img_ld = roi::padded_ld(h->N);
-    fa.imgT_ld = roi::padded_ld(h->N);
-    fa.p = h->p;
-    fa.nd = h->nd;
-    roi::launch_forward_batch(fa, h->b_items.p, n, stride_max, h->st);
-    LAUNCHED(h, "batched exterior reprojection");
-    // ---- all solves in one persistent launch
+    // ---- all solves, exterior steps included, in one persistent launch
     roi::BatchArgs B{};
     B.rois = h->b_rois.p;
     B.order = h->b_order.p;
     B.nroi = n;
     B.queue = h->b_queue.p;
+    B.slot_pp = h->s_pp.p;
     B.slot_u = h->s_u.p;
     B.slot_sig = h->s_sig.p;
     B.win_cap = win_cap;
@@ -978,7 +1012,6 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
     B.slot_xa = h->s_xa.p;
     B.slot_xaT = h->s_xaT.p;
     B.pad_cap = pad_cap;
-    B.alpha = (float)(1.0 / ((double)na * h->nd));
     B.smem_img_bytes = (int)(sizeof(float) * max_smem_img);
     B.err = h->d_err;
     B.wait_ns = h->opt_wait_ns;

@@ -68,6 +68,17 @@ __device__ __forceinline__ int to_fixed(ff v) {
     return ((int)n << F) + __float2int_rn(fr * (float)(1 << F));
 }
 
+// Float-float coordinate v split into its integer part j0 and the Q.22 fixed-point offset
+// from j0 (the return value, in [0, 2^22] up to rounding): any grid size fits, and
+// (j0 << 22) + offset is what to_fixed<22>(v) gives wherever that does not overflow
+// (|v| < 2^9).
+__device__ __forceinline__ int split_fixed22(ff v, int& j0) {
+    const float n = floorf(v.hi);
+    j0 = (int)n;
+    const float fr = (v.hi - n) + v.lo;
+    return __float2int_rn(fr * 4194304.0f);
+}
+
 // The F <= 23 fraction bits of a Q.F number as an integer-valued float in [0, 2^F):
 // OR-ing them into the mantissa of 2^23 and subtracting 2^23 is exact (one logic op and
 // one add, no conversion instruction).

@@ -21,8 +21,8 @@
 //
 // Inner loops run in fixed point, so they need no float-to-integer conversion (a
 // quarter-rate instruction on this GPU): along a ray the interpolation coordinate is
-// a Q.22 integer re-anchored from float-float every 24 samples and stepped by
-// round(slope 2^22); across a gather tile row the window coordinate is a Q.23 integer
+// an integer column plus a Q.22 offset, re-anchored from float-float every 24 samples
+// and stepped by round(slope 2^22); across a gather tile row the window coordinate is a Q.23 integer
 // stepped by round(cos 2^23).  The fraction bits become a float by the exponent trick
 // (one logic op and one add).  Position errors stay below 3e-6 pixel.
 //
@@ -171,11 +171,12 @@ __device__ __forceinline__ ff ray_segment(const AngleRec& r, int k, int seg, int
     mhi = min(mhi, min(s0 + seg_len, M));
     const int step = r.slope_q22;
     for (int m0 = mlo; m0 < mhi; m0 += SEGA) {
-        int q = to_fixed<22>(ff_add(Ak, ff_mul_f((float)m0 - halfM, r.slope)));  // sample m0
+        int j0;
+        int q = split_fixed22(ff_add(Ak, ff_mul_f((float)m0 - halfM, r.slope)), j0);  // sample m0
         const int mend = min(m0 + SEGA, mhi);
         // sum of v0 + f (v1 - v0) with f = mf 2^-22: the two parts are summed separately
         float s0 = 0.f, s1 = 0.f;
-        const float* rp = img + m0 * ld;
+        const float* rp = img + m0 * ld + j0;
 #pragma unroll 4
         for (int m = m0; m < mend; ++m, rp += ld, q += step) {
             const int j = q >> 22;

@@ -12,6 +12,7 @@
 // a ray whose weight rounds to zero on the GPU is still kept).
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "roi_internal.h"
 
@@ -71,6 +72,21 @@ int plan_angles(int N, int na, int nd, const double* angles, Rect frame, Rect ta
         wmax = std::max(wmax, width);
     }
     return wmax;
+}
+
+// Box-frame table of a region for the whole-region solvers: the angles sampled per row
+// first, then the others (stable); AngleRec::aidx keeps each angle's index in the
+// sinogram.  Returns the largest window width.
+int plan_region_table(int N, int na, int nd, const double* angles, Rect box, AngleRec* out, int* nrow) {
+    std::vector<AngleRec> loc(na);
+    const int wl = plan_angles(N, na, nd, angles, box, box, false, loc.data());
+    int k = 0;
+    for (int a = 0; a < na; ++a)
+        if (loc[a].row) out[k++] = loc[a];
+    *nrow = k;
+    for (int a = 0; a < na; ++a)
+        if (!loc[a].row) out[k++] = loc[a];
+    return wl;
 }
 
 }  // namespace roi

@@ -51,15 +51,8 @@ constexpr int TARGET_THREADS = 152 * 2048;
 // |m - anchor| <= 8 are formed in float.  Sums: float within a segment, Neumaier
 // carry across segments, float-float across the S threads of a ray.
 template <int MODE>
-__global__ void __launch_bounds__(FWD_RAYS* FWD_MAXSEG) k_forward(FwdArgs A) {
+__global__ void __launch_bounds__(FWD_RAYS* FWD_MAXSEG) k_forward(const FwdArgs A) {
     __shared__ float red_s[FWD_MAXSEG][FWD_RAYS];
-    if (MODE == FWD_EXTERIOR && A.items) {  // batched: this block's region
-        const ExtItem& it = A.items[blockIdx.z];
-        A.rec = it.rec;
-        A.stride = it.stride;
-        A.hole = it.hole;
-        A.out = it.out;
-    }
     __shared__ float red_c[FWD_MAXSEG][FWD_RAYS];
     const int a = blockIdx.y;
     const int k = blockIdx.x * FWD_RAYS + threadIdx.x;
@@ -401,17 +394,6 @@ void launch_forward(FwdMode mode, const FwdArgs& a0, cudaStream_t st) {
         case FWD_SIRT: k_forward<FWD_SIRT><<<grid, block, 0, st>>>(a); break;
         case FWD_CP: k_forward<FWD_CP><<<grid, block, 0, st>>>(a); break;
     }
-}
-
-void launch_forward_batch(const FwdArgs& a0, const ExtItem* items, int nroi, int stride_max, cudaStream_t st) {
-    if (a0.na <= 0 || stride_max <= 0 || nroi <= 0) return;
-    FwdArgs a = a0;
-    a.items = items;
-    a.stride = stride_max;  // sizes the segment split; each block uses its region's stride
-    const int S = forward_segments(a.na, stride_max, a.nx, a.ny, &a.seg_len);
-    dim3 grid((stride_max + FWD_RAYS - 1) / FWD_RAYS, a.na, nroi), block(FWD_RAYS, S);
-    count_launches(1);
-    k_forward<FWD_EXTERIOR><<<grid, block, 0, st>>>(a);
 }
 
 void launch_back(BackMode mode, const BackArgs& a, cudaStream_t st) {

@@ -1,0 +1,462 @@
+// region_solver.cuh -- one whole local solve by a team of blocks (device code shared by
+// the batched solver and the serving kernel).
+//
+// A region (paper Sec. 1 scheme on the extended box L, Sec. 2.1 operators W_L, W_L^T)
+// is solved end to end by a team of `size` blocks of 1024 threads:
+//   exterior   p' = (p - W x_fbp) + W_L x_fbp|_L  (Eq. locouter: W_F = W - W_L); the
+//              residual p - W x_fbp of every ray is computed once per sinogram, so a
+//              region costs one local forward projection of the box of x_fbp;
+//   set-up     row sums W_L 1 and column sums W_L^T 1 (SIRT weights, CP steps);
+//   iterations SIRT (Eq. sirtit with the clamp of Eq. sirtbox) or Chambolle-Pock TV
+//              (Eq. priorsys), each as
+//     phase A  forward W_L: warps take 32-ray units (one angle); a warp sums whole rays
+//              (fixed point along the ray) and fuses the residual (SIRT) or data-dual
+//              (CP) update; CP also updates the gradient dual on every pixel;
+//     phase B  back W_L^T: warps take 16 x 16 pixel tiles; a lane owns a run of 8
+//              pixels, angles are streamed in chunks of 16 (per-warp staging of the
+//              window bins), and the lane applies the primal update to its pixels.
+// The units and tiles of a phase are dealt round-robin to the blocks of the team and
+// picked up dynamically by the warps of a block.  Every ray and every tile is computed
+// by one warp in a fixed order, so a region's result is bit-identical whatever team
+// solves it, whatever else runs beside it and however the work is dealt.
+//
+// A team of one block synchronises with __syncthreads and may stage the box image in
+// shared memory (one TMA bulk copy per branch and iteration); larger teams read the
+// image from global memory and meet at a barrier counter with bounded waits.  Data
+// written by one block of a team and read by another is ordered by that barrier's
+// release / acquire at GPU scope.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dev_common.cuh"
+#include "roi_internal.h"
+
+namespace roi {
+namespace rs {
+
+constexpr int BPT = 1024;
+constexpr int BNW = BPT / 32;
+constexpr int SEGB = 24;     // samples per float-float anchor
+constexpr int TB = 16;       // tile side
+constexpr int RUNB = 8;      // pixels per lane
+constexpr int ACH = 16;      // angles per staging chunk (one per lane of the first half-warp)
+// Tile pixels lie within sqrt(7.5^2 + 7.5^2) = 10.61 bins of the tile centre; the hat
+// reaches one bin further, so with kbase = floor(kappa_centre) - 12 every staged index
+// touched is in [0, 24] < SBB.
+constexpr int KOFFB = 12;
+constexpr int SBB = 26;      // staged bins per angle
+constexpr int WARP_STAGE = ACH * SBB + 3 * ACH * 2;  // floats per warp in phase B (bins + consts)
+
+enum PassA { A_SOLVE = 0, A_ROWSUM = 1, A_EXTER = 2 };
+enum PassB { B_SOLVE = 0, B_COLSUM = 1 };
+
+// A team of blocks solving one region.
+struct Team {
+    int member, size;          // this block's index in the team, team size
+    unsigned* bar;             // monotonic arrival counter (size > 1), zeroed at launch
+    unsigned nbar;             // barriers passed by this block (thread 0's copy is used)
+    int* err;
+    unsigned long long wait_ns;
+};
+
+// Team barrier.  false: a wait gave up (error flag set) and the caller must leave.
+// SOLO: the team is one block (known at compile time).
+template <bool SOLO>
+__device__ __forceinline__ bool team_sync(Team& T) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (SOLO || T.size == 1) return true;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        ++T.nbar;
+        const unsigned target = T.nbar * (unsigned)T.size;
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(T.bar) : "memory");
+        unsigned long long t0 = 0;
+        for (unsigned polls = 1;; ++polls) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(T.bar) : "memory");
+            if ((int)(v - target) >= 0) break;
+            if ((polls & 255u) == 0) {
+                const unsigned long long now = global_ns();
+                if (t0 == 0) {
+                    t0 = now;
+                } else if (now - t0 > T.wait_ns) {
+                    atomicExch(T.err, 1);
+                    ok = 0;
+                    break;
+                }
+                if (*(volatile int*)T.err) {
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+using roi::RegionBufs;
+
+struct Ctx {
+    const BatchRoi* R;
+    RegionBufs b;
+    float* xa;     // padded row image, element (0,0)
+    float* xaT;    // padded column image, element (0,0)
+    int lda, ldaT;
+    int nchunk;
+    int gtid, gthreads;   // thread index / count over the team
+    bool smem_img;
+};
+
+// Whole-ray Joseph sum of ray k (fixed point along the ray).  Samples whose minor
+// coordinate lies in [-1.5, Mm + 0.5] are visited, so both taps stay inside the padded
+// row; every SEGB samples the position is re-anchored from float-float as an integer
+// column plus a Q.22 offset from it (the offset stays below 2^31 whatever the box size).
+__device__ __forceinline__ ff ray_full(const AngleRec& r, int k, int M, int Mm, const float* img, int ld) {
+    float sum = 0.f, cmp = 0.f;
+    const float halfM = 0.5f * (float)(M - 1);
+    const ff Ak = ff_add(r.A0, ff_mul_f((float)k, r.a_scale));
+    int mlo = 0, mhi = M;
+    if (!r.flat) {
+        const float ma = (-1.5f - Ak.hi) * r.inv_slope + halfM;
+        const float mb = ((float)Mm + 0.5f - Ak.hi) * r.inv_slope + halfM;
+        const float lo = fminf(ma, mb), hi = fmaxf(ma, mb);
+        mlo = (int)fminf(fmaxf(0.f, ceilf(lo)), (float)M);
+        mhi = (int)fmaxf(fminf((float)M, floorf(hi) + 1.f), 0.f);
+    } else if (!(Ak.hi >= -1.5f && Ak.hi <= (float)Mm + 0.5f)) {
+        mhi = 0;
+    }
+    const int step = r.slope_q22;
+    for (int m0 = mlo; m0 < mhi; m0 += SEGB) {
+        int j0;
+        int q = split_fixed22(ff_add(Ak, ff_mul_f((float)m0 - halfM, r.slope)), j0);
+        const int mend = min(m0 + SEGB, mhi);
+        float s0 = 0.f, s1 = 0.f;
+        const float* rp = img + (size_t)m0 * ld + j0;
+#pragma unroll 4
+        for (int m = m0; m < mend; ++m, rp += ld, q += step) {
+            const int j = q >> 22;
+            const float mf = frac_int<22>(q);
+            const float v0 = rp[j], v1 = rp[j + 1];
+            s0 += v0;
+            s1 = fmaf(mf, v1 - v0, s1);
+        }
+        neu_add(sum, cmp, fmaf(s1, 2.384185791015625e-07f, s0));
+    }
+    return two_sum(sum, cmp);
+}
+
+// Phase A over the units of one branch (row = 1: per-row sampling; the table lists those
+// angles first).  This block's units are ustart + member + i * size; warps take i from
+// *counter (preset to BNW by the caller, warp w starting at i = w).
+template <bool SOLO>
+__device__ __forceinline__ void phase_a_branch(const Ctx& C, const Team& T, int row, const float* img, int ld,
+                                               int pass, int* counter) {
+    const int tm = SOLO ? 0 : T.member, ts = SOLO ? 1 : T.size;
+    const BatchRoi& R = *C.R;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int M = row ? R.ny : R.nx, Mm = row ? R.nx : R.ny;
+    const int ustart = row ? 0 : R.nrow * C.nchunk;
+    const int uend = (row ? R.nrow : R.na) * C.nchunk;
+    for (int i = warp;;) {
+        const int unit = ustart + tm + i * ts;
+        if (unit >= uend) break;
+        const int a = unit / C.nchunk;
+        const int k = (unit - a * C.nchunk) * 32 + lane;
+        const AngleRec& r = R.rec[a];
+        if (k < r.width) {
+            ff tot = ray_full(r, k, M, Mm, img, ld);
+            tot = ff_mul_f(r.inv_w, tot);
+            const size_t o = (size_t)a * R.stride + k;
+            if (pass == A_EXTER) {  // p' = (p - W x_fbp) + W_L x_fbp
+                const ff d = two_sum(R.resid[(size_t)r.aidx * R.resid_ld + r.d0 + k], tot.hi);
+                C.b.pp[o] = d.hi + (d.lo + tot.lo);
+            } else {
+                const float acc = tot.hi + tot.lo;
+                if (pass == A_ROWSUM) {
+                    const float thr = R.reg == 0 ? 1e-3f : 1e-6f;
+                    C.b.sig[o] = acc > thr ? 1.f / acc : 0.f;
+                } else if (R.reg == 0) {
+                    float res = C.b.pp[o] - acc;
+                    if (R.weighting) res *= C.b.sig[o];
+                    C.b.u[o] = res;
+                } else {
+                    const float sg = C.b.sig[o];
+                    C.b.u[o] = (C.b.u[o] + sg * (acc - C.b.pp[o])) / (1.f + 0.5f * sg);
+                }
+            }
+        }
+        int nxt = 0;
+        if (lane == 0) nxt = atomicAdd(counter, 1);
+        i = __shfl_sync(0xffffffffu, nxt, 0);
+    }
+}
+
+// Phase B: this block's tiles are member + i * size, warps take i from *counter (preset
+// to BNW); lane = run of 8 pixels.  wstage: this warp's shared area.
+template <bool SOLO>
+__device__ __forceinline__ void phase_b(const Ctx& C, const Team& T, int pass, int* counter, float* wstage) {
+    const int tm = SOLO ? 0 : T.member, ts = SOLO ? 1 : T.size;
+    const BatchRoi& R = *C.R;
+    const int lane = threadIdx.x & 31;
+    const int nx = R.nx, ny = R.ny;
+    const int tiles_x = (nx + TB - 1) / TB, tiles = tiles_x * ((ny + TB - 1) / TB);
+    float* st = wstage;                                            // [ACH][SBB]
+    int* cb = reinterpret_cast<int*>(wstage + ACH * SBB);          // [ACH] base (Q.23)
+    int* cc = cb + ACH;                                            // [ACH] c step
+    int* cs = cc + ACH;                                            // [ACH] s step
+    float* ciw = reinterpret_cast<float*>(cs + ACH);               // [ACH] 1/w
+    int* ckb = reinterpret_cast<int*>(ciw + ACH);                  // [ACH] kbase
+    int* cwd = ckb + ACH;                                          // [ACH] width
+    const int li = lane >> 1, lj0 = (lane & 1) * RUNB;
+    for (int i = threadIdx.x >> 5;;) {
+        const int t = tm + i * ts;
+        if (t >= tiles) break;
+        const int tile_x0 = (t % tiles_x) * TB, tile_y0 = (t / tiles_x) * TB;
+        const float xi_t = (float)tile_x0 + 0.5f * (TB - 1) - 0.5f * (float)(nx - 1);
+        const float eta_t = 0.5f * (float)(ny - 1) - ((float)tile_y0 + 0.5f * (TB - 1));
+        float sum[RUNB], cmp[RUNB];
+#pragma unroll
+        for (int p = 0; p < RUNB; ++p) sum[p] = cmp[p] = 0.f;
+        for (int a0 = 0; a0 < R.na; a0 += ACH) {
+            const int nch = min(ACH, R.na - a0);
+            __syncwarp();
+            if (lane < nch) {
+                const AngleRec& r = R.rec[a0 + lane];
+                ff kt = ff_add(ff_mul_f(xi_t, r.c), ff_mul_f(eta_t, r.s));
+                kt = ff_add(kt, ff{-r.phi.hi, -r.phi.lo});
+                const int kbase = (int)floorf(kt.hi) - KOFFB;
+                kt = ff_add(kt, ff{-(float)kbase, 0.f});
+                kt = ff_add(kt, ff_mul_f(-0.5f * (TB - 1), r.c));
+                kt = ff_add(kt, ff_mul_f(0.5f * (TB - 1), r.s));
+                cb[lane] = to_fixed<23>(kt);
+                cc[lane] = r.c_q23;
+                cs[lane] = r.s_q23;
+                ciw[lane] = r.inv_w;
+                ckb[lane] = kbase;
+                cwd[lane] = r.width;
+            }
+            __syncwarp();
+            for (int e = lane; e < nch * SBB; e += 32) {
+                const int al = e / SBB, kk = ckb[al] + (e - al * SBB);
+                float v = 0.f;
+                if (kk >= 0 && kk < cwd[al]) v = pass == B_COLSUM ? 1.f : C.b.u[(size_t)(a0 + al) * R.stride + kk];
+                st[e] = v;
+            }
+            __syncwarp();
+            float acc[RUNB];
+#pragma unroll
+            for (int p = 0; p < RUNB; ++p) acc[p] = 0.f;
+            for (int al = 0; al < nch; ++al) {
+                const float iw = ciw[al], iw2 = iw * iw, iwm = iw - iw2;
+                const float iw2s = iw2 * 1.1920928955078125e-07f;
+                const int c = cc[al];
+                int K = cb[al] + lj0 * c - li * cs[al];
+                const float* srow = st + al * SBB;
+#pragma unroll
+                for (int p = 0; p < RUNB; ++p) {
+                    const int kl = K >> 23;
+                    const float mf = frac_int<23>(K);
+                    const float w0 = fmaxf(0.f, fmaf(-mf, iw2s, iw));
+                    const float w1 = fmaxf(0.f, fmaf(mf, iw2s, iwm));
+                    acc[p] = fmaf(w0, srow[kl], fmaf(w1, srow[kl + 1], acc[p]));
+                    K += c;
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < RUNB; ++p) neu_add(sum[p], cmp[p], acc[p]);
+        }
+        // epilogue for this lane's pixels
+        const int gi = tile_y0 + li;
+#pragma unroll
+        for (int p = 0; p < RUNB; ++p) {
+            const int gj = tile_x0 + lj0 + p;
+            if (gi >= ny || gj >= nx) continue;
+            const float acc = sum[p] + cmp[p];
+            const int o = gi * nx + gj;
+            if (pass == B_COLSUM) {
+                if (R.reg == 0) {
+                    C.b.tau[o] = acc > 1e-3f ? 1.f / acc : 0.f;
+                } else {
+                    const int cnt = (gj < nx - 1) + (gj > 0) + (gi < ny - 1) + (gi > 0);
+                    C.b.tau[o] = 1.f / (acc + (float)cnt);
+                }
+            } else if (R.reg == 0) {
+                const float step = R.weighting ? C.b.tau[o] : R.alpha;
+                float xn = fmaf(step, acc, C.xa[gi * C.lda + gj]);
+                xn = fmaxf(xn, 0.f);
+                C.xa[gi * C.lda + gj] = xn;
+                C.xaT[gj * C.ldaT + gi] = xn;
+            } else {
+                float dv = 0.f;
+                if (gj < nx - 1) dv += C.b.vx[o];
+                if (gj > 0) dv -= C.b.vx[o - 1];
+                if (gi < ny - 1) dv += C.b.vy[o];
+                if (gi > 0) dv -= C.b.vy[o - nx];
+                const float xo = C.b.x[o];
+                const float xn = xo - C.b.tau[o] * (acc - dv);
+                C.b.x[o] = xn;
+                const float xb = 2.f * xn - xo;
+                C.xa[gi * C.lda + gj] = xb;
+                C.xaT[gj * C.ldaT + gi] = xb;
+            }
+        }
+        int nxt = 0;
+        if (lane == 0) nxt = atomicAdd(counter, 1);
+        i = __shfl_sync(0xffffffffu, nxt, 0);
+    }
+}
+
+__device__ __forceinline__ void fill_team(const Ctx& C, float* p, size_t n, float v) {
+    for (size_t i = C.gtid; i < n; i += C.gthreads) p[i] = v;
+}
+
+// Interior of both padded images := v, borders 0.
+__device__ __forceinline__ void set_images(const Ctx& C, float v) {
+    const BatchRoi& R = *C.R;
+    const int nx = R.nx, ny = R.ny;
+    for (int i = C.gtid; i < ny * C.lda; i += C.gthreads) {
+        const int col = i % C.lda - kPad;
+        C.b.xa_base[i] = (col >= 0 && col < nx) ? v : 0.f;
+    }
+    for (int i = C.gtid; i < nx * C.ldaT; i += C.gthreads) {
+        const int col = i % C.ldaT - kPad;
+        C.b.xaT_base[i] = (col >= 0 && col < ny) ? v : 0.f;
+    }
+}
+
+// Both padded images := the box of x_fbp (rows from the padded grid image, columns
+// from its padded transpose), borders 0.
+__device__ __forceinline__ void load_fbp_box(const Ctx& C) {
+    const BatchRoi& R = *C.R;
+    const int nx = R.nx, ny = R.ny;
+    for (int i = C.gtid; i < ny * C.lda; i += C.gthreads) {
+        const int r = i / C.lda, col = i - r * C.lda - kPad;
+        C.b.xa_base[i] = (col >= 0 && col < nx) ? R.xfbp[(size_t)(R.box_y0 + r) * R.xfbp_ld + R.box_x0 + col] : 0.f;
+    }
+    for (int i = C.gtid; i < nx * C.ldaT; i += C.gthreads) {
+        const int r = i / C.ldaT, col = i - r * C.ldaT - kPad;
+        C.b.xaT_base[i] =
+            (col >= 0 && col < ny) ? R.xfbpT[(size_t)(R.box_x0 + r) * R.xfbp_ld + R.box_y0 + col] : 0.f;
+    }
+}
+
+// Both branches of phase A reading the images from global memory.
+template <bool SOLO>
+__device__ __forceinline__ void phase_a_global(const Ctx& C, const Team& T, int pass, int* s_cnt) {
+    for (int row = 1; row >= 0; --row) {
+        if (threadIdx.x == 0) *s_cnt = BNW;
+        __syncthreads();
+        phase_a_branch<SOLO>(C, T, row, row ? C.xa : C.xaT, row ? C.lda : C.ldaT, pass, s_cnt);
+        __syncthreads();
+    }
+}
+
+// CP gradient dual on this thread's pixels: v = proj_{|v| <= lambda}(v + sigma_v grad xbar).
+__device__ __forceinline__ void dual_grad(const Ctx& C) {
+    const BatchRoi& R = *C.R;
+    const int nimg = R.nx * R.ny;
+    for (int p = C.gtid; p < nimg; p += C.gthreads) {
+        const int i = p / R.nx, j = p - i * R.nx;
+        const float* xp = C.xa + i * C.lda + j;
+        const float x0 = xp[0];
+        const float gx = j < R.nx - 1 ? xp[1] - x0 : 0.f;
+        const float gy = i < R.ny - 1 ? xp[C.lda] - x0 : 0.f;
+        const float ax = fmaf(R.sigma_v, gx, C.b.vx[p]);
+        const float ay = fmaf(R.sigma_v, gy, C.b.vy[p]);
+        const float m = sqrtf(ax * ax + ay * ay);
+        const float sc = m > R.lambda ? R.lambda / m : 1.f;
+        C.b.vx[p] = ax * sc;
+        C.b.vy[p] = ay * sc;
+    }
+}
+
+// Solve region R into R.out.  smem: dynamic shared memory (the staged image, then the
+// per-warp phase-B areas); images of at most smem_img_bytes are staged when the team is
+// one block.  Returns false when a wait gave up (error flag set): leave the kernel.
+template <bool SOLO>
+__device__ __forceinline__ bool solve_region(const BatchRoi& R, const RegionBufs& bufs, Team& T, float* smem,
+                                             int smem_img_bytes, uint64_t* mbar, unsigned& parity, int* s_cnt) {
+    const int tid = threadIdx.x, warp = tid >> 5;
+    Ctx C;
+    C.R = &R;
+    C.b = bufs;
+    C.lda = padded_ld(R.nx);
+    C.ldaT = padded_ld(R.ny);
+    C.xa = bufs.xa_base + kPad;
+    C.xaT = bufs.xaT_base + kPad;
+    C.nchunk = (R.stride + 31) / 32;
+    C.gtid = T.member * BPT + tid;
+    C.gthreads = T.size * BPT;
+    const size_t nimg = (size_t)R.nx * R.ny, nwin = (size_t)R.na * R.stride;
+    const size_t bytes_row = sizeof(float) * (size_t)R.ny * C.lda;
+    const size_t bytes_col = sizeof(float) * (size_t)R.nx * C.ldaT;
+    C.smem_img = (SOLO || T.size == 1) && (bytes_row > bytes_col ? bytes_row : bytes_col) <= (size_t)smem_img_bytes;
+
+    // ---- exterior: p' on the window rays, zero state
+    fill_team(C, C.b.u, nwin, 0.f);
+    fill_team(C, C.b.x, nimg, 0.f);
+    fill_team(C, C.b.vx, nimg, 0.f);
+    fill_team(C, C.b.vy, nimg, 0.f);
+    load_fbp_box(C);
+    if (!team_sync<SOLO>(T)) return false;
+    phase_a_global<SOLO>(C, T, A_EXTER, s_cnt);
+    // ---- set-up: preconditioners / weights from the row and column sums
+    if (R.reg == 1 || R.weighting) {
+        if (!team_sync<SOLO>(T)) return false;  // the exterior pass has read the images
+        set_images(C, 1.f);
+        if (!team_sync<SOLO>(T)) return false;
+        phase_a_global<SOLO>(C, T, A_ROWSUM, s_cnt);
+        if (tid == 0) *s_cnt = BNW;
+        __syncthreads();
+        phase_b<SOLO>(C, T, B_COLSUM, s_cnt, smem + warp * WARP_STAGE);
+    }
+    if (!team_sync<SOLO>(T)) return false;
+    set_images(C, 0.f);
+    if (!team_sync<SOLO>(T)) return false;
+
+    // ---- iterations
+    for (int it = 0; it < R.iters; ++it) {
+        if (C.smem_img) {
+            for (int row = 1; row >= 0; --row) {
+                if (tid == 0)
+                    bulk_load(smem, row ? bufs.xa_base : bufs.xaT_base, (unsigned)(row ? bytes_row : bytes_col), mbar);
+                if (row == 1 && R.reg == 1) dual_grad(C);  // reads xbar^k while the copy runs
+                if (tid == 0) *s_cnt = BNW;
+                if (!mbar_wait(mbar, parity, T.wait_ns, T.err)) return false;
+                parity ^= 1u;
+                __syncthreads();
+                phase_a_branch<SOLO>(C, T, row, smem + kPad, row ? C.lda : C.ldaT, A_SOLVE, s_cnt);
+                __syncthreads();
+            }
+        } else {
+            if (R.reg == 1) dual_grad(C);
+            phase_a_global<SOLO>(C, T, A_SOLVE, s_cnt);
+        }
+        if (!team_sync<SOLO>(T)) return false;  // u, v of this iteration complete
+        if (tid == 0) *s_cnt = BNW;
+        __syncthreads();
+        phase_b<SOLO>(C, T, B_SOLVE, s_cnt, smem + warp * WARP_STAGE);
+        if (!team_sync<SOLO>(T)) return false;  // x, xbar complete
+    }
+    // ---- crop into the output buffer
+    const float* xs = R.reg == 0 ? C.xa : C.b.x;
+    const int xs_ld = R.reg == 0 ? C.lda : R.nx;
+    for (int p = C.gtid; p < (int)nimg; p += C.gthreads) {
+        const int i = p / R.nx, j = p - i * R.nx;
+        float v = xs[i * xs_ld + j];
+        if (R.crop) {
+            const float dx = (float)j - R.cxl, dy = (float)i - R.cyl;
+            if (dx * dx + dy * dy > R.r2) v = 0.f;
+        }
+        R.out[p] = v;
+    }
+    return true;
+}
+
+}  // namespace rs
+}  // namespace roi

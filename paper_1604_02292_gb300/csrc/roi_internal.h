@@ -12,6 +12,9 @@
 #include <stdint.h>
 
 #include <cmath>
+#include <string>
+
+struct roi_recon;  // the C ABI handle (capi.cu)
 
 namespace roi {
 
@@ -127,6 +130,9 @@ bool plan_box(int N, double cx, double cy, double radius, double margin, Rect* b
 int plan_angles(int N, int na, int nd, const double* angles, Rect frame, Rect target, bool full_detector,
                 AngleRec* rec);
 int round_stride(int wmax);
+// Box-frame table for the whole-region solvers: per-row-branch angles first (stable),
+// aidx = sinogram index; *nrow = their count; returns the largest window width.
+int plan_region_table(int N, int na, int nd, const double* angles, Rect box, AngleRec* out, int* nrow);
 
 // ----------------------------------------------------------------- launchers
 // Process-wide count of kernels launched by the library.
@@ -143,16 +149,7 @@ enum BackMode { BACK_PLAIN = 0, BACK_SIRT = 1, BACK_CP = 2 };
 constexpr int kPad = 2;
 ROI_HD int padded_ld(int extent) { return (extent + 2 * kPad + 3) / 4 * 4; }
 
-// One region of a batched exterior projection (blockIdx.z of k_forward selects it).
-struct ExtItem {
-    const AngleRec* rec;   // grid-frame table of the region's windows
-    int stride;
-    Rect hole;             // the region's box
-    float* out;            // p' window [na][stride]
-};
-
 struct FwdArgs {
-    const ExtItem* items;  // FWD_EXTERIOR only: per-region overrides of rec/stride/hole/out, or null
     const AngleRec* rec;   // [na]
     int na, stride;        // window rows and their stride
     int nx, ny;            // frame size
@@ -260,17 +257,24 @@ size_t persist_smem_bytes(int na, int nx, int ny, int blocks);
 int persist_max_blocks(int na, int nx, int ny, int stride, int device);
 cudaError_t launch_persist(const PersistLaunch& L, cudaStream_t st);
 
-// ---- batched solves: one block per SM pulls regions and solves each one completely
+// ---- whole-region solves by one block (batched) or a team of blocks (serving)
 struct BatchRoi {
     const AngleRec* rec;   // box-frame table, per-row-branch angles first
-    const float* pp;       // p' window [na][stride] (same angle order)
-    float* out;            // result [ny][nx], device
+    float* out;            // result [ny][nx] (device, or page-locked host memory mapped)
     int na, nrow;          // angles; the first nrow sample per row
     int nx, ny, stride;
     int reg, iters, weighting;
     float lambda, sigma_v;
+    float alpha;           // SIRT scalar step 1/(N_theta N_d)
     int crop;
     float cxl, cyl, r2;    // disk crop in box coordinates
+    // exterior inputs: p' = resid + W_L (box of x_fbp)
+    const float* resid;    // p - W x_fbp over every ray [N_theta][resid_ld] (original angle order)
+    int resid_ld;
+    const float* xfbp;     // padded grid image, element (0,0), row stride xfbp_ld
+    const float* xfbpT;    // its padded transpose, same stride
+    int xfbp_ld;
+    int box_x0, box_y0;
 };
 
 struct BatchArgs {
@@ -278,7 +282,8 @@ struct BatchArgs {
     const int* order;      // solve order (largest first)
     int nroi;
     int* queue;            // zeroed by the launcher
-    float* slot_u;         // per-block windows and box buffers
+    float* slot_pp;        // per-block windows and box buffers
+    float* slot_u;
     float* slot_sig;
     size_t win_cap;
     float* slot_x;
@@ -289,14 +294,79 @@ struct BatchArgs {
     float* slot_xa;        // padded images (row / column), from row 0 column -2
     float* slot_xaT;
     size_t pad_cap;
-    float alpha;           // SIRT scalar step 1/(N_theta N_d)
     int smem_img_bytes;    // boxes whose padded image fits here are staged in shared memory
     int* err;
     unsigned long long wait_ns;
 };
+// Device buffers of one whole-region solve: windows [na][stride]; box arrays [ny][nx];
+// padded images from row 0 column -kPad, row strides padded_ld(nx) / padded_ld(ny).
+struct RegionBufs {
+    float* pp;
+    float* u;
+    float* sig;
+    float* x;
+    float* vx;
+    float* vy;
+    float* tau;
+    float* xa_base;
+    float* xaT_base;
+};
+
+// ---- serving: one cooperative launch whose blocks take requests from rings in
+// page-locked host memory (mapped), published by the host while the kernel runs.
+// A ring slot holds a ServeSlot followed (at serve_slot_header_bytes) by the request's
+// box-frame table of `na` AngleRec.
+struct ServeSlot {
+    BatchRoi roi;                  // rec is replaced on the device by the block's copy
+    RegionBufs bufs;
+    unsigned long long seq;        // ticket + 1, written to done[slot] on completion
+};
+constexpr size_t serve_slot_header_bytes = (sizeof(ServeSlot) + 255) / 256 * 256;
+
+struct ServePool {
+    const unsigned char* ring;     // device view of the ring
+    unsigned long long slot_bytes;
+    int slots;
+    int first_block, team, nteams, team_base;
+    unsigned long long* head;      // device memory: next ticket to claim
+    const unsigned long long* tail;  // device view of the host-written count of published tickets
+    unsigned long long* done;      // device view of the per-slot completion words
+};
+
+struct ServeArgs {
+    ServePool pool[2];             // 0: requests solved by one block, 1: by a team of blocks
+    const int* close;              // device view of the host's close flag
+    int* busy;                     // requests being solved (device memory)
+    unsigned long long* last_ns;   // time of the last claim or completion
+    unsigned* bars;                // team barriers, one per team (both pools), zeroed at launch
+    unsigned* mail_seq;            // leader -> members claim mailboxes, zeroed at launch
+    long long* mail_val;
+    AngleRec* rec_slots;           // per-block private copies of the request table [grid][max_na]
+    int max_na;
+    unsigned long long idle_ns;    // leave when nothing was claimed or finished for this long and nothing runs
+    unsigned long long cap_ns;     // longest poll of one block
+    int smem_img_bytes;
+    int* err;
+    unsigned long long wait_ns;
+};
+size_t serve_smem_bytes();
+int serve_max_blocks(int device);  // co-resident blocks of the serving kernel
+cudaError_t launch_serve(const ServeArgs& A, int blocks, cudaStream_t st);
+
+// A resident sinogram as seen by the server (pointers into a roi_recon handle).
+struct SinoView {
+    int N, na, nd;
+    const double* angles;
+    const float* xfbp;
+    const float* xfbpT;
+    int xfbp_ld;
+    const float* resid;
+    int resid_ld;
+};
+
+int sino_view(::roi_recon* h, SinoView* v, std::string* msg);
+
 size_t batch_smem_bytes(size_t max_img_floats);
 cudaError_t launch_batch(const BatchArgs& B, int blocks, size_t smem, cudaStream_t st);
-// Batched exterior projection: items[nroi], grid (ceil(stride_max / 32), na, nroi)
-void launch_forward_batch(const FwdArgs& a, const ExtItem* items, int nroi, int stride_max, cudaStream_t st);
 
 }  // namespace roi

@@ -110,3 +110,57 @@ def region(w: Workload, seed: int = 0, centred: bool = False):
 
 def box_side(w: Workload) -> int:
     return 2 * math.ceil(w.radius + w.margin)
+
+
+@dataclasses.dataclass(frozen=True)
+class ServeWorkload:
+    """ROI requests over resident sinograms: Poisson arrivals, radius log-uniform, margin
+    r / 2, centre uniform in the disk where the ROI lies inside the object, SIRT or TV by a
+    seeded coin."""
+    name: str
+    N: int
+    n_angles: int
+    n_det: int
+    n_ellipses: int
+    I0: float
+    n_sinos: int
+    rate: float           # requests per second
+    r_lo: float
+    r_hi: float
+    iters: int
+    lam: float
+
+    def geometry(self):
+        return self.N, self.n_angles, self.n_det
+
+
+SERVING = {
+    # 8 resident 2048 x 2048 / 180-angle / 2048-bin sinograms (50 ellipses, noise-free);
+    # requests at 2000 / s, radius log-uniform in [16, 256] px, margin r/2, SIRT/TV 50/50,
+    # 200 iterations
+    "roi_serve_2048": ServeWorkload("roi_serve_2048", 2048, 180, 2048, 50, 0.0, 8, 2000.0, 16.0, 256.0, 200, 0.01),
+}
+
+
+def serve_requests(w: ServeWorkload, seed: int = 0, count: int = 256, radii=None):
+    """[(sino, region, params)] in arrival order; radii overrides the drawn radii."""
+    rng = np.random.default_rng(seed + 5000)
+    out = []
+    for i in range(count):
+        r = float(radii[i]) if radii is not None else float(np.exp(rng.uniform(math.log(w.r_lo), math.log(w.r_hi))))
+        rho = (w.N / 2.0 - r) * math.sqrt(rng.uniform(0.0, 1.0))
+        phi = rng.uniform(0.0, 2.0 * math.pi)
+        c = (w.N - 1) / 2.0
+        cx, cy = c + rho * math.cos(phi), c + rho * math.sin(phi)
+        tv = bool(rng.integers(0, 2))
+        prm = dict(reg=1 if tv else 0, iters=w.iters, lam=w.lam if tv else 0.0)
+        out.append((int(rng.integers(0, w.n_sinos)), (cx, cy, r, r / 2.0), prm))
+    return out
+
+
+def arrivals(w: ServeWorkload, seed: int = 0, count: int = 256, rate: float | None = None) -> np.ndarray:
+    """Poisson arrival times in seconds from 0 (exponential gaps at `rate`, default w.rate)."""
+    rng = np.random.default_rng(seed + 6000)
+    gaps = rng.exponential(1.0 / (rate or w.rate), size=count)
+    gaps[0] = 0.0
+    return np.cumsum(gaps)

@@ -18,7 +18,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "roi_recon.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(roi_recon_\w+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(roi_(?:recon|server)_\w+)\s*\(", src)))
 
 
 def test_library_exports_every_declared_symbol():
@@ -96,3 +96,29 @@ def test_poisson_noise_model():
     a = synth.poisson_noise(p, 1e3, seed=3)
     b = synth.poisson_noise(p, 1e3, seed=3)
     assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("region", [(1000.0, 900.0, 16.0, 8.0), (1024.0, 1024.0, 256.0, 128.0),
+                                    (5.0, 2040.0, 100.0, 50.0)])
+def test_server_footprint_host_only(region):
+    """The server's per-request budget: three windows [N_theta][stride], four box arrays and
+    the two padded images, each rounded to 256 bytes; the result area is the box."""
+    N, na, nd = 2048, 180, 2048
+    dev, host, side = R.server_footprint(N, na, nd, region)
+    pl = R.plan(N, na, nd, region)
+    w, h = pl.box[2], pl.box[3]
+    assert side == max(w, h)
+    r256 = lambda n: (n + 255) // 256 * 256
+    ld = lambda e: (e + 4 + 3) // 4 * 4
+    expect = 3 * r256(4 * na * pl.window_stride) + 4 * r256(4 * w * h) + r256(4 * h * ld(w)) + r256(4 * w * ld(h))
+    assert dev == expect
+    assert host == r256(4 * w * h)
+
+
+def test_server_footprint_rejects_bad_input():
+    with pytest.raises(R.RoiError):
+        R.server_footprint(256, 96, 272, (900.0, 900.0, 5.0, 1.0))
+    with pytest.raises(R.RoiError):
+        R.server_footprint(256, 96, 272, (100.0, 100.0, -1.0, 1.0))
+    with pytest.raises(R.RoiError):
+        R.server_footprint(0, 96, 272, (100.0, 100.0, 5.0, 1.0))
