@@ -25,10 +25,13 @@ __global__ void __launch_bounds__(BPT, 1) k_batch(BatchArgs B) {
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
     __shared__ int s_roi, s_cnt;
-    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ __align__(8) uint64_t s_mbar[2];
     const int tid = threadIdx.x;
     const size_t slot = blockIdx.x;
-    if (tid == 0) mbar_init(&s_mbar, 1);
+    if (tid == 0) {
+        mbar_init(&s_mbar[0], 1);
+        mbar_init(&s_mbar[1], 1);
+    }
     unsigned parity = 0;
     rs::Team T{0, 1, nullptr, 0u, B.err, B.wait_ns};
     rs::RegionBufs bufs;
@@ -47,15 +50,15 @@ __global__ void __launch_bounds__(BPT, 1) k_batch(BatchArgs B) {
         __syncthreads();
         const int qi = s_roi;
         if (qi >= B.nroi) break;
-        if (!rs::solve_region<true>(B.rois[B.order[qi]], bufs, T, smem, B.smem_img_bytes, &s_mbar, parity, &s_cnt)) return;
+        if (!rs::solve_region<true>(B.rois[B.order[qi]], bufs, T, smem, s_mbar, parity, &s_cnt)) return;
     }
 }
 
 }  // namespace
 
-size_t batch_smem_bytes(size_t max_img_floats) {
-    const size_t phase_b = (size_t)rs::BNW * rs::WARP_STAGE;
-    return sizeof(float) * std::max(max_img_floats, phase_b);
+size_t batch_smem_bytes(size_t max_stage_bytes) {
+    const size_t phase_b = sizeof(float) * (size_t)rs::BNW * rs::WARP_STAGE;
+    return std::max(max_stage_bytes, phase_b);
 }
 
 cudaError_t launch_batch(const BatchArgs& B, int blocks, size_t smem, cudaStream_t st) {

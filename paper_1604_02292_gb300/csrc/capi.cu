@@ -893,8 +893,7 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
     // ---- host plan of every region
     std::vector<Rect> boxes(n);
     std::vector<int> strides(n);
-    size_t out_total = 0, win_cap = 0, img_cap = 0, pad_cap = 0, max_smem_img = 0;
-    const size_t smem_img_limit = std::min<size_t>(200 * 1024, h->max_smem_optin > 4096 ? h->max_smem_optin - 4096 : 0);
+    size_t out_total = 0, win_cap = 0, img_cap = 0, pad_cap = 0, max_stage = 0;
     std::vector<double> cost(n);
     std::vector<AngleRec> loc(na);
     for (int i = 0; i < n; ++i) {
@@ -919,7 +918,7 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
         img_cap = std::max(img_cap, (size_t)box.w * box.h);
         const size_t pr = (size_t)box.h * roi::padded_ld(box.w), pc = (size_t)box.w * roi::padded_ld(box.h);
         pad_cap = std::max(pad_cap, std::max(pr, pc));
-        if (sizeof(float) * std::max(pr, pc) <= smem_img_limit) max_smem_img = std::max(max_smem_img, std::max(pr, pc));
+        max_stage = std::max(max_stage, roi::stage_bytes(box.w, box.h));
         cost[i] = (double)box.w * box.h * na * (double)std::max(P.iters, 1);
     }
     roi_status s0 = ensure_residual(h);
@@ -1012,10 +1011,9 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
     B.slot_xa = h->s_xa.p;
     B.slot_xaT = h->s_xaT.p;
     B.pad_cap = pad_cap;
-    B.smem_img_bytes = (int)(sizeof(float) * max_smem_img);
     B.err = h->d_err;
     B.wait_ns = h->opt_wait_ns;
-    const size_t smem = roi::batch_smem_bytes(max_smem_img);
+    const size_t smem = roi::batch_smem_bytes(max_stage);
     cudaError_t e;
     {
         Span sp(h, 2);

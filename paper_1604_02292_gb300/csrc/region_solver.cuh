@@ -109,7 +109,7 @@ struct Ctx {
     int lda, ldaT;
     int nchunk;
     int gtid, gthreads;   // thread index / count over the team
-    bool smem_img;
+    int stage;            // stage_mode of the box (0 whole image, 1 bands, 2 global)
 };
 
 // Whole-ray Joseph sum of ray k (fixed point along the ray).  Samples whose minor
@@ -356,6 +356,102 @@ __device__ __forceinline__ void phase_a_global(const Ctx& C, const Team& T, int 
     }
 }
 
+// Phase A of one branch with the image streamed through shared memory in bands of
+// kBandRows rows (two buffers, one bulk copy each, refilled while the other is read).
+// This block's units (ustart + member + i * size) are taken in groups of 32, one per
+// warp; each group walks all bands, each lane accumulating its ray over the samples
+// that fall in the band (one float-float anchor per band and ray), then finishes the
+// ray as phase_a_branch does.  mbar[0..1]: the buffers' barriers, parity: their phase
+// bits (bit b for buffer b).  false: a wait gave up.
+template <bool SOLO>
+__device__ __forceinline__ bool phase_a_banded(const Ctx& C, const Team& T, int row, const float* img_base, int ld,
+                                               float* smem, uint64_t* mbar, unsigned& parity) {
+    const BatchRoi& R = *C.R;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tm = SOLO ? 0 : T.member, ts = SOLO ? 1 : T.size;
+    const int M = row ? R.ny : R.nx, Mm = row ? R.nx : R.ny;
+    const int ustart = row ? 0 : R.nrow * C.nchunk;
+    const int total = (row ? R.nrow : R.na) * C.nchunk - ustart;
+    const int nu = total > tm ? (total - tm + ts - 1) / ts : 0;
+    const int nb = (M + kBandRows - 1) / kBandRows;
+    const int band_floats = kBandRows * ld;
+    const float halfM = 0.5f * (float)(M - 1);
+    for (int g0 = 0; g0 < nu; g0 += BNW) {
+        const int i = g0 + warp;
+        int a = 0, k = 0;
+        bool valid = i < nu;
+        if (valid) {
+            const int unit = ustart + tm + i * ts;
+            a = unit / C.nchunk;
+            k = (unit - a * C.nchunk) * 32 + lane;
+            valid = k < R.rec[a].width;
+        }
+        const AngleRec& r = R.rec[a];
+        ff Ak{0.f, 0.f};
+        int mlo = 0, mhi = 0;
+        if (valid) {
+            Ak = ff_add(r.A0, ff_mul_f((float)k, r.a_scale));
+            mhi = M;
+            if (!r.flat) {
+                const float ma = (-1.5f - Ak.hi) * r.inv_slope + halfM;
+                const float mb = ((float)Mm + 0.5f - Ak.hi) * r.inv_slope + halfM;
+                const float lo = fminf(ma, mb), hi = fmaxf(ma, mb);
+                mlo = (int)fminf(fmaxf(0.f, ceilf(lo)), (float)M);
+                mhi = (int)fmaxf(fminf((float)M, floorf(hi) + 1.f), 0.f);
+            } else if (!(Ak.hi >= -1.5f && Ak.hi <= (float)Mm + 0.5f)) {
+                mhi = 0;
+            }
+        }
+        float sum = 0.f, cmp = 0.f;
+        if (threadIdx.x == 0) {
+            const int rows0 = M < kBandRows ? M : kBandRows;
+            bulk_load(smem, img_base, (unsigned)(sizeof(float) * rows0 * ld), &mbar[0]);
+        }
+        for (int b = 0; b < nb; ++b) {
+            const int bi = b & 1;
+            if (threadIdx.x == 0 && b + 1 < nb) {  // the other buffer was released by the last barrier
+                const int rows = min(kBandRows, M - (b + 1) * kBandRows);
+                bulk_load(smem + (bi ^ 1) * band_floats, img_base + (size_t)(b + 1) * band_floats,
+                          (unsigned)(sizeof(float) * rows * ld), &mbar[bi ^ 1]);
+            }
+            if (!mbar_wait(&mbar[bi], (parity >> bi) & 1u, T.wait_ns, T.err)) return false;
+            parity ^= 1u << bi;
+            const int m0 = max(mlo, b * kBandRows), m1 = min(mhi, (b + 1) * kBandRows);
+            if (valid && m0 < m1) {
+                int j0;
+                int q = split_fixed22(ff_add(Ak, ff_mul_f((float)m0 - halfM, r.slope)), j0);
+                const int step = r.slope_q22;
+                const float* rp = smem + bi * band_floats + (m0 - b * kBandRows) * ld + kPad + j0;
+                float s0 = 0.f, s1 = 0.f;
+#pragma unroll 4
+                for (int m = m0; m < m1; ++m, rp += ld, q += step) {
+                    const int j = q >> 22;
+                    const float mf = frac_int<22>(q);
+                    const float v0 = rp[j], v1 = rp[j + 1];
+                    s0 += v0;
+                    s1 = fmaf(mf, v1 - v0, s1);
+                }
+                neu_add(sum, cmp, fmaf(s1, 2.384185791015625e-07f, s0));
+            }
+            __syncthreads();
+        }
+        if (valid) {
+            ff tot = ff_mul_f(r.inv_w, two_sum(sum, cmp));
+            const float acc = tot.hi + tot.lo;
+            const size_t o = (size_t)a * R.stride + k;
+            if (R.reg == 0) {
+                float res = C.b.pp[o] - acc;
+                if (R.weighting) res *= C.b.sig[o];
+                C.b.u[o] = res;
+            } else {
+                const float sg = C.b.sig[o];
+                C.b.u[o] = (C.b.u[o] + sg * (acc - C.b.pp[o])) / (1.f + 0.5f * sg);
+            }
+        }
+    }
+    return true;
+}
+
 // CP gradient dual on this thread's pixels: v = proj_{|v| <= lambda}(v + sigma_v grad xbar).
 __device__ __forceinline__ void dual_grad(const Ctx& C) {
     const BatchRoi& R = *C.R;
@@ -375,12 +471,12 @@ __device__ __forceinline__ void dual_grad(const Ctx& C) {
     }
 }
 
-// Solve region R into R.out.  smem: dynamic shared memory (the staged image, then the
-// per-warp phase-B areas); images of at most smem_img_bytes are staged when the team is
-// one block.  Returns false when a wait gave up (error flag set): leave the kernel.
+// Solve region R into R.out.  smem: dynamic shared memory, at least stage_bytes(nx, ny)
+// and the per-warp phase-B areas; mbar[0..1]: two initialised mbarriers, parity their
+// phase bits.  Returns false when a wait gave up (error flag set): leave the kernel.
 template <bool SOLO>
 __device__ __forceinline__ bool solve_region(const BatchRoi& R, const RegionBufs& bufs, Team& T, float* smem,
-                                             int smem_img_bytes, uint64_t* mbar, unsigned& parity, int* s_cnt) {
+                                             uint64_t* mbar, unsigned& parity, int* s_cnt) {
     const int tid = threadIdx.x, warp = tid >> 5;
     Ctx C;
     C.R = &R;
@@ -395,7 +491,8 @@ __device__ __forceinline__ bool solve_region(const BatchRoi& R, const RegionBufs
     const size_t nimg = (size_t)R.nx * R.ny, nwin = (size_t)R.na * R.stride;
     const size_t bytes_row = sizeof(float) * (size_t)R.ny * C.lda;
     const size_t bytes_col = sizeof(float) * (size_t)R.nx * C.ldaT;
-    C.smem_img = (SOLO || T.size == 1) && (bytes_row > bytes_col ? bytes_row : bytes_col) <= (size_t)smem_img_bytes;
+    C.stage = stage_mode(R.nx, R.ny);
+    if (C.stage == 0 && !(SOLO || T.size == 1)) C.stage = 2;  // same arithmetic as the staged image
 
     // ---- exterior: p' on the window rays, zero state
     fill_team(C, C.b.u, nwin, 0.f);
@@ -421,18 +518,24 @@ __device__ __forceinline__ bool solve_region(const BatchRoi& R, const RegionBufs
 
     // ---- iterations
     for (int it = 0; it < R.iters; ++it) {
-        if (C.smem_img) {
+        if (C.stage == 0) {
             for (int row = 1; row >= 0; --row) {
                 if (tid == 0)
                     bulk_load(smem, row ? bufs.xa_base : bufs.xaT_base, (unsigned)(row ? bytes_row : bytes_col), mbar);
                 if (row == 1 && R.reg == 1) dual_grad(C);  // reads xbar^k while the copy runs
                 if (tid == 0) *s_cnt = BNW;
-                if (!mbar_wait(mbar, parity, T.wait_ns, T.err)) return false;
+                if (!mbar_wait(mbar, parity & 1u, T.wait_ns, T.err)) return false;
                 parity ^= 1u;
                 __syncthreads();
                 phase_a_branch<SOLO>(C, T, row, smem + kPad, row ? C.lda : C.ldaT, A_SOLVE, s_cnt);
                 __syncthreads();
             }
+        } else if (C.stage == 1) {
+            if (R.reg == 1) dual_grad(C);
+            for (int row = 1; row >= 0; --row)
+                if (!phase_a_banded<SOLO>(C, T, row, row ? bufs.xa_base : bufs.xaT_base, row ? C.lda : C.ldaT, smem,
+                                          mbar, parity))
+                    return false;
         } else {
             if (R.reg == 1) dual_grad(C);
             phase_a_global<SOLO>(C, T, A_SOLVE, s_cnt);

@@ -257,6 +257,30 @@ size_t persist_smem_bytes(int na, int nx, int ny, int blocks);
 int persist_max_blocks(int na, int nx, int ny, int stride, int device);
 cudaError_t launch_persist(const PersistLaunch& L, cudaStream_t st);
 
+// ---- how the whole-region solvers read a box image in the forward projection
+// (a function of the box size alone, so a region's result never depends on where it
+// is solved): 0 = the whole padded image staged in shared memory by one bulk copy
+// (teams read it from global memory instead, with the same arithmetic); 1 = streamed
+// through shared memory in bands of kBandRows rows, double-buffered; 2 = read from
+// global memory.
+constexpr size_t kStageMaxBytes = 200 * 1024;
+constexpr int kBandRows = 24;
+ROI_HD int stage_mode(int nx, int ny) {
+    const size_t lr = (size_t)padded_ld(nx), lc = (size_t)padded_ld(ny);
+    const size_t full = sizeof(float) * (ny * lr > nx * lc ? ny * lr : nx * lc);
+    if (full <= kStageMaxBytes) return 0;
+    const size_t band = sizeof(float) * 2 * kBandRows * (lr > lc ? lr : lc);
+    return band <= kStageMaxBytes ? 1 : 2;
+}
+// Dynamic shared memory the staging of a box of nx x ny needs.
+ROI_HD size_t stage_bytes(int nx, int ny) {
+    const size_t lr = (size_t)padded_ld(nx), lc = (size_t)padded_ld(ny);
+    const int m = stage_mode(nx, ny);
+    if (m == 0) return sizeof(float) * (ny * lr > nx * lc ? ny * lr : nx * lc);
+    if (m == 1) return sizeof(float) * 2 * kBandRows * (lr > lc ? lr : lc);
+    return 0;
+}
+
 // ---- whole-region solves by one block (batched) or a team of blocks (serving)
 struct BatchRoi {
     const AngleRec* rec;   // box-frame table, per-row-branch angles first
@@ -294,7 +318,6 @@ struct BatchArgs {
     float* slot_xa;        // padded images (row / column), from row 0 column -2
     float* slot_xaT;
     size_t pad_cap;
-    int smem_img_bytes;    // boxes whose padded image fits here are staged in shared memory
     int* err;
     unsigned long long wait_ns;
 };
@@ -345,7 +368,6 @@ struct ServeArgs {
     int max_na;
     unsigned long long idle_ns;    // leave when nothing was claimed or finished for this long and nothing runs
     unsigned long long cap_ns;     // longest poll of one block
-    int smem_img_bytes;
     int* err;
     unsigned long long wait_ns;
 };
@@ -366,7 +388,7 @@ struct SinoView {
 
 int sino_view(::roi_recon* h, SinoView* v, std::string* msg);
 
-size_t batch_smem_bytes(size_t max_img_floats);
+size_t batch_smem_bytes(size_t max_stage_bytes);
 cudaError_t launch_batch(const BatchArgs& B, int blocks, size_t smem, cudaStream_t st);
 
 }  // namespace roi

@@ -106,63 +106,73 @@ __global__ void __launch_bounds__(BPT, 1) k_serve(const ServeArgs A) {
     float* smem = reinterpret_cast<float*>(smem4);
     __shared__ int s_cnt;
     __shared__ long long s_claim;
-    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ __align__(8) uint64_t s_mbar[2];
     __shared__ __align__(16) ServeSlot s_slot;
+    __shared__ rs::Team s_team;      // per-block state kept out of registers
+    __shared__ int s_pool;
+    __shared__ unsigned s_mail;
     const int tid = threadIdx.x;
-    const int b = blockIdx.x;
-    const int pi = (A.pool[1].nteams > 0 && b >= A.pool[1].first_block) ? 1 : 0;
-    const ServePool& P = A.pool[pi];
-    const int rel = b - P.first_block;
-    const int team_id = rel / P.team, member = rel - team_id * P.team;
-    if (rel < 0 || team_id >= P.nteams) return;  // not part of a unit
-    const int gteam = P.team_base + team_id;
-    rs::Team T{member, P.team, A.bars + gteam, 0u, A.err, A.wait_ns};
-    if (tid == 0) mbar_init(&s_mbar, 1);
-    unsigned parity = 0, mail_k = 0;
-    AngleRec* myrec = A.rec_slots + (size_t)b * A.max_na;
+    if (tid == 0) {
+        const int b = blockIdx.x;
+        const int pi = (A.pool[1].nteams > 0 && b >= A.pool[1].first_block) ? 1 : 0;
+        const ServePool& P = A.pool[pi];
+        const int rel = b - P.first_block;
+        const int team_id = rel / P.team;
+        s_pool = (rel < 0 || team_id >= P.nteams) ? -1 : pi;  // -1: not part of a unit
+        s_team = rs::Team{rel - team_id * P.team, P.team, A.bars + P.team_base + team_id, 0u, A.err, A.wait_ns};
+        s_mail = 0;
+        mbar_init(&s_mbar[0], 1);
+        mbar_init(&s_mbar[1], 1);
+    }
+    __syncthreads();
+    if (s_pool < 0) return;
+    unsigned parity = 0;
     constexpr int kHeadWords = (int)(sizeof(ServeSlot) / 4);
     for (;;) {
         __syncthreads();
         if (tid == 0) {
+            const ServePool& P = A.pool[s_pool];
+            const int gteam = (int)(s_team.bar - A.bars);
             long long c;
-            if (member == 0) {
+            if (s_team.member == 0) {
                 c = claim_ticket(P, A);
                 if (P.team > 1) {
                     asm volatile("st.relaxed.gpu.global.s64 [%0], %1;" ::"l"(A.mail_val + gteam), "l"(c) : "memory");
-                    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(A.mail_seq + gteam), "r"(mail_k + 1)
+                    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(A.mail_seq + gteam), "r"(s_mail + 1)
                                  : "memory");
                 }
             } else {
-                c = wait_mail(A, gteam, mail_k + 1);
+                c = wait_mail(A, gteam, s_mail + 1);
             }
-            ++mail_k;
+            ++s_mail;
             s_claim = c;
         }
         __syncthreads();
         const long long c = s_claim;
         if (c < 0) return;
+        const ServePool& P = A.pool[s_pool];
         const size_t slot = (size_t)(c % P.slots);
         const unsigned char* sp = P.ring + slot * P.slot_bytes;
+        AngleRec* myrec = A.rec_slots + (size_t)blockIdx.x * A.max_na;
         // descriptor and table out of the page-locked ring (system-scope loads)
         for (int w = tid; w < kHeadWords; w += BPT)
             reinterpret_cast<unsigned*>(&s_slot)[w] = ld_relaxed_sys_u32(sp + 4 * (size_t)w);
         __syncthreads();
-        const int na = s_slot.roi.na;
-        const int rec_words = na * (int)(sizeof(AngleRec) / 4);
+        const int rec_words = s_slot.roi.na * (int)(sizeof(AngleRec) / 4);
         const unsigned char* rp = sp + serve_slot_header_bytes;
         for (int w = tid; w < rec_words; w += BPT)
             reinterpret_cast<unsigned*>(myrec)[w] = ld_relaxed_sys_u32(rp + 4 * (size_t)w);
         if (tid == 0) s_slot.roi.rec = myrec;
         __syncthreads();
-        const bool ok =
-            P.team == 1 ? rs::solve_region<true>(s_slot.roi, s_slot.bufs, T, smem, A.smem_img_bytes, &s_mbar, parity, &s_cnt)
-                        : rs::solve_region<false>(s_slot.roi, s_slot.bufs, T, smem, A.smem_img_bytes, &s_mbar, parity,
-                                                  &s_cnt);
+        const bool ok = s_team.size == 1 ? rs::solve_region<true>(s_slot.roi, s_slot.bufs, s_team, smem, s_mbar, parity, &s_cnt)
+                                         : rs::solve_region<false>(s_slot.roi, s_slot.bufs, s_team, smem, s_mbar, parity,
+                                                                   &s_cnt);
         if (!ok) return;
         __threadfence_system();  // this thread's output stores, before the completion word
-        if (!rs::team_sync<false>(T)) return;
-        if (member == 0 && tid == 0) {
-            asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(P.done + slot), "l"(s_slot.seq) : "memory");
+        if (!rs::team_sync<false>(s_team)) return;
+        if (s_team.member == 0 && tid == 0) {
+            asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(A.pool[s_pool].done + slot), "l"(s_slot.seq)
+                         : "memory");
             atomicMax(A.last_ns, global_ns());
             atomicSub(A.busy, 1);
         }
@@ -172,10 +182,9 @@ __global__ void __launch_bounds__(BPT, 1) k_serve(const ServeArgs A) {
 }  // namespace
 
 size_t serve_smem_bytes() {
-    // the largest staged image (200 KiB) covers the per-warp phase-B areas
+    // any request's staging (at most kStageMaxBytes) and the per-warp phase-B areas
     const size_t phase_b = sizeof(float) * (size_t)rs::BNW * rs::WARP_STAGE;
-    const size_t img = 200 * 1024;
-    return img > phase_b ? img : phase_b;
+    return kStageMaxBytes > phase_b ? kStageMaxBytes : phase_b;
 }
 
 int serve_max_blocks(int device) {

@@ -431,7 +431,6 @@ roi_status launch(roi_server* s) {
     A.max_na = s->max_na;
     A.idle_ns = (unsigned long long)s->cfg.idle_us * 1000ull;
     A.cap_ns = 60ull * 1000000000ull;
-    A.smem_img_bytes = 200 * 1024;
     A.err = s->err_d;
     A.wait_ns = 2000000000ull;
     cudaError_t e = roi::launch_serve(A, s->blocks, s->st);
