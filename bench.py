@@ -14,6 +14,15 @@ sides; each step is bracketed by CUDA events on the library's stream and a
 (steps x ranks) / max over ranks of the summed step time.  ``e2e`` repeats the
 step through the C ABI with host buffers: pinned host sinogram in, host image out.
 
+The default line also carries ``serving``: the 2048 x 2048 serving workload (8
+resident sinograms, Poisson arrivals at 2000 requests/s, radii log-uniform in
+[16, 256] px, SIRT/TV 50/50, 200 iterations; ``--requests`` of them) served with
+continuous batching, against the same requests solved one at a time ("plain"):
+solves/s and p50/p99 latency from arrival to the result in host memory.
+
+``--workload roi_batch_2048`` and ``--workload roi_serve_2048`` print the batched and
+served workloads' own lines instead.
+
 ``--impl reference`` times the FP64 CPU oracle on the host cores instead (rank 0
 only): each step is FBP + exterior + a bounded number of CP iterations, scaled to
 a whole solve.
@@ -47,6 +56,7 @@ FLUSH_BYTES = 256 << 20
 # both giving 16 lerps per clock per SM
 LERPS_PER_CLK_SM = 16
 N_SM = 152
+PERSIST_SRCS = ("paper_1604_02292_gb300/csrc/persist.cu", "paper_1604_02292_gb300/csrc/dev_common.cuh")
 
 
 def parse():
@@ -65,6 +75,7 @@ def parse():
     ap.add_argument("--teams", type=int, default=-1, help="serving: teams (-1: library default)")
     ap.add_argument("--large-side", type=int, default=0, help="serving: box side served by teams (0: default)")
     ap.add_argument("--no-plain", action="store_true", help="serving: skip the one-at-a-time comparison")
+    ap.add_argument("--no-serving", action="store_true", help="default workload: skip the serving comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -77,13 +88,14 @@ def dist_env():
     return ws, rank, local
 
 
-def profile_traffic(kernel_src, profile_md):
-    """DRAM bytes per launch from a committed ncu summary, only while the kernel source still
-    hashes to the value recorded with the counters (else None: the kernel has changed)."""
+def profile_traffic(kernel_srcs, profile_md):
+    """DRAM bytes per launch from a committed ncu summary, only while the kernel's sources
+    (concatenated) still hash to the value recorded with the counters (else None: the kernel
+    has changed)."""
     import hashlib
     try:
         text = open(os.path.join(ROOT, profile_md)).read()
-        src = open(os.path.join(ROOT, kernel_src), "rb").read()
+        src = b"".join(open(os.path.join(ROOT, f), "rb").read() for f in kernel_srcs)
     except OSError:
         return None
     fields = dict(line.split(":", 1) for line in text.splitlines() if line.startswith(("source_sha256:", "dram_bytes_per_launch:")))
@@ -117,7 +129,7 @@ class ClockSampler:
 
     def __enter__(self):
         smi = shutil.which("nvidia-smi")
-        if smi:
+        if smi and self.gpu is not None:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.f = open(self.path, "w")
@@ -334,8 +346,7 @@ def run_ours(args):
         kernel = "k_back (CP)" if msb >= msf else "k_forward (CP)"
         lerps, avg_ms, alg_bytes = (lb, avg_b, bb) if msb >= msf else (lf, avg_f, bf)
     achieved = lerps / (avg_ms * 1e-3) / 1e9
-    traffic = profile_traffic("paper_1604_02292_gb300/csrc/persist.cu", "profiles/k_persist_cptv_1024.md") \
-        if n_single else None
+    traffic = profile_traffic(PERSIST_SRCS, "profiles/k_persist_cptv_1024.md") if n_single else None
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -359,6 +370,13 @@ def run_ours(args):
         te = shard.max_over_ranks(te, dist, device="cuda")
         e2e = {"value": shard.throughput(ke, ws, te), "unit": "solves/s", "h2d_bytes_per_step": int(p_host.nbytes),
                "d2h_bytes_per_step": int(outs_h[0].nbytes), "steps": ke}
+
+    # ---- serving on the 2048 x 2048 serving workload: continuous batching vs one at a time
+    serving = None
+    if not args.no_serving:
+        serving = serve_measure(args, args.requests, dist, ws, rank, local, clock=False)
+        serving.pop("w")
+        serving.pop("clocks")
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, one GPU only)
     cpu = None
@@ -398,6 +416,7 @@ def run_ours(args):
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     rr.close()
@@ -481,25 +500,18 @@ def _pct(v, q):
     return v[k]
 
 
-def run_serve(args):
-    """Serving workload: the requests arrive by a seeded Poisson process and are submitted
-    to the server (continuous batching over resident sinograms) at their arrival times;
-    latency = completion seen on the host - arrival.  The same requests are then solved
-    one at a time with roi_recon_solve_local (FP32, whole GPU per request, host output)
-    in arrival order ("plain"), each starting at max(arrival, previous completion).
+def serve_measure(args, count, dist, ws, rank, local, clock=True):
+    """Serving run on the serving workload: the requests arrive by a seeded Poisson process
+    and are submitted to the server (continuous batching over resident sinograms) at their
+    arrival times; latency = completion seen on the host - arrival.  The same requests are
+    then solved one at a time with roi_recon_solve_local (FP32, whole GPU per request, host
+    output) in arrival order ("plain"), each starting at max(arrival, previous completion).
     Times are host monotonic clocks; results land in host memory in both arms."""
     import torch
 
     import paper_1604_02292_gb300 as R
 
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    dist = None
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    w = WL.SERVING[args.workload]
-    count = args.requests
+    w = WL.SERVING["roi_serve_2048"] if args.workload not in WL.SERVING else WL.SERVING[args.workload]
     reqs = WL.serve_requests(w, seed=0, count=count)
     arr = WL.arrivals(w, seed=0, count=count, rate=args.rate)
     mine = [i for i in range(count) if i % ws == rank]
@@ -515,7 +527,7 @@ def run_serve(args):
         srv.add(rr)
     # warm-up: a few short requests through both paths (first launch, ring allocation)
     for sino, reg, prm in WL.serve_requests(w, seed=99, count=max(args.warmup, 1)):
-        rid = srv.submit(sino, reg, dict(prm, iters=5))
+        srv.submit(sino, reg, dict(prm, iters=5))
         recons[sino].solve_local(reg, reg=prm["reg"], iters=5, lam=prm["lam"])
     srv.drain()
     for c in srv.poll():
@@ -527,7 +539,7 @@ def run_serve(args):
     n0 = R.roi_recon_launch_count()
     lat, done, who = [], {}, {}
     nbytes = 0
-    with ClockSampler(local) as clk:
+    with ClockSampler(local if clock else None) as clk:
         t0 = time.monotonic()
         i = 0
         while len(done) < len(mine):
@@ -577,27 +589,49 @@ def run_serve(args):
         pl = recons[sino].plan(reg)
         nx, ny = pl.box[2], pl.box[3]
         n_lerps += prm["iters"] * (sum(pl.width) * max(nx, ny) + nx * ny * w.n_angles)
-    line = {
-        "metric": "roi_solves_per_s_served", "value": count / t_served, "unit": "solves/s", "n_gpus": ws,
-        "steps": 1, "warmup": args.warmup, "ms_per_step": t_served * 1e3, "higher_is_better": True,
-        "dtype": "f32", "data": "synthetic", "scaling": "strong",
-        "config": {"workload": w.name, "N": w.N, "n_angles": w.n_angles, "n_det": w.n_det, "sinograms": w.n_sinos,
-                   "requests": count, "rate_per_s": args.rate or w.rate, "radius": [w.r_lo, w.r_hi],
-                   "iters": w.iters, "solvers": "SIRT/TV 50/50", "timing": "host monotonic clock, arrival to result"},
+    for rr in recons:
+        rr.close()
+    return {
+        "workload": w.name, "requests": count, "rate_per_s": args.rate or w.rate, "value": count / t_served,
+        "unit": "solves/s", "wall_s": t_served,
         "latency_ms": {"p50": _pct(lat, 50), "p99": _pct(lat, 99), "mean": statistics.mean(lat)},
         "plain": plain,
         "server": {k: st[k] for k in ("blocks", "single_units", "teams", "team_blocks", "kernel_launches",
                                       "device_peak", "host_peak")},
-        "e2e": {"value": count / t_served, "unit": "solves/s", "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": nbytes},
-        "gpu_launches": launches,
-        "projector_Glerp_s_rank0": n_lerps / t_served / 1e9,
-        "clocks": clk.summary(),
+        "d2h_bytes": nbytes, "gpu_launches": launches, "Glerp_s_rank0": n_lerps / t_served / 1e9,
+        "clocks": clk.summary(), "w": w,
+    }
+
+
+def run_serve(args):
+    """Serving workload line (see serve_measure)."""
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    m = serve_measure(args, args.requests, dist, ws, rank, local)
+    w = m.pop("w")
+    line = {
+        "metric": "roi_solves_per_s_served", "value": m["value"], "unit": "solves/s", "n_gpus": ws,
+        "steps": 1, "warmup": args.warmup, "ms_per_step": m["wall_s"] * 1e3, "higher_is_better": True,
+        "dtype": "f32", "data": "synthetic", "scaling": "strong",
+        "config": {"workload": w.name, "N": w.N, "n_angles": w.n_angles, "n_det": w.n_det, "sinograms": w.n_sinos,
+                   "requests": m["requests"], "rate_per_s": m["rate_per_s"], "radius": [w.r_lo, w.r_hi],
+                   "iters": w.iters, "solvers": "SIRT/TV 50/50", "timing": "host monotonic clock, arrival to result"},
+        "latency_ms": m["latency_ms"],
+        "plain": m["plain"],
+        "server": m["server"],
+        "e2e": {"value": m["value"], "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": m["d2h_bytes"]},
+        "gpu_launches": m["gpu_launches"],
+        "projector_Glerp_s_rank0": m["Glerp_s_rank0"],
+        "clocks": m["clocks"],
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
-    for rr in recons:
-        rr.close()
     if dist:
         dist.destroy_process_group()
     return 0
