@@ -66,7 +66,9 @@ typedef struct {
     int n_angles;          /* N_theta >= 1                                             */
     int n_det;             /* N_d >= 1                                                 */
     const double* angles;  /* host array of n_angles radians, copied; NULL: a*pi/N_theta */
-    roi_dtype storage;     /* storage type of the resident sinogram: ROI_F32 only       */
+    roi_dtype storage;     /* storage of the resident sinogram and FBP image, and of the
+                              projector images of batched / served solves: ROI_F32,
+                              ROI_BF16 or ROI_F16 (arithmetic is float throughout)        */
 } roi_geometry;
 
 /* Region of interest in pixel-index units (see Conventions). */
@@ -103,8 +105,11 @@ typedef struct {
 
 /* Create a handle for geometry *geom, ordering all work on `cuda_stream`
  * (a cudaStream_t; NULL = the legacy default stream) of the current device.
- * Allocates the sinogram, filter and FBP buffers (4 (2 N_theta N_d + 2 N^2) bytes).
- * ROI_EINVAL for non-positive sizes or storage != ROI_F32, ROI_ENOMEM if the
+ * Allocates the sinogram, filter and FBP buffers (s N_theta N_d + 4 N_theta N_d + 2 s N^2
+ * bytes, s = 4 for ROI_F32, 2 for ROI_BF16 / ROI_F16; 16-bit storage adds a float N^2
+ * scratch at the first fbp).  With 16-bit storage every stored value is rounded to
+ * nearest even; the ramp filter, projections and solves still compute in float.
+ * ROI_EINVAL for non-positive sizes or an unknown storage type, ROI_ENOMEM if the
  * device allocation fails.  *out is NULL on failure. */
 roi_status roi_recon_create(const roi_geometry* geom, void* cuda_stream, roi_recon_t* out);
 
@@ -114,18 +119,19 @@ void roi_recon_destroy(roi_recon_t h);
 /* Message of the last failed call on this handle ("" if none).  Valid until the next call. */
 const char* roi_recon_last_error(roi_recon_t h);
 
-/* Copy the measured sinogram p (Sec. 2.1), [n_angles][n_det] float32, into the handle.
+/* Copy the measured sinogram p (Sec. 2.1), [n_angles][n_det] of type dt (ROI_F32,
+ * ROI_BF16 or ROI_F16), into the handle, converting it to the handle's storage type
+ * (round to nearest even) on the device when the two differ.
  * on_device = 1: p is a device pointer (device-to-device copy, asynchronous);
  * on_device = 0: p is host memory, copied with cudaMemcpyAsync semantics: pageable
  * memory is consumed before the call returns, page-locked memory must stay unchanged
- * until the handle's stream has passed the copy.  dt must be ROI_F32.
- * Invalidates the cached FBP image. */
+ * until the handle's stream has passed the copy.  Invalidates the cached FBP image. */
 roi_status roi_recon_set_sinogram(roi_recon_t h, const void* p, roi_dtype dt, int on_device);
 
 /* Global filtered backprojection FBP(p, h) = W^T C_h p (Eq. fbp), Ram-Lak filter
  * scaled by pi/N_theta, on the whole N x N grid; the result is cached in the
- * handle for the exterior step.  out_or_null: optional device [N][N] float32 copy.
- * ROI_ESTATE before set_sinogram. */
+ * handle (in its storage type) for the exterior step.  out_or_null: optional device
+ * [N][N] float32 copy of the cached image.  ROI_ESTATE before set_sinogram. */
 roi_status roi_recon_fbp(roi_recon_t h, float* out_or_null);
 
 /* Exterior subtraction (Sec. 1; Eq. locouter): p' = p - W M_F x_fbp on every ray that
@@ -330,8 +336,8 @@ const char* roi_server_last_error(roi_server_t s);
 void roi_server_destroy(roi_server_t s);
 
 /* Host only (no GPU): the device-state and result bytes the server budgets for a request
- * on a sinogram of n_pix / n_angles / n_det, and its box side. */
-roi_status roi_server_footprint(int n_pix, int n_angles, int n_det, const roi_region* region,
+ * on a sinogram of n_pix / n_angles / n_det with the given storage type, and its box side. */
+roi_status roi_server_footprint(int n_pix, int n_angles, int n_det, roi_dtype storage, const roi_region* region,
                                 size_t* device_bytes, size_t* host_bytes, int* box_side);
 
 /* --------------------------------------------------------------------------

@@ -179,7 +179,8 @@ def lib() -> ctypes.CDLL:
             L.roi_server_last_error.restype = ctypes.c_char_p
             L.roi_server_destroy.argtypes = [_H]
             L.roi_server_destroy.restype = None
-            L.roi_server_footprint.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Region),
+            L.roi_server_footprint.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                               ctypes.POINTER(Region),
                                                ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
                                                ctypes.POINTER(ctypes.c_int)]
             L.roi_server_footprint.restype = st
@@ -330,10 +331,10 @@ def roi_server_last_error(s) -> str:
     return (lib().roi_server_last_error(s) or b"").decode()
 
 
-def roi_server_footprint(n_pix: int, n_angles: int, n_det: int, region: Region):
+def roi_server_footprint(n_pix: int, n_angles: int, n_det: int, storage: int, region: Region):
     dev, host, side = ctypes.c_size_t(0), ctypes.c_size_t(0), ctypes.c_int(0)
-    st = lib().roi_server_footprint(int(n_pix), int(n_angles), int(n_det), ctypes.byref(region), ctypes.byref(dev),
-                                    ctypes.byref(host), ctypes.byref(side))
+    st = lib().roi_server_footprint(int(n_pix), int(n_angles), int(n_det), int(storage), ctypes.byref(region),
+                                    ctypes.byref(dev), ctypes.byref(host), ctypes.byref(side))
     return st, dev.value, host.value, side.value
 
 
@@ -345,8 +346,8 @@ class RoiError(RuntimeError):
         self.status = status
 
 
-def _geometry(N, n_angles, n_det, angles=None):
-    g = Geometry(int(N), int(n_angles), int(n_det), None, ROI_F32)
+def _geometry(N, n_angles, n_det, angles=None, storage=ROI_F32):
+    g = Geometry(int(N), int(n_angles), int(n_det), None, int(storage))
     keep = None
     if angles is not None:
         import numpy as np
@@ -386,12 +387,15 @@ class RoiRecon:
     Tensors must be contiguous float32 CUDA tensors on the current device.
     """
 
-    def __init__(self, N, n_angles, n_det, angles=None, stream=None):
+    def __init__(self, N, n_angles, n_det, angles=None, stream=None, storage=ROI_F32):
+        """storage: ROI_F32, ROI_BF16 or ROI_F16 -- the type the resident sinogram and FBP
+        image (and the projector images of batched / served solves) are stored in."""
         import torch
         self._torch = torch
         self.N, self.n_angles, self.n_det = int(N), int(n_angles), int(n_det)
+        self.storage = int(storage)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        g, self._angles_keep = _geometry(N, n_angles, n_det, angles)
+        g, self._angles_keep = _geometry(N, n_angles, n_det, angles, storage)
         s, h = roi_recon_create(g, self.stream.cuda_stream)
         if s != ROI_OK:
             raise RoiError(s, "roi_recon_create failed")
@@ -425,11 +429,15 @@ class RoiRecon:
                     None if self._angles_keep is None else self._angles_keep)
 
     def set_sinogram(self, p):
-        """p: float32 [n_angles][n_det], a CUDA tensor or host (numpy / CPU tensor) array."""
+        """p: [n_angles][n_det], a CUDA tensor (float32, bfloat16 or float16) or a host
+        float32 array (numpy / CPU tensor); converted to the handle's storage type."""
         torch = self._torch
         shape = (self.n_angles, self.n_det)
         if isinstance(p, torch.Tensor) and p.is_cuda:
-            self._check(roi_recon_set_sinogram(self.h, self._dev(p, shape), ROI_F32, 1))
+            dts = {torch.float32: ROI_F32, torch.bfloat16: ROI_BF16, torch.float16: ROI_F16}
+            if p.dtype not in dts or not p.is_contiguous() or tuple(p.shape) != shape:
+                raise TypeError(f"device sinogram must be a contiguous float32/bfloat16/float16 tensor {shape}")
+            self._check(roi_recon_set_sinogram(self.h, p.data_ptr(), dts[p.dtype], 1))
             self._sino_keep = p
         else:
             import numpy as np
@@ -555,9 +563,9 @@ def _params(p: dict) -> SolveParams:
                        int(p.get("weighting", 0)), 1, int(p.get("crop_disk", 0)), 0)
 
 
-def server_footprint(N, n_angles, n_det, region):
+def server_footprint(N, n_angles, n_det, region, storage=ROI_F32):
     """(device_bytes, host_bytes, box_side) the server budgets for a request; host only."""
-    st, dev, host, side = roi_server_footprint(N, n_angles, n_det, Region(*map(float, region)))
+    st, dev, host, side = roi_server_footprint(N, n_angles, n_det, storage, Region(*map(float, region)))
     if st != ROI_OK:
         raise RoiError(st, "roi_server_footprint failed")
     return dev, host, side

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(BPT, 1) k_batch(BatchArgs B) {
         __syncthreads();
         const int qi = s_roi;
         if (qi >= B.nroi) break;
-        if (!rs::solve_region<true>(B.rois[B.order[qi]], bufs, T, smem, s_mbar, parity, &s_cnt)) return;
+        if (!rs::solve_region_dt<true>(B.rois[B.order[qi]], bufs, T, smem, s_mbar, parity, &s_cnt)) return;
     }
 }
 

@@ -68,13 +68,17 @@ struct roi_recon {
     std::vector<double> angles;
     cudaStream_t st = nullptr;
     std::string err;
-    // resident data
-    float* p = nullptr;      // [na][nd]
-    float* q = nullptr;      // [na][nd] filtered sinogram
-    float* xfbp = nullptr;   // [N][N] padded (row stride N + 4), element (0,0)
-    float* xfbpT = nullptr;  // its transpose, padded
-    float* xfbp_base = nullptr;
-    float* xfbpT_base = nullptr;
+    // resident data, stored as dt (0 float, 1 bfloat16, 2 half; esz bytes an element)
+    int dt = 0, esz = 4;
+    void* p = nullptr;       // [na][nd]
+    float* q = nullptr;      // [na][nd] filtered sinogram (float)
+    void* xfbp = nullptr;    // [N][N] padded (row stride xld), element (0,0)
+    void* xfbpT = nullptr;   // its transpose, padded
+    unsigned char* xfbp_base = nullptr;
+    unsigned char* xfbpT_base = nullptr;
+    int xld = 0;             // padded_ld_e(N, esz)
+    DevBuf fbp32;            // 16-bit storage: the float FBP image before narrowing [N][N]
+    DevBufT<unsigned char> in_tmp;  // set_sinogram input awaiting conversion
     float* hodd = nullptr;   // Ram-Lak odd taps scaled by pi/na, [nd/2 + 1]
     float ctail = 0.f;       // (pi/na) (h0 + 2 sum_{odd m < nd} h_m)
     AngleRec* rec_fbp = nullptr;  // frame = grid, window = whole detector
@@ -199,7 +203,7 @@ roi_status check_geometry(const roi_geometry* g) {
     if (!g) return ROI_EINVAL;
     if (g->n_pix < 1 || g->n_angles < 1 || g->n_det < 1) return ROI_EINVAL;
     if (g->n_pix > 65536 || g->n_angles > 65536 || g->n_det > 8192) return ROI_EINVAL;
-    if (g->storage != ROI_F32) return ROI_EINVAL;
+    if (g->storage != ROI_F32 && g->storage != ROI_BF16 && g->storage != ROI_F16) return ROI_EINVAL;
     if (g->angles)
         for (int a = 0; a < g->n_angles; ++a)
             if (!std::isfinite(g->angles[a])) return ROI_EINVAL;
@@ -338,8 +342,9 @@ roi_status ensure_residual(roi_recon* h) {
     a.ny = h->N;
     a.img = h->xfbp;
     a.imgT = h->xfbpT;
-    a.img_ld = roi::padded_ld(h->N);
-    a.imgT_ld = roi::padded_ld(h->N);
+    a.img_ld = h->xld;
+    a.imgT_ld = h->xld;
+    a.dt = h->dt;
     a.hole = Rect{0, 0, 0, 0};
     a.out = h->resid.p;
     a.p = h->p;
@@ -356,7 +361,8 @@ void exterior_inputs(const roi_recon* h, roi::BatchRoi& R, Rect box) {
     R.resid_ld = h->resid_ld;
     R.xfbp = h->xfbp;
     R.xfbpT = h->xfbpT;
-    R.xfbp_ld = roi::padded_ld(h->N);
+    R.xfbp_ld = h->xld;
+    R.dt = h->dt;
     R.box_x0 = box.x0;
     R.box_y0 = box.y0;
     R.alpha = (float)(1.0 / ((double)h->na * h->nd));
@@ -371,8 +377,9 @@ roi_status run_exterior(roi_recon* h) {
     a.ny = h->N;
     a.img = h->xfbp;
     a.imgT = h->xfbpT;
-    a.img_ld = roi::padded_ld(h->N);
-    a.imgT_ld = roi::padded_ld(h->N);
+    a.img_ld = h->xld;
+    a.imgT_ld = h->xld;
+    a.dt = h->dt;
     a.hole = h->box;
     a.out = h->pp.p;
     a.p = h->p;
@@ -581,7 +588,8 @@ int sino_view(roi_recon* h, SinoView* v, std::string* msg) {
     v->angles = h->angles.data();
     v->xfbp = h->xfbp;
     v->xfbpT = h->xfbpT;
-    v->xfbp_ld = roi::padded_ld(h->N);
+    v->xfbp_ld = h->xld;
+    v->dt = h->dt;
     v->resid = h->resid.p;
     v->resid_ld = h->resid_ld;
     return ROI_OK;
@@ -601,18 +609,21 @@ roi_status roi_recon_create(const roi_geometry* geom, void* cuda_stream, roi_rec
     h->nd = geom->n_det;
     h->angles = make_angles(geom);
     h->st = (cudaStream_t)cuda_stream;
+    h->dt = (int)geom->storage;
+    h->esz = roi::dt_size(h->dt);
+    h->xld = roi::padded_ld_e(h->N, h->esz);
     const size_t ns = (size_t)h->na * h->nd;
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = dev_alloc(&h->p, ns);
+    if (e == cudaSuccess) e = cudaMalloc(&h->p, (size_t)h->esz * ns);
     if (e == cudaSuccess) e = dev_alloc(&h->q, ns);
-    const size_t npad = (size_t)h->N * roi::padded_ld(h->N);
-    if (e == cudaSuccess) e = dev_alloc(&h->xfbp_base, npad);
-    if (e == cudaSuccess) e = dev_alloc(&h->xfbpT_base, npad);
-    if (e == cudaSuccess) e = cudaMemset(h->xfbp_base, 0, sizeof(float) * npad);
-    if (e == cudaSuccess) e = cudaMemset(h->xfbpT_base, 0, sizeof(float) * npad);
+    const size_t npad_bytes = (size_t)h->esz * h->N * h->xld;
+    if (e == cudaSuccess) e = dev_alloc(&h->xfbp_base, npad_bytes);
+    if (e == cudaSuccess) e = dev_alloc(&h->xfbpT_base, npad_bytes);
+    if (e == cudaSuccess) e = cudaMemset(h->xfbp_base, 0, npad_bytes);
+    if (e == cudaSuccess) e = cudaMemset(h->xfbpT_base, 0, npad_bytes);
     if (e == cudaSuccess) {
-        h->xfbp = h->xfbp_base + roi::kPad;
-        h->xfbpT = h->xfbpT_base + roi::kPad;
+        h->xfbp = h->xfbp_base + (size_t)roi::kPad * h->esz;
+        h->xfbpT = h->xfbpT_base + (size_t)roi::kPad * h->esz;
     }
     if (e == cudaSuccess) e = dev_alloc(&h->hodd, (size_t)h->nd / 2 + 1);
     if (e == cudaSuccess) e = dev_alloc(&h->rec_fbp, (size_t)h->na);
@@ -660,8 +671,10 @@ roi_status roi_recon_create(const roi_geometry* geom, void* cuda_stream, roi_rec
 void roi_recon_destroy(roi_recon_t h) {
     if (!h) return;
     cudaStreamSynchronize(h->st);
-    for (float* b : {h->p, h->q, h->xfbp_base, h->xfbpT_base, h->hodd})
+    for (void* b : {h->p, (void*)h->q, (void*)h->xfbp_base, (void*)h->xfbpT_base, (void*)h->hodd})
         if (b) cudaFree(b);
+    h->fbp32.release();
+    h->in_tmp.release();
     for (AngleRec* b : {h->rec_fbp, h->rec_loc, h->rec_ext})
         if (b) cudaFree(b);
     if (h->red) cudaFree(h->red);
@@ -690,9 +703,18 @@ roi_status roi_recon_set_sinogram(roi_recon_t h, const void* p, roi_dtype dt, in
     if (!h) return ROI_EINVAL;
     h->err.clear();
     if (!p) return fail(h, ROI_EINVAL, "set_sinogram: null pointer");
-    if (dt != ROI_F32) return fail(h, ROI_EINVAL, "set_sinogram: only ROI_F32 input is supported");
-    CU(h, cudaMemcpyAsync(h->p, p, sizeof(float) * (size_t)h->na * h->nd,
-                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st));
+    if (dt != ROI_F32 && dt != ROI_BF16 && dt != ROI_F16) return fail(h, ROI_EINVAL, "set_sinogram: unknown dtype");
+    const size_t n = (size_t)h->na * h->nd;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if ((int)dt == h->dt) {
+        CU(h, cudaMemcpyAsync(h->p, p, (size_t)h->esz * n, kind, h->st));
+    } else {  // narrow (or widen) to the storage type on the device
+        const size_t in_bytes = (size_t)roi::dt_size((int)dt) * n;
+        CU(h, h->in_tmp.ensure(in_bytes));
+        CU(h, cudaMemcpyAsync(h->in_tmp.p, p, in_bytes, kind, h->st));
+        roi::launch_convert(h->in_tmp.p, (int)dt, h->p, h->dt, n, h->st);
+        LAUNCHED(h, "set_sinogram conversion");
+    }
     h->have_sino = true;
     h->have_fbp = false;
     h->exterior_ready = 0;
@@ -705,7 +727,7 @@ roi_status roi_recon_ramp_filter(roi_recon_t h, float* q) {
     h->err.clear();
     if (!q) return fail(h, ROI_EINVAL, "ramp_filter: null output");
     if (!h->have_sino) return fail(h, ROI_ESTATE, "ramp_filter: no sinogram (call set_sinogram first)");
-    roi::launch_ramp(h->p, h->hodd, q, h->na, h->nd, h->ctail, h->st);
+    roi::launch_ramp(h->p, h->dt, h->hodd, q, h->na, h->nd, h->ctail, h->st);
     LAUNCHED(h, "ramp filter");
     return ROI_OK;
 }
@@ -714,7 +736,7 @@ roi_status roi_recon_fbp(roi_recon_t h, float* out_or_null) {
     if (!h) return ROI_EINVAL;
     h->err.clear();
     if (!h->have_sino) return fail(h, ROI_ESTATE, "fbp: no sinogram (call set_sinogram first)");
-    roi::launch_ramp(h->p, h->hodd, h->q, h->na, h->nd, h->ctail, h->st);
+    roi::launch_ramp(h->p, h->dt, h->hodd, h->q, h->na, h->nd, h->ctail, h->st);
     roi::BackArgs b{};
     b.rec = h->rec_fbp;
     b.na = h->na;
@@ -722,16 +744,29 @@ roi_status roi_recon_fbp(roi_recon_t h, float* out_or_null) {
     b.nx = h->N;
     b.ny = h->N;
     b.win = h->q;
-    b.out = h->xfbp;
-    b.out_ld = roi::padded_ld(h->N);
-    b.outT = h->xfbpT;
-    b.outT_ld = roi::padded_ld(h->N);
     b.part = nullptr;  // the whole grid has enough tiles for one angle group
-    roi::launch_back(roi::BACK_PLAIN, b, h->st);
+    if (h->dt == 0) {  // straight into the padded image and its transpose
+        b.out = static_cast<float*>(h->xfbp);
+        b.out_ld = h->xld;
+        b.outT = static_cast<float*>(h->xfbpT);
+        b.outT_ld = h->xld;
+        roi::launch_back(roi::BACK_PLAIN, b, h->st);
+    } else {  // float image, then narrowed into the padded image and its transpose
+        CU(h, h->fbp32.ensure((size_t)h->N * h->N));
+        b.out = h->fbp32.p;
+        b.out_ld = h->N;
+        roi::launch_back(roi::BACK_PLAIN, b, h->st);
+        roi::launch_store_padded(h->fbp32.p, h->N, h->xfbp, h->dt, h->xld, h->N, h->N, 0, h->st);
+        roi::launch_store_padded(h->fbp32.p, h->N, h->xfbpT, h->dt, h->xld, h->N, h->N, 1, h->st);
+    }
     LAUNCHED(h, "fbp");
-    if (out_or_null)
-        CU(h, cudaMemcpy2DAsync(out_or_null, sizeof(float) * h->N, h->xfbp, sizeof(float) * roi::padded_ld(h->N),
-                                sizeof(float) * h->N, h->N, cudaMemcpyDeviceToDevice, h->st));
+    if (out_or_null) {
+        if (h->dt == 0)
+            CU(h, cudaMemcpy2DAsync(out_or_null, sizeof(float) * h->N, h->xfbp, sizeof(float) * h->xld,
+                                    sizeof(float) * h->N, h->N, cudaMemcpyDeviceToDevice, h->st));
+        else  // the resident (narrowed) image, widened
+            roi::launch_load_padded(h->xfbp, h->dt, h->xld, out_or_null, h->N, h->N, h->N, h->st);
+    }
     h->have_fbp = true;
     h->exterior_ready = 0;
     h->resid_ready = 0;
@@ -916,9 +951,11 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
         out_total += (size_t)box.w * box.h;
         win_cap = std::max(win_cap, (size_t)na * strides[i]);
         img_cap = std::max(img_cap, (size_t)box.w * box.h);
-        const size_t pr = (size_t)box.h * roi::padded_ld(box.w), pc = (size_t)box.w * roi::padded_ld(box.h);
-        pad_cap = std::max(pad_cap, std::max(pr, pc));
-        max_stage = std::max(max_stage, roi::stage_bytes(box.w, box.h));
+        // padded images in the storage type, counted in floats (whole 16-byte units)
+        const size_t pr = (size_t)box.h * roi::padded_ld_e(box.w, h->esz) * h->esz;
+        const size_t pc = (size_t)box.w * roi::padded_ld_e(box.h, h->esz) * h->esz;
+        pad_cap = std::max(pad_cap, (std::max(pr, pc) + 15) / 16 * 4);
+        max_stage = std::max(max_stage, roi::stage_bytes(box.w, box.h, h->esz));
         cost[i] = (double)box.w * box.h * na * (double)std::max(P.iters, 1);
     }
     roi_status s0 = ensure_residual(h);

@@ -2,12 +2,45 @@
 // TMA bulk copies with mbarrier completion and bounded waits, fixed-point conversions.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "roi_internal.h"
 
 namespace roi {
+
+// Storage element of a resident array or a projector image: DT 0 = float, 1 = bfloat16,
+// 2 = IEEE half (16-bit patterns).  Arithmetic is always float.
+template <int DT>
+struct Stor {
+    using T = unsigned short;
+};
+template <>
+struct Stor<0> {
+    using T = float;
+};
+template <int DT>
+__device__ __forceinline__ float to_f32(typename Stor<DT>::T v) {
+    if constexpr (DT == 0) {
+        return v;
+    } else if constexpr (DT == 1) {
+        return __uint_as_float((unsigned)v << 16);  // bfloat16 -> float is exact
+    } else {
+        return __half2float(__ushort_as_half(v));
+    }
+}
+template <int DT>
+__device__ __forceinline__ typename Stor<DT>::T from_f32(float x) {  // round to nearest even
+    if constexpr (DT == 0) {
+        return x;
+    } else if constexpr (DT == 1) {
+        return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+    } else {
+        return __half_as_ushort(__float2half_rn(x));
+    }
+}
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;

@@ -20,6 +20,7 @@
 // leaves a bias; the sum is accumulated with Neumaier's compensation.
 #include <cuda_runtime.h>
 
+#include "dev_common.cuh"
 #include "roi_internal.h"
 
 namespace roi {
@@ -28,16 +29,18 @@ namespace {
 
 constexpr int OUT_PER_THREAD = 8;
 
-__global__ void k_ramp(const float* __restrict__ p, const float* __restrict__ hodd, float* __restrict__ q, int nd,
+template <int DT>
+__global__ void k_ramp(const void* __restrict__ pv, const float* __restrict__ hodd, float* __restrict__ q, int nd,
                        float ctail) {
+    using T = typename Stor<DT>::T;  // sinogram storage; the filter works in float
     extern __shared__ float sm[];
     const int pad = nd + 8;
     float* P = sm + pad;  // P[-pad .. nd + pad)
     const int a = blockIdx.x;
-    const float* prow = p + (size_t)a * nd;
+    const T* prow = static_cast<const T*>(pv) + (size_t)a * nd;
     for (int i = threadIdx.x; i < nd + 2 * pad; i += blockDim.x) {
         const int d = i - pad;
-        sm[i] = (d >= 0 && d < nd) ? prow[d] : 0.f;
+        sm[i] = (d >= 0 && d < nd) ? to_f32<DT>(prow[d]) : 0.f;
     }
     __syncthreads();
     const int d0 = threadIdx.x * OUT_PER_THREAD;
@@ -82,15 +85,23 @@ __global__ void k_ramp(const float* __restrict__ p, const float* __restrict__ ho
 // Index bounds (P spans [-(nd + 8), 2 nd + 8)): with d0 <= nd - 1 and odd m <= nd - 1
 // the loads reach down to P[d0 - m - 2] >= P[-(nd + 1)] and up to
 // P[d0 + 7 + m + 2] <= P[2 nd + 7].  hodd needs nd / 2 + 1 entries (index m >> 1).
-void launch_ramp(const float* p, const float* hodd, float* q, int na, int nd, float ctail, cudaStream_t st) {
+void launch_ramp(const void* p, int dt, const float* hodd, float* q, int na, int nd, float ctail, cudaStream_t st) {
     if (na <= 0 || nd <= 0) return;
     int threads = (nd + OUT_PER_THREAD - 1) / OUT_PER_THREAD;
     threads = (threads + 31) / 32 * 32;
     if (threads > 1024) threads = 1024;  // nd <= 8192 is checked by the caller
     const size_t smem = sizeof(float) * (size_t)(nd + 2 * (nd + 8));
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k_ramp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     count_launches(1);
-    k_ramp<<<na, threads, smem, st>>>(p, hodd, q, nd, ctail);
+    if (dt == 1) {
+        if (smem > 48 * 1024) cudaFuncSetAttribute(k_ramp<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_ramp<1><<<na, threads, smem, st>>>(p, hodd, q, nd, ctail);
+    } else if (dt == 2) {
+        if (smem > 48 * 1024) cudaFuncSetAttribute(k_ramp<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_ramp<2><<<na, threads, smem, st>>>(p, hodd, q, nd, ctail);
+    } else {
+        if (smem > 48 * 1024) cudaFuncSetAttribute(k_ramp<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_ramp<0><<<na, threads, smem, st>>>(p, hodd, q, nd, ctail);
+    }
 }
 
 }  // namespace roi

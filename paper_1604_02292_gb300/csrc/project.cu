@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "dev_common.cuh"
 #include "roi_internal.h"
 
 namespace roi {
@@ -50,8 +51,9 @@ constexpr int TARGET_THREADS = 152 * 2048;
 // Positions: each 16-sample segment is anchored in float-float, then offsets
 // |m - anchor| <= 8 are formed in float.  Sums: float within a segment, Neumaier
 // carry across segments, float-float across the S threads of a ray.
-template <int MODE>
+template <int MODE, int DT>
 __global__ void __launch_bounds__(FWD_RAYS* FWD_MAXSEG) k_forward(const FwdArgs A) {
+    using T = typename Stor<DT>::T;  // element of the frame image (and of p): float or 16-bit
     __shared__ float red_s[FWD_MAXSEG][FWD_RAYS];
     __shared__ float red_c[FWD_MAXSEG][FWD_RAYS];
     const int a = blockIdx.y;
@@ -64,7 +66,7 @@ __global__ void __launch_bounds__(FWD_RAYS* FWD_MAXSEG) k_forward(const FwdArgs 
         const int row = r.row;
         const int M = row ? A.ny : A.nx;           // samples along the ray
         const int Mm = row ? A.nx : A.ny;          // extent of the interpolation axis
-        const float* src = row ? A.img : A.imgT;   // [M][ld], element (0,0)
+        const T* src = static_cast<const T*>(row ? A.img : A.imgT);  // [M][ld], element (0,0)
         const int ld = row ? A.img_ld : A.imgT_ld;
         const float halfM = 0.5f * (float)(M - 1);
         const ff Ak = ff_add(r.A0, ff_mul_f((float)k, r.a_scale));
@@ -100,15 +102,15 @@ __global__ void __launch_bounds__(FWD_RAYS* FWD_MAXSEG) k_forward(const FwdArgs 
             const float bf = (bd.hi - bfl) + bd.lo;
             const int mend = min(m0 + SEG, mhi);
             float acc = 0.f;
-            const float* rp = src + (size_t)m0 * ld + bi;
+            const T* rp = src + (size_t)m0 * ld + bi;
 #pragma unroll 4
             for (int m = m0; m < mend; ++m, rp += ld) {
                 const float q = fmaf((float)(m - m0) - 0.5f * (SEG - 1), slope, bf);
                 const float fl = floorf(q);
                 const int j = (int)fl;
                 const float f = q - fl;
-                float v0 = __ldg(rp + j);
-                float v1 = __ldg(rp + j + 1);
+                float v0 = to_f32<DT>(__ldg(rp + j));
+                float v1 = to_f32<DT>(__ldg(rp + j + 1));
                 if (MODE == FWD_EXTERIOR) {
                     if (m >= hM0 && m < hM1) {
                         const int j0 = bi + j;
@@ -142,7 +144,8 @@ __global__ void __launch_bounds__(FWD_RAYS* FWD_MAXSEG) k_forward(const FwdArgs 
     }
     tot = ff_mul_f(r.inv_w, tot);
     if (MODE == FWD_EXTERIOR) {  // p - sum, with the float-float sum
-        const ff d = two_sum(A.p[(size_t)r.aidx * A.nd + r.d0 + k], -tot.hi);
+        const float pv = to_f32<DT>(__ldg(static_cast<const T*>(A.p) + (size_t)r.aidx * A.nd + r.d0 + k));
+        const ff d = two_sum(pv, -tot.hi);
         *out = d.hi + (d.lo - tot.lo);
         return;
     }
@@ -389,10 +392,17 @@ void launch_forward(FwdMode mode, const FwdArgs& a0, cudaStream_t st) {
     dim3 grid((a.stride + FWD_RAYS - 1) / FWD_RAYS, a.na), block(FWD_RAYS, S);
     count_launches(1);
     switch (mode) {
-        case FWD_PLAIN: k_forward<FWD_PLAIN><<<grid, block, 0, st>>>(a); break;
-        case FWD_EXTERIOR: k_forward<FWD_EXTERIOR><<<grid, block, 0, st>>>(a); break;
-        case FWD_SIRT: k_forward<FWD_SIRT><<<grid, block, 0, st>>>(a); break;
-        case FWD_CP: k_forward<FWD_CP><<<grid, block, 0, st>>>(a); break;
+        case FWD_PLAIN: k_forward<FWD_PLAIN, 0><<<grid, block, 0, st>>>(a); break;
+        case FWD_EXTERIOR:
+            if (a.dt == 1)
+                k_forward<FWD_EXTERIOR, 1><<<grid, block, 0, st>>>(a);
+            else if (a.dt == 2)
+                k_forward<FWD_EXTERIOR, 2><<<grid, block, 0, st>>>(a);
+            else
+                k_forward<FWD_EXTERIOR, 0><<<grid, block, 0, st>>>(a);
+            break;
+        case FWD_SIRT: k_forward<FWD_SIRT, 0><<<grid, block, 0, st>>>(a); break;
+        case FWD_CP: k_forward<FWD_CP, 0><<<grid, block, 0, st>>>(a); break;
     }
 }
 

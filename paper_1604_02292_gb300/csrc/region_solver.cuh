@@ -104,19 +104,26 @@ using roi::RegionBufs;
 struct Ctx {
     const BatchRoi* R;
     RegionBufs b;
-    float* xa;     // padded row image, element (0,0)
-    float* xaT;    // padded column image, element (0,0)
-    int lda, ldaT;
+    void* xa;      // padded row image (storage R.dt), element (0,0)
+    void* xaT;     // padded column image, element (0,0)
+    int lda, ldaT; // row strides in elements
     int nchunk;
-    int gtid, gthreads;   // thread index / count over the team
+    int member, gthreads; // this block's index in the team, threads of the team
     int stage;            // stage_mode of the box (0 whole image, 1 bands, 2 global)
 };
+// (A Ctx lives in shared memory: it is uniform over the block, and keeping it out of
+// registers leaves them to the inner loops.)
+
+// This thread's index over the team.
+__device__ __forceinline__ int team_tid(const Ctx& C) { return C.member * BPT + (int)threadIdx.x; }
 
 // Whole-ray Joseph sum of ray k (fixed point along the ray).  Samples whose minor
 // coordinate lies in [-1.5, Mm + 0.5] are visited, so both taps stay inside the padded
 // row; every SEGB samples the position is re-anchored from float-float as an integer
 // column plus a Q.22 offset from it (the offset stays below 2^31 whatever the box size).
-__device__ __forceinline__ ff ray_full(const AngleRec& r, int k, int M, int Mm, const float* img, int ld) {
+template <int DT>
+__device__ __forceinline__ ff ray_full(const AngleRec& r, int k, int M, int Mm, const typename Stor<DT>::T* img,
+                                       int ld) {
     float sum = 0.f, cmp = 0.f;
     const float halfM = 0.5f * (float)(M - 1);
     const ff Ak = ff_add(r.A0, ff_mul_f((float)k, r.a_scale));
@@ -136,12 +143,12 @@ __device__ __forceinline__ ff ray_full(const AngleRec& r, int k, int M, int Mm, 
         int q = split_fixed22(ff_add(Ak, ff_mul_f((float)m0 - halfM, r.slope)), j0);
         const int mend = min(m0 + SEGB, mhi);
         float s0 = 0.f, s1 = 0.f;
-        const float* rp = img + (size_t)m0 * ld + j0;
+        const typename Stor<DT>::T* rp = img + (size_t)m0 * ld + j0;
 #pragma unroll 4
         for (int m = m0; m < mend; ++m, rp += ld, q += step) {
             const int j = q >> 22;
             const float mf = frac_int<22>(q);
-            const float v0 = rp[j], v1 = rp[j + 1];
+            const float v0 = to_f32<DT>(rp[j]), v1 = to_f32<DT>(rp[j + 1]);
             s0 += v0;
             s1 = fmaf(mf, v1 - v0, s1);
         }
@@ -153,9 +160,10 @@ __device__ __forceinline__ ff ray_full(const AngleRec& r, int k, int M, int Mm, 
 // Phase A over the units of one branch (row = 1: per-row sampling; the table lists those
 // angles first).  This block's units are ustart + member + i * size; warps take i from
 // *counter (preset to BNW by the caller, warp w starting at i = w).
-template <bool SOLO>
-__device__ __forceinline__ void phase_a_branch(const Ctx& C, const Team& T, int row, const float* img, int ld,
+template <bool SOLO, int DT>
+__device__ __forceinline__ void phase_a_branch(const Ctx& C, const Team& T, int row, const void* img_v, int ld,
                                                int pass, int* counter) {
+    const auto* img = static_cast<const typename Stor<DT>::T*>(img_v);
     const int tm = SOLO ? 0 : T.member, ts = SOLO ? 1 : T.size;
     const BatchRoi& R = *C.R;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -169,7 +177,7 @@ __device__ __forceinline__ void phase_a_branch(const Ctx& C, const Team& T, int 
         const int k = (unit - a * C.nchunk) * 32 + lane;
         const AngleRec& r = R.rec[a];
         if (k < r.width) {
-            ff tot = ray_full(r, k, M, Mm, img, ld);
+            ff tot = ray_full<DT>(r, k, M, Mm, img, ld);
             tot = ff_mul_f(r.inv_w, tot);
             const size_t o = (size_t)a * R.stride + k;
             if (pass == A_EXTER) {  // p' = (p - W x_fbp) + W_L x_fbp
@@ -198,8 +206,10 @@ __device__ __forceinline__ void phase_a_branch(const Ctx& C, const Team& T, int 
 
 // Phase B: this block's tiles are member + i * size, warps take i from *counter (preset
 // to BNW); lane = run of 8 pixels.  wstage: this warp's shared area.
-template <bool SOLO>
+template <bool SOLO, int DT>
 __device__ __forceinline__ void phase_b(const Ctx& C, const Team& T, int pass, int* counter, float* wstage) {
+    auto* xa = static_cast<typename Stor<DT>::T*>(C.xa);
+    auto* xaT = static_cast<typename Stor<DT>::T*>(C.xaT);
     const int tm = SOLO ? 0 : T.member, ts = SOLO ? 1 : T.size;
     const BatchRoi& R = *C.R;
     const int lane = threadIdx.x & 31;
@@ -285,12 +295,14 @@ __device__ __forceinline__ void phase_b(const Ctx& C, const Team& T, int pass, i
                     const int cnt = (gj < nx - 1) + (gj > 0) + (gi < ny - 1) + (gi > 0);
                     C.b.tau[o] = 1.f / (acc + (float)cnt);
                 }
-            } else if (R.reg == 0) {
+            } else if (R.reg == 0) {  // x in float; the projector reads its stored copy
                 const float step = R.weighting ? C.b.tau[o] : R.alpha;
-                float xn = fmaf(step, acc, C.xa[gi * C.lda + gj]);
+                float xn = fmaf(step, acc, C.b.x[o]);
                 xn = fmaxf(xn, 0.f);
-                C.xa[gi * C.lda + gj] = xn;
-                C.xaT[gj * C.ldaT + gi] = xn;
+                C.b.x[o] = xn;
+                const auto xs = from_f32<DT>(xn);
+                xa[gi * C.lda + gj] = xs;
+                xaT[gj * C.ldaT + gi] = xs;
             } else {
                 float dv = 0.f;
                 if (gj < nx - 1) dv += C.b.vx[o];
@@ -300,9 +312,9 @@ __device__ __forceinline__ void phase_b(const Ctx& C, const Team& T, int pass, i
                 const float xo = C.b.x[o];
                 const float xn = xo - C.b.tau[o] * (acc - dv);
                 C.b.x[o] = xn;
-                const float xb = 2.f * xn - xo;
-                C.xa[gi * C.lda + gj] = xb;
-                C.xaT[gj * C.ldaT + gi] = xb;
+                const auto xb = from_f32<DT>(2.f * xn - xo);
+                xa[gi * C.lda + gj] = xb;
+                xaT[gj * C.ldaT + gi] = xb;
             }
         }
         int nxt = 0;
@@ -312,46 +324,57 @@ __device__ __forceinline__ void phase_b(const Ctx& C, const Team& T, int pass, i
 }
 
 __device__ __forceinline__ void fill_team(const Ctx& C, float* p, size_t n, float v) {
-    for (size_t i = C.gtid; i < n; i += C.gthreads) p[i] = v;
+    for (size_t i = team_tid(C); i < n; i += C.gthreads) p[i] = v;
 }
 
 // Interior of both padded images := v, borders 0.
+template <int DT>
 __device__ __forceinline__ void set_images(const Ctx& C, float v) {
     const BatchRoi& R = *C.R;
     const int nx = R.nx, ny = R.ny;
-    for (int i = C.gtid; i < ny * C.lda; i += C.gthreads) {
+    auto* xab = static_cast<typename Stor<DT>::T*>(C.b.xa_base);
+    auto* xaTb = static_cast<typename Stor<DT>::T*>(C.b.xaT_base);
+    const auto sv = from_f32<DT>(v), zero = from_f32<DT>(0.f);
+    for (int i = team_tid(C); i < ny * C.lda; i += C.gthreads) {
         const int col = i % C.lda - kPad;
-        C.b.xa_base[i] = (col >= 0 && col < nx) ? v : 0.f;
+        xab[i] = (col >= 0 && col < nx) ? sv : zero;
     }
-    for (int i = C.gtid; i < nx * C.ldaT; i += C.gthreads) {
+    for (int i = team_tid(C); i < nx * C.ldaT; i += C.gthreads) {
         const int col = i % C.ldaT - kPad;
-        C.b.xaT_base[i] = (col >= 0 && col < ny) ? v : 0.f;
+        xaTb[i] = (col >= 0 && col < ny) ? sv : zero;
     }
 }
 
 // Both padded images := the box of x_fbp (rows from the padded grid image, columns
 // from its padded transpose), borders 0.
+// (The grid image has the region's storage type, so elements are copied as they are.)
+template <int DT>
 __device__ __forceinline__ void load_fbp_box(const Ctx& C) {
+    using T = typename Stor<DT>::T;
     const BatchRoi& R = *C.R;
     const int nx = R.nx, ny = R.ny;
-    for (int i = C.gtid; i < ny * C.lda; i += C.gthreads) {
+    auto* xab = static_cast<T*>(C.b.xa_base);
+    auto* xaTb = static_cast<T*>(C.b.xaT_base);
+    const T* g = static_cast<const T*>(R.xfbp);
+    const T* gT = static_cast<const T*>(R.xfbpT);
+    const T zero = from_f32<DT>(0.f);
+    for (int i = team_tid(C); i < ny * C.lda; i += C.gthreads) {
         const int r = i / C.lda, col = i - r * C.lda - kPad;
-        C.b.xa_base[i] = (col >= 0 && col < nx) ? R.xfbp[(size_t)(R.box_y0 + r) * R.xfbp_ld + R.box_x0 + col] : 0.f;
+        xab[i] = (col >= 0 && col < nx) ? g[(size_t)(R.box_y0 + r) * R.xfbp_ld + R.box_x0 + col] : zero;
     }
-    for (int i = C.gtid; i < nx * C.ldaT; i += C.gthreads) {
+    for (int i = team_tid(C); i < nx * C.ldaT; i += C.gthreads) {
         const int r = i / C.ldaT, col = i - r * C.ldaT - kPad;
-        C.b.xaT_base[i] =
-            (col >= 0 && col < ny) ? R.xfbpT[(size_t)(R.box_x0 + r) * R.xfbp_ld + R.box_y0 + col] : 0.f;
+        xaTb[i] = (col >= 0 && col < ny) ? gT[(size_t)(R.box_x0 + r) * R.xfbp_ld + R.box_y0 + col] : zero;
     }
 }
 
 // Both branches of phase A reading the images from global memory.
-template <bool SOLO>
+template <bool SOLO, int DT>
 __device__ __forceinline__ void phase_a_global(const Ctx& C, const Team& T, int pass, int* s_cnt) {
     for (int row = 1; row >= 0; --row) {
         if (threadIdx.x == 0) *s_cnt = BNW;
         __syncthreads();
-        phase_a_branch<SOLO>(C, T, row, row ? C.xa : C.xaT, row ? C.lda : C.ldaT, pass, s_cnt);
+        phase_a_branch<SOLO, DT>(C, T, row, row ? C.xa : C.xaT, row ? C.lda : C.ldaT, pass, s_cnt);
         __syncthreads();
     }
 }
@@ -363,9 +386,13 @@ __device__ __forceinline__ void phase_a_global(const Ctx& C, const Team& T, int 
 // that fall in the band (one float-float anchor per band and ray), then finishes the
 // ray as phase_a_branch does.  mbar[0..1]: the buffers' barriers, parity: their phase
 // bits (bit b for buffer b).  false: a wait gave up.
-template <bool SOLO>
-__device__ __forceinline__ bool phase_a_banded(const Ctx& C, const Team& T, int row, const float* img_base, int ld,
-                                               float* smem, uint64_t* mbar, unsigned& parity) {
+template <bool SOLO, int DT>
+__device__ __forceinline__ bool phase_a_banded(const Ctx& C, const Team& T, int row, const void* img_base_v, int ld,
+                                               float* smem_f, uint64_t* mbar, unsigned& parity) {
+    using TS = typename Stor<DT>::T;
+    constexpr unsigned ES = sizeof(TS);
+    const TS* img_base = static_cast<const TS*>(img_base_v);
+    TS* smem = reinterpret_cast<TS*>(smem_f);
     const BatchRoi& R = *C.R;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tm = SOLO ? 0 : T.member, ts = SOLO ? 1 : T.size;
@@ -405,14 +432,14 @@ __device__ __forceinline__ bool phase_a_banded(const Ctx& C, const Team& T, int 
         float sum = 0.f, cmp = 0.f;
         if (threadIdx.x == 0) {
             const int rows0 = M < kBandRows ? M : kBandRows;
-            bulk_load(smem, img_base, (unsigned)(sizeof(float) * rows0 * ld), &mbar[0]);
+            bulk_load(smem, img_base, ES * rows0 * ld, &mbar[0]);
         }
         for (int b = 0; b < nb; ++b) {
             const int bi = b & 1;
             if (threadIdx.x == 0 && b + 1 < nb) {  // the other buffer was released by the last barrier
                 const int rows = min(kBandRows, M - (b + 1) * kBandRows);
-                bulk_load(smem + (bi ^ 1) * band_floats, img_base + (size_t)(b + 1) * band_floats,
-                          (unsigned)(sizeof(float) * rows * ld), &mbar[bi ^ 1]);
+                bulk_load(smem + (bi ^ 1) * band_floats, img_base + (size_t)(b + 1) * band_floats, ES * rows * ld,
+                          &mbar[bi ^ 1]);
             }
             if (!mbar_wait(&mbar[bi], (parity >> bi) & 1u, T.wait_ns, T.err)) return false;
             parity ^= 1u << bi;
@@ -421,13 +448,13 @@ __device__ __forceinline__ bool phase_a_banded(const Ctx& C, const Team& T, int 
                 int j0;
                 int q = split_fixed22(ff_add(Ak, ff_mul_f((float)m0 - halfM, r.slope)), j0);
                 const int step = r.slope_q22;
-                const float* rp = smem + bi * band_floats + (m0 - b * kBandRows) * ld + kPad + j0;
+                const TS* rp = smem + bi * band_floats + (m0 - b * kBandRows) * ld + kPad + j0;
                 float s0 = 0.f, s1 = 0.f;
 #pragma unroll 4
                 for (int m = m0; m < m1; ++m, rp += ld, q += step) {
                     const int j = q >> 22;
                     const float mf = frac_int<22>(q);
-                    const float v0 = rp[j], v1 = rp[j + 1];
+                    const float v0 = to_f32<DT>(rp[j]), v1 = to_f32<DT>(rp[j + 1]);
                     s0 += v0;
                     s1 = fmaf(mf, v1 - v0, s1);
                 }
@@ -453,15 +480,17 @@ __device__ __forceinline__ bool phase_a_banded(const Ctx& C, const Team& T, int 
 }
 
 // CP gradient dual on this thread's pixels: v = proj_{|v| <= lambda}(v + sigma_v grad xbar).
+template <int DT>
 __device__ __forceinline__ void dual_grad(const Ctx& C) {
     const BatchRoi& R = *C.R;
     const int nimg = R.nx * R.ny;
-    for (int p = C.gtid; p < nimg; p += C.gthreads) {
+    const auto* xa = static_cast<const typename Stor<DT>::T*>(C.xa);
+    for (int p = team_tid(C); p < nimg; p += C.gthreads) {
         const int i = p / R.nx, j = p - i * R.nx;
-        const float* xp = C.xa + i * C.lda + j;
-        const float x0 = xp[0];
-        const float gx = j < R.nx - 1 ? xp[1] - x0 : 0.f;
-        const float gy = i < R.ny - 1 ? xp[C.lda] - x0 : 0.f;
+        const auto* xp = xa + i * C.lda + j;
+        const float x0 = to_f32<DT>(xp[0]);
+        const float gx = j < R.nx - 1 ? to_f32<DT>(xp[1]) - x0 : 0.f;
+        const float gy = i < R.ny - 1 ? to_f32<DT>(xp[C.lda]) - x0 : 0.f;
         const float ax = fmaf(R.sigma_v, gx, C.b.vx[p]);
         const float ay = fmaf(R.sigma_v, gy, C.b.vy[p]);
         const float m = sqrtf(ax * ax + ay * ay);
@@ -471,87 +500,93 @@ __device__ __forceinline__ void dual_grad(const Ctx& C) {
     }
 }
 
-// Solve region R into R.out.  smem: dynamic shared memory, at least stage_bytes(nx, ny)
-// and the per-warp phase-B areas; mbar[0..1]: two initialised mbarriers, parity their
-// phase bits.  Returns false when a wait gave up (error flag set): leave the kernel.
-template <bool SOLO>
+// Solve region R into R.out.  DT: storage of x_fbp and of the projector images (R.dt).
+// smem: dynamic shared memory, at least stage_bytes(nx, ny, esz) and the per-warp phase-B
+// areas; mbar[0..1]: two initialised mbarriers, parity their phase bits.  Returns false
+// when a wait gave up (error flag set): leave the kernel.
+template <bool SOLO, int DT>
 __device__ __forceinline__ bool solve_region(const BatchRoi& R, const RegionBufs& bufs, Team& T, float* smem,
                                              uint64_t* mbar, unsigned& parity, int* s_cnt) {
+    using TS = typename Stor<DT>::T;
+    constexpr int ES = (int)sizeof(TS);
     const int tid = threadIdx.x, warp = tid >> 5;
-    Ctx C;
-    C.R = &R;
-    C.b = bufs;
-    C.lda = padded_ld(R.nx);
-    C.ldaT = padded_ld(R.ny);
-    C.xa = bufs.xa_base + kPad;
-    C.xaT = bufs.xaT_base + kPad;
-    C.nchunk = (R.stride + 31) / 32;
-    C.gtid = T.member * BPT + tid;
-    C.gthreads = T.size * BPT;
+    __shared__ Ctx s_ctx;
+    if (tid == 0) {
+        Ctx& W = s_ctx;
+        W.R = &R;
+        W.b = bufs;
+        W.lda = padded_ld_e(R.nx, ES);
+        W.ldaT = padded_ld_e(R.ny, ES);
+        W.xa = static_cast<TS*>(bufs.xa_base) + kPad;
+        W.xaT = static_cast<TS*>(bufs.xaT_base) + kPad;
+        W.nchunk = (R.stride + 31) / 32;
+        W.member = SOLO ? 0 : T.member;
+        W.gthreads = (SOLO ? 1 : T.size) * BPT;
+        W.stage = stage_mode(R.nx, R.ny, ES);
+        if (W.stage == 0 && !(SOLO || T.size == 1)) W.stage = 2;  // same arithmetic as the staged image
+    }
+    __syncthreads();
+    const Ctx& C = s_ctx;
     const size_t nimg = (size_t)R.nx * R.ny, nwin = (size_t)R.na * R.stride;
-    const size_t bytes_row = sizeof(float) * (size_t)R.ny * C.lda;
-    const size_t bytes_col = sizeof(float) * (size_t)R.nx * C.ldaT;
-    C.stage = stage_mode(R.nx, R.ny);
-    if (C.stage == 0 && !(SOLO || T.size == 1)) C.stage = 2;  // same arithmetic as the staged image
+    const unsigned bytes_row = (unsigned)(ES * (size_t)R.ny * C.lda);
+    const unsigned bytes_col = (unsigned)(ES * (size_t)R.nx * C.ldaT);
 
     // ---- exterior: p' on the window rays, zero state
     fill_team(C, C.b.u, nwin, 0.f);
     fill_team(C, C.b.x, nimg, 0.f);
     fill_team(C, C.b.vx, nimg, 0.f);
     fill_team(C, C.b.vy, nimg, 0.f);
-    load_fbp_box(C);
+    load_fbp_box<DT>(C);
     if (!team_sync<SOLO>(T)) return false;
-    phase_a_global<SOLO>(C, T, A_EXTER, s_cnt);
+    phase_a_global<SOLO, DT>(C, T, A_EXTER, s_cnt);
     // ---- set-up: preconditioners / weights from the row and column sums
     if (R.reg == 1 || R.weighting) {
         if (!team_sync<SOLO>(T)) return false;  // the exterior pass has read the images
-        set_images(C, 1.f);
+        set_images<DT>(C, 1.f);
         if (!team_sync<SOLO>(T)) return false;
-        phase_a_global<SOLO>(C, T, A_ROWSUM, s_cnt);
+        phase_a_global<SOLO, DT>(C, T, A_ROWSUM, s_cnt);
         if (tid == 0) *s_cnt = BNW;
         __syncthreads();
-        phase_b<SOLO>(C, T, B_COLSUM, s_cnt, smem + warp * WARP_STAGE);
+        phase_b<SOLO, DT>(C, T, B_COLSUM, s_cnt, smem + warp * WARP_STAGE);
     }
     if (!team_sync<SOLO>(T)) return false;
-    set_images(C, 0.f);
+    set_images<DT>(C, 0.f);
     if (!team_sync<SOLO>(T)) return false;
 
     // ---- iterations
     for (int it = 0; it < R.iters; ++it) {
         if (C.stage == 0) {
             for (int row = 1; row >= 0; --row) {
-                if (tid == 0)
-                    bulk_load(smem, row ? bufs.xa_base : bufs.xaT_base, (unsigned)(row ? bytes_row : bytes_col), mbar);
-                if (row == 1 && R.reg == 1) dual_grad(C);  // reads xbar^k while the copy runs
+                if (tid == 0) bulk_load(smem, row ? bufs.xa_base : bufs.xaT_base, row ? bytes_row : bytes_col, mbar);
+                if (row == 1 && R.reg == 1) dual_grad<DT>(C);  // reads xbar^k while the copy runs
                 if (tid == 0) *s_cnt = BNW;
                 if (!mbar_wait(mbar, parity & 1u, T.wait_ns, T.err)) return false;
                 parity ^= 1u;
                 __syncthreads();
-                phase_a_branch<SOLO>(C, T, row, smem + kPad, row ? C.lda : C.ldaT, A_SOLVE, s_cnt);
+                phase_a_branch<SOLO, DT>(C, T, row, reinterpret_cast<TS*>(smem) + kPad, row ? C.lda : C.ldaT,
+                                         A_SOLVE, s_cnt);
                 __syncthreads();
             }
         } else if (C.stage == 1) {
-            if (R.reg == 1) dual_grad(C);
+            if (R.reg == 1) dual_grad<DT>(C);
             for (int row = 1; row >= 0; --row)
-                if (!phase_a_banded<SOLO>(C, T, row, row ? bufs.xa_base : bufs.xaT_base, row ? C.lda : C.ldaT, smem,
-                                          mbar, parity))
+                if (!phase_a_banded<SOLO, DT>(C, T, row, row ? bufs.xa_base : bufs.xaT_base, row ? C.lda : C.ldaT,
+                                              smem, mbar, parity))
                     return false;
         } else {
-            if (R.reg == 1) dual_grad(C);
-            phase_a_global<SOLO>(C, T, A_SOLVE, s_cnt);
+            if (R.reg == 1) dual_grad<DT>(C);
+            phase_a_global<SOLO, DT>(C, T, A_SOLVE, s_cnt);
         }
         if (!team_sync<SOLO>(T)) return false;  // u, v of this iteration complete
         if (tid == 0) *s_cnt = BNW;
         __syncthreads();
-        phase_b<SOLO>(C, T, B_SOLVE, s_cnt, smem + warp * WARP_STAGE);
+        phase_b<SOLO, DT>(C, T, B_SOLVE, s_cnt, smem + warp * WARP_STAGE);
         if (!team_sync<SOLO>(T)) return false;  // x, xbar complete
     }
-    // ---- crop into the output buffer
-    const float* xs = R.reg == 0 ? C.xa : C.b.x;
-    const int xs_ld = R.reg == 0 ? C.lda : R.nx;
-    for (int p = C.gtid; p < (int)nimg; p += C.gthreads) {
+    // ---- crop into the output buffer (x is kept in float for both solvers)
+    for (int p = team_tid(C); p < (int)nimg; p += C.gthreads) {
         const int i = p / R.nx, j = p - i * R.nx;
-        float v = xs[i * xs_ld + j];
+        float v = C.b.x[p];
         if (R.crop) {
             const float dx = (float)j - R.cxl, dy = (float)i - R.cyl;
             if (dx * dx + dy * dy > R.r2) v = 0.f;
@@ -559,6 +594,15 @@ __device__ __forceinline__ bool solve_region(const BatchRoi& R, const RegionBufs
         R.out[p] = v;
     }
     return true;
+}
+
+// Dispatch on the region's storage type.
+template <bool SOLO>
+__device__ __forceinline__ bool solve_region_dt(const BatchRoi& R, const RegionBufs& bufs, Team& T, float* smem,
+                                                uint64_t* mbar, unsigned& parity, int* s_cnt) {
+    if (R.dt == 1) return solve_region<SOLO, 1>(R, bufs, T, smem, mbar, parity, s_cnt);
+    if (R.dt == 2) return solve_region<SOLO, 2>(R, bufs, T, smem, mbar, parity, s_cnt);
+    return solve_region<SOLO, 0>(R, bufs, T, smem, mbar, parity, s_cnt);
 }
 
 }  // namespace rs

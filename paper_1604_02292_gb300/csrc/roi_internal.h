@@ -148,19 +148,27 @@ enum BackMode { BACK_PLAIN = 0, BACK_SIRT = 1, BACK_CP = 2 };
 // of each row (indices -2, -1 and extent .. ld - 3) hold zeros.
 constexpr int kPad = 2;
 ROI_HD int padded_ld(int extent) { return (extent + 2 * kPad + 3) / 4 * 4; }
+// The same for elements of esz bytes (rows stay multiples of 16 bytes).
+ROI_HD int padded_ld_e(int extent, int esz) {
+    const int unit = 16 / esz;
+    return (extent + 2 * kPad + unit - 1) / unit * unit;
+}
+// Bytes of a storage type: 0 float, 1 bfloat16, 2 half.
+ROI_HD int dt_size(int dt) { return dt == 0 ? 4 : 2; }
 
 struct FwdArgs {
     const AngleRec* rec;   // [na]
     int na, stride;        // window rows and their stride
     int nx, ny;            // frame size
-    const float* img;      // frame image [ny][img_ld], padded
-    const float* imgT;     // its transpose [nx][imgT_ld], padded
+    const void* img;       // frame image [ny][img_ld], padded (float, or dt for FWD_EXTERIOR)
+    const void* imgT;      // its transpose [nx][imgT_ld], padded
     int img_ld, imgT_ld;
+    int dt;                // FWD_EXTERIOR: storage of img, imgT and p (0 float, 1 bfloat16, 2 half)
     int seg_len;           // set by launch_forward
     Rect hole;             // FWD_EXTERIOR: frame pixels treated as zero (w = 0: none)
     float* out;            // [na][stride]
     // FWD_EXTERIOR: out = p[a][d0 + k] - W_F x
-    const float* p;        // [na][nd]
+    const void* p;         // [na][nd], storage dt
     int nd;
     // FWD_SIRT: out = (pp - W x) * (R ? R[a][k] : 1)
     // FWD_CP:   out = (out + sig (W x - pp)) / (1 + sig / 2), sig = R ? R[a][k] : sig_scalar
@@ -197,7 +205,17 @@ int back_groups(int na, int nx, int ny);
 void launch_forward(FwdMode mode, const FwdArgs& a, cudaStream_t st);
 void launch_back(BackMode mode, const BackArgs& a, cudaStream_t st);
 // hodd[t] = s h_{2t+1}; ctail = s (h0 + 2 sum_{odd m < nd} h_m), s = pi / N_theta
-void launch_ramp(const float* p, const float* hodd, float* q, int na, int nd, float ctail, cudaStream_t st);
+void launch_ramp(const void* p, int dt, const float* hodd, float* q, int na, int nd, float ctail, cudaStream_t st);
+// Storage conversions (dt: 0 float, 1 bfloat16, 2 half; round to nearest even):
+// dst[i] = src[i] for n elements
+void launch_convert(const void* src, int src_dt, void* dst, int dst_dt, size_t n, cudaStream_t st);
+// dst (storage dt, padded rows of dst_ld, pads untouched) = src [rows][cols] float (row stride
+// src_ld); transpose: dst[c][r] = src[r][c]
+void launch_store_padded(const float* src, int src_ld, void* dst, int dst_dt, int dst_ld, int rows, int cols,
+                         int transpose, cudaStream_t st);
+// dst [rows][cols] float (row stride dst_ld) = src (storage dt, row stride src_ld)
+void launch_load_padded(const void* src, int src_dt, int src_ld, float* dst, int dst_ld, int rows, int cols,
+                        cudaStream_t st);
 // out[c][r] = in[r][c] (row strides in_ld, out_ld)
 void launch_transpose(const float* in, int in_ld, float* out, int out_ld, int rows, int cols, cudaStream_t st);
 // out[r][c] = in[r][c] with row strides in_ld, out_ld (pads untouched)
@@ -265,19 +283,19 @@ cudaError_t launch_persist(const PersistLaunch& L, cudaStream_t st);
 // global memory.
 constexpr size_t kStageMaxBytes = 200 * 1024;
 constexpr int kBandRows = 24;
-ROI_HD int stage_mode(int nx, int ny) {
-    const size_t lr = (size_t)padded_ld(nx), lc = (size_t)padded_ld(ny);
-    const size_t full = sizeof(float) * (ny * lr > nx * lc ? ny * lr : nx * lc);
+ROI_HD int stage_mode(int nx, int ny, int esz) {
+    const size_t lr = (size_t)padded_ld_e(nx, esz), lc = (size_t)padded_ld_e(ny, esz);
+    const size_t full = (size_t)esz * (ny * lr > nx * lc ? ny * lr : nx * lc);
     if (full <= kStageMaxBytes) return 0;
-    const size_t band = sizeof(float) * 2 * kBandRows * (lr > lc ? lr : lc);
+    const size_t band = (size_t)esz * 2 * kBandRows * (lr > lc ? lr : lc);
     return band <= kStageMaxBytes ? 1 : 2;
 }
-// Dynamic shared memory the staging of a box of nx x ny needs.
-ROI_HD size_t stage_bytes(int nx, int ny) {
-    const size_t lr = (size_t)padded_ld(nx), lc = (size_t)padded_ld(ny);
-    const int m = stage_mode(nx, ny);
-    if (m == 0) return sizeof(float) * (ny * lr > nx * lc ? ny * lr : nx * lc);
-    if (m == 1) return sizeof(float) * 2 * kBandRows * (lr > lc ? lr : lc);
+// Dynamic shared memory the staging of a box of nx x ny (elements of esz bytes) needs.
+ROI_HD size_t stage_bytes(int nx, int ny, int esz) {
+    const size_t lr = (size_t)padded_ld_e(nx, esz), lc = (size_t)padded_ld_e(ny, esz);
+    const int m = stage_mode(nx, ny, esz);
+    if (m == 0) return (size_t)esz * (ny * lr > nx * lc ? ny * lr : nx * lc);
+    if (m == 1) return (size_t)esz * 2 * kBandRows * (lr > lc ? lr : lc);
     return 0;
 }
 
@@ -295,10 +313,11 @@ struct BatchRoi {
     // exterior inputs: p' = resid + W_L (box of x_fbp)
     const float* resid;    // p - W x_fbp over every ray [N_theta][resid_ld] (original angle order)
     int resid_ld;
-    const float* xfbp;     // padded grid image, element (0,0), row stride xfbp_ld
-    const float* xfbpT;    // its padded transpose, same stride
+    const void* xfbp;      // padded grid image (storage dt), element (0,0), row stride xfbp_ld
+    const void* xfbpT;     // its padded transpose, same stride
     int xfbp_ld;
     int box_x0, box_y0;
+    int dt;                // storage of x_fbp and of the solver's projector images xa / xaT
 };
 
 struct BatchArgs {
@@ -331,8 +350,8 @@ struct RegionBufs {
     float* vx;
     float* vy;
     float* tau;
-    float* xa_base;
-    float* xaT_base;
+    void* xa_base;         // storage dt of the region (float, bfloat16 or half)
+    void* xaT_base;
 };
 
 // ---- serving: one cooperative launch whose blocks take requests from rings in
@@ -379,9 +398,10 @@ cudaError_t launch_serve(const ServeArgs& A, int blocks, cudaStream_t st);
 struct SinoView {
     int N, na, nd;
     const double* angles;
-    const float* xfbp;
-    const float* xfbpT;
+    const void* xfbp;
+    const void* xfbpT;
     int xfbp_ld;
+    int dt;
     const float* resid;
     int resid_ld;
 };

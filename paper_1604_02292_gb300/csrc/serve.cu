@@ -164,9 +164,8 @@ __global__ void __launch_bounds__(BPT, 1) k_serve(const ServeArgs A) {
             reinterpret_cast<unsigned*>(myrec)[w] = ld_relaxed_sys_u32(rp + 4 * (size_t)w);
         if (tid == 0) s_slot.roi.rec = myrec;
         __syncthreads();
-        const bool ok = s_team.size == 1 ? rs::solve_region<true>(s_slot.roi, s_slot.bufs, s_team, smem, s_mbar, parity, &s_cnt)
-                                         : rs::solve_region<false>(s_slot.roi, s_slot.bufs, s_team, smem, s_mbar, parity,
-                                                                   &s_cnt);
+        // one code path for both pools (a single block is a team of one at run time)
+        const bool ok = rs::solve_region_dt<false>(s_slot.roi, s_slot.bufs, s_team, smem, s_mbar, parity, &s_cnt);
         if (!ok) return;
         __threadfence_system();  // this thread's output stores, before the completion word
         if (!rs::team_sync<false>(s_team)) return;

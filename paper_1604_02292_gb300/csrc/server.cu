@@ -92,12 +92,12 @@ struct Arena {
 struct StateLayout {
     size_t pp, u, sig, x, vx, vy, tau, xa, xaT, total;
 };
-StateLayout state_layout(int na, int stride, int nx, int ny) {
+StateLayout state_layout(int na, int stride, int nx, int ny, int esz) {
     StateLayout L{};
     const size_t win = round_up(sizeof(float) * (size_t)na * stride);
     const size_t img = round_up(sizeof(float) * (size_t)nx * ny);
-    const size_t pr = round_up(sizeof(float) * (size_t)ny * roi::padded_ld(nx));
-    const size_t pc = round_up(sizeof(float) * (size_t)nx * roi::padded_ld(ny));
+    const size_t pr = round_up((size_t)esz * ny * roi::padded_ld_e(nx, esz));  // projector images: storage type
+    const size_t pc = round_up((size_t)esz * nx * roi::padded_ld_e(ny, esz));
     size_t o = 0;
     L.pp = o, o += win;
     L.u = o, o += win;
@@ -351,6 +351,7 @@ void publish(roi_server* s, int pi, Req* r, size_t slot) {
     R.xfbp_ld = v.xfbp_ld;
     R.box_x0 = r->box.x0;
     R.box_y0 = r->box.y0;
+    R.dt = v.dt;
     unsigned char* base = s->arena_d + r->dev_off;
     roi::RegionBufs& B = hdr.bufs;
     B.pp = reinterpret_cast<float*>(base + r->lay.pp);
@@ -360,8 +361,8 @@ void publish(roi_server* s, int pi, Req* r, size_t slot) {
     B.vx = reinterpret_cast<float*>(base + r->lay.vx);
     B.vy = reinterpret_cast<float*>(base + r->lay.vy);
     B.tau = reinterpret_cast<float*>(base + r->lay.tau);
-    B.xa_base = reinterpret_cast<float*>(base + r->lay.xa);
-    B.xaT_base = reinterpret_cast<float*>(base + r->lay.xaT);
+    B.xa_base = base + r->lay.xa;
+    B.xaT_base = base + r->lay.xaT;
     hdr.seq = (unsigned long long)r->ticket + 1ull;
     std::memcpy(sp, &hdr, sizeof hdr);
     std::memcpy(sp + roi::serve_slot_header_bytes, r->rec.data(), sizeof(AngleRec) * r->rec.size());
@@ -654,7 +655,7 @@ roi_status roi_server_submit(roi_server_t s, int sino_id, const roi_region* regi
         delete r;
         return sfail(s, ROI_EINVAL, "submit: extended box misses the %d x %d grid", v.N, v.N);
     }
-    r->lay = state_layout(v.na, r->stride, r->box.w, r->box.h);
+    r->lay = state_layout(v.na, r->stride, r->box.w, r->box.h, roi::dt_size(v.dt));
     r->host_bytes = sizeof(float) * (size_t)r->box.w * r->box.h;
     if (round_up(r->lay.total) > s->darena.size || round_up(r->host_bytes) > s->harena.size) {
         const size_t need = r->lay.total;
@@ -793,17 +794,17 @@ void roi_server_destroy(roi_server_t s) {
     delete s;
 }
 
-roi_status roi_server_footprint(int n_pix, int n_angles, int n_det, const roi_region* region, size_t* device_bytes,
-                                size_t* host_bytes, int* box_side) {
+roi_status roi_server_footprint(int n_pix, int n_angles, int n_det, roi_dtype storage, const roi_region* region,
+                                size_t* device_bytes, size_t* host_bytes, int* box_side) {
     if (n_pix < 1 || n_angles < 1 || n_det < 1 || n_pix > 65536 || n_angles > 65536 || n_det > 8192 ||
-        !finite_region(region))
+        !finite_region(region) || (storage != ROI_F32 && storage != ROI_BF16 && storage != ROI_F16))
         return ROI_EINVAL;
     std::vector<double> ang(n_angles);
     for (int a = 0; a < n_angles; ++a) ang[a] = a * 3.14159265358979323846 / n_angles;
     Rect box{};
     int stride = 0, nrow = 0;
     if (!plan_request(n_pix, n_angles, n_det, ang.data(), *region, &box, &stride, &nrow, nullptr)) return ROI_EINVAL;
-    const StateLayout L = state_layout(n_angles, stride, box.w, box.h);
+    const StateLayout L = state_layout(n_angles, stride, box.w, box.h, roi::dt_size((int)storage));
     if (device_bytes) *device_bytes = round_up(L.total);
     if (host_bytes) *host_bytes = round_up(sizeof(float) * (size_t)box.w * box.h);
     if (box_side) *box_side = std::max(box.w, box.h);

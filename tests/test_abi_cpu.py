@@ -77,8 +77,10 @@ def test_plan_rejects_bad_geometry():
     g = R.Geometry(0, 64, 128, None, R.ROI_F32)
     info = R.SolveInfo()
     assert R.roi_recon_plan(g, R.Region(1, 1, 1, 0), info, None, None) == R.ROI_EINVAL
-    g = R.Geometry(128, 64, 128, None, R.ROI_BF16)
+    g = R.Geometry(128, 64, 128, None, 7)  # unknown storage type
     assert R.roi_recon_plan(g, R.Region(1, 1, 1, 0), info, None, None) == R.ROI_EINVAL
+    g = R.Geometry(128, 64, 128, None, R.ROI_BF16)  # 16-bit storage plans like float32
+    assert R.roi_recon_plan(g, R.Region(64, 64, 8, 4), info, None, None) == R.ROI_OK
 
 
 def test_create_rejects_bad_geometry_without_touching_the_gpu():
@@ -98,19 +100,22 @@ def test_poisson_noise_model():
     assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("storage", [R.ROI_F32, R.ROI_BF16])
 @pytest.mark.parametrize("region", [(1000.0, 900.0, 16.0, 8.0), (1024.0, 1024.0, 256.0, 128.0),
                                     (5.0, 2040.0, 100.0, 50.0)])
-def test_server_footprint_host_only(region):
-    """The server's per-request budget: three windows [N_theta][stride], four box arrays and
-    the two padded images, each rounded to 256 bytes; the result area is the box."""
+def test_server_footprint_host_only(region, storage):
+    """The server's per-request budget: three float windows [N_theta][stride], four float box
+    arrays and the two padded projector images in the storage type (rows padded to 16 bytes),
+    each rounded to 256 bytes; the result area is the box."""
     N, na, nd = 2048, 180, 2048
-    dev, host, side = R.server_footprint(N, na, nd, region)
+    dev, host, side = R.server_footprint(N, na, nd, region, storage)
     pl = R.plan(N, na, nd, region)
     w, h = pl.box[2], pl.box[3]
     assert side == max(w, h)
     r256 = lambda n: (n + 255) // 256 * 256
-    ld = lambda e: (e + 4 + 3) // 4 * 4
-    expect = 3 * r256(4 * na * pl.window_stride) + 4 * r256(4 * w * h) + r256(4 * h * ld(w)) + r256(4 * w * ld(h))
+    es = 4 if storage == R.ROI_F32 else 2
+    ld = lambda e: (e + 4 + 16 // es - 1) // (16 // es) * (16 // es)
+    expect = 3 * r256(4 * na * pl.window_stride) + 4 * r256(4 * w * h) + r256(es * h * ld(w)) + r256(es * w * ld(h))
     assert dev == expect
     assert host == r256(4 * w * h)
 
@@ -122,3 +127,5 @@ def test_server_footprint_rejects_bad_input():
         R.server_footprint(256, 96, 272, (100.0, 100.0, -1.0, 1.0))
     with pytest.raises(R.RoiError):
         R.server_footprint(0, 96, 272, (100.0, 100.0, 5.0, 1.0))
+    with pytest.raises(R.RoiError):
+        R.server_footprint(256, 96, 272, (100.0, 100.0, 5.0, 1.0), storage=9)
