@@ -66,7 +66,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=sorted(WL.WORKLOADS) + sorted(WL.BATCHES) + sorted(WL.SERVING))
+                    choices=sorted(WL.WORKLOADS) + sorted(WL.BATCHES) + sorted(WL.SERVING) + sorted(WL.PRECISION))
+    ap.add_argument("--storage", default="bf16", choices=["f32", "bf16", "f16"],
+                    help="precision workloads: storage type measured against float32 storage")
     ap.add_argument("--batch-count", type=int, default=None,
                     help="batch workloads: solve this many of the regions per step (default: all)")
     ap.add_argument("--requests", type=int, default=256, help="serving workloads: requests in the run")
@@ -637,6 +639,88 @@ def run_serve(args):
     return 0
 
 
+def run_precision(args):
+    """Precision workload: the regions solved through the server (all by teams, submitted at
+    once) with 16-bit storage of the resident sinogram, FBP image and projector images;
+    value = regions/s of that run.  Errors per result, relative L2: against the float32-
+    storage path fed the same quantized sinogram (the error the 16-bit storage adds), and
+    against the float32 path on the unrounded sinogram (adds the rounding of the data)."""
+    import torch
+
+    import paper_1604_02292_gb300 as R
+    from paper_1604_02292_gb300 import synth
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    w = WL.PRECISION[args.workload]
+    count = args.batch_count or 32
+    items = WL.precision_regions(w, seed=0, count=count)
+    phantom = synth.random_phantom(w.N, w.n_ellipses, texture=w.texture, seed=0)
+    p = synth.poisson_noise(synth.analytic_sinogram(phantom, w.n_angles, w.n_det), w.I0, seed=1000).astype(np.float32)
+    st_code = {"f32": R.ROI_F32, "bf16": R.ROI_BF16, "f16": R.ROI_F16}[args.storage]
+    tdt = {R.ROI_F32: torch.float32, R.ROI_BF16: torch.bfloat16, R.ROI_F16: torch.float16}[st_code]
+    p_dev = torch.from_numpy(p).cuda()
+    p_q = p_dev.to(tdt)  # the quantized data, as the 16-bit handle stores it
+
+    def serve(storage, sino):
+        rr = R.RoiRecon(*w.geometry(), storage=storage)
+        rr.set_sinogram(sino)
+        rr.fbp()
+        torch.cuda.synchronize()
+        srv = R.Server(team_blocks=args.team_blocks or 8, teams=args.teams, large_side=1, idle_us=1000)
+        srv.add(rr)
+        srv.submit(0, items[0][0], dict(items[0][1], iters=2))  # warm-up
+        srv.drain()
+        for c in srv.poll():
+            srv.take(c["id"], (c["box"][3], c["box"][2]))
+        time.sleep(0.05)  # the serving kernel leaves after 1 ms idle: the timed run launches it
+        n0 = R.roi_recon_launch_count()
+        with ClockSampler(local) as clk:
+            t0 = time.monotonic()
+            ids = {srv.submit(0, reg, prm): k for k, (reg, prm) in enumerate(items)}
+            srv.drain(3600e3)
+            t = time.monotonic() - t0
+        res = {}
+        for c in srv.poll():
+            res[ids[c["id"]]] = srv.take(c["id"], (c["box"][3], c["box"][2]))
+        st = srv.stats()
+        srv.close()
+        launches = int(R.roi_recon_launch_count() - n0)
+        rr.close()
+        return t, res, st, launches, clk.summary()
+
+    def rel(a, b):
+        return float(np.linalg.norm(a.astype(np.float64) - b) / max(np.linalg.norm(b), 1e-30))
+
+    t16, r16, st16, launches, clocks = serve(st_code, p_dev)
+    t32, r32q, _, _, _ = serve(R.ROI_F32, p_q)        # float32 storage, same quantized data
+    _, r32, _, _, _ = serve(R.ROI_F32, p_dev)          # float32 storage, unrounded data
+    e_store = [rel(r16[k], r32q[k]) for k in range(count)]
+    e_total = [rel(r16[k], r32[k]) for k in range(count)]
+    pl = R.plan(*w.geometry(), items[0][0])
+    nx, ny = pl.box[2], pl.box[3]
+    lerps_one = w.iters * (sum(pl.width) * max(nx, ny) + nx * ny * w.n_angles)
+    line = {
+        "metric": "roi_solves_per_s", "value": count / t16, "unit": "solves/s", "n_gpus": ws, "steps": 1,
+        "warmup": 1, "ms_per_step": t16 * 1e3, "higher_is_better": True, "dtype": args.storage + " storage, f32 math",
+        "data": "synthetic", "scaling": "strong",
+        "config": {"workload": w.name, "N": w.N, "n_angles": w.n_angles, "n_det": w.n_det, "regions": count,
+                   "radius": w.radius, "margin": w.margin, "box": nx, "iters": w.iters, "solver": "CP-TV",
+                   "lambda": w.lam, "I0": w.I0, "path": "server, teams of blocks, all submitted at once"},
+        "float32_storage": {"value": count / t32, "unit": "solves/s"},
+        "error_storage_vs_float32_same_data": {"max": max(e_store), "median": statistics.median(e_store),
+                                               "per_result": e_store},
+        "error_vs_float32_unrounded_data": {"max": max(e_total), "median": statistics.median(e_total)},
+        "server": {k: st16[k] for k in ("teams", "team_blocks", "device_peak")},
+        "gpu_launches": launches,
+        "projector_Glerp_s": lerps_one * count / t16 / 1e9,
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -645,6 +729,8 @@ def main():
         return run_batch(args)
     if args.workload in WL.SERVING:
         return run_serve(args)
+    if args.workload in WL.PRECISION:
+        return run_precision(args)
     return run_ours(args)
 
 

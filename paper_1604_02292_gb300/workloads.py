@@ -164,3 +164,45 @@ def arrivals(w: ServeWorkload, seed: int = 0, count: int = 256, rate: float | No
     gaps = rng.exponential(1.0 / (rate or w.rate), size=count)
     gaps[0] = 0.0
     return np.cumsum(gaps)
+
+
+@dataclasses.dataclass(frozen=True)
+class PrecisionWorkload:
+    """Large regions on a large grid with 16-bit storage: ROI centres uniform in the disk
+    where the ROI lies inside the object, fixed radius and margin, TV by Chambolle-Pock."""
+    name: str
+    N: int
+    n_angles: int
+    n_det: int
+    n_ellipses: int
+    texture: bool
+    I0: float
+    count: int
+    radius: float
+    margin: float
+    iters: int
+    lam: float
+
+    def geometry(self):
+        return self.N, self.n_angles, self.n_det
+
+
+PRECISION = {
+    # 4096 x 4096, 1024 angles, 4096 bins, 50 ellipses, I0 = 1e3; 256 regions of radius 256 px,
+    # margin 128 px (box 768 x 768), CP-TV lambda = 0.01, 200 iterations
+    "roi_precision_4096": PrecisionWorkload("roi_precision_4096", 4096, 1024, 4096, 50, False, 1e3, 256, 256.0,
+                                            128.0, 200, 0.01),
+}
+
+
+def precision_regions(w: PrecisionWorkload, seed: int = 0, count: int | None = None):
+    """[(region, params)] of the precision workload (the first `count`)."""
+    rng = np.random.default_rng(seed + 7000)
+    out = []
+    c = (w.N - 1) / 2.0
+    for _ in range(w.count if count is None else count):
+        rho = (w.N / 2.0 - w.radius) * math.sqrt(rng.uniform(0.0, 1.0))
+        phi = rng.uniform(0.0, 2.0 * math.pi)
+        out.append(((c + rho * math.cos(phi), c + rho * math.sin(phi), w.radius, w.margin),
+                    dict(reg=1, iters=w.iters, lam=w.lam)))
+    return out

@@ -148,6 +148,38 @@ def test_batch_and_server_16bit(data, handle):
         assert err <= SOLVE_TOL[st]
 
 
+
+def test_precision_geometry_4096_sampled():
+    """The 4096 x 4096 / 1024-angle / 4096-bin geometry with bfloat16 storage: one region of
+    radius 256 px (box 768 x 768, band-streamed), 3 CP iterations, served by a team, against
+    the oracle fed the same quantized sinogram."""
+    from paper_1604_02292_gb300 import workloads as WL
+
+    w = WL.PRECISION["roi_precision_4096"]
+    (region, prm), = WL.precision_regions(w, seed=0, count=1)
+    prm = dict(prm, iters=3)
+    ph = synth.random_phantom(w.N, w.n_ellipses, texture=w.texture, seed=0)
+    p = synth.poisson_noise(synth.analytic_sinogram(ph, w.n_angles, w.n_det), w.I0, seed=1000).astype(np.float32)
+    rr = R.RoiRecon(*w.geometry(), storage=R.ROI_BF16)
+    rr.set_sinogram(torch.from_numpy(p).cuda())
+    rr.fbp()
+    with R.Server(team_blocks=8, teams=4, large_side=1) as s:
+        s.add(rr)
+        rid = s.submit(0, region, prm)
+        s.drain(300000.0)
+        (c,) = s.poll()
+        x = s.take(rid, (c["box"][3], c["box"][2]))
+    g = oracle.Geometry(*w.geometry())
+    pq = quantize(p, R.ROI_BF16)
+    xf = oracle.fbp(g, pq)
+    box = oracle.roi_box(w.N, *region)
+    pp = oracle.exterior(g, box, pq, xf)
+    xo = oracle.cp_tv(g, box, pp, prm["iters"], prm["lam"], precond=1)
+    err = rel_l2(x, xo)
+    MEASURED[("geometry_4096", R.ROI_BF16)] = err
+    assert err <= SOLVE_TOL[R.ROI_BF16]
+
+
 def test_report_measured_errors():
     """Prints the measured errors (pytest -s) so they can be quoted."""
     for key in sorted(MEASURED, key=str):
