@@ -64,6 +64,12 @@ def _load():
             lib.orc_objective.restype = ctypes.c_double
             lib.orc_power_norm.argtypes = [_I, _I, _I, _D] + i7 + [_I]
             lib.orc_power_norm.restype = ctypes.c_double
+            lib.orc_filtcalc.argtypes = [_I, _I, _I, _D, _I, ctypes.c_double, _D]
+            lib.orc_filter_conv.argtypes = [_I, _I, _D, _D, _D]
+            lib.orc_disc.argtypes = [_I, _I, _I, _D, _D, _D, _D]
+            lib.orc_disc.restype = ctypes.c_double
+            lib.orc_filter_method.argtypes = [_I, _I, _I, _D] + i7 + [_D, _I, ctypes.c_double, _D, _D,
+                                                                      ctypes.c_double, ctypes.c_double, _D]
             lib.orc_grad.argtypes = [_I, _I, _D, _D, _D]
             lib.orc_div.argtypes = [_I, _I, _D, _D, _D]
             _lib = lib
@@ -237,3 +243,61 @@ def solve_local(g: Geometry, p, region, reg: str = "sirt", iters: int = 200, lam
     else:
         x = cp_tv(g, box, pp, iters, lam, precond=precond)
     return x, box, pp, xfbp
+
+
+# ---- the paper's own local method (Sec. 3) ------------------------------------------
+
+def filtcalc(g: Geometry, n: int, alpha=None) -> np.ndarray:
+    """Alg. filtcalc: filters u_k = alpha W' q_k, k = 1..n, [n][n_angles][2 n_det - 1]
+    (tap m at index m + n_det - 1)."""
+    alpha = 1.0 / (g.na * g.nd) if alpha is None else float(alpha)
+    out = np.empty((int(n), g.na, 2 * g.nd - 1), np.float64)
+    _load().orc_filtcalc(*g._g(), int(n), alpha, _p(out))
+    return out
+
+
+def filter_conv(g: Geometry, uk, p) -> np.ndarray:
+    """C_{u_k} p: per-angle linear convolution of the sinogram with filter uk [n_angles][2 n_det - 1]."""
+    uk = _f64(uk).reshape(g.na, 2 * g.nd - 1)
+    p = _f64(p).reshape(g.na, g.nd)
+    out = np.empty_like(p)
+    _load().orc_filter_conv(g.na, g.nd, _p(uk), _p(p), _p(out))
+    return out
+
+
+def disc(g: Geometry, p):
+    """Disc subtraction (Sec. 3.3): (grey value, p - g W D, D)."""
+    p = _f64(p).reshape(g.na, g.nd)
+    pd = np.empty_like(p)
+    D = np.empty((g.N, g.N), np.float64)
+    gv = _load().orc_disc(*g._g(), _p(p), _p(pd), _p(D))
+    return gv, pd, D
+
+
+def filter_method(g: Geometry, box, p, u, n=None, alpha=None, shift=None, lo=0.0, hi=np.inf) -> np.ndarray:
+    """Alg. method with the box constraint [lo, hi] on the local part ``box``; ``p`` is the
+    (disc-subtracted) sinogram, ``u`` the filters of ``filtcalc``, ``shift`` the image added
+    back after reconstruction (box-shaped, or None)."""
+    alpha = 1.0 / (g.na * g.nd) if alpha is None else float(alpha)
+    n = u.shape[0] if n is None else int(n)
+    box = _rect(box)
+    p = _f64(p).reshape(g.na, g.nd)
+    u = _f64(u)
+    x = np.empty((box[3], box[2]), np.float64)
+    sh = None if shift is None else _f64(shift).reshape(box[3], box[2])
+    _load().orc_filter_method(*g._g(), *box, _p(p), n, alpha, _p(u), _p(sh) if sh is not None else None,
+                              float(lo), float(hi), _p(x))
+    return x
+
+
+def filter_solve(g: Geometry, p, region, iters: int, u=None, nonneg: bool = True):
+    """The paper's local method end to end: disc subtraction, filters, Alg. method with
+    x >= 0 (or no constraint), the disc added back on the box.  Returns (x_box, box)."""
+    box = roi_box(g.N, *region)
+    gv, pd, D = disc(g, p)
+    if u is None:
+        u = filtcalc(g, iters)
+    x0, y0, w, h = box
+    shift = gv * D[y0:y0 + h, x0:x0 + w]
+    x = filter_method(g, box, pd, u, n=iters, shift=shift, lo=0.0 if nonneg else -np.inf)
+    return x, box

@@ -20,6 +20,9 @@
  *   Sec. 1     the exterior-subtraction ROI scheme: subtract the reprojection of a
  *              global reconstruction outside the ROI, then reconstruct the ROI
  *              algebraically.
+ *   Sec. 3     the paper's own local method: filters approximating SIRT (Alg. filtcalc,
+ *              Eq. filtcalc, Eq. sirtapp), the local recursion with a prior term
+ *              (Alg. method, Eq. localmethod) and the disc subtraction (Sec. 3.3).
  *
  * Readings where the paper is silent (each one is listed in the design notes):
  *   - W is Joseph's method: one ray per bin centre; when |cos| >= |sin| (ties,
@@ -38,6 +41,11 @@
  *   - Chambolle-Pock uses the diagonal preconditioning of Pock & Chambolle (2011,
  *     alpha = 1) or scalar steps 0.99/||K|| from a power iteration.
  *   - The data term keeps the paper's form ||p - Wx||^2 without a factor 1/2.
+ *   - Alg. filtcalc: the impulse sits on the rotation axis (shared by the four central
+ *     pixels when N is even); u_k = alpha W q_k is read at the integer offsets of a
+ *     linear convolution from a detector with the acquisition's bin phase (see
+ *     orc_filtcalc).  The approximation of SIRT it gives is checked loosely (it is an
+ *     approximation); the algorithm's steps are pinned exactly.
  *
  * Coordinates: pixel (i, j) -- row from the top, column -- has its centre at
  * (x_j, y_i) = (j - (N-1)/2, (N-1)/2 - i); bin d has centre t_d = d - (N_d-1)/2.
@@ -426,4 +434,167 @@ void orc_cp(int N, int na, int nd, const double* ang,
     free(dv);
     free(su);
     free(tau);
+}
+
+/* ===========================================================================
+ * The paper's own local method (Sec. 3): SIRT approximated by filtered
+ * backprojection with iteration-dependent filters, the prior applied only on
+ * the local part.
+ * ======================================================================== */
+
+/* Unit impulse at the grid centre.  For even N the centre is the corner of four
+ * pixels and the impulse is shared by them (1/4 each), so that it stays centred
+ * on the rotation axis; for odd N it is the central pixel. */
+static void centre_impulse(int N, double* c) {
+    memset(c, 0, sizeof(double) * (size_t)N * N);
+    if (N % 2) {
+        c[(size_t)(N / 2) * N + N / 2] = 1.0;
+    } else {
+        int m = N / 2;
+        c[(size_t)(m - 1) * N + m - 1] = 0.25;
+        c[(size_t)(m - 1) * N + m] = 0.25;
+        c[(size_t)m * N + m - 1] = 0.25;
+        c[(size_t)m * N + m] = 0.25;
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * Alg. filtcalc (Sec. 3.1; Eq. filtcalc, Eq. sirtapp), one filter per iteration:
+ *     q_0 = 0, c = impulse;  for k = 1..n:  q_k = q_{k-1} + c;  c = c - alpha W^T W c;
+ *     u_k = alpha W q_k, sampled at the integer detector offsets a convolution uses.
+ * W is the acquisition projector on the N x N grid (so q_k = sum_{j<k} A^j c with
+ * A = I - alpha W^T W).  Reading of "u_k = alpha W q_k": the projection of q_k is taken
+ * on a detector that extends the acquisition one (same bin phase relative to the
+ * rotation axis) to the offsets -(N_d - 1) .. N_d - 1 around the axis, then read at
+ * those integer offsets by linear interpolation: for odd N_d the bins lie on the
+ * integers (2 N_d - 1 bins, read as they are); for even N_d they lie on the
+ * half-integers (2 N_d bins) and tap m is the mean of the bins at m - 1/2 and m + 1/2.
+ * u: [n][na][2 nd - 1], tap m of angle a of filter k at u[k-1][a][m + nd - 1].
+ * ------------------------------------------------------------------------- */
+void orc_filtcalc(int N, int na, int nd, const double* ang, int n, double alpha, double* u) {
+    const int nd2 = 2 * nd - 1, ndp = (nd % 2) ? nd2 : 2 * nd;
+    const size_t nn = (size_t)N * N, ns = (size_t)na * nd, nu = (size_t)na * nd2;
+    double* c = (double*)malloc(sizeof(double) * nn);
+    double* q = (double*)calloc(nn, sizeof(double));
+    double* wc = (double*)malloc(sizeof(double) * ns);
+    double* g = (double*)malloc(sizeof(double) * nn);
+    double* h = (double*)malloc(sizeof(double) * (size_t)na * ndp);
+    centre_impulse(N, c);
+    for (int k = 1; k <= n; ++k) {
+        for (size_t i = 0; i < nn; ++i) q[i] += c[i];
+        double* uk = u + (size_t)(k - 1) * nu;
+        orc_forward(N, na, ndp, ang, 0, 0, N, N, q, 0, 0, 0, 0, h);
+        for (int a = 0; a < na; ++a)
+            for (int m = 0; m < nd2; ++m) {
+                const double* ha = h + (size_t)a * ndp;
+                double v = (nd % 2) ? ha[m] : 0.5 * (ha[m] + ha[m + 1]);
+                uk[(size_t)a * nd2 + m] = alpha * v;
+            }
+        orc_forward(N, na, nd, ang, 0, 0, N, N, c, 0, 0, 0, 0, wc);
+        orc_back(N, na, nd, ang, 0, 0, N, N, 0, 0, 0, 0, wc, g);
+        for (size_t i = 0; i < nn; ++i) c[i] -= alpha * g[i];
+    }
+    free(c);
+    free(q);
+    free(wc);
+    free(g);
+    free(h);
+}
+
+/* C_{u_k} p (Sec. 3.1, Eq. sirtapp): for every angle a linear, zero-padded
+ * convolution of the row p[a] with the filter row uk[a]:
+ *     out[a][d] = sum_{d'} uk[a][(d - d') + nd - 1] p[a][d'].   uk: [na][2 nd - 1]. */
+void orc_filter_conv(int na, int nd, const double* uk, const double* p, double* out) {
+    const int nd2 = 2 * nd - 1;
+#pragma omp parallel for schedule(static)
+    for (long r = 0; r < (long)na * nd; ++r) {
+        int a = (int)(r / nd), d = (int)(r % nd);
+        double acc = 0.0;
+        for (int e = 0; e < nd; ++e) acc += uk[(size_t)a * nd2 + (d - e) + nd - 1] * p[(size_t)a * nd + e];
+        out[r] = acc;
+    }
+}
+
+/* Disc subtraction (Sec. 3.3).  D = the disc of diameter N centred on the rotation
+ * axis: the pixels whose centre lies within N/2 of it.  Its grey value g minimises
+ * sum_a (sum_d (p - g W D)[a][d])^2, the squared l2 norm of the zero-frequency
+ * components of all projections:  g = sum_a P_a T_a / sum_a T_a^2,
+ * P_a = sum_d p[a][d], T_a = sum_d (W D)[a][d].  Writes pd = p - g W D, returns g.
+ * disc (optional): receives D [N][N]. */
+double orc_disc(int N, int na, int nd, const double* ang, const double* p, double* pd, double* disc) {
+    const size_t nn = (size_t)N * N, ns = (size_t)na * nd;
+    double* D = (double*)malloc(sizeof(double) * nn);
+    double* wd = (double*)malloc(sizeof(double) * ns);
+    const double half = 0.5 * (N - 1), r2 = 0.25 * (double)N * N;
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) {
+            double x = j - half, y = half - i;
+            D[(size_t)i * N + j] = (x * x + y * y <= r2) ? 1.0 : 0.0;
+        }
+    orc_forward(N, na, nd, ang, 0, 0, N, N, D, 0, 0, 0, 0, wd);
+    double num = 0.0, den = 0.0;
+    for (int a = 0; a < na; ++a) {
+        double P = 0.0, T = 0.0;
+        for (int d = 0; d < nd; ++d) {
+            P += p[(size_t)a * nd + d];
+            T += wd[(size_t)a * nd + d];
+        }
+        num += P * T;
+        den += T * T;
+    }
+    double g = den > 0.0 ? num / den : 0.0;
+    for (size_t r = 0; r < ns; ++r) pd[r] = p[r] - g * wd[r];
+    if (disc) memcpy(disc, D, sizeof(double) * nn);
+    free(D);
+    free(wd);
+    return g;
+}
+
+/* ---------------------------------------------------------------------------
+ * Alg. method (Sec. 3.2, Eq. localmethod) on the local part L = the box, with the
+ * box constraint of Eq. sirtbox as the prior term d:
+ *     y^0 = 0;  for k = 1..n:
+ *         x_s^k = FBP_L(p, u_k) = W_L^T C_{u_k} p
+ *         s     = x_s^k + y^{k-1} - alpha W_L^T W_L y^{k-1}      (= S(x^{k-1}) on L)
+ *         x^k   = clamp(s + shift, lo, hi) - shift              (d^k = x^k - s)
+ *         y^k   = x^k - x_s^k
+ *     result x^n + shift.
+ * shift (optional, box [bh][bw]) is an image that is added back after the
+ * reconstruction (the disc of Sec. 3.3, restricted to the box), so the constraint
+ * applies to the final image; lo = -inf / hi = +inf switch a side off.
+ * W_L and W_L^T use every bin of the detector (bins whose rays miss the box add 0).
+ * p: [na][nd] (disc-subtracted data), u: [n][na][2 nd - 1], x: box [bh][bw].
+ * ------------------------------------------------------------------------- */
+void orc_filter_method(int N, int na, int nd, const double* ang,
+                       int bx0, int by0, int bw, int bh,
+                       const double* p, int n, double alpha, const double* u,
+                       const double* shift, double lo, double hi, double* x) {
+    const size_t nb = (size_t)bw * bh, ns = (size_t)na * nd, nu = (size_t)na * (2 * nd - 1);
+    double* cp = (double*)malloc(sizeof(double) * ns);
+    double* xs = (double*)malloc(sizeof(double) * nb);
+    double* y = (double*)calloc(nb, sizeof(double));
+    double* wy = (double*)malloc(sizeof(double) * ns);
+    double* g = (double*)malloc(sizeof(double) * nb);
+    for (size_t i = 0; i < nb; ++i) x[i] = 0.0;
+    for (int k = 1; k <= n; ++k) {
+        orc_filter_conv(na, nd, u + (size_t)(k - 1) * nu, p, cp);
+        orc_back(N, na, nd, ang, bx0, by0, bw, bh, 0, 0, 0, 0, cp, xs);
+        orc_forward(N, na, nd, ang, bx0, by0, bw, bh, y, 0, 0, 0, 0, wy);
+        orc_back(N, na, nd, ang, bx0, by0, bw, bh, 0, 0, 0, 0, wy, g);
+        for (size_t i = 0; i < nb; ++i) {
+            double sh = shift ? shift[i] : 0.0;
+            double s = xs[i] + y[i] - alpha * g[i];
+            double v = s + sh;
+            if (v < lo) v = lo;
+            if (v > hi) v = hi;
+            x[i] = v - sh;
+        }
+        for (size_t i = 0; i < nb; ++i) y[i] = x[i] - xs[i];
+    }
+    for (size_t i = 0; i < nb; ++i) x[i] += shift ? shift[i] : 0.0;
+    free(cp);
+    free(xs);
+    free(y);
+    free(wy);
+    free(g);
 }
