@@ -58,7 +58,13 @@ typedef enum {
 
 typedef enum { ROI_F32 = 0, ROI_BF16 = 1, ROI_F16 = 2 } roi_dtype;
 
-typedef enum { ROI_SIRT_NONNEG = 0, ROI_TV_CP = 1 } roi_regularizer;
+typedef enum {
+    ROI_SIRT_NONNEG = 0,   /* exterior subtraction, then nonnegative SIRT on the box (Sec. 1 scheme) */
+    ROI_TV_CP = 1,         /* exterior subtraction, then TV by Chambolle-Pock on the box             */
+    ROI_FILTER_SIRT = 2    /* the paper's own method (Sec. 3): SIRT approximated by FBP with the
+                              filters of Alg. filtcalc, the constraint x >= 0 applied on the box
+                              by Alg. method; needs roi_recon_filter_prepare                     */
+} roi_regularizer;
 
 /* Acquisition geometry (Sec. 2.1: N x N grid, N_d detectors, N_theta angles). */
 typedef struct {
@@ -169,6 +175,30 @@ roi_status roi_recon_solve_local(roi_recon_t h, const roi_region* region, const 
  * offending region. */
 roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions, const roi_solve_params* params,
                                  float* const* outs, int out_on_device, roi_solve_info* infos);
+
+/* --------------------------------------------------------------------------
+ * The paper's own local method (Sec. 3)
+ * ------------------------------------------------------------------------ */
+
+/* Prepares ROI_FILTER_SIRT solves of up to n_iters iterations on the resident sinogram:
+ *  1. Alg. filtcalc on the whole N x N grid: with A = I - alpha W^T W (alpha =
+ *     1/(N_theta N_d)) and c the unit impulse on the rotation axis (shared by the four
+ *     central pixels when N is even), q_k = sum_{j<k} A^j c and the filters
+ *     u_k = alpha W q_k, k = 1..n_iters, read at the integer detector offsets
+ *     -(N_d-1)..N_d-1 from a detector with the acquisition's bin phase (even N_d: the
+ *     mean of the bins at m -/+ 1/2).  Kept per handle (geometry-only) until a larger
+ *     n_iters is asked for; n_iters pairs of full-grid projections.
+ *  2. Disc subtraction (Sec. 3.3): p_d = p - g W D, D the disc of diameter N on the axis,
+ *     g minimising the squared norm of the per-angle sums of p_d.
+ *  3. The filtered sinograms C_{u_k} p_d for every k (4 n_iters N_theta N_d bytes), reused
+ *     by every region of this sinogram.
+ * ROI_ESTATE before set_sinogram, ROI_EINVAL for n_iters < 1 or > 100000. */
+roi_status roi_recon_filter_prepare(roi_recon_t h, int n_iters);
+
+/* After filter_prepare: the filters into device u_out [k][n_angles][2 n_det - 1] float32
+ * (the first k = min(n_filters, prepared) of them; NULL to skip) and the disc grey value
+ * into *disc_grey (host, optional).  ROI_ESTATE before filter_prepare. */
+roi_status roi_recon_filter_get(roi_recon_t h, int n_filters, float* u_out, double* disc_grey);
 
 /* --------------------------------------------------------------------------
  * Planning and single operators (for custom solvers and for verification)

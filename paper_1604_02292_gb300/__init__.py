@@ -22,7 +22,8 @@ from . import build as _build
 
 __all__ = [
     "ROI_OK", "ROI_EINVAL", "ROI_ENOMEM", "ROI_ESTATE", "ROI_ECUDA", "ROI_ETIMEOUT", "ROI_EBUSY",
-    "ROI_F32", "ROI_BF16", "ROI_F16", "ROI_SIRT_NONNEG", "ROI_TV_CP",
+    "ROI_F32", "ROI_BF16", "ROI_F16", "ROI_SIRT_NONNEG", "ROI_TV_CP", "ROI_FILTER_SIRT",
+    "roi_recon_filter_prepare", "roi_recon_filter_get",
     "Geometry", "Region", "SolveParams", "SolveInfo", "RoiError", "lib", "EXPORTS",
     "roi_recon_create", "roi_recon_destroy", "roi_recon_last_error", "roi_recon_set_sinogram",
     "roi_recon_fbp", "roi_recon_reproject_exterior", "roi_recon_solve_local", "roi_recon_plan",
@@ -38,7 +39,7 @@ __all__ = [
 
 ROI_OK, ROI_EINVAL, ROI_ENOMEM, ROI_ESTATE, ROI_ECUDA, ROI_ETIMEOUT, ROI_EBUSY = range(7)
 ROI_F32, ROI_BF16, ROI_F16 = range(3)
-ROI_SIRT_NONNEG, ROI_TV_CP = range(2)
+ROI_SIRT_NONNEG, ROI_TV_CP, ROI_FILTER_SIRT = range(3)
 ROI_OPT_SINGLE_LAUNCH, ROI_OPT_WAIT_LIMIT_US, ROI_OPT_TEST_ABSENT_BLOCKS = range(3)
 
 _STATUS = {0: "ROI_OK", 1: "ROI_EINVAL", 2: "ROI_ENOMEM", 3: "ROI_ESTATE", 4: "ROI_ECUDA",
@@ -99,6 +100,7 @@ EXPORTS = [
     "roi_server_create", "roi_server_add_sinogram", "roi_server_submit", "roi_server_start", "roi_server_stop",
     "roi_server_progress", "roi_server_poll", "roi_server_take", "roi_server_drain", "roi_server_stats_get",
     "roi_server_last_error", "roi_server_destroy", "roi_server_footprint",
+    "roi_recon_filter_prepare", "roi_recon_filter_get",
 ]
 
 _lib = None
@@ -157,6 +159,10 @@ def lib() -> ctypes.CDLL:
                                                 ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
                                                 ctypes.POINTER(SolveInfo)]
             L.roi_recon_solve_batch.restype = st
+            L.roi_recon_filter_prepare.argtypes = [_H, ctypes.c_int]
+            L.roi_recon_filter_prepare.restype = st
+            L.roi_recon_filter_get.argtypes = [_H, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_double)]
+            L.roi_recon_filter_get.restype = st
             L.roi_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(_H)]
             L.roi_server_create.restype = st
             L.roi_server_add_sinogram.argtypes = [_H, _H, ctypes.POINTER(ctypes.c_int)]
@@ -274,6 +280,16 @@ def roi_recon_solve_batch(h, regions, params, outs, out_on_device: int, infos=No
     """regions, params: ctypes arrays (Region * n, SolveParams * n); outs: (c_void_p * n) pointers."""
     n = len(regions)
     return lib().roi_recon_solve_batch(h, n, regions, params, outs, int(out_on_device), infos)
+
+
+def roi_recon_filter_prepare(h, n_iters: int) -> int:
+    return lib().roi_recon_filter_prepare(h, int(n_iters))
+
+
+def roi_recon_filter_get(h, n_filters: int, u_out: int | None):
+    g = ctypes.c_double(0.0)
+    s = lib().roi_recon_filter_get(h, int(n_filters), u_out or None, ctypes.byref(g))
+    return s, g.value
 
 
 def roi_server_create(cfg: ServerConfig | None):
@@ -534,6 +550,20 @@ class RoiRecon:
                                          self._dev(y, (self.n_angles, pl.window_stride)),
                                          self._dev(x, (pl.box[3], pl.box[2]))))
         return x
+
+    def filter_prepare(self, n_iters: int):
+        """The paper's own method (Sec. 3): filters of Alg. filtcalc for n_iters iterations, disc
+        subtraction and filtered sinograms of the resident sinogram (then solve_local with
+        reg=ROI_FILTER_SIRT and iters <= n_iters)."""
+        self._check(roi_recon_filter_prepare(self.h, n_iters))
+
+    def filters(self, n_filters: int):
+        """(u [n][n_angles][2 n_det - 1] CUDA tensor, disc grey value) after filter_prepare."""
+        u = self._torch.empty((n_filters, self.n_angles, 2 * self.n_det - 1), dtype=self._torch.float32,
+                              device="cuda")
+        s, g = roi_recon_filter_get(self.h, n_filters, u.data_ptr())
+        self._check(s)
+        return u, g
 
     def set_option(self, opt: int, value: int):
         self._check(roi_recon_set_option(self.h, opt, value))

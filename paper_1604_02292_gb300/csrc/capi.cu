@@ -125,6 +125,15 @@ struct roi_recon {
     DevBuf resid;
     int resid_ld = 0;
     int resid_ready = 0;
+    // the paper's own local method (Sec. 3): filters (geometry), disc subtraction and
+    // filtered sinograms (current sinogram)
+    int filt_n = 0;                 // filters u_1..u_filt_n in filt_u
+    DevBuf filt_u;                  // [filt_n][na][2 nd - 1]
+    AngleRec* rec_filt = nullptr;   // frame = grid, full detector of the filter bins
+    int fcp_n = 0;                  // filtered sinograms C_{u_k} p_d, k = 1..fcp_n, in filt_cp
+    DevBuf filt_cp;                 // [fcp_n][na][nd]
+    DevBuf filt_pd;                 // disc-subtracted sinogram [na][nd]
+    double disc_g = 0.0;
     unsigned char* pin = nullptr;  // page-locked staging of the uploads
     size_t pin_cap = 0;
     cudaEvent_t pin_free = nullptr;  // recorded after the last upload from `pin`
@@ -565,6 +574,156 @@ roi_status solve_cp(roi_recon* h, const roi_solve_params* prm, double* L_out) {
 
 }  // namespace
 
+namespace {
+
+// Alg. filtcalc on the whole grid (Sec. 3.1): filters u_1..u_n into filt_u.
+roi_status filter_compute(roi_recon* h, int n) {
+    const int N = h->N, na = h->na, nd = h->nd, nd2 = 2 * nd - 1, ndp = (nd % 2) ? nd2 : 2 * nd;
+    const int ld = roi::padded_ld(N);
+    const Rect grid{0, 0, N, N};
+    std::vector<AngleRec> rf(na);
+    roi::plan_angles(N, na, ndp, h->angles.data(), grid, grid, true, rf.data());
+    if (!h->rec_filt) CU(h, dev_alloc(&h->rec_filt, (size_t)na));
+    CU(h, cudaMemcpyAsync(h->rec_filt, rf.data(), sizeof(AngleRec) * na, cudaMemcpyHostToDevice, h->st));
+    CU(h, h->filt_u.ensure((size_t)n * na * nd2));
+    DevBuf c, cT, hc, wc, g;
+    DevBufT<double> hq;
+    const size_t npad = (size_t)N * ld;
+    CU(h, c.ensure(npad));
+    CU(h, cT.ensure(npad));
+    CU(h, hc.ensure((size_t)na * ndp));
+    CU(h, wc.ensure((size_t)na * nd));
+    CU(h, g.ensure((size_t)N * N));
+    CU(h, hq.ensure((size_t)na * ndp));
+    CU(h, cudaMemsetAsync(hq.p, 0, sizeof(double) * na * ndp, h->st));
+    float* c0 = c.p + roi::kPad;
+    float* cT0 = cT.p + roi::kPad;
+    roi::launch_impulse(c0, cT0, ld, N, h->st);
+    const double alpha = 1.0 / ((double)na * nd);
+    roi::FwdArgs ff{};  // W_f c onto the filter detector
+    ff.rec = h->rec_filt;
+    ff.na = na;
+    ff.stride = ndp;
+    ff.nx = N;
+    ff.ny = N;
+    ff.img = c0;
+    ff.imgT = cT0;
+    ff.img_ld = ld;
+    ff.imgT_ld = ld;
+    ff.out = hc.p;
+    roi::FwdArgs fw = ff;  // W c onto the acquisition detector
+    fw.rec = h->rec_fbp;
+    fw.stride = nd;
+    fw.out = wc.p;
+    roi::BackArgs bw{};
+    bw.rec = h->rec_fbp;
+    bw.na = na;
+    bw.stride = nd;
+    bw.nx = N;
+    bw.ny = N;
+    bw.win = wc.p;
+    bw.out = g.p;
+    bw.out_ld = N;
+    bw.part = nullptr;
+    for (int k = 1; k <= n; ++k) {
+        roi::launch_forward(roi::FWD_PLAIN, ff, h->st);  // hq = W_f q_k once accumulated
+        roi::launch_filter_accum(hc.p, hq.p, h->filt_u.p + (size_t)(k - 1) * na * nd2, na, nd, ndp, alpha, h->st);
+        roi::launch_forward(roi::FWD_PLAIN, fw, h->st);
+        roi::launch_back(roi::BACK_PLAIN, bw, h->st);
+        roi::launch_axpy_padded(c0, cT0, ld, g.p, (float)alpha, N, h->st);
+    }
+    LAUNCHED(h, "filter computation");
+    CU(h, cudaStreamSynchronize(h->st));  // the local buffers are freed on return
+    for (DevBuf* b : {&c, &cT, &hc, &wc, &g}) b->release();
+    hq.release();
+    h->filt_n = n;
+    return ROI_OK;
+}
+
+// Disc subtraction (Sec. 3.3) and the filtered sinograms C_{u_k} p_d, k = 1..n.
+roi_status filter_sinogram(roi_recon* h, int n) {
+    const int N = h->N, na = h->na, nd = h->nd;
+    const int ld = roi::padded_ld(N);
+    const size_t ns = (size_t)na * nd;
+    DevBuf D, DT, wd;
+    DevBufT<double> sums;
+    CU(h, D.ensure((size_t)N * ld));
+    CU(h, DT.ensure((size_t)N * ld));
+    CU(h, wd.ensure(ns));
+    CU(h, sums.ensure(2 * (size_t)na));
+    CU(h, h->filt_pd.ensure(ns));
+    CU(h, cudaMemsetAsync(D.p, 0, sizeof(float) * N * ld, h->st));
+    CU(h, cudaMemsetAsync(DT.p, 0, sizeof(float) * N * ld, h->st));
+    roi::launch_disc_image(D.p + roi::kPad, DT.p + roi::kPad, ld, N, h->st);
+    roi::FwdArgs fw{};
+    fw.rec = h->rec_fbp;
+    fw.na = na;
+    fw.stride = nd;
+    fw.nx = N;
+    fw.ny = N;
+    fw.img = D.p + roi::kPad;
+    fw.imgT = DT.p + roi::kPad;
+    fw.img_ld = ld;
+    fw.imgT_ld = ld;
+    fw.out = wd.p;
+    roi::launch_forward(roi::FWD_PLAIN, fw, h->st);
+    roi::launch_disc_subtract(h->p, h->dt, wd.p, 0.f, h->filt_pd.p, ns, h->st);  // p as float
+    roi::launch_row_sums(h->filt_pd.p, na, nd, sums.p, h->st);
+    roi::launch_row_sums(wd.p, na, nd, sums.p + na, h->st);
+    LAUNCHED(h, "disc projection");
+    std::vector<double> hs(2 * (size_t)na);
+    CU(h, cudaMemcpyAsync(hs.data(), sums.p, sizeof(double) * 2 * na, cudaMemcpyDeviceToHost, h->st));
+    CU(h, cudaStreamSynchronize(h->st));
+    double num = 0.0, den = 0.0;
+    for (int a = 0; a < na; ++a) {
+        num += hs[a] * hs[na + a];
+        den += hs[na + a] * hs[na + a];
+    }
+    h->disc_g = den > 0.0 ? num / den : 0.0;
+    roi::launch_disc_subtract(h->p, h->dt, wd.p, (float)h->disc_g, h->filt_pd.p, ns, h->st);
+    CU(h, h->filt_cp.ensure((size_t)n * ns));
+    roi::launch_filter_conv(h->filt_u.p, h->filt_pd.p, h->filt_cp.p, n, na, nd, h->st);
+    LAUNCHED(h, "filtered sinograms");
+    CU(h, cudaStreamSynchronize(h->st));
+    D.release();
+    DT.release();
+    wd.release();
+    sums.release();
+    h->fcp_n = n;
+    return ROI_OK;
+}
+
+// Alg. method on the planned box with x >= 0 (Sec. 3.2); result (disc added back) in xc.
+roi_status solve_filter(roi_recon* h, const roi_solve_params* prm) {
+    const int nx = h->box.w, ny = h->box.h, na = h->na, nd = h->nd;
+    const size_t nimg = (size_t)nx * ny, ns = (size_t)na * nd;
+    const float alpha = (float)(1.0 / ((double)na * nd));
+    float* shift = h->tau.p;
+    float* y = h->vx.p;
+    float* xs = h->vy.p;
+    float* g = h->itmp.p;
+    float* x = h->xc.p;
+    roi::launch_disc_box(shift, h->box.x0, h->box.y0, nx, ny, h->N, (float)h->disc_g, h->st);
+    roi::launch_fill(y, 0.f, nimg, h->st);
+    roi::launch_fill(x, 0.f, nimg, h->st);
+    roi_status s = clear_padded(h);
+    if (s != ROI_OK) return s;
+    for (int k = 1; k <= prm->iters; ++k) {
+        roi::launch_window_gather(h->filt_cp.p + (size_t)(k - 1) * ns, nd, h->rec_loc, na, h->stride, h->wtmp.p,
+                                  h->st);
+        roi::launch_back(roi::BACK_PLAIN, back_local(h, h->wtmp.p, xs, nx, nullptr, 0), h->st);  // x_s^k
+        roi::launch_forward(roi::FWD_PLAIN, fwd_local(h, h->wrow.p), h->st);                   // W_L y
+        roi::launch_back(roi::BACK_PLAIN, back_local(h, h->wrow.p, g, nx, nullptr, 0), h->st);  // W_L^T W_L y
+        roi::launch_filter_update(xs, g, y, x, shift, 0.f, INFINITY, alpha, xa0(h), lda(h), xaT0(h), ldaT(h), nx, ny,
+                                  h->st);
+    }
+    roi::launch_add(x, shift, x, nimg, h->st);
+    LAUNCHED(h, "filter method");
+    return ROI_OK;
+}
+
+}  // namespace
+
 namespace roi {
 // The server's view of a handle's resident data; computes the residual and waits for
 // it (the server works on its own stream).  Returns a roi_status.
@@ -675,6 +834,8 @@ void roi_recon_destroy(roi_recon_t h) {
         if (b) cudaFree(b);
     h->fbp32.release();
     h->in_tmp.release();
+    for (DevBuf* b : {&h->filt_u, &h->filt_cp, &h->filt_pd}) b->release();
+    if (h->rec_filt) cudaFree(h->rec_filt);
     for (AngleRec* b : {h->rec_fbp, h->rec_loc, h->rec_ext})
         if (b) cudaFree(b);
     if (h->red) cudaFree(h->red);
@@ -719,6 +880,7 @@ roi_status roi_recon_set_sinogram(roi_recon_t h, const void* p, roi_dtype dt, in
     h->have_fbp = false;
     h->exterior_ready = 0;
     h->resid_ready = 0;
+    h->fcp_n = 0;
     return ROI_OK;
 }
 
@@ -844,26 +1006,38 @@ roi_status roi_recon_solve_local(roi_recon_t h, const roi_region* region, const 
     if (!h || !region || !params) return ROI_EINVAL;
     h->err.clear();
     if (!out) return fail(h, ROI_EINVAL, "solve_local: null output");
-    if (params->reg != ROI_SIRT_NONNEG && params->reg != ROI_TV_CP)
+    if (params->reg != ROI_SIRT_NONNEG && params->reg != ROI_TV_CP && params->reg != ROI_FILTER_SIRT)
         return fail(h, ROI_EINVAL, "solve_local: unknown regularizer %d", (int)params->reg);
     if (params->iters < 0 || params->iters > 1000000) return fail(h, ROI_EINVAL, "solve_local: iters out of range");
     if (!std::isfinite(params->lambda) || params->lambda < 0)
         return fail(h, ROI_EINVAL, "solve_local: lambda must be finite and >= 0");
-    if (!h->have_fbp) return fail(h, ROI_ESTATE, "solve_local: no FBP image (call fbp first)");
+    const bool filt = params->reg == ROI_FILTER_SIRT;
+    if (filt) {
+        if (params->eval_objective) return fail(h, ROI_EINVAL, "solve_local: no objective for ROI_FILTER_SIRT");
+        if (h->fcp_n < params->iters)
+            return fail(h, ROI_ESTATE, "solve_local: filters for %d iterations not prepared (filter_prepare)",
+                        params->iters);
+    } else if (!h->have_fbp) {
+        return fail(h, ROI_ESTATE, "solve_local: no FBP image (call fbp first)");
+    }
     roi_status s = ensure_plan(h, region);
     if (s != ROI_OK) return s;
-    s = run_exterior(h);
-    if (s != ROI_OK) return s;
     double L_flag = 0.0;
-    if (params->reg == ROI_SIRT_NONNEG)
-        s = solve_sirt(h, params);
-    else
-        s = solve_cp(h, params, &L_flag);
+    if (filt) {
+        s = solve_filter(h, params);
+    } else {
+        s = run_exterior(h);
+        if (s != ROI_OK) return s;
+        if (params->reg == ROI_SIRT_NONNEG)
+            s = solve_sirt(h, params);
+        else
+            s = solve_cp(h, params, &L_flag);
+    }
     if (s != ROI_OK) return s;
     const int nx = h->box.w, ny = h->box.h;
     const size_t nimg = (size_t)nx * ny;
     const double cxl = region->cx - h->box.x0, cyl = region->cy - h->box.y0;
-    // the solution: SIRT keeps x in the padded xa, CP in xc
+    // the solution: SIRT keeps x in the padded xa, CP and the filter method in xc
     const bool sirt = params->reg == ROI_SIRT_NONNEG;
     const float* xs = sirt ? xa0(h) : h->xc.p;
     const int xs_ld = sirt ? lda(h) : nx;
@@ -914,6 +1088,33 @@ roi_status roi_recon_solve_local(roi_recon_t h, const roi_region* region, const 
         info->step_L = L;
         info->objective = objective;
     }
+    return ROI_OK;
+}
+
+roi_status roi_recon_filter_prepare(roi_recon_t h, int n_iters) {
+    if (!h) return ROI_EINVAL;
+    h->err.clear();
+    if (n_iters < 1 || n_iters > 100000) return fail(h, ROI_EINVAL, "filter_prepare: n_iters out of range");
+    if (!h->have_sino) return fail(h, ROI_ESTATE, "filter_prepare: no sinogram (call set_sinogram first)");
+    if (h->filt_n < n_iters) {
+        h->fcp_n = 0;
+        roi_status s = filter_compute(h, n_iters);
+        if (s != ROI_OK) return s;
+    }
+    if (h->fcp_n < n_iters) return filter_sinogram(h, n_iters);
+    return ROI_OK;
+}
+
+roi_status roi_recon_filter_get(roi_recon_t h, int n_filters, float* u_out, double* disc_grey) {
+    if (!h) return ROI_EINVAL;
+    h->err.clear();
+    if (h->fcp_n < 1) return fail(h, ROI_ESTATE, "filter_get: call filter_prepare first");
+    if (n_filters < 0) return fail(h, ROI_EINVAL, "filter_get: n_filters < 0");
+    const int k = std::min(n_filters, h->filt_n);
+    if (u_out && k > 0)
+        CU(h, cudaMemcpyAsync(u_out, h->filt_u.p, sizeof(float) * (size_t)k * h->na * (2 * h->nd - 1),
+                              cudaMemcpyDeviceToDevice, h->st));
+    if (disc_grey) *disc_grey = h->disc_g;
     return ROI_OK;
 }
 

@@ -244,6 +244,22 @@ void launch_crop(const float* x, int x_ld, float* out, int nx, int ny, double cx
 void launch_objective(const float* wx, const float* pp, const float* rowsum, int nwin, const float* x, int x_ld,
                       int nx, int ny, double* scratch, int nscratch, double* out2, cudaStream_t st);
 
+// ---- the paper's own local method (Sec. 3), filtermethod.cu
+void launch_disc_image(float* img, float* imgT, int ld, int N, cudaStream_t st);  // interior only
+void launch_impulse(float* img, float* imgT, int ld, int N, cudaStream_t st);     // whole padded rows
+void launch_row_sums(const float* s, int rows, int cols, double* out, cudaStream_t st);
+void launch_disc_subtract(const void* p, int dt, const float* wd, float g, float* pd, size_t n, cudaStream_t st);
+void launch_filter_accum(const float* hc, double* hq, float* uk, int na, int nd, int ndp, double alpha,
+                         cudaStream_t st);
+void launch_axpy_padded(float* c, float* cT, int ld, const float* g, float alpha, int N, cudaStream_t st);
+void launch_filter_conv(const float* u, const float* pd, float* Cp, int n, int na, int nd, cudaStream_t st);
+void launch_window_gather(const float* Cp_k, int nd, const AngleRec* rec, int na, int stride, float* win,
+                          cudaStream_t st);
+void launch_filter_update(const float* xs, const float* g, float* y, float* x, const float* shift, float lo, float hi,
+                          float alpha, float* ya, int lda, float* yaT, int ldaT, int nx, int ny, cudaStream_t st);
+void launch_disc_box(float* shift, int x0, int y0, int nx, int ny, int N, float g, cudaStream_t st);
+void launch_add(const float* x, const float* shift, float* out, size_t n, cudaStream_t st);
+
 // ---- single-launch (cooperative) solver for boxes whose padded image fits in shared memory
 struct PersistLaunch {
     const AngleRec* rec;

@@ -1,0 +1,92 @@
+"""The paper's own local method (Sec. 3) on the GPU against the FP64 oracle: the filters of
+Alg. filtcalc, the disc grey value, and whole ROI_FILTER_SIRT solves (Alg. method with
+x >= 0, disc added back) for several regions of one prepared sinogram."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1604_02292_gb300 as R
+from paper_1604_02292_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FILTER_TOL = 1e-5   # filters: float projections, double accumulation of W q_k
+SOLVE_TOL = 1e-4    # whole solves, as for the other solvers
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+@pytest.mark.parametrize("nd", [64, 65])
+def test_filters_match_oracle(nd):
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need CUDA")
+    N, na, n = 64, 48, 20
+    ph = synth.random_phantom(N, 6, texture=False, seed=71)
+    p = synth.analytic_sinogram(ph, na, nd).astype(np.float32)
+    rr = R.RoiRecon(N, na, nd)
+    rr.set_sinogram(torch.from_numpy(p).cuda())
+    rr.filter_prepare(n)
+    u, gv = rr.filters(n)
+    g = oracle.Geometry(N, na, nd)
+    uo = oracle.filtcalc(g, n)
+    u = u.cpu().numpy()
+    for k in (0, 4, n - 1):
+        assert rel_l2(u[k], uo[k]) <= FILTER_TOL, k
+    go, _, _ = oracle.disc(g, p.astype(np.float64))
+    assert abs(gv - go) <= 1e-6 * abs(go)
+
+
+@pytest.fixture(scope="module")
+def prepared():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need CUDA")
+    N, na, nd, n = 128, 64, 128, 50
+    ph = synth.random_phantom(N, 10, texture=False, seed=72)
+    p = synth.poisson_noise(synth.analytic_sinogram(ph, na, nd), 1e4, seed=73).astype(np.float32)
+    rr = R.RoiRecon(N, na, nd)
+    rr.set_sinogram(torch.from_numpy(p).cuda())
+    rr.filter_prepare(n)
+    g = oracle.Geometry(N, na, nd)
+    return rr, p, g, oracle.filtcalc(g, n), n
+
+
+@pytest.mark.parametrize("region", [(64.0, 64.0, 16.0, 8.0), (30.5, 90.2, 12.0, 6.0), (120.0, 4.0, 10.0, 5.0),
+                                    (64.0, 60.0, 40.0, 20.0)])
+def test_filter_solve_matches_oracle(prepared, region):
+    rr, p, g, uo, n = prepared
+    out, info = rr.solve_local(region, R.ROI_FILTER_SIRT, iters=n)
+    x, box = oracle.filter_solve(g, p.astype(np.float64), region, n, u=uo)
+    assert (info.box_x0, info.box_y0, info.box_w, info.box_h) == box
+    assert rel_l2(out.cpu().numpy(), x) <= SOLVE_TOL
+    assert (out.cpu().numpy() >= 0).all()
+
+
+def test_fewer_iterations_reuse_the_prepared_filters(prepared):
+    rr, p, g, uo, n = prepared
+    region = (64.0, 64.0, 16.0, 8.0)
+    out, _ = rr.solve_local(region, R.ROI_FILTER_SIRT, iters=7)
+    x, _ = oracle.filter_solve(g, p.astype(np.float64), region, 7, u=uo)
+    assert rel_l2(out.cpu().numpy(), x) <= SOLVE_TOL
+
+
+def test_filter_state_errors(prepared):
+    rr, p, g, uo, n = prepared
+    with pytest.raises(R.RoiError) as e:
+        rr.solve_local((64.0, 64.0, 16.0, 8.0), R.ROI_FILTER_SIRT, iters=n + 1)
+    assert e.value.status == R.ROI_ESTATE
+    fresh = R.RoiRecon(128, 64, 128)
+    with pytest.raises(R.RoiError) as e:
+        fresh.filter_prepare(10)
+    assert e.value.status == R.ROI_ESTATE
+    fresh.set_sinogram(torch.from_numpy(p).cuda())
+    with pytest.raises(R.RoiError) as e:
+        fresh.solve_local((64.0, 64.0, 16.0, 8.0), R.ROI_FILTER_SIRT, iters=5)
+    assert e.value.status == R.ROI_ESTATE
+    with pytest.raises(R.RoiError) as e:
+        fresh.filter_prepare(0)
+    assert e.value.status == R.ROI_EINVAL
