@@ -377,6 +377,14 @@ void exterior_inputs(const roi_recon* h, roi::BatchRoi& R, Rect box) {
     R.alpha = (float)(1.0 / ((double)h->na * h->nd));
 }
 
+// The inputs of the paper's own method (reg 2) for a whole-region solve.
+void filter_inputs(const roi_recon* h, roi::BatchRoi& R) {
+    R.fcp = h->filt_cp.p;
+    R.fcp_nd = h->nd;
+    R.disc_g = (float)h->disc_g;
+    R.grid_n = h->N;
+}
+
 roi_status run_exterior(roi_recon* h) {
     roi::FwdArgs a{};
     a.rec = h->rec_ext;
@@ -728,11 +736,11 @@ namespace roi {
 // The server's view of a handle's resident data; computes the residual and waits for
 // it (the server works on its own stream).  Returns a roi_status.
 int sino_view(roi_recon* h, SinoView* v, std::string* msg) {
-    if (!h->have_fbp) {
-        *msg = "no FBP image (call fbp first)";
+    if (!h->have_fbp && h->fcp_n < 1) {
+        *msg = "no FBP image and no prepared filters (call fbp or filter_prepare first)";
         return ROI_ESTATE;
     }
-    roi_status s = ensure_residual(h);
+    roi_status s = h->have_fbp ? ensure_residual(h) : ROI_OK;
     if (s == ROI_OK) {
         cudaError_t e = cudaStreamSynchronize(h->st);
         if (e != cudaSuccess) s = cuda_fail(h, e, "residual reprojection");
@@ -745,12 +753,16 @@ int sino_view(roi_recon* h, SinoView* v, std::string* msg) {
     v->na = h->na;
     v->nd = h->nd;
     v->angles = h->angles.data();
+    v->have_fbp = h->have_fbp;
     v->xfbp = h->xfbp;
     v->xfbpT = h->xfbpT;
     v->xfbp_ld = h->xld;
     v->dt = h->dt;
     v->resid = h->resid.p;
     v->resid_ld = h->resid_ld;
+    v->fcp = h->filt_cp.p;
+    v->fcp_n = h->fcp_n;
+    v->disc_g = (float)h->disc_g;
     return ROI_OK;
 }
 }  // namespace roi
@@ -1124,7 +1136,9 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
     h->err.clear();
     if (n < 0 || (n > 0 && (!regions || !params || !outs))) return fail(h, ROI_EINVAL, "solve_batch: bad arguments");
     if (n == 0) return ROI_OK;
-    if (!h->have_fbp) return fail(h, ROI_ESTATE, "solve_batch: no FBP image (call fbp first)");
+    bool need_fbp = false;
+    for (int i = 0; i < n; ++i) need_fbp = need_fbp || params[i].reg != ROI_FILTER_SIRT;
+    if (need_fbp && !h->have_fbp) return fail(h, ROI_ESTATE, "solve_batch: no FBP image (call fbp first)");
     const int na = h->na;
     // ---- host plan of every region
     std::vector<Rect> boxes(n);
@@ -1136,8 +1150,10 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
         const roi_solve_params& P = params[i];
         if (!finite_region(&regions[i]))
             return fail(h, ROI_EINVAL, "solve_batch: region %d: radius must be > 0, margin >= 0, all finite", i);
-        if (P.reg != ROI_SIRT_NONNEG && P.reg != ROI_TV_CP)
+        if (P.reg != ROI_SIRT_NONNEG && P.reg != ROI_TV_CP && P.reg != ROI_FILTER_SIRT)
             return fail(h, ROI_EINVAL, "solve_batch: region %d: unknown regularizer", i);
+        if (P.reg == ROI_FILTER_SIRT && h->fcp_n < P.iters)
+            return fail(h, ROI_ESTATE, "solve_batch: region %d: filters for %d iterations not prepared", i, P.iters);
         if (P.iters < 0 || P.iters > 1000000) return fail(h, ROI_EINVAL, "solve_batch: region %d: iters out of range", i);
         if (!std::isfinite(P.lambda) || P.lambda < 0) return fail(h, ROI_EINVAL, "solve_batch: region %d: bad lambda", i);
         if (P.reg == ROI_TV_CP && !P.precond)
@@ -1159,8 +1175,10 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
         max_stage = std::max(max_stage, roi::stage_bytes(box.w, box.h, h->esz));
         cost[i] = (double)box.w * box.h * na * (double)std::max(P.iters, 1);
     }
-    roi_status s0 = ensure_residual(h);
-    if (s0 != ROI_OK) return s0;
+    if (need_fbp) {
+        roi_status s0 = ensure_residual(h);
+        if (s0 != ROI_OK) return s0;
+    }
     // ---- device storage
     CU(h, h->b_tab.ensure((size_t)n * na));
     CU(h, h->b_rois.ensure(n));
@@ -1202,7 +1220,7 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
         R.nx = box.w;
         R.ny = box.h;
         R.stride = strides[i];
-        R.reg = P.reg == ROI_TV_CP ? 1 : 0;
+        R.reg = P.reg == ROI_TV_CP ? 1 : P.reg == ROI_FILTER_SIRT ? 2 : 0;
         R.iters = P.iters;
         R.weighting = P.reg == ROI_SIRT_NONNEG && P.weighting ? 1 : 0;
         R.lambda = (float)P.lambda;
@@ -1212,6 +1230,7 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
         R.cyl = (float)(regions[i].cy - box.y0);
         R.r2 = (float)(regions[i].radius * regions[i].radius);
         exterior_inputs(h, R, box);
+        filter_inputs(h, R);
         ooff += (size_t)box.w * box.h;
         pord[i] = i;
         if (infos) {

@@ -47,10 +47,10 @@ constexpr int ACH = 16;      // angles per staging chunk (one per lane of the fi
 // touched is in [0, 24] < SBB.
 constexpr int KOFFB = 12;
 constexpr int SBB = 26;      // staged bins per angle
-constexpr int WARP_STAGE = ACH * SBB + 3 * ACH * 2;  // floats per warp in phase B (bins + consts)
+constexpr int WARP_STAGE = ACH * SBB + 4 * ACH * 2;  // floats per warp in phase B (bins + consts)
 
 enum PassA { A_SOLVE = 0, A_ROWSUM = 1, A_EXTER = 2 };
-enum PassB { B_SOLVE = 0, B_COLSUM = 1 };
+enum PassB { B_SOLVE = 0, B_COLSUM = 1, B_XS = 2 };  // B_XS: x_s^k = W_L^T C_{u_k} p (Sec. 3)
 
 // A team of blocks solving one region.
 struct Team {
@@ -192,6 +192,8 @@ __device__ __forceinline__ void phase_a_branch(const Ctx& C, const Team& T, int 
                     float res = C.b.pp[o] - acc;
                     if (R.weighting) res *= C.b.sig[o];
                     C.b.u[o] = res;
+                } else if (R.reg == 2) {
+                    C.b.u[o] = -R.alpha * acc;
                 } else {
                     const float sg = C.b.sig[o];
                     C.b.u[o] = (C.b.u[o] + sg * (acc - C.b.pp[o])) / (1.f + 0.5f * sg);
@@ -204,10 +206,19 @@ __device__ __forceinline__ void phase_a_branch(const Ctx& C, const Team& T, int 
     }
 }
 
+// The disc of Sec. 3.3 at box pixel (i, j): grey value g where the grid pixel's centre lies
+// within N/2 of the rotation axis, else 0.
+__device__ __forceinline__ float disc_value(const BatchRoi& R, int i, int j) {
+    const float half = 0.5f * (float)(R.grid_n - 1);
+    const float x = (float)(R.box_x0 + j) - half, y = half - (float)(R.box_y0 + i);
+    return (x * x + y * y <= 0.25f * (float)R.grid_n * (float)R.grid_n) ? R.disc_g : 0.f;
+}
+
 // Phase B: this block's tiles are member + i * size, warps take i from *counter (preset
 // to BNW); lane = run of 8 pixels.  wstage: this warp's shared area.
 template <bool SOLO, int DT>
-__device__ __forceinline__ void phase_b(const Ctx& C, const Team& T, int pass, int* counter, float* wstage) {
+__device__ __forceinline__ void phase_b(const Ctx& C, const Team& T, int pass, int* counter, float* wstage,
+                                        int kiter = 0) {
     auto* xa = static_cast<typename Stor<DT>::T*>(C.xa);
     auto* xaT = static_cast<typename Stor<DT>::T*>(C.xaT);
     const int tm = SOLO ? 0 : T.member, ts = SOLO ? 1 : T.size;
@@ -222,6 +233,10 @@ __device__ __forceinline__ void phase_b(const Ctx& C, const Team& T, int pass, i
     float* ciw = reinterpret_cast<float*>(cs + ACH);               // [ACH] 1/w
     int* ckb = reinterpret_cast<int*>(ciw + ACH);                  // [ACH] kbase
     int* cwd = ckb + ACH;                                          // [ACH] width
+    int* cai = cwd + ACH;                                          // [ACH] sinogram angle index
+    int* cd0 = cai + ACH;                                          // [ACH] first bin of the window
+    // B_XS reads the window bins of the filtered sinogram of iteration kiter + 1
+    const float* fk = pass == B_XS ? R.fcp + (size_t)kiter * R.na * R.fcp_nd : nullptr;
     const int li = lane >> 1, lj0 = (lane & 1) * RUNB;
     for (int i = threadIdx.x >> 5;;) {
         const int t = tm + i * ts;
@@ -249,12 +264,21 @@ __device__ __forceinline__ void phase_b(const Ctx& C, const Team& T, int pass, i
                 ciw[lane] = r.inv_w;
                 ckb[lane] = kbase;
                 cwd[lane] = r.width;
+                cai[lane] = r.aidx;
+                cd0[lane] = r.d0;
             }
             __syncwarp();
             for (int e = lane; e < nch * SBB; e += 32) {
                 const int al = e / SBB, kk = ckb[al] + (e - al * SBB);
                 float v = 0.f;
-                if (kk >= 0 && kk < cwd[al]) v = pass == B_COLSUM ? 1.f : C.b.u[(size_t)(a0 + al) * R.stride + kk];
+                if (kk >= 0 && kk < cwd[al]) {
+                    if (pass == B_COLSUM)
+                        v = 1.f;
+                    else if (pass == B_XS)
+                        v = fk[(size_t)cai[al] * R.fcp_nd + cd0[al] + kk];
+                    else
+                        v = C.b.u[(size_t)(a0 + al) * R.stride + kk];
+                }
                 st[e] = v;
             }
             __syncwarp();
@@ -288,7 +312,20 @@ __device__ __forceinline__ void phase_b(const Ctx& C, const Team& T, int pass, i
             if (gi >= ny || gj >= nx) continue;
             const float acc = sum[p] + cmp[p];
             const int o = gi * nx + gj;
-            if (pass == B_COLSUM) {
+            if (pass == B_XS) {
+                C.b.vy[o] = acc;  // x_s^k
+            } else if (R.reg == 2) {  // Alg. method, x >= 0 on the final image (disc added back)
+                const float xs = C.b.vy[o];
+                const float sv = xs + C.b.x[o] + acc;  // acc = -alpha W_L^T W_L y
+                const float sh = disc_value(R, gi, gj);
+                const float xv = fmaxf(sv + sh, 0.f) - sh;
+                const float yn = xv - xs;
+                C.b.x[o] = yn;
+                C.b.vx[o] = xv;
+                const auto ys = from_f32<DT>(yn);
+                xa[gi * C.lda + gj] = ys;
+                xaT[gj * C.ldaT + gi] = ys;
+            } else if (pass == B_COLSUM) {
                 if (R.reg == 0) {
                     C.b.tau[o] = acc > 1e-3f ? 1.f / acc : 0.f;
                 } else {
@@ -470,6 +507,8 @@ __device__ __forceinline__ bool phase_a_banded(const Ctx& C, const Team& T, int 
                 float res = C.b.pp[o] - acc;
                 if (R.weighting) res *= C.b.sig[o];
                 C.b.u[o] = res;
+            } else if (R.reg == 2) {
+                C.b.u[o] = -R.alpha * acc;
             } else {
                 const float sg = C.b.sig[o];
                 C.b.u[o] = (C.b.u[o] + sg * (acc - C.b.pp[o])) / (1.f + 0.5f * sg);
@@ -536,9 +575,11 @@ __device__ __forceinline__ bool solve_region(const BatchRoi& R, const RegionBufs
     fill_team(C, C.b.x, nimg, 0.f);
     fill_team(C, C.b.vx, nimg, 0.f);
     fill_team(C, C.b.vy, nimg, 0.f);
-    load_fbp_box<DT>(C);
-    if (!team_sync<SOLO>(T)) return false;
-    phase_a_global<SOLO, DT>(C, T, A_EXTER, s_cnt);
+    if (R.reg != 2) {  // the paper's own method (reg 2) needs no exterior step
+        load_fbp_box<DT>(C);
+        if (!team_sync<SOLO>(T)) return false;
+        phase_a_global<SOLO, DT>(C, T, A_EXTER, s_cnt);
+    }
     // ---- set-up: preconditioners / weights from the row and column sums
     if (R.reg == 1 || R.weighting) {
         if (!team_sync<SOLO>(T)) return false;  // the exterior pass has read the images
@@ -578,6 +619,12 @@ __device__ __forceinline__ bool solve_region(const BatchRoi& R, const RegionBufs
             phase_a_global<SOLO, DT>(C, T, A_SOLVE, s_cnt);
         }
         if (!team_sync<SOLO>(T)) return false;  // u, v of this iteration complete
+        if (R.reg == 2) {  // x_s^k first (tiles stay with their block, so a block barrier suffices)
+            if (tid == 0) *s_cnt = BNW;
+            __syncthreads();
+            phase_b<SOLO, DT>(C, T, B_XS, s_cnt, smem + warp * WARP_STAGE, it);
+            __syncthreads();
+        }
         if (tid == 0) *s_cnt = BNW;
         __syncthreads();
         phase_b<SOLO, DT>(C, T, B_SOLVE, s_cnt, smem + warp * WARP_STAGE);
@@ -586,7 +633,7 @@ __device__ __forceinline__ bool solve_region(const BatchRoi& R, const RegionBufs
     // ---- crop into the output buffer (x is kept in float for both solvers)
     for (int p = team_tid(C); p < (int)nimg; p += C.gthreads) {
         const int i = p / R.nx, j = p - i * R.nx;
-        float v = C.b.x[p];
+        float v = R.reg == 2 ? C.b.vx[p] + disc_value(R, i, j) : C.b.x[p];
         if (R.crop) {
             const float dx = (float)j - R.cxl, dy = (float)i - R.cyl;
             if (dx * dx + dy * dy > R.r2) v = 0.f;

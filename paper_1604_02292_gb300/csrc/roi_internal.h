@@ -334,6 +334,12 @@ struct BatchRoi {
     int xfbp_ld;
     int box_x0, box_y0;
     int dt;                // storage of x_fbp and of the solver's projector images xa / xaT
+    // reg = 2, the paper's own method (Sec. 3): filtered sinograms C_{u_k} p_d of the whole
+    // detector, [iters][N_theta][fcp_nd], and the disc added back (grey value, grid size)
+    const float* fcp;
+    int fcp_nd;
+    float disc_g;
+    int grid_n;
 };
 
 struct BatchArgs {
@@ -414,6 +420,10 @@ cudaError_t launch_serve(const ServeArgs& A, int blocks, cudaStream_t st);
 struct SinoView {
     int N, na, nd;
     const double* angles;
+    bool have_fbp;         // exterior-step solvers available
+    const float* fcp;      // filtered sinograms of the paper's own method, fcp_n iterations
+    int fcp_n;
+    float disc_g;
     const void* xfbp;
     const void* xfbpT;
     int xfbp_ld;

@@ -334,7 +334,7 @@ void publish(roi_server* s, int pi, Req* r, size_t slot) {
     R.nx = r->box.w;
     R.ny = r->box.h;
     R.stride = r->stride;
-    R.reg = r->prm.reg == ROI_TV_CP ? 1 : 0;
+    R.reg = r->prm.reg == ROI_TV_CP ? 1 : r->prm.reg == ROI_FILTER_SIRT ? 2 : 0;
     R.iters = r->prm.iters;
     R.weighting = r->prm.reg == ROI_SIRT_NONNEG && r->prm.weighting ? 1 : 0;
     R.lambda = (float)r->prm.lambda;
@@ -352,6 +352,10 @@ void publish(roi_server* s, int pi, Req* r, size_t slot) {
     R.box_x0 = r->box.x0;
     R.box_y0 = r->box.y0;
     R.dt = v.dt;
+    R.fcp = v.fcp;
+    R.fcp_nd = v.nd;
+    R.disc_g = v.disc_g;
+    R.grid_n = v.N;
     unsigned char* base = s->arena_d + r->dev_off;
     roi::RegionBufs& B = hdr.bufs;
     B.pp = reinterpret_cast<float*>(base + r->lay.pp);
@@ -642,13 +646,19 @@ roi_status roi_server_submit(roi_server_t s, int sino_id, const roi_region* regi
     if (sino_id < 0 || sino_id >= (int)s->sinos.size()) return sfail(s, ROI_EINVAL, "submit: unknown sinogram %d", sino_id);
     const roi_solve_params& P = *params;
     if (!finite_region(region)) return sfail(s, ROI_EINVAL, "submit: radius must be > 0, margin >= 0, all finite");
-    if (P.reg != ROI_SIRT_NONNEG && P.reg != ROI_TV_CP) return sfail(s, ROI_EINVAL, "submit: unknown regularizer");
+    if (P.reg != ROI_SIRT_NONNEG && P.reg != ROI_TV_CP && P.reg != ROI_FILTER_SIRT)
+        return sfail(s, ROI_EINVAL, "submit: unknown regularizer");
     if (P.iters < 0 || P.iters > 1000000) return sfail(s, ROI_EINVAL, "submit: iters out of range");
     if (!std::isfinite(P.lambda) || P.lambda < 0) return sfail(s, ROI_EINVAL, "submit: bad lambda");
     if (P.reg == ROI_TV_CP && !P.precond) return sfail(s, ROI_EINVAL, "submit: served CP uses the diagonal steps (precond = 1)");
     roi_status rs = ensure_rings(s);
     if (rs != ROI_OK) return rs;
     const roi::SinoView& v = s->sinos[sino_id];
+    if (P.reg == ROI_FILTER_SIRT && v.fcp_n < P.iters)
+        return sfail(s, ROI_ESTATE, "submit: sinogram %d has filters for %d iterations, %d asked", sino_id, v.fcp_n,
+                     P.iters);
+    if (P.reg != ROI_FILTER_SIRT && !v.have_fbp)
+        return sfail(s, ROI_ESTATE, "submit: sinogram %d has no FBP image", sino_id);
     Req* r = new (std::nothrow) Req;
     if (!r) return sfail(s, ROI_ENOMEM, "submit: out of host memory");
     if (!plan_request(v.N, v.na, v.nd, v.angles, *region, &r->box, &r->stride, &r->nrow, &r->rec)) {

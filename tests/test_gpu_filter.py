@@ -90,3 +90,29 @@ def test_filter_state_errors(prepared):
     with pytest.raises(R.RoiError) as e:
         fresh.filter_prepare(0)
     assert e.value.status == R.ROI_EINVAL
+
+
+def test_batched_and_served_filter_solves(prepared):
+    """The paper's method in the whole-region solvers (one block or a team per region):
+    batched and served results are identical to each other, agree with the one-launch-per-
+    operator path to rounding and with the oracle within the solve tolerance."""
+    rr, p, g, uo, n = prepared
+    regions = [(64.0, 64.0, 16.0, 8.0), (30.5, 90.2, 12.0, 6.0), (64.0, 60.0, 40.0, 20.0)]
+    prm = dict(reg=R.ROI_FILTER_SIRT, iters=n)
+    outs, infos = rr.solve_batch(regions, [prm] * len(regions))
+    rr.sync()
+    with R.Server(team_blocks=4, teams=8, large_side=100) as s:
+        s.add(rr)
+        ids = {s.submit(0, r, prm): k for k, r in enumerate(regions)}
+        s.drain(120000.0)
+        served = {}
+        for c in s.poll():
+            assert c["status"] == R.ROI_OK
+            served[ids[c["id"]]] = s.take(c["id"], (c["box"][3], c["box"][2]))
+    for k, region in enumerate(regions):
+        b = outs[k].cpu().numpy()
+        assert np.array_equal(b, served[k]), k
+        single, _ = rr.solve_local(region, R.ROI_FILTER_SIRT, iters=n)
+        assert rel_l2(b, single.cpu().numpy()) <= 1e-5
+        x, _ = oracle.filter_solve(g, p.astype(np.float64), region, n, u=uo)
+        assert rel_l2(b, x) <= SOLVE_TOL
