@@ -134,6 +134,17 @@ const char* roi_recon_last_error(roi_recon_t h);
  * until the handle's stream has passed the copy.  Invalidates the cached FBP image. */
 roi_status roi_recon_set_sinogram(roi_recon_t h, const void* p, roi_dtype dt, int on_device);
 
+/* Truncated projection data (Sec. 5.6): p [n_angles][n_measured] holds only the central
+ * n_measured bins of the handle's n_det-bin detector (bins [(n_det - n_measured)/2,
+ * (n_det + n_measured)/2)); the bins outside are filled by constant padding with each
+ * row's first / last measured value, as FBP-based methods do to reduce truncation
+ * artifacts.  Everything downstream (fbp, exterior step, solves, filter_prepare) then
+ * runs on the padded sinogram; results are meaningful inside the disk of diameter
+ * n_measured around the rotation axis.  Other arguments as for roi_recon_set_sinogram.
+ * ROI_EINVAL unless 1 <= n_measured <= n_det with n_det - n_measured even. */
+roi_status roi_recon_set_sinogram_truncated(roi_recon_t h, const void* p, roi_dtype dt, int on_device,
+                                           int n_measured);
+
 /* Global filtered backprojection FBP(p, h) = W^T C_h p (Eq. fbp), Ram-Lak filter
  * scaled by pi/N_theta, on the whole N x N grid; the result is cached in the
  * handle (in its storage type) for the exterior step.  out_or_null: optional device
@@ -159,7 +170,7 @@ roi_status roi_recon_reproject_exterior(roi_recon_t h, const roi_region* region,
 roi_status roi_recon_solve_local(roi_recon_t h, const roi_region* region, const roi_solve_params* params,
                                  float* out, int out_on_device, roi_solve_info* info);
 
-/* Many local solves in one call (Sec. 4.4: local reconstructions are independent and can
+/* Many local solves in one call (Sec. 5.5: local reconstructions are independent and can
  * be computed in parallel; Sec. 1 scheme for each).  regions[n], params[n] (one per region;
  * SIRT and CP may be mixed; CP must use precond = 1; eval_objective is ignored), outs[n]:
  * [box_h][box_w] float32 each, device pointers when out_on_device = 1, host memory
@@ -175,6 +186,15 @@ roi_status roi_recon_solve_local(roi_recon_t h, const roi_region* region, const 
  * offending region. */
 roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions, const roi_solve_params* params,
                                  float* const* outs, int out_on_device, roi_solve_info* infos);
+
+/* Tiling (Sec. 5.5): the whole N x N image as non-overlapping tile x tile local
+ * reconstructions placed next to each other.  Tile (ti, tj) covers rows [ti tile, (ti+1)
+ * tile) and columns [tj tile, (tj+1) tile); it is solved as the region centred on the tile
+ * with radius tile/2 and the given margin (its extended box, clipped to the grid), all
+ * tiles in one roi_recon_solve_batch call, and the tile's square is copied from the box
+ * result into out (device [N][N] float32).  params as for roi_recon_solve_batch, with
+ * crop_disk = 0.  Synchronizes.  ROI_EINVAL unless tile is even and divides N. */
+roi_status roi_recon_solve_tiled(roi_recon_t h, int tile, int margin, const roi_solve_params* params, float* out);
 
 /* --------------------------------------------------------------------------
  * The paper's own local method (Sec. 3)
@@ -276,7 +296,7 @@ unsigned long long roi_recon_launch_count(void);
  * ------------------------------------------------------------------------ */
 
 /* A server solves ROI requests (each the Sec. 1 scheme on one region of one resident
- * sinogram, Sec. 4.4: regions are independent) while more keep arriving.  One
+ * sinogram, Sec. 5.5: regions are independent) while more keep arriving.  One
  * cooperative kernel runs while there is work: its blocks form units -- single blocks
  * for small boxes, teams of team_blocks blocks for boxes of side >= large_side -- that
  * take requests from rings in page-locked host memory mapped into the device, so a

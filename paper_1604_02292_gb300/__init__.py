@@ -23,7 +23,8 @@ from . import build as _build
 __all__ = [
     "ROI_OK", "ROI_EINVAL", "ROI_ENOMEM", "ROI_ESTATE", "ROI_ECUDA", "ROI_ETIMEOUT", "ROI_EBUSY",
     "ROI_F32", "ROI_BF16", "ROI_F16", "ROI_SIRT_NONNEG", "ROI_TV_CP", "ROI_FILTER_SIRT",
-    "roi_recon_filter_prepare", "roi_recon_filter_get",
+    "roi_recon_filter_prepare", "roi_recon_filter_get", "roi_recon_set_sinogram_truncated",
+    "roi_recon_solve_tiled",
     "Geometry", "Region", "SolveParams", "SolveInfo", "RoiError", "lib", "EXPORTS",
     "roi_recon_create", "roi_recon_destroy", "roi_recon_last_error", "roi_recon_set_sinogram",
     "roi_recon_fbp", "roi_recon_reproject_exterior", "roi_recon_solve_local", "roi_recon_plan",
@@ -100,7 +101,8 @@ EXPORTS = [
     "roi_server_create", "roi_server_add_sinogram", "roi_server_submit", "roi_server_start", "roi_server_stop",
     "roi_server_progress", "roi_server_poll", "roi_server_take", "roi_server_drain", "roi_server_stats_get",
     "roi_server_last_error", "roi_server_destroy", "roi_server_footprint",
-    "roi_recon_filter_prepare", "roi_recon_filter_get",
+    "roi_recon_filter_prepare", "roi_recon_filter_get", "roi_recon_set_sinogram_truncated",
+    "roi_recon_solve_tiled",
 ]
 
 _lib = None
@@ -159,6 +161,10 @@ def lib() -> ctypes.CDLL:
                                                 ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
                                                 ctypes.POINTER(SolveInfo)]
             L.roi_recon_solve_batch.restype = st
+            L.roi_recon_set_sinogram_truncated.argtypes = [_H, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            L.roi_recon_set_sinogram_truncated.restype = st
+            L.roi_recon_solve_tiled.argtypes = [_H, ctypes.c_int, ctypes.c_int, ctypes.POINTER(SolveParams), _P]
+            L.roi_recon_solve_tiled.restype = st
             L.roi_recon_filter_prepare.argtypes = [_H, ctypes.c_int]
             L.roi_recon_filter_prepare.restype = st
             L.roi_recon_filter_get.argtypes = [_H, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_double)]
@@ -280,6 +286,14 @@ def roi_recon_solve_batch(h, regions, params, outs, out_on_device: int, infos=No
     """regions, params: ctypes arrays (Region * n, SolveParams * n); outs: (c_void_p * n) pointers."""
     n = len(regions)
     return lib().roi_recon_solve_batch(h, n, regions, params, outs, int(out_on_device), infos)
+
+
+def roi_recon_set_sinogram_truncated(h, p: int, dtype: int, on_device: int, n_measured: int) -> int:
+    return lib().roi_recon_set_sinogram_truncated(h, p, int(dtype), int(on_device), int(n_measured))
+
+
+def roi_recon_solve_tiled(h, tile: int, margin: int, params: SolveParams, out: int) -> int:
+    return lib().roi_recon_solve_tiled(h, int(tile), int(margin), ctypes.byref(params), out)
 
 
 def roi_recon_filter_prepare(h, n_iters: int) -> int:
@@ -463,6 +477,16 @@ class RoiRecon:
             self._check(roi_recon_set_sinogram(self.h, arr.ctypes.data, ROI_F32, 0))
             self._sino_keep = arr
 
+    def set_sinogram_truncated(self, p):
+        """p: [n_angles][n_measured] float32 CUDA tensor, the central bins of the detector;
+        the rest of each row is padded with its edge values (Sec. 5.6)."""
+        torch = self._torch
+        if not (isinstance(p, torch.Tensor) and p.is_cuda and p.dtype == torch.float32 and p.is_contiguous()
+                and p.dim() == 2 and p.shape[0] == self.n_angles):
+            raise TypeError("expected a contiguous float32 CUDA tensor [n_angles][n_measured]")
+        self._check(roi_recon_set_sinogram_truncated(self.h, p.data_ptr(), ROI_F32, 1, p.shape[1]))
+        self._sino_keep = p
+
     def fbp(self, out=None):
         self._check(roi_recon_fbp(self.h, self._dev(out, (self.N, self.N)) if out is not None else None))
         return out
@@ -550,6 +574,14 @@ class RoiRecon:
                                          self._dev(y, (self.n_angles, pl.window_stride)),
                                          self._dev(x, (pl.box[3], pl.box[2]))))
         return x
+
+    def solve_tiled(self, tile: int, margin: int, params: dict, out=None):
+        """The whole image as non-overlapping tile x tile local solves (Sec. 5.5); returns a CUDA
+        tensor [N][N].  params: dict as for solve_batch."""
+        if out is None:
+            out = self._torch.empty((self.N, self.N), dtype=self._torch.float32, device="cuda")
+        self._check(roi_recon_solve_tiled(self.h, tile, margin, _params(params), self._dev(out, (self.N, self.N))))
+        return out
 
     def filter_prepare(self, n_iters: int):
         """The paper's own method (Sec. 3): filters of Alg. filtcalc for n_iters iterations, disc

@@ -896,6 +896,30 @@ roi_status roi_recon_set_sinogram(roi_recon_t h, const void* p, roi_dtype dt, in
     return ROI_OK;
 }
 
+roi_status roi_recon_set_sinogram_truncated(roi_recon_t h, const void* p, roi_dtype dt, int on_device,
+                                           int n_measured) {
+    if (!h) return ROI_EINVAL;
+    h->err.clear();
+    if (!p) return fail(h, ROI_EINVAL, "set_sinogram_truncated: null pointer");
+    if (dt != ROI_F32 && dt != ROI_BF16 && dt != ROI_F16)
+        return fail(h, ROI_EINVAL, "set_sinogram_truncated: unknown dtype");
+    if (n_measured < 1 || n_measured > h->nd || (h->nd - n_measured) % 2)
+        return fail(h, ROI_EINVAL, "set_sinogram_truncated: n_measured must be in [1, n_det] with n_det - n_measured even");
+    const size_t in_bytes = (size_t)roi::dt_size((int)dt) * h->na * n_measured;
+    CU(h, h->in_tmp.ensure(in_bytes));
+    CU(h, cudaMemcpyAsync(h->in_tmp.p, p, in_bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          h->st));
+    roi::launch_pad_truncated(h->in_tmp.p, (int)dt, n_measured, h->p, h->dt, h->na, h->nd,
+                              (h->nd - n_measured) / 2, h->st);
+    LAUNCHED(h, "set_sinogram_truncated padding");
+    h->have_sino = true;
+    h->have_fbp = false;
+    h->exterior_ready = 0;
+    h->resid_ready = 0;
+    h->fcp_n = 0;
+    return ROI_OK;
+}
+
 roi_status roi_recon_ramp_filter(roi_recon_t h, float* q) {
     if (!h) return ROI_EINVAL;
     h->err.clear();
@@ -1289,6 +1313,56 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
             o += m;
         }
     }
+    return ROI_OK;
+}
+
+roi_status roi_recon_solve_tiled(roi_recon_t h, int tile, int margin, const roi_solve_params* params, float* out) {
+    if (!h) return ROI_EINVAL;
+    h->err.clear();
+    if (!params || !out) return fail(h, ROI_EINVAL, "solve_tiled: null argument");
+    if (tile < 2 || tile % 2 || h->N % tile) return fail(h, ROI_EINVAL, "solve_tiled: tile must be even and divide N");
+    if (margin < 0 || margin > h->N) return fail(h, ROI_EINVAL, "solve_tiled: margin out of range");
+    if (params->crop_disk) return fail(h, ROI_EINVAL, "solve_tiled: tiles are squares (crop_disk = 0)");
+    const int nt = h->N / tile, n = nt * nt;
+    std::vector<roi_region> regions(n);
+    std::vector<roi_solve_params> prms(n, *params);
+    std::vector<Rect> boxes(n);
+    size_t total = 0;
+    for (int ti = 0; ti < nt; ++ti)
+        for (int tj = 0; tj < nt; ++tj) {
+            roi_region& r = regions[ti * nt + tj];
+            r.cx = tj * tile + 0.5 * (tile - 1);
+            r.cy = ti * tile + 0.5 * (tile - 1);
+            r.radius = 0.5 * tile;
+            r.margin = margin;
+            Rect box;
+            roi::plan_box(h->N, r.cx, r.cy, r.radius, r.margin, &box);
+            boxes[ti * nt + tj] = box;
+            total += (size_t)box.w * box.h;
+        }
+    DevBuf boxes_out;
+    CU(h, boxes_out.ensure(total));
+    std::vector<float*> outs(n);
+    size_t off = 0;
+    for (int k = 0; k < n; ++k) {
+        outs[k] = boxes_out.p + off;
+        off += (size_t)boxes[k].w * boxes[k].h;
+    }
+    roi_status s = roi_recon_solve_batch(h, n, regions.data(), prms.data(), outs.data(), 1, nullptr);
+    if (s != ROI_OK) return s;
+    std::vector<unsigned char> tab(roi::tile_src_bytes() * n);
+    for (int ti = 0; ti < nt; ++ti)
+        for (int tj = 0; tj < nt; ++tj) {
+            const int k = ti * nt + tj;
+            roi::tile_src_fill(tab.data(), k, outs[k], boxes[k].w, tj * tile - boxes[k].x0, ti * tile - boxes[k].y0,
+                               tj * tile, ti * tile);
+        }
+    DevBufT<unsigned char> tab_dev;
+    CU(h, tab_dev.ensure(tab.size()));
+    CU(h, cudaMemcpyAsync(tab_dev.p, tab.data(), tab.size(), cudaMemcpyHostToDevice, h->st));
+    roi::launch_paste_tiles(tab_dev.p, n, tile, out, h->N, h->st);
+    LAUNCHED(h, "tile paste");
+    CU(h, cudaStreamSynchronize(h->st));  // the scratch buffers are freed on return
     return ROI_OK;
 }
 

@@ -72,7 +72,7 @@ __global__ void k_filter_accum(const float* hc, double* hq, float* uk, int na, i
     double* hr = hq + (size_t)a * ndp;
     const float* cr = hc + (size_t)a * ndp;
     for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < ndp; m += gridDim.x * blockDim.x) hr[m] += (double)cr[m];
-    __syncthreads();  // each block owns a disjoint slice [blockIdx.x-th stride] of one row only when gridDim.x == 1
+    __syncthreads();  // one block per row (gridDim.x == 1): the row is complete here
     for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < nd2; m += gridDim.x * blockDim.x) {
         const double v = (nd & 1) ? hr[m] : 0.5 * (hr[m] + hr[m + 1]);
         uk[(size_t)a * nd2 + m] = (float)(alpha * v);
@@ -192,6 +192,20 @@ __global__ void k_add(const float* x, const float* shift, float* out, size_t n) 
         out[i] = x[i] + shift[i];
 }
 
+// Tiling (Sec. 5.5): out[y][x] for the pixels of tile t, copied from that tile's box result.
+struct TileSrc {
+    const float* box;   // [bh][bw]
+    int bw, tx, ty;     // box width; tile origin inside the box
+    int gx, gy;         // tile origin on the grid
+};
+__global__ void k_paste_tiles(const TileSrc* tiles, int T, float* out, int N) {
+    const TileSrc t = tiles[blockIdx.z];
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= T || j >= T) return;
+    out[(size_t)(t.gy + i) * N + t.gx + j] = t.box[(size_t)(t.ty + i) * t.bw + t.tx + j];
+}
+
 int blocks_for(size_t n) { return (int)((n + 255) / 256 < 152 * 8 ? (n + 255) / 256 : 152 * 8); }
 
 }  // namespace
@@ -255,6 +269,17 @@ void launch_filter_update(const float* xs, const float* g, float* y, float* x, c
 void launch_disc_box(float* shift, int x0, int y0, int nx, int ny, int N, float g, cudaStream_t st) {
     count_launches(1);
     k_disc_box<<<dim3((nx + 127) / 128, ny), 128, 0, st>>>(shift, x0, y0, nx, ny, N, g);
+}
+
+void launch_paste_tiles(const void* tiles, int ntiles, int T, float* out, int N, cudaStream_t st) {
+    if (ntiles <= 0) return;
+    count_launches(1);
+    dim3 grid((T + 31) / 32, (T + 7) / 8, ntiles);
+    k_paste_tiles<<<grid, dim3(32, 8), 0, st>>>(static_cast<const TileSrc*>(tiles), T, out, N);
+}
+size_t tile_src_bytes() { return sizeof(TileSrc); }
+void tile_src_fill(void* dst, int k, const float* box, int bw, int tx, int ty, int gx, int gy) {
+    static_cast<TileSrc*>(dst)[k] = TileSrc{box, bw, tx, ty, gx, gy};
 }
 
 void launch_add(const float* x, const float* shift, float* out, size_t n, cudaStream_t st) {

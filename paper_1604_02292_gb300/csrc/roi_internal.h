@@ -209,6 +209,10 @@ void launch_ramp(const void* p, int dt, const float* hodd, float* q, int na, int
 // Storage conversions (dt: 0 float, 1 bfloat16, 2 half; round to nearest even):
 // dst[i] = src[i] for n elements
 void launch_convert(const void* src, int src_dt, void* dst, int dst_dt, size_t n, cudaStream_t st);
+// dst [na][nd] (storage dst_dt) = src [na][nm] (src_dt) placed at bins [off, off + nm), the
+// bins outside filled with the row's first / last measured value
+void launch_pad_truncated(const void* src, int src_dt, int nm, void* dst, int dst_dt, int na, int nd, int off,
+                          cudaStream_t st);
 // dst (storage dt, padded rows of dst_ld, pads untouched) = src [rows][cols] float (row stride
 // src_ld); transpose: dst[c][r] = src[r][c]
 void launch_store_padded(const float* src, int src_ld, void* dst, int dst_dt, int dst_ld, int rows, int cols,
@@ -259,6 +263,11 @@ void launch_filter_update(const float* xs, const float* g, float* y, float* x, c
                           float alpha, float* ya, int lda, float* yaT, int ldaT, int nx, int ny, cudaStream_t st);
 void launch_disc_box(float* shift, int x0, int y0, int nx, int ny, int N, float g, cudaStream_t st);
 void launch_add(const float* x, const float* shift, float* out, size_t n, cudaStream_t st);
+// Tiling: a host-filled table of tiles (tile_src_fill into tile_src_bytes() * n bytes, copied
+// to the device) pasted into out [N][N].
+size_t tile_src_bytes();
+void tile_src_fill(void* dst, int k, const float* box, int bw, int tx, int ty, int gx, int gy);
+void launch_paste_tiles(const void* tiles_dev, int ntiles, int T, float* out, int N, cudaStream_t st);
 
 // ---- single-launch (cooperative) solver for boxes whose padded image fits in shared memory
 struct PersistLaunch {

@@ -2,7 +2,7 @@
 // memory budget, publication into the rings read by the serving kernel (serve.cu),
 // completion polling, memory recycling and kernel relaunch.
 //
-// Sec. 4.4 of the paper: local reconstructions are independent, so many of them can be
+// Sec. 5.5 of the paper: local reconstructions are independent, so many of them can be
 // in flight at once.  Requests are planned on the host at submission (box, per-angle
 // windows), queued per unit pool in arrival order and admitted in that order while the
 // state of the admitted requests fits the device budget and their results fit the

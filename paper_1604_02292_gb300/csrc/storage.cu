@@ -52,6 +52,30 @@ __global__ void k_load_padded(const void* __restrict__ src, int src_ld, float* _
     if (r < rows && c < cols) dst[(size_t)r * dst_ld + c] = to_f32<SD>(s[(size_t)r * src_ld + c]);
 }
 
+// Truncated rows (Sec. 5.6): dst[a][d] = src[a][clamp(d - off, 0, nm - 1)] -- the measured
+// central bins, constant (edge-value) padding on both sides, converted to the storage type.
+template <int SD, int DD>
+__global__ void k_pad_truncated(const void* __restrict__ src, int nm, void* __restrict__ dst, int nd, int off) {
+    const auto* s = static_cast<const typename Stor<SD>::T*>(src);
+    auto* d = static_cast<typename Stor<DD>::T*>(dst);
+    const int a = blockIdx.y;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nd; j += gridDim.x * blockDim.x) {
+        const int k = min(max(j - off, 0), nm - 1);
+        d[(size_t)a * nd + j] = from_f32<DD>(to_f32<SD>(s[(size_t)a * nm + k]));
+    }
+}
+
+template <int SD>
+void pad_from(const void* src, int nm, void* dst, int dst_dt, int na, int nd, int off, cudaStream_t st) {
+    dim3 grid((nd + 255) / 256, na);
+    if (dst_dt == 1)
+        k_pad_truncated<SD, 1><<<grid, 256, 0, st>>>(src, nm, dst, nd, off);
+    else if (dst_dt == 2)
+        k_pad_truncated<SD, 2><<<grid, 256, 0, st>>>(src, nm, dst, nd, off);
+    else
+        k_pad_truncated<SD, 0><<<grid, 256, 0, st>>>(src, nm, dst, nd, off);
+}
+
 template <int SD>
 void convert_from(const void* src, void* dst, int dst_dt, size_t n, int blocks, cudaStream_t st) {
     if (dst_dt == 1)
@@ -74,6 +98,18 @@ void launch_convert(const void* src, int src_dt, void* dst, int dst_dt, size_t n
         convert_from<2>(src, dst, dst_dt, n, blocks, st);
     else
         convert_from<0>(src, dst, dst_dt, n, blocks, st);
+}
+
+void launch_pad_truncated(const void* src, int src_dt, int nm, void* dst, int dst_dt, int na, int nd, int off,
+                          cudaStream_t st) {
+    if (na <= 0 || nd <= 0 || nm <= 0) return;
+    count_launches(1);
+    if (src_dt == 1)
+        pad_from<1>(src, nm, dst, dst_dt, na, nd, off, st);
+    else if (src_dt == 2)
+        pad_from<2>(src, nm, dst, dst_dt, na, nd, off, st);
+    else
+        pad_from<0>(src, nm, dst, dst_dt, na, nd, off, st);
 }
 
 void launch_store_padded(const float* src, int src_ld, void* dst, int dst_dt, int dst_ld, int rows, int cols,

@@ -1,6 +1,6 @@
 """Sharding of independent local solves over ranks (one process per GPU).
 
-Local reconstructions are independent (paper Sec. 4.4: they can be computed in parallel),
+Local reconstructions are independent (paper Sec. 5.5: they can be computed in parallel),
 so the work splits by region with no exchange on the data path: each rank solves its own
 share and only the timing is reduced.  Assignment is greedy longest-processing-time by
 estimated cost (box pixels x angles x iterations), deterministic for a given input.

@@ -41,6 +41,13 @@ WORKLOADS = {
     # 1024 x 1024, 256 angles, 1024 bins, 50 ellipses + fine texture, I0 = 5e3,
     # ROI radius 64 px + margin 32 px, Chambolle-Pock TV lambda = 0.01, 500 iterations
     "roi_cptv_1024": Workload("roi_cptv_1024", 1024, 256, 1024, 50, True, 5e3, 64.0, 32.0, "tv", 500, 0.01),
+    # the paper's own method on the 1024 geometry: ROI radius 64 px + margin 32 px, 200
+    # iterations of nonnegative SIRT approximated by filtered backprojections (Sec. 3)
+    "roi_filter_1024": Workload("roi_filter_1024", 1024, 256, 1024, 50, True, 5e3, 64.0, 32.0, "filter", 200),
+    # tiling (Sec. 5.5) on the 1024 geometry: 64 tiles of 128 x 128 (radius 64 px), margin 16 px
+    # (1/8 of the tile side, Sec. 3.3), the paper's method with x >= 0, 200 iterations, against
+    # 200 nonnegative SIRT iterations on the whole grid
+    "roi_tile_1024": Workload("roi_tile_1024", 1024, 256, 1024, 50, True, 5e3, 64.0, 16.0, "tile", 200),
 }
 
 
