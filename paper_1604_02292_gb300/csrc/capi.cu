@@ -119,6 +119,7 @@ struct roi_recon {
     DevBufT<roi::BatchRoi> b_rois;
     DevBufT<int> b_order;
     DevBufT<int> b_queue;
+    DevBufT<unsigned> b_bars;
     DevBuf s_pp, s_u, s_sig, s_x, s_vx, s_vy, s_tau, s_xa, s_xaT;
     // residual p - W x_fbp over every ray, [na][resid_ld] (exterior step of the
     // whole-region solvers, Eq. locouter); valid while resid_ready
@@ -857,6 +858,7 @@ void roi_recon_destroy(roi_recon_t h) {
     h->b_rois.release();
     h->b_order.release();
     h->b_queue.release();
+    h->b_bars.release();
     for (DevBuf* b : {&h->b_out, &h->s_pp, &h->s_u, &h->s_sig, &h->s_x, &h->s_vx, &h->s_vy, &h->s_tau, &h->s_xa,
                       &h->s_xaT, &h->resid})
         b->release();
@@ -1209,7 +1211,14 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
     CU(h, h->b_order.ensure(n));
     CU(h, h->b_queue.ensure(1));
     if (!out_on_device) CU(h, h->b_out.ensure(out_total));
-    const int blocks = std::max(1, h->sms);
+    // few regions: teams of blocks per region (co-resident: at most one block per SM)
+    int blocks = std::max(1, h->sms);
+    const int team = std::min(16, blocks / n);
+    if (team > 1) {
+        blocks = std::min(blocks, roi::serve_max_blocks(h->device));
+        blocks = (blocks / team) * team;
+        CU(h, h->b_bars.ensure((size_t)blocks / team));
+    }
     for (DevBuf* b : {&h->s_pp, &h->s_u, &h->s_sig}) CU(h, b->ensure(win_cap * blocks));
     for (DevBuf* b : {&h->s_x, &h->s_vx, &h->s_vy, &h->s_tau}) CU(h, b->ensure(img_cap * blocks));
     for (DevBuf* b : {&h->s_xa, &h->s_xaT}) CU(h, b->ensure(pad_cap * blocks));
@@ -1294,6 +1303,8 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
     B.pad_cap = pad_cap;
     B.err = h->d_err;
     B.wait_ns = h->opt_wait_ns;
+    B.team = team > 1 ? team : 1;
+    B.bars = team > 1 ? h->b_bars.p : nullptr;
     const size_t smem = roi::batch_smem_bytes(max_stage);
     cudaError_t e;
     {

@@ -370,6 +370,8 @@ struct BatchArgs {
     size_t pad_cap;
     int* err;
     unsigned long long wait_ns;
+    int team;              // blocks per region: 1, or > 1 for a cooperative launch of teams
+    unsigned* bars;        // team > 1: one barrier counter per team (zeroed by the launcher)
 };
 // Device buffers of one whole-region solve: windows [na][stride]; box arrays [ny][nx];
 // padded images from row 0 column -kPad, row strides padded_ld(nx) / padded_ld(ny).
