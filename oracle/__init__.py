@@ -70,6 +70,9 @@ def _load():
             lib.orc_disc.restype = ctypes.c_double
             lib.orc_filter_method.argtypes = [_I, _I, _I, _D] + i7 + [_D, _I, ctypes.c_double, _D, _D,
                                                                       ctypes.c_double, ctypes.c_double, _D]
+            lib.orc_fgp.argtypes = [_I, _I, _D, ctypes.c_double, _I, _D]
+            lib.orc_filter_fista.argtypes = [_I, _I, _I, _D] + i7 + [_D, _I, ctypes.c_double, _D, _D,
+                                                                     ctypes.c_double, _I, _D]
             lib.orc_grad.argtypes = [_I, _I, _D, _D, _D]
             lib.orc_div.argtypes = [_I, _I, _D, _D, _D]
             _lib = lib
@@ -301,3 +304,39 @@ def filter_solve(g: Geometry, p, region, iters: int, u=None, nonneg: bool = True
     shift = gv * D[y0:y0 + h, x0:x0 + w]
     x = filter_method(g, box, pd, u, n=iters, shift=shift, lo=0.0 if nonneg else -np.inf)
     return x, box
+
+
+def fgp(z, lam: float, iters: int) -> np.ndarray:
+    """FGP for min ||x - z||^2 + 2 lam TV(x) (isotropic, forward differences)."""
+    z = _f64(z)
+    h, w = z.shape
+    x = np.empty_like(z)
+    _load().orc_fgp(w, h, _p(z), float(lam), int(iters), _p(x))
+    return x
+
+
+def filter_fista(g: Geometry, box, p, u, lam: float, n_fgp: int = 100, n=None, alpha=None, shift=None):
+    """Alg. methodfista on the local part ``box``: FISTA for ||p - Wx||^2 + lam TV(x) with the
+    SIRT step approximated by the filters ``u`` and the TV prox by FGP."""
+    alpha = 1.0 / (g.na * g.nd) if alpha is None else float(alpha)
+    n = u.shape[0] if n is None else int(n)
+    box = _rect(box)
+    p = _f64(p).reshape(g.na, g.nd)
+    u = _f64(u)
+    x = np.empty((box[3], box[2]), np.float64)
+    sh = None if shift is None else _f64(shift).reshape(box[3], box[2])
+    _load().orc_filter_fista(*g._g(), *box, _p(p), n, alpha, _p(u), _p(sh) if sh is not None else None,
+                             float(lam), int(n_fgp), _p(x))
+    return x
+
+
+def filter_fista_solve(g: Geometry, p, region, iters: int, lam: float, n_fgp: int = 100, u=None):
+    """Alg. methodfista end to end: disc subtraction, filters, FISTA-TV on the box, disc added
+    back.  Returns (x_box, box)."""
+    box = roi_box(g.N, *region)
+    gv, pd, D = disc(g, p)
+    if u is None:
+        u = filtcalc(g, iters)
+    x0, y0, w, h = box
+    shift = gv * D[y0:y0 + h, x0:x0 + w]
+    return filter_fista(g, box, pd, u, lam, n_fgp=n_fgp, n=iters, shift=shift), box

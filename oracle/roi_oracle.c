@@ -22,7 +22,8 @@
  *              algebraically.
  *   Sec. 3     the paper's own local method: filters approximating SIRT (Alg. filtcalc,
  *              Eq. filtcalc, Eq. sirtapp), the local recursion with a prior term
- *              (Alg. method, Eq. localmethod) and the disc subtraction (Sec. 3.3).
+ *              (Alg. method, Eq. localmethod), its FISTA form with a TV prox computed
+ *              by FGP (Alg. methodfista) and the disc subtraction (Sec. 3.3).
  *
  * Readings where the paper is silent (each one is listed in the design notes):
  *   - W is Joseph's method: one ray per bin centre; when |cos| >= |sin| (ties,
@@ -595,6 +596,123 @@ void orc_filter_method(int N, int na, int nd, const double* ang,
     free(cp);
     free(xs);
     free(y);
+    free(wy);
+    free(g);
+}
+
+/* ---------------------------------------------------------------------------
+ * FGP (the fast gradient projection of Beck & Teboulle 2009, named in Sec. 3.2 for
+ * Alg. methodfista): the TV denoising problem
+ *     min_x ||x - z||^2 + 2 lam TV(x),  TV(x) = sum |grad x|_2 (isotropic, orc_grad),
+ * solved through its dual: x(v) = z + lam div v, and projected gradient ascent on v with
+ * |v_ij|_2 <= 1, step 1/(8 lam) (||div||^2 <= 8), accelerated by the FISTA sequence:
+ *     v_0 = r_1 = 0, t_1 = 1;  for k = 1..iters:
+ *         x   = z + lam div r_k
+ *         v_k = P(r_k + grad x / (8 lam))          P: v_ij <- v_ij / max(1, |v_ij|)
+ *         t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2
+ *         r_{k+1} = v_k + ((t_k - 1) / t_{k+1}) (v_k - v_{k-1})
+ *     x = z + lam div v_iters.
+ * lam = 0 returns z.  Image [h][w].
+ * ------------------------------------------------------------------------- */
+void orc_fgp(int w, int h, const double* z, double lam, int iters, double* x) {
+    const size_t n = (size_t)w * h;
+    if (lam <= 0.0 || iters <= 0) {
+        memcpy(x, z, sizeof(double) * n);
+        return;
+    }
+    double* vx = (double*)calloc(n, sizeof(double));
+    double* vy = (double*)calloc(n, sizeof(double));
+    double* rx = (double*)calloc(n, sizeof(double));
+    double* ry = (double*)calloc(n, sizeof(double));
+    double* gx = (double*)malloc(sizeof(double) * n);
+    double* gy = (double*)malloc(sizeof(double) * n);
+    double* dv = (double*)malloc(sizeof(double) * n);
+    double t = 1.0;
+    for (int k = 1; k <= iters; ++k) {
+        orc_div(w, h, rx, ry, dv);
+        for (size_t i = 0; i < n; ++i) x[i] = z[i] + lam * dv[i];
+        orc_grad(w, h, x, gx, gy);
+        const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+        const double beta = (t - 1.0) / tn;
+        for (size_t i = 0; i < n; ++i) {
+            double ax = rx[i] + gx[i] / (8.0 * lam), ay = ry[i] + gy[i] / (8.0 * lam);
+            double m = sqrt(ax * ax + ay * ay);
+            if (m > 1.0) {
+                ax /= m;
+                ay /= m;
+            }
+            rx[i] = ax + beta * (ax - vx[i]);
+            ry[i] = ay + beta * (ay - vy[i]);
+            vx[i] = ax;
+            vy[i] = ay;
+        }
+        t = tn;
+    }
+    orc_div(w, h, vx, vy, dv);
+    for (size_t i = 0; i < n; ++i) x[i] = z[i] + lam * dv[i];
+    free(vx);
+    free(vy);
+    free(rx);
+    free(ry);
+    free(gx);
+    free(gy);
+    free(dv);
+}
+
+/* ---------------------------------------------------------------------------
+ * Alg. methodfista (Sec. 3.2): the paper's local method with FISTA minimising
+ * ||p - W x||^2 + lambda TV(x) (Eq. priorsys with g = TV), the TV prox by FGP:
+ *     t_0 = 1, x_L = 0, x^0 = 0;  for k = 1..n:
+ *         x_s = FBP_L(p, u_k) = W_L^T C_{u_k} p
+ *         q   = x_L - alpha W_L^T W_L x_L
+ *         x^k = FGP(x_s + q + shift, lam_f, n_fgp) - shift
+ *         t_k = (1 + sqrt(1 + 4 t_{k-1}^2)) / 2
+ *         r   = x^k + ((t_{k-1} - 1) / t_k) (x^k - x^{k-1})
+ *         x_L = r - x_s
+ *     result x^n + shift.
+ * Readings: the t and r lines of the printed algorithm are garbled; they are taken as
+ * the standard FISTA updates above.  The SIRT step x + alpha W^T (p - W x) is a gradient
+ * step of ||p - W x||^2 with step alpha / 2, so the prox of lambda TV at that step is the
+ * FGP problem with lam_f = alpha lambda / 2.  The prox acts on the image with the disc of
+ * Sec. 3.3 added back (shift), like the box constraint of orc_filter_method.
+ * ------------------------------------------------------------------------- */
+void orc_filter_fista(int N, int na, int nd, const double* ang,
+                      int bx0, int by0, int bw, int bh,
+                      const double* p, int n, double alpha, const double* u,
+                      const double* shift, double lambda, int n_fgp, double* x) {
+    const size_t nb = (size_t)bw * bh, ns = (size_t)na * nd, nu = (size_t)na * (2 * nd - 1);
+    double* cp = (double*)malloc(sizeof(double) * ns);
+    double* xs = (double*)malloc(sizeof(double) * nb);
+    double* xl = (double*)calloc(nb, sizeof(double));
+    double* xprev = (double*)calloc(nb, sizeof(double));
+    double* z = (double*)malloc(sizeof(double) * nb);
+    double* wy = (double*)malloc(sizeof(double) * ns);
+    double* g = (double*)malloc(sizeof(double) * nb);
+    const double lam_f = 0.5 * alpha * lambda;
+    double t = 1.0;
+    for (int k = 1; k <= n; ++k) {
+        orc_filter_conv(na, nd, u + (size_t)(k - 1) * nu, p, cp);
+        orc_back(N, na, nd, ang, bx0, by0, bw, bh, 0, 0, 0, 0, cp, xs);
+        orc_forward(N, na, nd, ang, bx0, by0, bw, bh, xl, 0, 0, 0, 0, wy);
+        orc_back(N, na, nd, ang, bx0, by0, bw, bh, 0, 0, 0, 0, wy, g);
+        for (size_t i = 0; i < nb; ++i) z[i] = xs[i] + xl[i] - alpha * g[i] + (shift ? shift[i] : 0.0);
+        orc_fgp(bw, bh, z, lam_f, n_fgp, x);
+        const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+        const double beta = (t - 1.0) / tn;
+        for (size_t i = 0; i < nb; ++i) {
+            double xk = x[i] - (shift ? shift[i] : 0.0);
+            double r = xk + beta * (xk - xprev[i]);
+            xl[i] = r - xs[i];
+            xprev[i] = xk;
+        }
+        t = tn;
+    }
+    for (size_t i = 0; i < nb; ++i) x[i] = xprev[i] + (shift ? shift[i] : 0.0);
+    free(cp);
+    free(xs);
+    free(xl);
+    free(xprev);
+    free(z);
     free(wy);
     free(g);
 }
