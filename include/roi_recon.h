@@ -61,9 +61,12 @@ typedef enum { ROI_F32 = 0, ROI_BF16 = 1, ROI_F16 = 2 } roi_dtype;
 typedef enum {
     ROI_SIRT_NONNEG = 0,   /* exterior subtraction, then nonnegative SIRT on the box (Sec. 1 scheme) */
     ROI_TV_CP = 1,         /* exterior subtraction, then TV by Chambolle-Pock on the box             */
-    ROI_FILTER_SIRT = 2    /* the paper's own method (Sec. 3): SIRT approximated by FBP with the
+    ROI_FILTER_SIRT = 2,   /* the paper's own method (Sec. 3): SIRT approximated by FBP with the
                               filters of Alg. filtcalc, the constraint x >= 0 applied on the box
                               by Alg. method; needs roi_recon_filter_prepare                     */
+    ROI_FILTER_TV = 3      /* the paper's method with FISTA for ||p - Wx||^2 + lambda TV(x), the
+                              TV prox by inner_iters FGP iterations (Alg. methodfista); needs
+                              roi_recon_filter_prepare                                           */
 } roi_regularizer;
 
 /* Acquisition geometry (Sec. 2.1: N x N grid, N_d detectors, N_theta angles). */
@@ -93,6 +96,7 @@ typedef struct {
     int precond;           /* CP: 1 = diagonal steps (Pock & Chambolle 2011), 0 = 0.99/||K||  */
     int crop_disk;         /* 1: set output pixels outside the disk of radius r to 0          */
     int eval_objective;    /* 1: fill info->objective (the call then synchronizes)            */
+    int inner_iters;       /* ROI_FILTER_TV: FGP iterations per outer iteration (0: 100)     */
 } roi_solve_params;
 
 /* Plan and result description of one local solve. */

@@ -22,7 +22,7 @@ from . import build as _build
 
 __all__ = [
     "ROI_OK", "ROI_EINVAL", "ROI_ENOMEM", "ROI_ESTATE", "ROI_ECUDA", "ROI_ETIMEOUT", "ROI_EBUSY",
-    "ROI_F32", "ROI_BF16", "ROI_F16", "ROI_SIRT_NONNEG", "ROI_TV_CP", "ROI_FILTER_SIRT",
+    "ROI_F32", "ROI_BF16", "ROI_F16", "ROI_SIRT_NONNEG", "ROI_TV_CP", "ROI_FILTER_SIRT", "ROI_FILTER_TV",
     "roi_recon_filter_prepare", "roi_recon_filter_get", "roi_recon_set_sinogram_truncated",
     "roi_recon_solve_tiled",
     "Geometry", "Region", "SolveParams", "SolveInfo", "RoiError", "lib", "EXPORTS",
@@ -40,7 +40,7 @@ __all__ = [
 
 ROI_OK, ROI_EINVAL, ROI_ENOMEM, ROI_ESTATE, ROI_ECUDA, ROI_ETIMEOUT, ROI_EBUSY = range(7)
 ROI_F32, ROI_BF16, ROI_F16 = range(3)
-ROI_SIRT_NONNEG, ROI_TV_CP, ROI_FILTER_SIRT = range(3)
+ROI_SIRT_NONNEG, ROI_TV_CP, ROI_FILTER_SIRT, ROI_FILTER_TV = range(4)
 ROI_OPT_SINGLE_LAUNCH, ROI_OPT_WAIT_LIMIT_US, ROI_OPT_TEST_ABSENT_BLOCKS = range(3)
 
 _STATUS = {0: "ROI_OK", 1: "ROI_EINVAL", 2: "ROI_ENOMEM", 3: "ROI_ESTATE", 4: "ROI_ECUDA",
@@ -60,7 +60,7 @@ class Region(ctypes.Structure):
 class SolveParams(ctypes.Structure):
     _fields_ = [("reg", ctypes.c_int), ("lam", ctypes.c_double), ("iters", ctypes.c_int),
                 ("weighting", ctypes.c_int), ("precond", ctypes.c_int), ("crop_disk", ctypes.c_int),
-                ("eval_objective", ctypes.c_int)]
+                ("eval_objective", ctypes.c_int), ("inner_iters", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -501,13 +501,13 @@ class RoiRecon:
         return d0
 
     def solve_local(self, region, reg=ROI_SIRT_NONNEG, iters=200, lam=0.0, weighting=0, precond=1,
-                    crop_disk=0, eval_objective=0, out=None):
+                    crop_disk=0, eval_objective=0, out=None, inner_iters=0):
         """Returns (out, info); out is a CUDA tensor [box_h][box_w] or a host numpy array."""
         torch = self._torch
         pl = self.plan(region)
         shape = (pl.box[3], pl.box[2])
         prm = SolveParams(int(reg), float(lam), int(iters), int(weighting), int(precond), int(crop_disk),
-                          int(eval_objective))
+                          int(eval_objective), int(inner_iters))
         info = SolveInfo()
         if out is None:
             out = torch.empty(shape, dtype=torch.float32, device="cuda")
@@ -532,9 +532,7 @@ class RoiRecon:
         regs = (Region * n)(*[Region(*map(float, r)) for r in regions])
         prms = (SolveParams * n)()
         for i, p in enumerate(params):
-            prms[i] = SolveParams(int(p.get("reg", ROI_SIRT_NONNEG)), float(p.get("lam", 0.0)),
-                                  int(p.get("iters", 200)), int(p.get("weighting", 0)), 1,
-                                  int(p.get("crop_disk", 0)), 0)
+            prms[i] = _params(p)
         infos = (SolveInfo * n)()
         on_device = 1
         if outs is None:
@@ -622,7 +620,7 @@ class RoiRecon:
 
 def _params(p: dict) -> SolveParams:
     return SolveParams(int(p.get("reg", ROI_SIRT_NONNEG)), float(p.get("lam", 0.0)), int(p.get("iters", 200)),
-                       int(p.get("weighting", 0)), 1, int(p.get("crop_disk", 0)), 0)
+                       int(p.get("weighting", 0)), 1, int(p.get("crop_disk", 0)), 0, int(p.get("inner_iters", 0)))
 
 
 def server_footprint(N, n_angles, n_det, region, storage=ROI_F32):

@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(BPT, 1) k_batch(BatchArgs B) {
     bufs.tau = B.slot_tau + slot * B.img_cap;
     bufs.xa_base = B.slot_xa + slot * B.pad_cap;
     bufs.xaT_base = B.slot_xaT + slot * B.pad_cap;
+    bufs.fgp = B.slot_fgp ? B.slot_fgp + slot * 5 * B.img_cap : nullptr;
     for (;;) {
         __syncthreads();
         if (tid == 0) s_roi = atomicAdd(B.queue, 1);
@@ -83,6 +84,7 @@ __global__ void __launch_bounds__(BPT, 1) k_batch_team(BatchArgs B) {
         s_bufs.tau = B.slot_tau + slot * B.img_cap;
         s_bufs.xa_base = B.slot_xa + slot * B.pad_cap;
         s_bufs.xaT_base = B.slot_xaT + slot * B.pad_cap;
+        s_bufs.fgp = B.slot_fgp ? B.slot_fgp + slot * 5 * B.img_cap : nullptr;
     }
     __syncthreads();
     unsigned parity = 0;

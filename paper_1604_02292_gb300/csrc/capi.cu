@@ -120,7 +120,7 @@ struct roi_recon {
     DevBufT<int> b_order;
     DevBufT<int> b_queue;
     DevBufT<unsigned> b_bars;
-    DevBuf s_pp, s_u, s_sig, s_x, s_vx, s_vy, s_tau, s_xa, s_xaT;
+    DevBuf s_pp, s_u, s_sig, s_x, s_vx, s_vy, s_tau, s_xa, s_xaT, s_fgp;
     // residual p - W x_fbp over every ray, [na][resid_ld] (exterior step of the
     // whole-region solvers, Eq. locouter); valid while resid_ready
     DevBuf resid;
@@ -860,7 +860,7 @@ void roi_recon_destroy(roi_recon_t h) {
     h->b_queue.release();
     h->b_bars.release();
     for (DevBuf* b : {&h->b_out, &h->s_pp, &h->s_u, &h->s_sig, &h->s_x, &h->s_vx, &h->s_vy, &h->s_tau, &h->s_xa,
-                      &h->s_xaT, &h->resid})
+                      &h->s_xaT, &h->resid, &h->s_fgp})
         b->release();
     if (h->pin) cudaFreeHost(h->pin);
     if (h->pin_free) cudaEventDestroy(h->pin_free);
@@ -1044,6 +1044,11 @@ roi_status roi_recon_solve_local(roi_recon_t h, const roi_region* region, const 
     if (!h || !region || !params) return ROI_EINVAL;
     h->err.clear();
     if (!out) return fail(h, ROI_EINVAL, "solve_local: null output");
+    if (params->reg == ROI_FILTER_TV) {  // Alg. methodfista runs in the whole-region solver
+        if (params->eval_objective) return fail(h, ROI_EINVAL, "solve_local: no objective for ROI_FILTER_TV");
+        float* outs[1] = {out};
+        return roi_recon_solve_batch(h, 1, region, params, outs, out_on_device, info);
+    }
     if (params->reg != ROI_SIRT_NONNEG && params->reg != ROI_TV_CP && params->reg != ROI_FILTER_SIRT)
         return fail(h, ROI_EINVAL, "solve_local: unknown regularizer %d", (int)params->reg);
     if (params->iters < 0 || params->iters > 1000000) return fail(h, ROI_EINVAL, "solve_local: iters out of range");
@@ -1163,7 +1168,11 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
     if (n < 0 || (n > 0 && (!regions || !params || !outs))) return fail(h, ROI_EINVAL, "solve_batch: bad arguments");
     if (n == 0) return ROI_OK;
     bool need_fbp = false;
-    for (int i = 0; i < n; ++i) need_fbp = need_fbp || params[i].reg != ROI_FILTER_SIRT;
+    bool need_fgp = false;
+    for (int i = 0; i < n; ++i) {
+        need_fbp = need_fbp || (params[i].reg != ROI_FILTER_SIRT && params[i].reg != ROI_FILTER_TV);
+        need_fgp = need_fgp || params[i].reg == ROI_FILTER_TV;
+    }
     if (need_fbp && !h->have_fbp) return fail(h, ROI_ESTATE, "solve_batch: no FBP image (call fbp first)");
     const int na = h->na;
     // ---- host plan of every region
@@ -1176,10 +1185,12 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
         const roi_solve_params& P = params[i];
         if (!finite_region(&regions[i]))
             return fail(h, ROI_EINVAL, "solve_batch: region %d: radius must be > 0, margin >= 0, all finite", i);
-        if (P.reg != ROI_SIRT_NONNEG && P.reg != ROI_TV_CP && P.reg != ROI_FILTER_SIRT)
+        if (P.reg != ROI_SIRT_NONNEG && P.reg != ROI_TV_CP && P.reg != ROI_FILTER_SIRT && P.reg != ROI_FILTER_TV)
             return fail(h, ROI_EINVAL, "solve_batch: region %d: unknown regularizer", i);
-        if (P.reg == ROI_FILTER_SIRT && h->fcp_n < P.iters)
+        if ((P.reg == ROI_FILTER_SIRT || P.reg == ROI_FILTER_TV) && h->fcp_n < P.iters)
             return fail(h, ROI_ESTATE, "solve_batch: region %d: filters for %d iterations not prepared", i, P.iters);
+        if (P.inner_iters < 0 || P.inner_iters > 100000)
+            return fail(h, ROI_EINVAL, "solve_batch: region %d: inner_iters out of range", i);
         if (P.iters < 0 || P.iters > 1000000) return fail(h, ROI_EINVAL, "solve_batch: region %d: iters out of range", i);
         if (!std::isfinite(P.lambda) || P.lambda < 0) return fail(h, ROI_EINVAL, "solve_batch: region %d: bad lambda", i);
         if (P.reg == ROI_TV_CP && !P.precond)
@@ -1222,6 +1233,7 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
     for (DevBuf* b : {&h->s_pp, &h->s_u, &h->s_sig}) CU(h, b->ensure(win_cap * blocks));
     for (DevBuf* b : {&h->s_x, &h->s_vx, &h->s_vy, &h->s_tau}) CU(h, b->ensure(img_cap * blocks));
     for (DevBuf* b : {&h->s_xa, &h->s_xaT}) CU(h, b->ensure(pad_cap * blocks));
+    if (need_fgp) CU(h, h->s_fgp.ensure(5 * img_cap * blocks));
     // ---- page-locked staging: tables, descriptors, order
     const size_t tab_bytes = sizeof(AngleRec) * (size_t)n * na;
     const size_t roi_bytes = sizeof(roi::BatchRoi) * (size_t)n;
@@ -1253,7 +1265,7 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
         R.nx = box.w;
         R.ny = box.h;
         R.stride = strides[i];
-        R.reg = P.reg == ROI_TV_CP ? 1 : P.reg == ROI_FILTER_SIRT ? 2 : 0;
+        R.reg = P.reg == ROI_TV_CP ? 1 : P.reg == ROI_FILTER_SIRT ? 2 : P.reg == ROI_FILTER_TV ? 3 : 0;
         R.iters = P.iters;
         R.weighting = P.reg == ROI_SIRT_NONNEG && P.weighting ? 1 : 0;
         R.lambda = (float)P.lambda;
@@ -1264,6 +1276,8 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
         R.r2 = (float)(regions[i].radius * regions[i].radius);
         exterior_inputs(h, R, box);
         filter_inputs(h, R);
+        R.n_fgp = P.inner_iters ? P.inner_iters : 100;
+        R.lam_f = (float)(0.5 * P.lambda / ((double)na * h->nd));
         ooff += (size_t)box.w * box.h;
         pord[i] = i;
         if (infos) {
@@ -1301,6 +1315,7 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
     B.slot_xa = h->s_xa.p;
     B.slot_xaT = h->s_xaT.p;
     B.pad_cap = pad_cap;
+    B.slot_fgp = need_fgp ? h->s_fgp.p : nullptr;
     B.err = h->d_err;
     B.wait_ns = h->opt_wait_ns;
     B.team = team > 1 ? team : 1;

@@ -192,7 +192,7 @@ __device__ __forceinline__ void phase_a_branch(const Ctx& C, const Team& T, int 
                     float res = C.b.pp[o] - acc;
                     if (R.weighting) res *= C.b.sig[o];
                     C.b.u[o] = res;
-                } else if (R.reg == 2) {
+                } else if (R.reg >= 2) {
                     C.b.u[o] = -R.alpha * acc;
                 } else {
                     const float sg = C.b.sig[o];
@@ -314,6 +314,8 @@ __device__ __forceinline__ void phase_b(const Ctx& C, const Team& T, int pass, i
             const int o = gi * nx + gj;
             if (pass == B_XS) {
                 C.b.vy[o] = acc;  // x_s^k
+            } else if (R.reg == 3) {  // Alg. methodfista: z = x_s + x_L - alpha W_L^T W_L x_L, disc added
+                C.b.vx[o] = C.b.vy[o] + C.b.x[o] + acc + disc_value(R, gi, gj);
             } else if (R.reg == 2) {  // Alg. method, x >= 0 on the final image (disc added back)
                 const float xs = C.b.vy[o];
                 const float sv = xs + C.b.x[o] + acc;  // acc = -alpha W_L^T W_L y
@@ -507,7 +509,7 @@ __device__ __forceinline__ bool phase_a_banded(const Ctx& C, const Team& T, int 
                 float res = C.b.pp[o] - acc;
                 if (R.weighting) res *= C.b.sig[o];
                 C.b.u[o] = res;
-            } else if (R.reg == 2) {
+            } else if (R.reg >= 2) {
                 C.b.u[o] = -R.alpha * acc;
             } else {
                 const float sg = C.b.sig[o];
@@ -536,6 +538,91 @@ __device__ __forceinline__ void dual_grad(const Ctx& C) {
         const float sc = m > R.lambda ? R.lambda / m : 1.f;
         C.b.vx[p] = ax * sc;
         C.b.vy[p] = ay * sc;
+    }
+}
+
+// FGP on the box (Alg. methodfista's TV prox): x = argmin ||x - z||^2 + 2 lam_f TV(x) by
+// R.n_fgp accelerated projected-gradient steps on the dual (step 1/(8 lam_f)); z in C.b.vx,
+// x into fgp[4].  Pixels are dealt over the team; neighbours are read only across a
+// team barrier.  false: a wait gave up.
+template <bool SOLO>
+__device__ __forceinline__ bool fgp_prox_t(const Ctx& C, Team& T) {
+    const BatchRoi& R = *C.R;
+    const int nx = R.nx, ny = R.ny, nimg = nx * ny;
+    float* vx = C.b.fgp;
+    float* vy = vx + nimg;
+    float* rx = vy + nimg;
+    float* ry = rx + nimg;
+    float* fx = ry + nimg;
+    const float* z = C.b.vx;
+    const float lam = R.lam_f;
+    if (!(lam > 0.f) || R.n_fgp <= 0) {
+        for (int p = team_tid(C); p < nimg; p += C.gthreads) fx[p] = z[p];
+        return team_sync<SOLO>(T);
+    }
+    for (int p = team_tid(C); p < nimg; p += C.gthreads) vx[p] = vy[p] = rx[p] = ry[p] = 0.f;
+    const float inv8 = 1.f / (8.f * lam);
+    float t = 1.f;
+    for (int k = 0; k <= R.n_fgp; ++k) {
+        if (!team_sync<SOLO>(T)) return false;
+        const bool last = k == R.n_fgp;
+        const float* dx = last ? vx : rx;
+        const float* dy = last ? vy : ry;
+        for (int p = team_tid(C); p < nimg; p += C.gthreads) {  // x = z + lam div(r), or div(v) at the end
+            const int i = p / nx, j = p - i * nx;
+            float d = 0.f;
+            if (j < nx - 1) d += dx[p];
+            if (j > 0) d -= dx[p - 1];
+            if (i < ny - 1) d += dy[p];
+            if (i > 0) d -= dy[p - nx];
+            fx[p] = fmaf(lam, d, z[p]);
+        }
+        if (last) break;
+        if (!team_sync<SOLO>(T)) return false;
+        const float tn = 0.5f * (1.f + sqrtf(1.f + 4.f * t * t));
+        const float beta = (t - 1.f) / tn;
+        for (int p = team_tid(C); p < nimg; p += C.gthreads) {  // v = P(r + grad x / (8 lam)), r extrapolated
+            const int i = p / nx, j = p - i * nx;
+            const float x0 = fx[p];
+            const float gx = j < nx - 1 ? fx[p + 1] - x0 : 0.f;
+            const float gy = i < ny - 1 ? fx[p + nx] - x0 : 0.f;
+            float ax = fmaf(gx, inv8, rx[p]), ay = fmaf(gy, inv8, ry[p]);
+            const float m = sqrtf(ax * ax + ay * ay);
+            if (m > 1.f) {
+                ax /= m;
+                ay /= m;
+            }
+            rx[p] = fmaf(beta, ax - vx[p], ax);
+            ry[p] = fmaf(beta, ay - vy[p], ay);
+            vx[p] = ax;
+            vy[p] = ay;
+        }
+        t = tn;
+    }
+    return team_sync<SOLO>(T);
+}
+
+// FISTA step of Alg. methodfista on this thread's pixels (t = t_{k-1}):
+//   x^k = FGP result - disc;  r = x^k + ((t - 1) / t_k) (x^k - x^{k-1});  x_L = r - x_s.
+template <int DT>
+__device__ __forceinline__ void fista_update(const Ctx& C, float t) {
+    const BatchRoi& R = *C.R;
+    const int nx = R.nx, nimg = nx * R.ny;
+    auto* xa = static_cast<typename Stor<DT>::T*>(C.xa);
+    auto* xaT = static_cast<typename Stor<DT>::T*>(C.xaT);
+    const float* fx = C.b.fgp + 4 * (size_t)nimg;
+    const float tn = 0.5f * (1.f + sqrtf(1.f + 4.f * t * t));
+    const float beta = (t - 1.f) / tn;
+    for (int p = team_tid(C); p < nimg; p += C.gthreads) {
+        const int i = p / nx, j = p - i * nx;
+        const float xk = fx[p] - disc_value(R, i, j);
+        const float r = fmaf(beta, xk - C.b.tau[p], xk);
+        const float xl = r - C.b.vy[p];
+        C.b.tau[p] = xk;
+        C.b.x[p] = xl;
+        const auto xs = from_f32<DT>(xl);
+        xa[i * C.lda + j] = xs;
+        xaT[j * C.ldaT + i] = xs;
     }
 }
 
@@ -575,7 +662,7 @@ __device__ __forceinline__ bool solve_region(const BatchRoi& R, const RegionBufs
     fill_team(C, C.b.x, nimg, 0.f);
     fill_team(C, C.b.vx, nimg, 0.f);
     fill_team(C, C.b.vy, nimg, 0.f);
-    if (R.reg != 2) {  // the paper's own method (reg 2) needs no exterior step
+    if (R.reg < 2) {  // the paper's own method (reg 2, 3) needs no exterior step
         load_fbp_box<DT>(C);
         if (!team_sync<SOLO>(T)) return false;
         phase_a_global<SOLO, DT>(C, T, A_EXTER, s_cnt);
@@ -595,6 +682,8 @@ __device__ __forceinline__ bool solve_region(const BatchRoi& R, const RegionBufs
     if (!team_sync<SOLO>(T)) return false;
 
     // ---- iterations
+    float fista_t = 1.f;  // FISTA sequence t_{k-1} (reg 3)
+    if (R.reg == 3) fill_team(C, C.b.tau, nimg, 0.f);  // x^0 = 0
     for (int it = 0; it < R.iters; ++it) {
         if (C.stage == 0) {
             for (int row = 1; row >= 0; --row) {
@@ -619,7 +708,7 @@ __device__ __forceinline__ bool solve_region(const BatchRoi& R, const RegionBufs
             phase_a_global<SOLO, DT>(C, T, A_SOLVE, s_cnt);
         }
         if (!team_sync<SOLO>(T)) return false;  // u, v of this iteration complete
-        if (R.reg == 2) {  // x_s^k first (tiles stay with their block, so a block barrier suffices)
+        if (R.reg >= 2) {  // x_s^k first (tiles stay with their block, so a block barrier suffices)
             if (tid == 0) *s_cnt = BNW;
             __syncthreads();
             phase_b<SOLO, DT>(C, T, B_XS, s_cnt, smem + warp * WARP_STAGE, it);
@@ -628,12 +717,19 @@ __device__ __forceinline__ bool solve_region(const BatchRoi& R, const RegionBufs
         if (tid == 0) *s_cnt = BNW;
         __syncthreads();
         phase_b<SOLO, DT>(C, T, B_SOLVE, s_cnt, smem + warp * WARP_STAGE);
-        if (!team_sync<SOLO>(T)) return false;  // x, xbar complete
+        if (!team_sync<SOLO>(T)) return false;  // x, xbar complete (reg 3: z complete)
+        if (R.reg == 3) {
+            if (!fgp_prox_t<SOLO>(C, T)) return false;
+            fista_update<DT>(C, fista_t);
+            fista_t = 0.5f * (1.f + sqrtf(1.f + 4.f * fista_t * fista_t));
+            if (!team_sync<SOLO>(T)) return false;
+        }
     }
     // ---- crop into the output buffer (x is kept in float for both solvers)
     for (int p = team_tid(C); p < (int)nimg; p += C.gthreads) {
         const int i = p / R.nx, j = p - i * R.nx;
-        float v = R.reg == 2 ? C.b.vx[p] + disc_value(R, i, j) : C.b.x[p];
+        float v = R.reg == 2 ? C.b.vx[p] + disc_value(R, i, j)
+                  : R.reg == 3 ? C.b.tau[p] + disc_value(R, i, j) : C.b.x[p];
         if (R.crop) {
             const float dx = (float)j - R.cxl, dy = (float)i - R.cyl;
             if (dx * dx + dy * dy > R.r2) v = 0.f;

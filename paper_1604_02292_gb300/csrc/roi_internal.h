@@ -349,6 +349,9 @@ struct BatchRoi {
     int fcp_nd;
     float disc_g;
     int grid_n;
+    // reg = 3, Alg. methodfista: FGP iterations and weight (lam_f = alpha lambda / 2)
+    int n_fgp;
+    float lam_f;
 };
 
 struct BatchArgs {
@@ -368,6 +371,7 @@ struct BatchArgs {
     float* slot_xa;        // padded images (row / column), from row 0 column -2
     float* slot_xaT;
     size_t pad_cap;
+    float* slot_fgp;       // 5 img_cap per slot when a region uses reg = 3, else null
     int* err;
     unsigned long long wait_ns;
     int team;              // blocks per region: 1, or > 1 for a cooperative launch of teams
@@ -385,6 +389,7 @@ struct RegionBufs {
     float* tau;
     void* xa_base;         // storage dt of the region (float, bfloat16 or half)
     void* xaT_base;
+    float* fgp;            // reg = 3: FGP state, 5 box arrays (v_x, v_y, r_x, r_y, x)
 };
 
 // ---- serving: one cooperative launch whose blocks take requests from rings in

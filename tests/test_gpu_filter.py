@@ -116,3 +116,30 @@ def test_batched_and_served_filter_solves(prepared):
         assert rel_l2(b, single.cpu().numpy()) <= 1e-5
         x, _ = oracle.filter_solve(g, p.astype(np.float64), region, n, u=uo)
         assert rel_l2(b, x) <= SOLVE_TOL
+
+
+@pytest.mark.parametrize("region,lam", [((64.0, 64.0, 16.0, 8.0), 300.0), ((30.5, 90.2, 12.0, 6.0), 800.0),
+                                        ((64.0, 60.0, 40.0, 20.0), 300.0)])
+def test_fista_tv_matches_oracle(prepared, region, lam):
+    """Alg. methodfista (ROI_FILTER_TV): FISTA with the filtered SIRT step and an FGP TV prox."""
+    rr, p, g, uo, n = prepared
+    iters, nf = 20, 25
+    out, _ = rr.solve_local(region, R.ROI_FILTER_TV, iters=iters, lam=lam, inner_iters=nf)
+    x, box = oracle.filter_fista_solve(g, p.astype(np.float64), region, iters, lam, n_fgp=nf, u=uo)
+    assert rel_l2(out.cpu().numpy(), x) <= SOLVE_TOL
+
+
+def test_fista_tv_batched_equals_served(prepared):
+    rr, p, g, uo, n = prepared
+    regions = [(64.0, 64.0, 16.0, 8.0), (90.0, 40.0, 20.0, 10.0)]
+    prm = dict(reg=R.ROI_FILTER_TV, iters=10, lam=300.0)
+    outs, _ = rr.solve_batch(regions, [prm] * len(regions))
+    rr.sync()
+    with R.Server(teams=0) as s:
+        s.add(rr)
+        ids = {s.submit(0, r, prm): k for k, r in enumerate(regions)}
+        s.drain(120000.0)
+        for c in s.poll():
+            assert c["status"] == R.ROI_OK
+            got = s.take(c["id"], (c["box"][3], c["box"][2]))
+            assert np.array_equal(got, outs[ids[c["id"]]].cpu().numpy())
