@@ -73,6 +73,10 @@ def _load():
             lib.orc_fgp.argtypes = [_I, _I, _D, ctypes.c_double, _I, _D]
             lib.orc_filter_fista.argtypes = [_I, _I, _I, _D] + i7 + [_D, _I, ctypes.c_double, _D, _D,
                                                                      ctypes.c_double, _I, _D]
+            lib.orc_haar.argtypes = [_I, _I, _I, _D, _D]
+            lib.orc_haar_inv.argtypes = [_I, _I, _I, _D, _D]
+            lib.orc_filter_ista.argtypes = [_I, _I, _I, _D] + i7 + [_D, _I, ctypes.c_double, _D, _D,
+                                                                    ctypes.c_double, _I, _D]
             lib.orc_grad.argtypes = [_I, _I, _D, _D, _D]
             lib.orc_div.argtypes = [_I, _I, _D, _D, _D]
             _lib = lib
@@ -340,3 +344,45 @@ def filter_fista_solve(g: Geometry, p, region, iters: int, lam: float, n_fgp: in
     x0, y0, w, h = box
     shift = gv * D[y0:y0 + h, x0:x0 + w]
     return filter_fista(g, box, pd, u, lam, n_fgp=n_fgp, n=iters, shift=shift), box
+
+
+def haar(x, levels: int = 32) -> np.ndarray:
+    """Orthonormal 2D Haar decomposition (see orc_haar)."""
+    x = _f64(x)
+    h, w = x.shape
+    out = np.empty_like(x)
+    _load().orc_haar(w, h, int(levels), _p(x), _p(out))
+    return out
+
+
+def haar_inv(c, levels: int = 32) -> np.ndarray:
+    c = _f64(c)
+    h, w = c.shape
+    out = np.empty_like(c)
+    _load().orc_haar_inv(w, h, int(levels), _p(c), _p(out))
+    return out
+
+
+def filter_ista(g: Geometry, box, p, u, lam: float, levels: int = 32, n=None, alpha=None, shift=None):
+    """Alg. method with the Haar-ISTA prior (Eq. sirtista) on the local part ``box``."""
+    alpha = 1.0 / (g.na * g.nd) if alpha is None else float(alpha)
+    n = u.shape[0] if n is None else int(n)
+    box = _rect(box)
+    p = _f64(p).reshape(g.na, g.nd)
+    u = _f64(u)
+    x = np.empty((box[3], box[2]), np.float64)
+    sh = None if shift is None else _f64(shift).reshape(box[3], box[2])
+    _load().orc_filter_ista(*g._g(), *box, _p(p), n, alpha, _p(u), _p(sh) if sh is not None else None,
+                            float(lam), int(levels), _p(x))
+    return x
+
+
+def filter_ista_solve(g: Geometry, p, region, iters: int, lam: float, levels: int = 32, u=None):
+    """Haar-ISTA in the paper's method end to end (disc subtraction and add-back)."""
+    box = roi_box(g.N, *region)
+    gv, pd, D = disc(g, p)
+    if u is None:
+        u = filtcalc(g, iters)
+    x0, y0, w, h = box
+    shift = gv * D[y0:y0 + h, x0:x0 + w]
+    return filter_ista(g, box, pd, u, lam, levels=levels, n=iters, shift=shift), box

@@ -23,7 +23,8 @@
  *   Sec. 3     the paper's own local method: filters approximating SIRT (Alg. filtcalc,
  *              Eq. filtcalc, Eq. sirtapp), the local recursion with a prior term
  *              (Alg. method, Eq. localmethod), its FISTA form with a TV prox computed
- *              by FGP (Alg. methodfista) and the disc subtraction (Sec. 3.3).
+ *              by FGP (Alg. methodfista), Haar-wavelet ISTA (Eq. sirtista) as its prior
+ *              term, and the disc subtraction (Sec. 3.3).
  *
  * Readings where the paper is silent (each one is listed in the design notes):
  *   - W is Joseph's method: one ray per bin centre; when |cos| >= |sin| (ties,
@@ -715,4 +716,121 @@ void orc_filter_fista(int N, int na, int nd, const double* ang,
     free(z);
     free(wy);
     free(g);
+}
+
+/* ---------------------------------------------------------------------------
+ * Haar wavelet ISTA inside the paper's method (Eq. sirtista, d of Alg. method).
+ * B is the orthonormal 2D Haar decomposition of a [h][w] box image:
+ *   level 0 block = the whole image; at each level, while the block [hl][wl] has hl >= 2
+ *   and wl >= 2 (and at most `levels` levels): every row of the block becomes
+ *   [pair sums / sqrt(2) | pair differences / sqrt(2)] -- entries 2j, 2j+1 give sum j and
+ *   difference ceil(wl/2) + j; an odd last entry is copied to sum position wl/2 -- then
+ *   every column of the block the same way; the next block is [ceil(hl/2)][ceil(wl/2)].
+ * Every step is orthogonal, so B^-1 = B^T (orc_haar_inv undoes the steps in reverse).
+ * ------------------------------------------------------------------------- */
+static void haar_split(const double* in, double* out, int L, int stride) {
+    const int m = L / 2, c = (L + 1) / 2;
+    const double s = 1.0 / sqrt(2.0);
+    for (int j = 0; j < m; ++j) {
+        double a = in[(size_t)(2 * j) * stride], b = in[(size_t)(2 * j + 1) * stride];
+        out[(size_t)j * stride] = s * (a + b);
+        out[(size_t)(c + j) * stride] = s * (a - b);
+    }
+    if (L % 2) out[(size_t)m * stride] = in[(size_t)(L - 1) * stride];
+}
+
+static void haar_merge(const double* in, double* out, int L, int stride) {
+    const int m = L / 2, c = (L + 1) / 2;
+    const double s = 1.0 / sqrt(2.0);
+    for (int j = 0; j < m; ++j) {
+        double u = in[(size_t)j * stride], v = in[(size_t)(c + j) * stride];
+        out[(size_t)(2 * j) * stride] = s * (u + v);
+        out[(size_t)(2 * j + 1) * stride] = s * (u - v);
+    }
+    if (L % 2) out[(size_t)(L - 1) * stride] = in[(size_t)m * stride];
+}
+
+static int haar_levels(int w, int h, int levels, int* hl, int* wl) {
+    int n = 0;
+    int H = h, Wd = w;
+    while (n < levels && H >= 2 && Wd >= 2) {
+        hl[n] = H;
+        wl[n] = Wd;
+        H = (H + 1) / 2;
+        Wd = (Wd + 1) / 2;
+        ++n;
+    }
+    return n;
+}
+
+void orc_haar(int w, int h, int levels, const double* x, double* c) {
+    int hl[32], wl[32];
+    const int n = haar_levels(w, h, levels > 32 ? 32 : levels, hl, wl);
+    double* t = (double*)malloc(sizeof(double) * (size_t)w * h);
+    memcpy(c, x, sizeof(double) * (size_t)w * h);
+    for (int l = 0; l < n; ++l) {
+        for (int i = 0; i < hl[l]; ++i) haar_split(c + (size_t)i * w, t + (size_t)i * w, wl[l], 1);
+        for (int j = 0; j < wl[l]; ++j) haar_split(t + j, c + j, hl[l], w);
+    }
+    free(t);
+}
+
+void orc_haar_inv(int w, int h, int levels, const double* c, double* x) {
+    int hl[32], wl[32];
+    const int n = haar_levels(w, h, levels > 32 ? 32 : levels, hl, wl);
+    double* t = (double*)malloc(sizeof(double) * (size_t)w * h);
+    memcpy(x, c, sizeof(double) * (size_t)w * h);
+    for (int l = n - 1; l >= 0; --l) {
+        for (int j = 0; j < wl[l]; ++j) haar_merge(x + j, t + j, hl[l], w);
+        for (int i = 0; i < hl[l]; ++i) haar_merge(t + (size_t)i * w, x + (size_t)i * w, wl[l], 1);
+    }
+    free(t);
+}
+
+/* Alg. method with the ISTA prior of Eq. sirtista (l1 norm of the Haar coefficients):
+ *     s   = x_s^k + y^{k-1} - alpha W_L^T W_L y^{k-1}
+ *     x^k = B^-1 P_tau(B (s + shift)) - shift,   tau = alpha lambda / 2
+ *     y^k = x^k - x_s^k;  result x^n + shift.
+ * P_tau is soft thresholding of every coefficient (sgn(c) max(|c| - tau, 0)); tau follows
+ * from the SIRT step being a gradient step of ||p - W x||^2 with step alpha / 2, as for
+ * orc_filter_fista. */
+void orc_filter_ista(int N, int na, int nd, const double* ang,
+                     int bx0, int by0, int bw, int bh,
+                     const double* p, int n, double alpha, const double* u,
+                     const double* shift, double lambda, int levels, double* x) {
+    const size_t nb = (size_t)bw * bh, ns = (size_t)na * nd, nu = (size_t)na * (2 * nd - 1);
+    double* cp = (double*)malloc(sizeof(double) * ns);
+    double* xs = (double*)malloc(sizeof(double) * nb);
+    double* y = (double*)calloc(nb, sizeof(double));
+    double* wy = (double*)malloc(sizeof(double) * ns);
+    double* g = (double*)malloc(sizeof(double) * nb);
+    double* z = (double*)malloc(sizeof(double) * nb);
+    double* cf = (double*)malloc(sizeof(double) * nb);
+    const double tau = 0.5 * alpha * lambda;
+    for (size_t i = 0; i < nb; ++i) x[i] = 0.0;
+    for (int k = 1; k <= n; ++k) {
+        orc_filter_conv(na, nd, u + (size_t)(k - 1) * nu, p, cp);
+        orc_back(N, na, nd, ang, bx0, by0, bw, bh, 0, 0, 0, 0, cp, xs);
+        orc_forward(N, na, nd, ang, bx0, by0, bw, bh, y, 0, 0, 0, 0, wy);
+        orc_back(N, na, nd, ang, bx0, by0, bw, bh, 0, 0, 0, 0, wy, g);
+        for (size_t i = 0; i < nb; ++i) z[i] = xs[i] + y[i] - alpha * g[i] + (shift ? shift[i] : 0.0);
+        orc_haar(bw, bh, levels, z, cf);
+        for (size_t i = 0; i < nb; ++i) {
+            double a = fabs(cf[i]) - tau;
+            cf[i] = a > 0.0 ? (cf[i] > 0.0 ? a : -a) : 0.0;
+        }
+        orc_haar_inv(bw, bh, levels, cf, x);
+        for (size_t i = 0; i < nb; ++i) {
+            x[i] -= shift ? shift[i] : 0.0;
+            y[i] = x[i] - xs[i];
+        }
+    }
+    for (size_t i = 0; i < nb; ++i) x[i] += shift ? shift[i] : 0.0;
+    free(cp);
+    free(xs);
+    free(y);
+    free(wy);
+    free(g);
+    free(z);
+    free(cf);
 }
