@@ -64,9 +64,12 @@ typedef enum {
     ROI_FILTER_SIRT = 2,   /* the paper's own method (Sec. 3): SIRT approximated by FBP with the
                               filters of Alg. filtcalc, the constraint x >= 0 applied on the box
                               by Alg. method; needs roi_recon_filter_prepare                     */
-    ROI_FILTER_TV = 3      /* the paper's method with FISTA for ||p - Wx||^2 + lambda TV(x), the
+    ROI_FILTER_TV = 3,     /* the paper's method with FISTA for ||p - Wx||^2 + lambda TV(x), the
                               TV prox by inner_iters FGP iterations (Alg. methodfista); needs
                               roi_recon_filter_prepare                                           */
+    ROI_FILTER_ISTA = 4    /* the paper's method with the ISTA prior of Eq. sirtista: soft
+                              thresholding (at alpha lambda / 2) of the orthonormal 2D Haar
+                              coefficients of the box, all levels; needs filter_prepare          */
 } roi_regularizer;
 
 /* Acquisition geometry (Sec. 2.1: N x N grid, N_d detectors, N_theta angles). */

@@ -22,7 +22,7 @@ from . import build as _build
 
 __all__ = [
     "ROI_OK", "ROI_EINVAL", "ROI_ENOMEM", "ROI_ESTATE", "ROI_ECUDA", "ROI_ETIMEOUT", "ROI_EBUSY",
-    "ROI_F32", "ROI_BF16", "ROI_F16", "ROI_SIRT_NONNEG", "ROI_TV_CP", "ROI_FILTER_SIRT", "ROI_FILTER_TV",
+    "ROI_F32", "ROI_BF16", "ROI_F16", "ROI_SIRT_NONNEG", "ROI_TV_CP", "ROI_FILTER_SIRT", "ROI_FILTER_TV", "ROI_FILTER_ISTA",
     "roi_recon_filter_prepare", "roi_recon_filter_get", "roi_recon_set_sinogram_truncated",
     "roi_recon_solve_tiled",
     "Geometry", "Region", "SolveParams", "SolveInfo", "RoiError", "lib", "EXPORTS",
@@ -40,7 +40,7 @@ __all__ = [
 
 ROI_OK, ROI_EINVAL, ROI_ENOMEM, ROI_ESTATE, ROI_ECUDA, ROI_ETIMEOUT, ROI_EBUSY = range(7)
 ROI_F32, ROI_BF16, ROI_F16 = range(3)
-ROI_SIRT_NONNEG, ROI_TV_CP, ROI_FILTER_SIRT, ROI_FILTER_TV = range(4)
+ROI_SIRT_NONNEG, ROI_TV_CP, ROI_FILTER_SIRT, ROI_FILTER_TV, ROI_FILTER_ISTA = range(5)
 ROI_OPT_SINGLE_LAUNCH, ROI_OPT_WAIT_LIMIT_US, ROI_OPT_TEST_ABSENT_BLOCKS = range(3)
 
 _STATUS = {0: "ROI_OK", 1: "ROI_EINVAL", 2: "ROI_ENOMEM", 3: "ROI_ESTATE", 4: "ROI_ECUDA",

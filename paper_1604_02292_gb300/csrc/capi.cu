@@ -1044,8 +1044,8 @@ roi_status roi_recon_solve_local(roi_recon_t h, const roi_region* region, const 
     if (!h || !region || !params) return ROI_EINVAL;
     h->err.clear();
     if (!out) return fail(h, ROI_EINVAL, "solve_local: null output");
-    if (params->reg == ROI_FILTER_TV) {  // Alg. methodfista runs in the whole-region solver
-        if (params->eval_objective) return fail(h, ROI_EINVAL, "solve_local: no objective for ROI_FILTER_TV");
+    if (params->reg == ROI_FILTER_TV || params->reg == ROI_FILTER_ISTA) {  // run in the whole-region solver
+        if (params->eval_objective) return fail(h, ROI_EINVAL, "solve_local: no objective for this regularizer");
         float* outs[1] = {out};
         return roi_recon_solve_batch(h, 1, region, params, outs, out_on_device, info);
     }
@@ -1170,8 +1170,10 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
     bool need_fbp = false;
     bool need_fgp = false;
     for (int i = 0; i < n; ++i) {
-        need_fbp = need_fbp || (params[i].reg != ROI_FILTER_SIRT && params[i].reg != ROI_FILTER_TV);
-        need_fgp = need_fgp || params[i].reg == ROI_FILTER_TV;
+        const bool filt = params[i].reg == ROI_FILTER_SIRT || params[i].reg == ROI_FILTER_TV ||
+                          params[i].reg == ROI_FILTER_ISTA;
+        need_fbp = need_fbp || !filt;
+        need_fgp = need_fgp || params[i].reg == ROI_FILTER_TV || params[i].reg == ROI_FILTER_ISTA;
     }
     if (need_fbp && !h->have_fbp) return fail(h, ROI_ESTATE, "solve_batch: no FBP image (call fbp first)");
     const int na = h->na;
@@ -1185,9 +1187,9 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
         const roi_solve_params& P = params[i];
         if (!finite_region(&regions[i]))
             return fail(h, ROI_EINVAL, "solve_batch: region %d: radius must be > 0, margin >= 0, all finite", i);
-        if (P.reg != ROI_SIRT_NONNEG && P.reg != ROI_TV_CP && P.reg != ROI_FILTER_SIRT && P.reg != ROI_FILTER_TV)
+        if (P.reg < ROI_SIRT_NONNEG || P.reg > ROI_FILTER_ISTA)
             return fail(h, ROI_EINVAL, "solve_batch: region %d: unknown regularizer", i);
-        if ((P.reg == ROI_FILTER_SIRT || P.reg == ROI_FILTER_TV) && h->fcp_n < P.iters)
+        if (P.reg >= ROI_FILTER_SIRT && h->fcp_n < P.iters)
             return fail(h, ROI_ESTATE, "solve_batch: region %d: filters for %d iterations not prepared", i, P.iters);
         if (P.inner_iters < 0 || P.inner_iters > 100000)
             return fail(h, ROI_EINVAL, "solve_batch: region %d: inner_iters out of range", i);
@@ -1265,7 +1267,7 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
         R.nx = box.w;
         R.ny = box.h;
         R.stride = strides[i];
-        R.reg = P.reg == ROI_TV_CP ? 1 : P.reg == ROI_FILTER_SIRT ? 2 : P.reg == ROI_FILTER_TV ? 3 : 0;
+        R.reg = (int)P.reg;  // 0 SIRT, 1 CP-TV, 2 filter SIRT, 3 filter FISTA-TV, 4 filter Haar-ISTA
         R.iters = P.iters;
         R.weighting = P.reg == ROI_SIRT_NONNEG && P.weighting ? 1 : 0;
         R.lambda = (float)P.lambda;

@@ -314,7 +314,7 @@ __device__ __forceinline__ void phase_b(const Ctx& C, const Team& T, int pass, i
             const int o = gi * nx + gj;
             if (pass == B_XS) {
                 C.b.vy[o] = acc;  // x_s^k
-            } else if (R.reg == 3) {  // Alg. methodfista: z = x_s + x_L - alpha W_L^T W_L x_L, disc added
+            } else if (R.reg >= 3) {  // z = x_s + x_L - alpha W_L^T W_L x_L, disc added (FISTA-TV, Haar-ISTA)
                 C.b.vx[o] = C.b.vy[o] + C.b.x[o] + acc + disc_value(R, gi, gj);
             } else if (R.reg == 2) {  // Alg. method, x >= 0 on the final image (disc added back)
                 const float xs = C.b.vy[o];
@@ -626,6 +626,85 @@ __device__ __forceinline__ void fista_update(const Ctx& C, float t) {
     }
 }
 
+// One orthonormal Haar step on the leading [hl][wl] block of an image of row stride ld,
+// along rows (dir 0) or columns (dir 1): split = pair sums / differences over sqrt(2), an
+// odd last entry carried as a sum; merge = its transpose.  Team-split over the block.
+__device__ __forceinline__ void haar_pass(const Ctx& C, const float* in, float* out, int ld, int hl, int wl, int dir,
+                                          bool merge) {
+    const float s = 0.70710678118654752f;
+    const int L = dir ? hl : wl, m = L / 2, c = (L + 1) / 2;
+    for (int q = team_tid(C); q < hl * wl; q += C.gthreads) {
+        const int i = q / wl, j = q - i * wl;
+        const int e = dir ? i : j;                          // index along the pass
+        const int base = dir ? j : i * ld, st = dir ? ld : 1;  // line start, element stride
+        float v;
+        if (!merge) {
+            if (e < m)
+                v = s * (in[base + 2 * e * st] + in[base + (2 * e + 1) * st]);
+            else if (e < c)
+                v = in[base + (L - 1) * st];
+            else
+                v = s * (in[base + 2 * (e - c) * st] - in[base + (2 * e - 2 * c + 1) * st]);
+        } else {
+            const int k = e / 2;
+            if ((L & 1) && e == L - 1)
+                v = in[base + m * st];
+            else if (e & 1)
+                v = s * (in[base + k * st] - in[base + (c + k) * st]);
+            else
+                v = s * (in[base + k * st] + in[base + (c + k) * st]);
+        }
+        out[i * ld + j] = v;
+    }
+}
+
+// Haar-ISTA step of Alg. method (Eq. sirtista): x = B^-1 P_tau(B z) - disc with z in
+// C.b.vx (transformed in place, fgp[0] as the other buffer), tau = R.lam_f; then
+// y = x - x_s into C.b.x and the projector images, x into C.b.tau.
+template <bool SOLO, int DT>
+__device__ __forceinline__ bool haar_ista_step(const Ctx& C, Team& T) {
+    const BatchRoi& R = *C.R;
+    const int nx = R.nx, ny = R.ny, nimg = nx * ny;
+    float* z = C.b.vx;
+    float* t = C.b.fgp;
+    // level l works on the leading [ceil(ny / 2^l)][ceil(nx / 2^l)] block (repeated ceil halving)
+    int nl = 0;
+    while (nl < 30 && ((ny + (1 << nl) - 1) >> nl) >= 2 && ((nx + (1 << nl) - 1) >> nl) >= 2) ++nl;
+    for (int l = 0; l < nl; ++l) {
+        const int hl = (ny + (1 << l) - 1) >> l, wl = (nx + (1 << l) - 1) >> l;
+        haar_pass(C, z, t, nx, hl, wl, 0, false);
+        if (!team_sync<SOLO>(T)) return false;
+        haar_pass(C, t, z, nx, hl, wl, 1, false);
+        if (!team_sync<SOLO>(T)) return false;
+    }
+    const float tau = R.lam_f;
+    for (int p = team_tid(C); p < nimg; p += C.gthreads) {
+        const float a = fabsf(z[p]) - tau;
+        z[p] = a > 0.f ? copysignf(a, z[p]) : 0.f;
+    }
+    for (int l = nl - 1; l >= 0; --l) {
+        const int hl = (ny + (1 << l) - 1) >> l, wl = (nx + (1 << l) - 1) >> l;
+        if (!team_sync<SOLO>(T)) return false;
+        haar_pass(C, z, t, nx, hl, wl, 1, true);
+        if (!team_sync<SOLO>(T)) return false;
+        haar_pass(C, t, z, nx, hl, wl, 0, true);
+    }
+    if (!team_sync<SOLO>(T)) return false;
+    auto* xa = static_cast<typename Stor<DT>::T*>(C.xa);
+    auto* xaT = static_cast<typename Stor<DT>::T*>(C.xaT);
+    for (int p = team_tid(C); p < nimg; p += C.gthreads) {
+        const int i = p / nx, j = p - i * nx;
+        const float xv = z[p] - disc_value(R, i, j);
+        const float yv = xv - C.b.vy[p];
+        C.b.tau[p] = xv;
+        C.b.x[p] = yv;
+        const auto ys = from_f32<DT>(yv);
+        xa[i * C.lda + j] = ys;
+        xaT[j * C.ldaT + i] = ys;
+    }
+    return team_sync<SOLO>(T);
+}
+
 // Solve region R into R.out.  DT: storage of x_fbp and of the projector images (R.dt).
 // smem: dynamic shared memory, at least stage_bytes(nx, ny, esz) and the per-warp phase-B
 // areas; mbar[0..1]: two initialised mbarriers, parity their phase bits.  Returns false
@@ -683,7 +762,7 @@ __device__ __forceinline__ bool solve_region(const BatchRoi& R, const RegionBufs
 
     // ---- iterations
     float fista_t = 1.f;  // FISTA sequence t_{k-1} (reg 3)
-    if (R.reg == 3) fill_team(C, C.b.tau, nimg, 0.f);  // x^0 = 0
+    if (R.reg >= 3) fill_team(C, C.b.tau, nimg, 0.f);  // x^0 = 0
     for (int it = 0; it < R.iters; ++it) {
         if (C.stage == 0) {
             for (int row = 1; row >= 0; --row) {
@@ -723,13 +802,15 @@ __device__ __forceinline__ bool solve_region(const BatchRoi& R, const RegionBufs
             fista_update<DT>(C, fista_t);
             fista_t = 0.5f * (1.f + sqrtf(1.f + 4.f * fista_t * fista_t));
             if (!team_sync<SOLO>(T)) return false;
+        } else if (R.reg == 4) {
+            if (!haar_ista_step<SOLO, DT>(C, T)) return false;
         }
     }
     // ---- crop into the output buffer (x is kept in float for both solvers)
     for (int p = team_tid(C); p < (int)nimg; p += C.gthreads) {
         const int i = p / R.nx, j = p - i * R.nx;
         float v = R.reg == 2 ? C.b.vx[p] + disc_value(R, i, j)
-                  : R.reg == 3 ? C.b.tau[p] + disc_value(R, i, j) : C.b.x[p];
+                  : R.reg >= 3 ? C.b.tau[p] + disc_value(R, i, j) : C.b.x[p];
         if (R.crop) {
             const float dx = (float)j - R.cxl, dy = (float)i - R.cyl;
             if (dx * dx + dy * dy > R.r2) v = 0.f;

@@ -336,7 +336,7 @@ void publish(roi_server* s, int pi, Req* r, size_t slot) {
     R.nx = r->box.w;
     R.ny = r->box.h;
     R.stride = r->stride;
-    R.reg = r->prm.reg == ROI_TV_CP ? 1 : r->prm.reg == ROI_FILTER_SIRT ? 2 : r->prm.reg == ROI_FILTER_TV ? 3 : 0;
+    R.reg = (int)r->prm.reg;  // 0 SIRT, 1 CP-TV, 2 filter SIRT, 3 filter FISTA-TV, 4 filter Haar-ISTA
     R.n_fgp = r->prm.inner_iters ? r->prm.inner_iters : 100;
     R.lam_f = (float)(0.5 * r->prm.lambda / ((double)v.na * v.nd));
     R.iters = r->prm.iters;
@@ -371,7 +371,7 @@ void publish(roi_server* s, int pi, Req* r, size_t slot) {
     B.tau = reinterpret_cast<float*>(base + r->lay.tau);
     B.xa_base = base + r->lay.xa;
     B.xaT_base = base + r->lay.xaT;
-    B.fgp = r->prm.reg == ROI_FILTER_TV ? reinterpret_cast<float*>(base + r->lay.fgp) : nullptr;
+    B.fgp = r->prm.reg >= ROI_FILTER_TV ? reinterpret_cast<float*>(base + r->lay.fgp) : nullptr;
     hdr.seq = (unsigned long long)r->ticket + 1ull;
     std::memcpy(sp, &hdr, sizeof hdr);
     std::memcpy(sp + roi::serve_slot_header_bytes, r->rec.data(), sizeof(AngleRec) * r->rec.size());
@@ -651,8 +651,7 @@ roi_status roi_server_submit(roi_server_t s, int sino_id, const roi_region* regi
     if (sino_id < 0 || sino_id >= (int)s->sinos.size()) return sfail(s, ROI_EINVAL, "submit: unknown sinogram %d", sino_id);
     const roi_solve_params& P = *params;
     if (!finite_region(region)) return sfail(s, ROI_EINVAL, "submit: radius must be > 0, margin >= 0, all finite");
-    if (P.reg != ROI_SIRT_NONNEG && P.reg != ROI_TV_CP && P.reg != ROI_FILTER_SIRT && P.reg != ROI_FILTER_TV)
-        return sfail(s, ROI_EINVAL, "submit: unknown regularizer");
+    if (P.reg < ROI_SIRT_NONNEG || P.reg > ROI_FILTER_ISTA) return sfail(s, ROI_EINVAL, "submit: unknown regularizer");
     if (P.inner_iters < 0 || P.inner_iters > 100000) return sfail(s, ROI_EINVAL, "submit: inner_iters out of range");
     if (P.iters < 0 || P.iters > 1000000) return sfail(s, ROI_EINVAL, "submit: iters out of range");
     if (!std::isfinite(P.lambda) || P.lambda < 0) return sfail(s, ROI_EINVAL, "submit: bad lambda");
@@ -660,7 +659,7 @@ roi_status roi_server_submit(roi_server_t s, int sino_id, const roi_region* regi
     roi_status rs = ensure_rings(s);
     if (rs != ROI_OK) return rs;
     const roi::SinoView& v = s->sinos[sino_id];
-    const bool filt = P.reg == ROI_FILTER_SIRT || P.reg == ROI_FILTER_TV;
+    const bool filt = P.reg >= ROI_FILTER_SIRT;
     if (filt && v.fcp_n < P.iters)
         return sfail(s, ROI_ESTATE, "submit: sinogram %d has filters for %d iterations, %d asked", sino_id, v.fcp_n,
                      P.iters);
@@ -672,7 +671,7 @@ roi_status roi_server_submit(roi_server_t s, int sino_id, const roi_region* regi
         delete r;
         return sfail(s, ROI_EINVAL, "submit: extended box misses the %d x %d grid", v.N, v.N);
     }
-    r->lay = state_layout(v.na, r->stride, r->box.w, r->box.h, roi::dt_size(v.dt), P.reg == ROI_FILTER_TV);
+    r->lay = state_layout(v.na, r->stride, r->box.w, r->box.h, roi::dt_size(v.dt), P.reg >= ROI_FILTER_TV);
     r->host_bytes = sizeof(float) * (size_t)r->box.w * r->box.h;
     if (round_up(r->lay.total) > s->darena.size || round_up(r->host_bytes) > s->harena.size) {
         const size_t need = r->lay.total;

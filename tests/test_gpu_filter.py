@@ -143,3 +143,15 @@ def test_fista_tv_batched_equals_served(prepared):
             assert c["status"] == R.ROI_OK
             got = s.take(c["id"], (c["box"][3], c["box"][2]))
             assert np.array_equal(got, outs[ids[c["id"]]].cpu().numpy())
+
+
+@pytest.mark.parametrize("region,lam", [((64.0, 64.0, 16.0, 8.0), 400.0), ((64.0, 60.0, 40.0, 20.0), 200.0),
+                                        ((3.0, 70.0, 9.0, 4.0), 400.0)])
+def test_haar_ista_matches_oracle(prepared, region, lam):
+    """Alg. method with the Haar-ISTA prior of Eq. sirtista (ROI_FILTER_ISTA)."""
+    rr, p, g, uo, n = prepared
+    iters = 20
+    out, _ = rr.solve_local(region, R.ROI_FILTER_ISTA, iters=iters, lam=lam)
+    x, box = oracle.filter_ista_solve(g, p.astype(np.float64), region, iters, lam, u=uo)
+    assert out.shape == x.shape
+    assert rel_l2(out.cpu().numpy(), x) <= SOLVE_TOL
