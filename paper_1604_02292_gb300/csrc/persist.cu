@@ -107,8 +107,9 @@ struct PhaseBConst {
 };
 
 // Grid barrier on a monotonic arrival counter: barrier number n (1, 2, ...) is passed
-// when the counter reaches n * expect.  Thread 0 of each block releases the block's
-// writes, adds one, and polls the counter with acquire loads; every 256 polls it checks
+// when the counter reaches n * expect.  Thread 0 of each block adds one with release
+// semantics (ordering the block's writes, gathered by the block barrier before it) and
+// polls the counter with acquire loads; every 256 polls it checks
 // the time limit and the error flag.  Returns 0 (in every thread of the block) when
 // this or another block gave up; the caller then returns.
 __device__ __forceinline__ int grid_sync(const PArgs& A, int* s_flag, unsigned& nbar) {
@@ -117,8 +118,7 @@ __device__ __forceinline__ int grid_sync(const PArgs& A, int* s_flag, unsigned& 
         int ok = 1;
         ++nbar;
         const unsigned target = nbar * A.expect;
-        __threadfence();
-        atomicAdd(A.bar, 1u);
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(A.bar) : "memory");
         unsigned long long t0 = 0;
         for (unsigned polls = 1;; ++polls) {
             unsigned v;
@@ -139,7 +139,6 @@ __device__ __forceinline__ int grid_sync(const PArgs& A, int* s_flag, unsigned& 
                 }
             }
         }
-        __threadfence();
         *s_flag = ok;
     }
     __syncthreads();
@@ -437,40 +436,56 @@ __global__ void __launch_bounds__(PT, 1) k_persist(PArgs A) {
 #pragma unroll
                 for (int p = 0; p < RUN; ++p) bpart[grp * BPIX + p * RUNS + run] = acc[p];
             }
+            // the 32 angle-group partials of each pixel: four quarters of 8 groups summed by
+            // all threads, then the quarters by one thread per pixel, which applies the update
+            const int slot = tid & (BPIX - 1), quarter = tid >> 8;
+            const int prun = slot % RUNS, pp = slot / RUNS;  // partial layout [group][p][run]
+            const int li = prun >> 1, lj = (prun & 1) * RUN + pp;
+            const int gi = tile_y0 + li, gj = tile_x0 + lj;
+            const bool upd = quarter == 0 && gi < ny && gj < nx;
+            const int o = gi * nx + gj;
+            float xo = 0.f, cw = 0.f, dv = 0.f;
+            if (upd) {  // operands of the update first, so their loads overlap the sums
+                if (A.mode == 0) {
+                    xo = __ldcg(xa + gi * A.lda + gj);
+                } else {
+                    xo = __ldcg(A.x + o);
+                    if (gj < nx - 1) dv += __ldcg(A.vx + o);
+                    if (gj > 0) dv -= __ldcg(A.vx + o - 1);
+                    if (gi < ny - 1) dv += __ldcg(A.vy + o);
+                    if (gi > 0) dv -= __ldcg(A.vy + o - nx);
+                }
+                cw = A.C ? __ldg(A.C + o) : A.step_scalar;
+            }
             __syncthreads();
-            if (tid < BPIX) {
-                const int li = tid / BT, lj = tid % BT;
-                const int gi = tile_y0 + li, gj = tile_x0 + lj;
-                if (gi < ny && gj < nx) {
-                    const int o = gi * nx + gj;
-                    // operands of the update first, so their loads overlap the partial sums
-                    float xo, cw, dv = 0.f;
-                    if (A.mode == 0) {
-                        xo = __ldcg(xa + gi * A.lda + gj);
-                    } else {
-                        xo = __ldcg(A.x + o);
-                        if (gj < nx - 1) dv += __ldcg(A.vx + o);
-                        if (gj > 0) dv -= __ldcg(A.vx + o - 1);
-                        if (gi < ny - 1) dv += __ldcg(A.vy + o);
-                        if (gi > 0) dv -= __ldcg(A.vy + o - nx);
-                    }
-                    cw = A.C ? __ldg(A.C + o) : A.step_scalar;
-                    const int slot = (lj % RUN) * RUNS + li * 2 + lj / RUN;  // [p][run] of this pixel
-                    float s = bpart[slot], c = 0.f;
-                    for (int g = 1; g < BGROUPS; ++g) neu_add(s, c, bpart[g * BPIX + slot]);
-                    const float acc = s + c;
-                    if (A.mode == 0) {
-                        float xn = fmaf(cw, acc, xo);
-                        if (A.nonneg) xn = fmaxf(xn, 0.f);
-                        xa[gi * A.lda + gj] = xn;
-                        xaT[gj * A.ldaT + gi] = xn;
-                    } else {
-                        const float xn = xo - cw * (acc - dv);
-                        A.x[o] = xn;
-                        const float xb = 2.f * xn - xo;
-                        xa[gi * A.lda + gj] = xb;
-                        xaT[gj * A.ldaT + gi] = xb;
-                    }
+            {
+                const float* src = bpart + (quarter * (BGROUPS / 4)) * BPIX + slot;
+                float s = src[0], c = 0.f;
+#pragma unroll
+                for (int g = 1; g < BGROUPS / 4; ++g) neu_add(s, c, src[g * BPIX]);
+                red_s[quarter * BPIX + slot] = s;
+                red_c[quarter * BPIX + slot] = c;
+            }
+            __syncthreads();
+            if (upd) {
+                float s = red_s[slot], c = red_c[slot];
+#pragma unroll
+                for (int q = 1; q < 4; ++q) {
+                    neu_add(s, c, red_s[q * BPIX + slot]);
+                    c += red_c[q * BPIX + slot];
+                }
+                const float acc = s + c;
+                if (A.mode == 0) {
+                    float xn = fmaf(cw, acc, xo);
+                    if (A.nonneg) xn = fmaxf(xn, 0.f);
+                    xa[gi * A.lda + gj] = xn;
+                    xaT[gj * A.ldaT + gi] = xn;
+                } else {
+                    const float xn = xo - cw * (acc - dv);
+                    A.x[o] = xn;
+                    const float xb = 2.f * xn - xo;
+                    xa[gi * A.lda + gj] = xb;
+                    xaT[gj * A.ldaT + gi] = xb;
                 }
             }
         }
