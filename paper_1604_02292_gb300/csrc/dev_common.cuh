@@ -67,6 +67,22 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
         : "memory");
 }
 
+// Plain arrival (completes the phase of a barrier initialised with count 1 when no copy
+// is due in it).
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Asynchronous 4-byte copy global -> shared (zero-filled when !valid, nothing read); the
+// issuing thread waits with cp_async_wait_all before it reads the word.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid = true) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_addr(dst)), "l"(src),
+                 "r"(valid ? 4 : 0)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
     unsigned ok;
     asm volatile(

@@ -49,6 +49,7 @@ constexpr int NWARP = PT / 32;
 constexpr int RAYS = 32;                 // rays per unit (one warp-wide ray group)
 constexpr int FSEG = 4;                  // segments per ray in phase A
 constexpr int CHUNK_UNITS = 16;          // phase A units whose partials are held at once
+constexpr int DG_WARPS = 8;              // warps that update the gradient dual while the others project
 constexpr int SEGA = 24;                 // samples per float-float anchor
 constexpr int MAXUNITS = 512;            // phase A units per block (checked by the host)
 constexpr int MAXPRE = 2;                // phase B tiles per block with precomputed constants
@@ -62,6 +63,9 @@ constexpr int BGROUPS = PT / RUNS;       // 32 angle groups
 // every staged index touched is in [1, 24] < BSB
 constexpr int BKOFF = 12;
 constexpr int BSB = 26;
+// operands fetched ahead of use: phase A [CHUNK_UNITS][u, p', weight][32]; phase B
+// [x, step, vx(o), vx(o-1), vy(o), vy(o-nx)][BPIX]
+constexpr int FIN = CHUNK_UNITS * 3 * 32 > 6 * BPIX ? CHUNK_UNITS * 3 * 32 : 6 * BPIX;
 
 struct PArgs {
     const AngleRec* rec;
@@ -214,19 +218,37 @@ __device__ __forceinline__ void tile_consts(const PArgs& A, int t, int tiles_x, 
     *wdp = r.width;
 }
 
+// Warp ul < nu starts asynchronous copies of the finishing operands of unit cu + ul (the
+// old dual for CP, the data p', the weight) into fin[ul]; the same thread waits for them
+// before the finish, and the copies overlap the projection.
+__device__ __forceinline__ void prefetch_finish(const PArgs& A, const int* units, int cu, int nu, int warp, int lane,
+                                                float* fin) {
+    if (warp >= nu) return;
+    const int unit = units[cu + warp];
+    const int a = unit / A.nchunk;
+    const int k = (unit - a * A.nchunk) * RAYS + lane;
+    if (k >= A.rec[a].width) return;
+    const size_t o = (size_t)a * A.stride + k;
+    float* f = fin + warp * 96 + lane;
+    if (A.mode == 1) cp_async4(f, A.u + o);
+    cp_async4(f + 32, A.pp + o);
+    if (A.R) cp_async4(f + 64, A.R + o);
+}
+
 __global__ void __launch_bounds__(PT, 1) k_persist(PArgs A) {
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
     float* img = smem;                              // phase A image
     float* red_s = smem + A.region_floats;          // [CHUNK_UNITS][FSEG][32] phase A partials
     float* red_c = red_s + CHUNK_UNITS * FSEG * 32;
-    PhaseBConst* pbc = reinterpret_cast<PhaseBConst*>(red_c + CHUNK_UNITS * FSEG * 32);  // [pre_tiles][na]
+    float* fin = red_c + CHUNK_UNITS * FSEG * 32;   // [FIN] operands fetched ahead of use
+    PhaseBConst* pbc = reinterpret_cast<PhaseBConst*>(fin + FIN);  // [pre_tiles][na]
     int* pkb = reinterpret_cast<int*>(pbc + A.pre_tiles * A.na);
     int* pwd = pkb + A.pre_tiles * A.na;
     __shared__ int s_flag;
-    __shared__ int s_nunits, s_row, s_next;
+    __shared__ int s_nunits, s_row, s_next, s_terr;
     __shared__ int s_units[MAXUNITS];               // this block's phase A units (angle * nchunk + chunk)
-    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ __align__(8) uint64_t s_mbar[FSEG];  // one per ray segment's rows
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int G = gridDim.x, b = blockIdx.x;
     const int nx = A.nx, ny = A.ny;
@@ -272,7 +294,9 @@ __global__ void __launch_bounds__(PT, 1) k_persist(PArgs A) {
             }
         s_nunits = nu;
         s_row = mine;
-        mbar_init(&s_mbar, 1);
+        s_next = 0;
+        s_terr = 0;
+        for (int q = 0; q < FSEG; ++q) mbar_init(&s_mbar[q], 1);
     }
     __syncthreads();
     const int nunits = s_nunits, my_row = s_row;
@@ -290,58 +314,74 @@ __global__ void __launch_bounds__(PT, 1) k_persist(PArgs A) {
 
     for (int it = 0; it < A.iters; ++it) {
         // ------------------------------------------------------------ phase A
+        const int M = my_row ? ny : nx, Mm = my_row ? nx : ny, ld = my_row ? A.lda : A.ldaT;
+        const int seg_len = ((M + FSEG - 1) / FSEG + SEGA - 1) / SEGA * SEGA;
         if (nunits > 0 && tid == 0) {
-            if (my_row)
-                bulk_load(img, A.xa_base, sizeof(float) * ny * A.lda, &s_mbar);
-            else
-                bulk_load(img, A.xaT_base, sizeof(float) * nx * A.ldaT, &s_mbar);
-        }
-        if (A.mode == 1) {  // gradient dual on this block's pixels (reads xbar^k), overlaps the copy
-            const float sv = A.sigma_v_dev ? __ldg(A.sigma_v_dev) : A.sigma_v;
-            for (int p = p0 + tid; p < p1; p += PT) {
-                const int i = p / nx, j = p - i * nx;
-                const float* xp = xa + i * A.lda + j;
-                const float x0 = __ldcg(xp);
-                const float gx = j < nx - 1 ? __ldcg(xp + 1) - x0 : 0.f;
-                const float gy = i < ny - 1 ? __ldcg(xp + A.lda) - x0 : 0.f;
-                const float ax = fmaf(sv, gx, __ldcg(A.vx + p));
-                const float ay = fmaf(sv, gy, __ldcg(A.vy + p));
-                const float m = sqrtf(ax * ax + ay * ay);
-                const float sc = m > A.lambda ? A.lambda / m : 1.f;
-                A.vx[p] = ax * sc;
-                A.vy[p] = ay * sc;
+            // one copy per ray segment (rows [q seg_len, (q + 1) seg_len) of the image), so
+            // warps start on the first segments while the rest is in flight
+            const float* src = my_row ? A.xa_base : A.xaT_base;
+            for (int q = 0; q < FSEG; ++q) {
+                const int r0 = min(q * seg_len, M), r1 = min(r0 + seg_len, M);
+                if (r1 > r0)
+                    bulk_load(img + (size_t)r0 * ld, src + (size_t)r0 * ld, sizeof(float) * (r1 - r0) * ld, &s_mbar[q]);
+                else
+                    mbar_arrive(&s_mbar[q]);
             }
         }
-        if (nunits > 0) {
-            if (!mbar_wait(&s_mbar, parity, A.wait_ns, A.err)) return;
-            parity ^= 1u;
+        if (nunits > 0) prefetch_finish(A, s_units, 0, min(CHUNK_UNITS, nunits), warp, lane, fin);
+        if (A.mode == 1) {
+            // gradient dual on this block's pixels (reads xbar^k) by the last DG_WARPS warps
+            // (all warps in a block without rays); they join the projection afterwards
+            const int dgw = nunits > 0 ? DG_WARPS : NWARP;
+            if (warp >= NWARP - dgw) {
+                const float sv = A.sigma_v_dev ? __ldg(A.sigma_v_dev) : A.sigma_v;
+                for (int p = p0 + tid - (NWARP - dgw) * 32; p < p1; p += dgw * 32) {
+                    const int i = p / nx, j = p - i * nx;
+                    const float* xp = xa + i * A.lda + j;
+                    const float x0 = __ldcg(xp);
+                    const float gx = j < nx - 1 ? __ldcg(xp + 1) - x0 : 0.f;
+                    const float gy = i < ny - 1 ? __ldcg(xp + A.lda) - x0 : 0.f;
+                    const float ax = fmaf(sv, gx, __ldcg(A.vx + p));
+                    const float ay = fmaf(sv, gy, __ldcg(A.vy + p));
+                    const float m = sqrtf(ax * ax + ay * ay);
+                    const float sc = m > A.lambda ? A.lambda / m : 1.f;
+                    A.vx[p] = ax * sc;
+                    A.vy[p] = ay * sc;
+                }
+            }
         }
         {
-            // Items (unit, segment) are taken dynamically by warps from a shared counter;
-            // each item's partial goes to its own slot, and the slots of a ray are added in
-            // segment order, so the result does not depend on which warp took what.
-            const int M = my_row ? ny : nx, Mm = my_row ? nx : ny, ld = my_row ? A.lda : A.ldaT;
-            const int seg_len = ((M + FSEG - 1) / FSEG + SEGA - 1) / SEGA * SEGA;
+            // Items (unit, segment), segment-major, are taken dynamically by warps from a
+            // shared counter; each item's partial goes to its own slot, and the slots of a
+            // ray are added in segment order, so the result does not depend on which warp
+            // took what.
+            unsigned ready = 0;  // segments whose rows this warp has seen arrive
             for (int cu = 0; cu < nunits; cu += CHUNK_UNITS) {
                 const int nu = min(CHUNK_UNITS, nunits - cu), nitems = nu * FSEG;
-                if (tid == 0) s_next = NWARP;
-                __syncthreads();
-                for (int item = warp; item < nitems;) {
-                    const int ul = item / FSEG, seg = item - ul * FSEG;
+                for (;;) {
+                    int item = 0;
+                    if (lane == 0) item = atomicAdd(&s_next, 1);
+                    item = __shfl_sync(0xffffffffu, item, 0);
+                    if (item >= nitems) break;
+                    const int seg = item / nu, ul = item - seg * nu;
+                    if (!((ready >> seg) & 1u)) {
+                        if (!mbar_wait(&s_mbar[seg], parity, A.wait_ns, A.err)) s_terr = 1;
+                        ready |= 1u << seg;
+                    }
                     const int unit = s_units[cu + ul];
                     const int a = unit / A.nchunk;
                     const int k = (unit - a * A.nchunk) * RAYS + lane;
                     const AngleRec& r = A.rec[a];
                     ff part = {0.f, 0.f};
                     if (k < r.width) part = ray_segment(r, k, seg, seg_len, M, Mm, img + kPad, ld);
-                    red_s[item * 32 + lane] = part.hi;
-                    red_c[item * 32 + lane] = part.lo;
-                    int nxt = 0;
-                    if (lane == 0) nxt = atomicAdd(&s_next, 1);
-                    item = __shfl_sync(0xffffffffu, nxt, 0);
+                    const int slot = (ul * FSEG + seg) * 32 + lane;
+                    red_s[slot] = part.hi;
+                    red_c[slot] = part.lo;
                 }
                 __syncthreads();
-                for (int ul = warp; ul < nu; ul += NWARP) {  // finish ray (unit cu + ul, lane)
+                if (tid == 0) s_next = 0;
+                if (warp < nu) {  // finish ray (unit cu + warp, lane)
+                    const int ul = warp;
                     const int unit = s_units[cu + ul];
                     const int a = unit / A.nchunk;
                     const int k = (unit - a * A.nchunk) * RAYS + lane;
@@ -355,19 +395,26 @@ __global__ void __launch_bounds__(PT, 1) k_persist(PArgs A) {
                         tot = ff_mul_f(r.inv_w, tot);
                         const float acc = tot.hi + tot.lo;
                         const size_t o = (size_t)a * A.stride + k;
+                        cp_async_wait_all();
+                        const float* f = fin + ul * 96 + lane;
                         if (A.mode == 0) {
-                            float res = __ldg(A.pp + o) - acc;
-                            if (A.R) res *= __ldg(A.R + o);
+                            float res = f[32] - acc;
+                            if (A.R) res *= f[64];
                             A.u[o] = res;
                         } else {
-                            const float sig = A.R ? __ldg(A.R + o) : A.sig_scalar;
-                            A.u[o] = (__ldcg(A.u + o) + sig * (acc - __ldg(A.pp + o))) / (1.f + 0.5f * sig);
+                            const float sig = A.R ? f[64] : A.sig_scalar;
+                            A.u[o] = (f[0] + sig * (acc - f[32])) / (1.f + 0.5f * sig);
                         }
                     }
                 }
                 __syncthreads();
+                if (cu + CHUNK_UNITS < nunits)
+                    prefetch_finish(A, s_units, cu + CHUNK_UNITS, min(CHUNK_UNITS, nunits - cu - CHUNK_UNITS), warp,
+                                    lane, fin);
             }
+            if (nunits > 0) parity ^= 1u;
         }
+        if (s_terr) return;  // a copy timed out (flag set); read after a block barrier
         if (!grid_sync(A, &s_flag, nbar)) return;
 
         // ------------------------------------------------------------ phase B
@@ -377,6 +424,25 @@ __global__ void __launch_bounds__(PT, 1) k_persist(PArgs A) {
             const int* tkb = kb;
             const int* twd = wdt;
             __syncthreads();
+            if (tid < BPIX) {
+                // operands of this pixel's update, copied while the window is gathered (the
+                // thread that updates pixel `tid` below is the one that waits for them)
+                const int prun = tid % RUNS, pp = tid / RUNS;  // partial layout [group][p][run]
+                const int gi = tile_y0 + (prun >> 1), gj = tile_x0 + (prun & 1) * RUN + pp;
+                if (gi < ny && gj < nx) {
+                    const int o = gi * nx + gj;
+                    if (A.mode == 0) {
+                        cp_async4(fin + tid, xa + gi * A.lda + gj);
+                    } else {
+                        cp_async4(fin + tid, A.x + o);
+                        cp_async4(fin + 2 * BPIX + tid, A.vx + o, gj < nx - 1);
+                        cp_async4(fin + 3 * BPIX + tid, A.vx + o - (gj > 0), gj > 0);
+                        cp_async4(fin + 4 * BPIX + tid, A.vy + o, gi < ny - 1);
+                        cp_async4(fin + 5 * BPIX + tid, A.vy + o - (gi > 0 ? nx : 0), gi > 0);
+                    }
+                    if (A.C) cp_async4(fin + BPIX + tid, A.C + o);
+                }
+            }
             if (pre) {
                 tbc = pbc + (t - t0) * A.na;
                 tkb = pkb + (t - t0) * A.na;
@@ -444,19 +510,6 @@ __global__ void __launch_bounds__(PT, 1) k_persist(PArgs A) {
             const int gi = tile_y0 + li, gj = tile_x0 + lj;
             const bool upd = quarter == 0 && gi < ny && gj < nx;
             const int o = gi * nx + gj;
-            float xo = 0.f, cw = 0.f, dv = 0.f;
-            if (upd) {  // operands of the update first, so their loads overlap the sums
-                if (A.mode == 0) {
-                    xo = __ldcg(xa + gi * A.lda + gj);
-                } else {
-                    xo = __ldcg(A.x + o);
-                    if (gj < nx - 1) dv += __ldcg(A.vx + o);
-                    if (gj > 0) dv -= __ldcg(A.vx + o - 1);
-                    if (gi < ny - 1) dv += __ldcg(A.vy + o);
-                    if (gi > 0) dv -= __ldcg(A.vy + o - nx);
-                }
-                cw = A.C ? __ldg(A.C + o) : A.step_scalar;
-            }
             __syncthreads();
             {
                 const float* src = bpart + (quarter * (BGROUPS / 4)) * BPIX + slot;
@@ -475,12 +528,18 @@ __global__ void __launch_bounds__(PT, 1) k_persist(PArgs A) {
                     c += red_c[q * BPIX + slot];
                 }
                 const float acc = s + c;
+                cp_async_wait_all();
+                const float xo = fin[slot];
+                const float cw = A.C ? fin[BPIX + slot] : A.step_scalar;
                 if (A.mode == 0) {
                     float xn = fmaf(cw, acc, xo);
                     if (A.nonneg) xn = fmaxf(xn, 0.f);
                     xa[gi * A.lda + gj] = xn;
                     xaT[gj * A.ldaT + gi] = xn;
                 } else {
+                    // div v with the terms outside the box zero (copies zero-filled)
+                    const float dv = fin[2 * BPIX + slot] - fin[3 * BPIX + slot] + fin[4 * BPIX + slot] -
+                                     fin[5 * BPIX + slot];
                     const float xn = xo - cw * (acc - dv);
                     A.x[o] = xn;
                     const float xb = 2.f * xn - xo;
@@ -514,7 +573,7 @@ static int pre_tiles(int nx, int ny, int blocks) {
 
 size_t persist_smem_bytes(int na, int nx, int ny, int blocks) {
     const size_t pre = (size_t)pre_tiles(nx, ny, blocks) * na * (sizeof(PhaseBConst) + 2 * sizeof(int));
-    return sizeof(float) * (region_floats(na, nx, ny) + 2 * CHUNK_UNITS * FSEG * 32) + pre;
+    return sizeof(float) * (region_floats(na, nx, ny) + 2 * CHUNK_UNITS * FSEG * 32 + FIN) + pre;
 }
 
 // Phase A units per block: each branch group gets at least one block per
