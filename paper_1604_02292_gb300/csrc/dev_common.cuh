@@ -55,9 +55,9 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// One thread: arm the barrier for `bytes` and start the bulk copy global -> shared.
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-    asm volatile("fence.proxy.async;" ::: "memory");
+// One thread: arm the barrier for `bytes` and start the bulk copy global -> shared; the
+// caller has ordered earlier generic writes of the destination (fence.proxy.async).
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
     asm volatile(
@@ -65,6 +65,12 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
             smem_addr(dst)),
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
+}
+
+// One thread: fence, arm the barrier for `bytes` and start the bulk copy global -> shared.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile("fence.proxy.async;" ::: "memory");
+    bulk_copy(dst, src, bytes, bar);
 }
 
 // Plain arrival (completes the phase of a barrier initialised with count 1 when no copy

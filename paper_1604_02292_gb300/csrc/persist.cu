@@ -113,8 +113,8 @@ struct PhaseBConst {
 // Grid barrier on a monotonic arrival counter: barrier number n (1, 2, ...) is passed
 // when the counter reaches n * expect.  Thread 0 of each block adds one with release
 // semantics (ordering the block's writes, gathered by the block barrier before it) and
-// polls the counter with acquire loads; every 256 polls it checks
-// the time limit and the error flag.  Returns 0 (in every thread of the block) when
+// polls the counter with acquire loads; every 256 polls it checks the time limit and the
+// error flag.  Returns 0 (in every thread of the block) when
 // this or another block gave up; the caller then returns.
 __device__ __forceinline__ int grid_sync(const PArgs& A, int* s_flag, unsigned& nbar) {
     __syncthreads();
@@ -177,18 +177,33 @@ __device__ __forceinline__ ff ray_segment(const AngleRec& r, int k, int seg, int
         int j0;
         int q = split_fixed22(ff_add(Ak, ff_mul_f((float)m0 - halfM, r.slope)), j0);  // sample m0
         const int mend = min(m0 + SEGA, mhi);
-        // sum of v0 + f (v1 - v0) with f = mf 2^-22: the two parts are summed separately
-        float s0 = 0.f, s1 = 0.f;
+        // sum of v0 + f (v1 - v0) with f = mf 2^-22: the two parts are summed separately,
+        // two samples per packed (f32x2) operation (even and odd samples in the two lanes
+        // of the pair, added at the end)
+        float2 S0 = make_float2(0.f, 0.f), S1 = make_float2(0.f, 0.f);
+        const float2 m1 = make_float2(-1.f, -1.f), e23 = make_float2(-8388608.0f, -8388608.0f);
         const float* rp = img + m0 * ld + j0;
-#pragma unroll 4
-        for (int m = m0; m < mend; ++m, rp += ld, q += step) {
+        int m = m0;
+#pragma unroll 2
+        for (; m + 1 < mend; m += 2, rp += 2 * ld, q += 2 * step) {
+            const int q1 = q + step;
+            const int ja = q >> 22, jb = q1 >> 22;
+            const float2 bits = make_float2(__uint_as_float(0x4B000000u | ((unsigned)q & 0x3FFFFFu)),
+                                            __uint_as_float(0x4B000000u | ((unsigned)q1 & 0x3FFFFFu)));
+            const float2 mf = __fadd2_rn(bits, e23);
+            const float2 v0 = make_float2(rp[ja], rp[ld + jb]);
+            const float2 v1 = make_float2(rp[ja + 1], rp[ld + jb + 1]);
+            S0 = __fadd2_rn(S0, v0);
+            S1 = __ffma2_rn(mf, __ffma2_rn(v0, m1, v1), S1);  // v1 - v0 exactly as a subtraction
+        }
+        if (m < mend) {
             const int j = q >> 22;
             const float mf = frac_int<22>(q);
             const float v0 = rp[j], v1 = rp[j + 1];
-            s0 += v0;
-            s1 = fmaf(mf, v1 - v0, s1);
+            S0.x += v0;
+            S1.x = fmaf(mf, v1 - v0, S1.x);
         }
-        neu_add(sum, cmp, fmaf(s1, 2.384185791015625e-07f, s0));  // s0 + s1 2^-22
+        neu_add(sum, cmp, fmaf(S1.x + S1.y, 2.384185791015625e-07f, S0.x + S0.y));  // s0 + s1 2^-22
     }
     return two_sum(sum, cmp);
 }
@@ -219,15 +234,16 @@ __device__ __forceinline__ void tile_consts(const PArgs& A, int t, int tiles_x, 
 }
 
 // Warp ul < nu starts asynchronous copies of the finishing operands of unit cu + ul (the
-// old dual for CP, the data p', the weight) into fin[ul]; the same thread waits for them
-// before the finish, and the copies overlap the projection.
+// old dual for CP, the data p', the weight) into fin[ul] (whole window rows, in bounds of
+// the [na][stride] arrays); the same thread waits for them before the finish, and the
+// copies overlap the projection.
 __device__ __forceinline__ void prefetch_finish(const PArgs& A, const int* units, int cu, int nu, int warp, int lane,
                                                 float* fin) {
     if (warp >= nu) return;
     const int unit = units[cu + warp];
     const int a = unit / A.nchunk;
     const int k = (unit - a * A.nchunk) * RAYS + lane;
-    if (k >= A.rec[a].width) return;
+    if (k >= A.stride) return;
     const size_t o = (size_t)a * A.stride + k;
     float* f = fin + warp * 96 + lane;
     if (A.mode == 1) cp_async4(f, A.u + o);
@@ -316,14 +332,16 @@ __global__ void __launch_bounds__(PT, 1) k_persist(PArgs A) {
         // ------------------------------------------------------------ phase A
         const int M = my_row ? ny : nx, Mm = my_row ? nx : ny, ld = my_row ? A.lda : A.ldaT;
         const int seg_len = ((M + FSEG - 1) / FSEG + SEGA - 1) / SEGA * SEGA;
-        if (nunits > 0 && tid == 0) {
+        if (nunits > 0 && tid == PT - 32) {
             // one copy per ray segment (rows [q seg_len, (q + 1) seg_len) of the image), so
-            // warps start on the first segments while the rest is in flight
+            // warps start on the first segments while the rest is in flight; issued by the
+            // last warp, which projects last (it first updates the gradient dual for CP)
             const float* src = my_row ? A.xa_base : A.xaT_base;
+            asm volatile("fence.proxy.async;" ::: "memory");
             for (int q = 0; q < FSEG; ++q) {
                 const int r0 = min(q * seg_len, M), r1 = min(r0 + seg_len, M);
                 if (r1 > r0)
-                    bulk_load(img + (size_t)r0 * ld, src + (size_t)r0 * ld, sizeof(float) * (r1 - r0) * ld, &s_mbar[q]);
+                    bulk_copy(img + (size_t)r0 * ld, src + (size_t)r0 * ld, sizeof(float) * (r1 - r0) * ld, &s_mbar[q]);
                 else
                     mbar_arrive(&s_mbar[q]);
             }
@@ -382,6 +400,7 @@ __global__ void __launch_bounds__(PT, 1) k_persist(PArgs A) {
                 if (tid == 0) s_next = 0;
                 if (warp < nu) {  // finish ray (unit cu + warp, lane)
                     const int ul = warp;
+                    cp_async_wait_all();
                     const int unit = s_units[cu + ul];
                     const int a = unit / A.nchunk;
                     const int k = (unit - a * A.nchunk) * RAYS + lane;
@@ -395,7 +414,6 @@ __global__ void __launch_bounds__(PT, 1) k_persist(PArgs A) {
                         tot = ff_mul_f(r.inv_w, tot);
                         const float acc = tot.hi + tot.lo;
                         const size_t o = (size_t)a * A.stride + k;
-                        cp_async_wait_all();
                         const float* f = fin + ul * 96 + lane;
                         if (A.mode == 0) {
                             float res = f[32] - acc;
@@ -425,8 +443,9 @@ __global__ void __launch_bounds__(PT, 1) k_persist(PArgs A) {
             const int* twd = wdt;
             __syncthreads();
             if (tid < BPIX) {
-                // operands of this pixel's update, copied while the window is gathered (the
-                // thread that updates pixel `tid` below is the one that waits for them)
+                // operands of this pixel's update (x, step, the four v terms of div v, zero
+                // outside the box), copied while the window is gathered (the thread that
+                // updates pixel `tid` below is the one that waits for them)
                 const int prun = tid % RUNS, pp = tid / RUNS;  // partial layout [group][p][run]
                 const int gi = tile_y0 + (prun >> 1), gj = tile_x0 + (prun & 1) * RUN + pp;
                 if (gi < ny && gj < nx) {
@@ -478,29 +497,43 @@ __global__ void __launch_bounds__(PT, 1) k_persist(PArgs A) {
                     }
                     __syncwarp();
                 }
-                float acc[RUN];
+                // two pixels of the run per packed (f32x2) operation: the same fused
+                // multiply-adds as one pixel at a time, half the instructions
+                float2 acc[RUN / 2];
 #pragma unroll
-                for (int p = 0; p < RUN; ++p) acc[p] = 0.f;
+                for (int p = 0; p < RUN / 2; ++p) acc[p] = make_float2(0.f, 0.f);
                 for (int a = a_lo; a < a_hi; ++a) {
                     const PhaseBConst q = tbc[a];
                     // weights (1 - d/w)/w of the two bins at distances f and 1 - f, f = mf 2^-23
                     const float iw = q.iw, iw2 = iw * iw, iwm = iw - iw2;
                     const float iw2s = iw2 * 1.1920928955078125e-07f;
+                    const float2 niw2s2 = make_float2(-iw2s, -iw2s), iw2s2 = make_float2(iw2s, iw2s);
+                    const float2 iw_2 = make_float2(iw, iw), iwm2 = make_float2(iwm, iwm);
                     int K = q.base + lj0 * q.c - li * q.s;
                     const float* srow = stage + a * BSB;
 #pragma unroll
-                    for (int p = 0; p < RUN; ++p) {
-                        const int kl = K >> 23;
-                        const float mf = frac_int<23>(K);
-                        const float w0 = fmaxf(0.f, fmaf(-mf, iw2s, iw));
-                        const float w1 = fmaxf(0.f, fmaf(mf, iw2s, iwm));
-                        acc[p] = fmaf(w0, srow[kl], fmaf(w1, srow[kl + 1], acc[p]));
-                        K += q.c;
+                    for (int p = 0; p < RUN / 2; ++p) {
+                        const int K1 = K + q.c;
+                        const int kl0 = K >> 23, kl1 = K1 >> 23;
+                        const float2 bits = make_float2(__uint_as_float(0x4B000000u | ((unsigned)K & 0x7FFFFFu)),
+                                                        __uint_as_float(0x4B000000u | ((unsigned)K1 & 0x7FFFFFu)));
+                        const float2 mf = __fadd2_rn(bits, make_float2(-8388608.0f, -8388608.0f));
+                        const float2 w0r = __ffma2_rn(mf, niw2s2, iw_2);
+                        const float2 w1r = __ffma2_rn(mf, iw2s2, iwm2);
+                        const float2 w0 = make_float2(fmaxf(0.f, w0r.x), fmaxf(0.f, w0r.y));
+                        const float2 w1 = make_float2(fmaxf(0.f, w1r.x), fmaxf(0.f, w1r.y));
+                        const float2 s0 = make_float2(srow[kl0], srow[kl1]);
+                        const float2 s1 = make_float2(srow[kl0 + 1], srow[kl1 + 1]);
+                        acc[p] = __ffma2_rn(w0, s0, __ffma2_rn(w1, s1, acc[p]));
+                        K = K1 + q.c;
                     }
                 }
                 // partials as [group][p][run]: consecutive lanes store consecutive words
 #pragma unroll
-                for (int p = 0; p < RUN; ++p) bpart[grp * BPIX + p * RUNS + run] = acc[p];
+                for (int p = 0; p < RUN / 2; ++p) {
+                    bpart[grp * BPIX + (2 * p) * RUNS + run] = acc[p].x;
+                    bpart[grp * BPIX + (2 * p + 1) * RUNS + run] = acc[p].y;
+                }
             }
             // the 32 angle-group partials of each pixel: four quarters of 8 groups summed by
             // all threads, then the quarters by one thread per pixel, which applies the update
