@@ -137,6 +137,14 @@ __device__ __forceinline__ int split_fixed22(ff v, int& j0) {
 // The F <= 23 fraction bits of a Q.F number as an integer-valued float in [0, 2^F):
 // OR-ing them into the mantissa of 2^23 and subtracting 2^23 is exact (one logic op and
 // one add, no conversion instruction).
+// a * b + c, rounded once and clamped to [0, 1] (the clamp is a modifier of the FMA, so a
+// hat weight max(0, 1 - |d|/w) costs one FMA-pipe instruction and no min/max).
+__device__ __forceinline__ float fma_sat(float a, float b, float c) {
+    float r;
+    asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 template <int F>
 __device__ __forceinline__ float frac_int(int q) {
     return __uint_as_float(0x4B000000u | ((unsigned)q & ((1u << F) - 1u))) - 8388608.0f;

@@ -480,20 +480,24 @@ __global__ void __launch_bounds__(PT, 1) k_persist(PArgs A) {
                 {
                     const int e_lo = a_lo * BSB, e_hi = a_hi * BSB;
                     constexpr int BATCH = 8;
+                    // bins are staged times 1/w of their angle (the hat weights below are then
+                    // max(0, 1 - d/w), one saturating FMA each)
                     for (int e0 = e_lo + lane; e0 < e_hi; e0 += 32 * BATCH) {
-                        float v[BATCH];
+                        float v[BATCH], iw[BATCH];
 #pragma unroll
                         for (int q = 0; q < BATCH; ++q) {
                             const int e = e0 + q * 32;
                             v[q] = 0.f;
+                            iw[q] = 0.f;
                             if (e < e_hi) {
                                 const int a = e / BSB, kk = tkb[a] + (e - a * BSB);
+                                iw[q] = tbc[a].iw;
                                 if (kk >= 0 && kk < twd[a]) v[q] = __ldcg(A.u + (size_t)a * A.stride + kk);
                             }
                         }
 #pragma unroll
                         for (int q = 0; q < BATCH; ++q)
-                            if (e0 + q * 32 < e_hi) stage[e0 + q * 32] = v[q];
+                            if (e0 + q * 32 < e_hi) stage[e0 + q * 32] = v[q] * iw[q];
                     }
                     __syncwarp();
                 }
@@ -504,11 +508,9 @@ __global__ void __launch_bounds__(PT, 1) k_persist(PArgs A) {
                 for (int p = 0; p < RUN / 2; ++p) acc[p] = make_float2(0.f, 0.f);
                 for (int a = a_lo; a < a_hi; ++a) {
                     const PhaseBConst q = tbc[a];
-                    // weights (1 - d/w)/w of the two bins at distances f and 1 - f, f = mf 2^-23
-                    const float iw = q.iw, iw2 = iw * iw, iwm = iw - iw2;
-                    const float iw2s = iw2 * 1.1920928955078125e-07f;
-                    const float2 niw2s2 = make_float2(-iw2s, -iw2s), iw2s2 = make_float2(iw2s, iw2s);
-                    const float2 iw_2 = make_float2(iw, iw), iwm2 = make_float2(iwm, iwm);
+                    // weights max(0, 1 - d/w) of the two bins at distances f and 1 - f,
+                    // f = mf 2^-23 (the staged bins carry the 1/w)
+                    const float iws = q.iw * 1.1920928955078125e-07f, niws = -iws, omiw = 1.f - q.iw;
                     int K = q.base + lj0 * q.c - li * q.s;
                     const float* srow = stage + a * BSB;
 #pragma unroll
@@ -518,10 +520,8 @@ __global__ void __launch_bounds__(PT, 1) k_persist(PArgs A) {
                         const float2 bits = make_float2(__uint_as_float(0x4B000000u | ((unsigned)K & 0x7FFFFFu)),
                                                         __uint_as_float(0x4B000000u | ((unsigned)K1 & 0x7FFFFFu)));
                         const float2 mf = __fadd2_rn(bits, make_float2(-8388608.0f, -8388608.0f));
-                        const float2 w0r = __ffma2_rn(mf, niw2s2, iw_2);
-                        const float2 w1r = __ffma2_rn(mf, iw2s2, iwm2);
-                        const float2 w0 = make_float2(fmaxf(0.f, w0r.x), fmaxf(0.f, w0r.y));
-                        const float2 w1 = make_float2(fmaxf(0.f, w1r.x), fmaxf(0.f, w1r.y));
+                        const float2 w0 = make_float2(fma_sat(mf.x, niws, 1.f), fma_sat(mf.y, niws, 1.f));
+                        const float2 w1 = make_float2(fma_sat(mf.x, iws, omiw), fma_sat(mf.y, iws, omiw));
                         const float2 s0 = make_float2(srow[kl0], srow[kl1]);
                         const float2 s1 = make_float2(srow[kl0 + 1], srow[kl1 + 1]);
                         acc[p] = __ffma2_rn(w0, s0, __ffma2_rn(w1, s1, acc[p]));

@@ -279,15 +279,17 @@ __device__ __forceinline__ void phase_b(const Ctx& C, const Team& T, int pass, i
                     else
                         v = C.b.u[(size_t)(a0 + al) * R.stride + kk];
                 }
-                st[e] = v;
+                st[e] = v * ciw[al];  // staged times 1/w: the hat weights below are max(0, 1 - d/w)
             }
             __syncwarp();
             float acc[RUNB];
 #pragma unroll
             for (int p = 0; p < RUNB; ++p) acc[p] = 0.f;
             for (int al = 0; al < nch; ++al) {
-                const float iw = ciw[al], iw2 = iw * iw, iwm = iw - iw2;
-                const float iw2s = iw2 * 1.1920928955078125e-07f;
+                // weights max(0, 1 - d/w) of the two bins at distances f and 1 - f, f = mf 2^-23,
+                // one saturating FMA each
+                const float iw = ciw[al];
+                const float iws = iw * 1.1920928955078125e-07f, niws = -iws, omiw = 1.f - iw;
                 const int c = cc[al];
                 int K = cb[al] + lj0 * c - li * cs[al];
                 const float* srow = st + al * SBB;
@@ -295,8 +297,8 @@ __device__ __forceinline__ void phase_b(const Ctx& C, const Team& T, int pass, i
                 for (int p = 0; p < RUNB; ++p) {
                     const int kl = K >> 23;
                     const float mf = frac_int<23>(K);
-                    const float w0 = fmaxf(0.f, fmaf(-mf, iw2s, iw));
-                    const float w1 = fmaxf(0.f, fmaf(mf, iw2s, iwm));
+                    const float w0 = fma_sat(mf, niws, 1.f);
+                    const float w1 = fma_sat(mf, iws, omiw);
                     acc[p] = fmaf(w0, srow[kl], fmaf(w1, srow[kl + 1], acc[p]));
                     K += c;
                 }
