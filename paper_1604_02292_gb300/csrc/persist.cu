@@ -52,6 +52,8 @@ constexpr int CHUNK_UNITS = 16;          // phase A units whose partials are hel
 constexpr int DG_WARPS = 8;              // warps that update the gradient dual while the others project
 constexpr int SEGA = 24;                 // samples per float-float anchor
 constexpr int MAXUNITS = 512;            // phase A units per block (checked by the host)
+constexpr int NBUCKET = 512;             // cost classes of the phase A balancing sort
+constexpr int ITEM_COST = 16;            // fixed cost of one (unit, segment) item, in samples
 constexpr int MAXPRE = 2;                // phase B tiles per block with precomputed constants
 constexpr int BT = 16;                   // phase B tile side
 constexpr int BPIX = BT * BT;
@@ -154,12 +156,13 @@ __device__ __forceinline__ int grid_sync(const PArgs& A, int* s_flag, unsigned& 
 // coordinate q lies in [-1.5, Mm + 0.5] are visited (range in float, error ~1e-4 <<
 // 0.5), so the taps stay in [-2, Mm + 1], inside the padded row; samples outside the
 // range have both taps outside [0, Mm) and contribute 0.
-__device__ __forceinline__ ff ray_segment(const AngleRec& r, int k, int seg, int seg_len, int M, int Mm,
-                                          const float* img, int ld) {
-    float sum = 0.f, cmp = 0.f;
+// Samples [mlo, mhi) of ray k whose minor coordinate lies in [-1.5, Mm + 0.5] (the others
+// contribute 0); returns the ray's coordinate A_k at the major-axis centre.
+__device__ __forceinline__ ff ray_range(const AngleRec& r, int k, int M, int Mm, int& mlo, int& mhi) {
     const float halfM = 0.5f * (float)(M - 1);
     const ff Ak = ff_add(r.A0, ff_mul_f((float)k, r.a_scale));
-    int mlo = 0, mhi = M;
+    mlo = 0;
+    mhi = M;
     if (!r.flat) {
         const float ma = (-1.5f - Ak.hi) * r.inv_slope + halfM;
         const float mb = ((float)Mm + 0.5f - Ak.hi) * r.inv_slope + halfM;
@@ -169,6 +172,15 @@ __device__ __forceinline__ ff ray_segment(const AngleRec& r, int k, int seg, int
     } else if (!(Ak.hi >= -1.5f && Ak.hi <= (float)Mm + 0.5f)) {
         mhi = 0;
     }
+    return Ak;
+}
+
+__device__ __forceinline__ ff ray_segment(const AngleRec& r, int k, int seg, int seg_len, int M, int Mm,
+                                          const float* img, int ld) {
+    float sum = 0.f, cmp = 0.f;
+    const float halfM = 0.5f * (float)(M - 1);
+    int mlo, mhi;
+    const ff Ak = ray_range(r, k, M, Mm, mlo, mhi);
     const int s0 = seg * seg_len;
     mlo = max(mlo, s0);
     mhi = min(mhi, min(s0 + seg_len, M));
@@ -262,7 +274,7 @@ __global__ void __launch_bounds__(PT, 1) k_persist(PArgs A) {
     int* pkb = reinterpret_cast<int*>(pbc + A.pre_tiles * A.na);
     int* pwd = pkb + A.pre_tiles * A.na;
     __shared__ int s_flag;
-    __shared__ int s_nunits, s_row, s_next, s_terr;
+    __shared__ int s_nunits, s_row, s_gsize, s_next, s_terr;
     __shared__ int s_units[MAXUNITS];               // this block's phase A units (angle * nchunk + chunk)
     __shared__ __align__(8) uint64_t s_mbar[FSEG];  // one per ray segment's rows
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -282,9 +294,11 @@ __global__ void __launch_bounds__(PT, 1) k_persist(PArgs A) {
     float* bpart = reinterpret_cast<float*>(wdt + A.na);
 
     // prologue 1: phase A work.  The blocks are split between the two branches in
-    // proportion to their units; within a branch, units are dealt round-robin, so each
-    // block stages one orientation and gets a mix of ray lengths.
-    int* rank_angle = reinterpret_cast<int*>(smem);  // scratch in the (not yet used) region
+    // proportion to their units, so each block stages one orientation.  Within a branch the
+    // units are sorted by their cost (samples of the longest ray in each segment plus a fixed
+    // cost per item) and dealt in snake order (0 .. g-1, g-1 .. 0, ...), which balances the
+    // blocks to within a fraction of a unit; every block computes the same deal.
+    int* rank_angle = reinterpret_cast<int*>(smem);  // scratch in the (not yet used) region: [na]
     if (tid == 0) {
         int nrow = 0, ncol = 0;
         for (int a = 0; a < A.na; ++a) (A.rec[a].row ? nrow : ncol)++;
@@ -295,26 +309,85 @@ __global__ void __launch_bounds__(PT, 1) k_persist(PArgs A) {
         if (uc == 0) gr = G;
         if (ur == 0) gr = 0;
         const int mine = b < gr;  // 1: this block takes row-branch units
-        const int gsize = mine ? gr : G - gr, bi = mine ? b : b - gr;
         int nb = 0;
         for (int a = 0; a < A.na; ++a)
             if (A.rec[a].row == mine) rank_angle[nb++] = a;
-        int nu = 0;
-        if (gsize > 0)
-            for (long j = bi; j < (long)nb * A.nchunk; j += gsize) {
-                if (nu == MAXUNITS) {  // the host sizes MAXUNITS; never silently drop work
-                    atomicExch(A.err, 1);
-                    break;
-                }
-                s_units[nu++] = rank_angle[j / A.nchunk] * A.nchunk + (int)(j % A.nchunk);
-            }
-        s_nunits = nu;
+        s_nunits = nb;  // angles of the branch, for now
         s_row = mine;
+        s_gsize = mine ? gr : G - gr;
         s_next = 0;
         s_terr = 0;
         for (int q = 0; q < FSEG; ++q) mbar_init(&s_mbar[q], 1);
     }
     __syncthreads();
+    {
+        const int mine = s_row, gsize = s_gsize, bi = mine ? b : b - (G - gsize);
+        const int U = s_nunits * A.nchunk;  // units of the branch
+        int* ucost = rank_angle + A.na;      // [U]
+        int* uorder = ucost + U;             // [U]
+        int* ubucket = uorder + U;           // [NBUCKET]
+        const int M = mine ? ny : nx, Mm = mine ? nx : ny;
+        const int seg_len = ((M + FSEG - 1) / FSEG + SEGA - 1) / SEGA * SEGA;
+        for (int j = warp; j < U; j += NWARP) {  // cost of unit j: one warp, a lane per ray
+            const int a = rank_angle[j / A.nchunk];
+            const int k = (j % A.nchunk) * RAYS + lane;
+            const AngleRec& r = A.rec[a];
+            int mlo = 0, mhi = 0;
+            if (k < r.width) ray_range(r, k, M, Mm, mlo, mhi);
+            int cost = 0;
+            for (int sg = 0; sg < FSEG; ++sg) {
+                const int s0 = sg * seg_len;
+                const int cnt = max(0, min(mhi, min(s0 + seg_len, M)) - max(mlo, s0));
+                cost += (int)__reduce_max_sync(0xffffffffu, (unsigned)cnt) + ITEM_COST;
+            }
+            if (lane == 0) ucost[j] = min(cost, NBUCKET - 1);
+        }
+        for (int i = tid; i < NBUCKET; i += PT) ubucket[i] = 0;
+        __syncthreads();
+        if (warp == 0) {  // stable counting sort by decreasing cost
+            for (int j = lane; j < U; j += 32) atomicAdd(&ubucket[ucost[j]], 1);
+            __syncwarp();
+            if (lane == 0) {
+                int run = 0;
+                for (int c = NBUCKET - 1; c >= 0; --c) {
+                    const int h = ubucket[c];
+                    ubucket[c] = run;
+                    run += h;
+                }
+            }
+            __syncwarp();
+            for (int j0 = 0; j0 < U; j0 += 32) {  // 32 units at a time, in unit order
+                const int j = j0 + lane;
+                const int c = j < U ? ucost[j] : -1 - lane;  // distinct keys for idle lanes
+                const unsigned peers = __match_any_sync(0xffffffffu, c);
+                const int rank = __popc(peers & ((1u << lane) - 1u));
+                const int base = j < U ? ubucket[c] : 0;
+                if (j < U) uorder[base + rank] = j;
+                __syncwarp();
+                if (j < U && rank == __popc(peers) - 1) ubucket[c] = base + rank + 1;
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {  // this block's units: sorted positions bi and 2 g - 1 - bi of every 2 g
+            int nu = 0;
+            for (int r0 = 0; r0 < U; r0 += 2 * gsize) {
+                const int rs[2] = {r0 + bi, r0 + 2 * gsize - 1 - bi};
+                for (int h = 0; h < 2; ++h) {
+                    const int r = rs[h];
+                    if (r >= U) continue;
+                    if (nu == MAXUNITS) {  // the host sizes MAXUNITS; never silently drop work
+                        atomicExch(A.err, 1);
+                        break;
+                    }
+                    const int j = uorder[r];
+                    s_units[nu++] = rank_angle[j / A.nchunk] * A.nchunk + j % A.nchunk;
+                }
+            }
+            s_nunits = nu;
+        }
+        __syncthreads();
+    }
     const int nunits = s_nunits, my_row = s_row;
     // prologue 2: phase B constants of this block's tiles (they do not change)
     const bool pre = A.pre_tiles > 0 && (t1 - t0) <= A.pre_tiles;
@@ -611,13 +684,15 @@ size_t persist_smem_bytes(int na, int nx, int ny, int blocks) {
 
 // Phase A units per block: each branch group gets at least one block per
 // units / (total units / blocks), rounded; bound it generously.
-static bool units_fit(int na, int stride, int blocks) {
+static bool units_fit(int na, int stride, int blocks, int nx, int ny) {
     const long units = (long)na * ((stride + RAYS - 1) / RAYS);
-    return (units + blocks - 1) / blocks * 2 + 2 <= MAXUNITS;
+    // the balancing sort's scratch (angle list, costs, order, buckets) lives in the region
+    const bool scratch = na + 2 * units + NBUCKET <= (long)region_floats(na, nx, ny);
+    return scratch && (units + blocks - 1) / blocks * 2 + 2 <= MAXUNITS;
 }
 
 cudaError_t launch_persist(const PersistLaunch& L, cudaStream_t st) {
-    if (!units_fit(L.na, L.stride, L.blocks)) return cudaErrorInvalidConfiguration;
+    if (!units_fit(L.na, L.stride, L.blocks, L.nx, L.ny)) return cudaErrorInvalidConfiguration;
     PArgs A{};
     A.rec = L.rec;
     A.na = L.na;
@@ -673,7 +748,7 @@ int persist_max_blocks(int na, int nx, int ny, int stride, int device) {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist, PT, smem) != cudaSuccess) return 0;
     const int blocks = std::min(per_sm, 1) * sms;
-    return units_fit(na, stride, blocks) ? blocks : 0;
+    return units_fit(na, stride, blocks, nx, ny) ? blocks : 0;
 }
 
 }  // namespace roi
