@@ -21,10 +21,11 @@
 //
 // Inner loops run in fixed point, so they need no float-to-integer conversion (a
 // quarter-rate instruction on this GPU): along a ray the interpolation coordinate is
-// an integer column plus a Q.22 offset, re-anchored from float-float every 24 samples
-// and stepped by round(slope 2^22); across a gather tile row the window coordinate is a Q.23 integer
+// an integer column plus a Q.22 offset, re-anchored from float-float every 48 samples
+// and stepped by round(slope 2^22) (drift <= 47 2^-23 < 6e-6 pixel, below the float ulp of
+// a coordinate near 192); across a gather tile row the window coordinate is a Q.23 integer
 // stepped by round(cos 2^23).  The fraction bits become a float by the exponent trick
-// (one logic op and one add).  Position errors stay below 3e-6 pixel.
+// (one logic op and one add).
 //
 // The grid barrier polls a monotonic arrival counter with a time limit (one second by
 // default, wall clock from %globaltimer): a block that waits longer sets the error flag
@@ -50,7 +51,7 @@ constexpr int RAYS = 32;                 // rays per unit (one warp-wide ray gro
 constexpr int FSEG = 4;                  // segments per ray in phase A
 constexpr int CHUNK_UNITS = 16;          // phase A units whose partials are held at once
 constexpr int DG_WARPS = 8;              // warps that update the gradient dual while the others project
-constexpr int SEGA = 24;                 // samples per float-float anchor
+constexpr int SEGA = 48;                 // samples per float-float anchor
 constexpr int MAXUNITS = 512;            // phase A units per block (checked by the host)
 constexpr int NBUCKET = 512;             // cost classes of the phase A balancing sort
 constexpr int ITEM_COST = 16;            // fixed cost of one (unit, segment) item, in samples
