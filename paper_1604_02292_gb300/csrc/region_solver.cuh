@@ -38,7 +38,7 @@ namespace rs {
 
 constexpr int BPT = 1024;
 constexpr int BNW = BPT / 32;
-constexpr int SEGB = 24;     // samples per float-float anchor
+constexpr int SEGB = 48;     // samples per float-float anchor (Q.22 drift < 6e-6 px)
 constexpr int TB = 16;       // tile side
 constexpr int RUNB = 8;      // pixels per lane
 constexpr int ACH = 16;      // angles per staging chunk (one per lane of the first half-warp)
