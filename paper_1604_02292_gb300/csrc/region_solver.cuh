@@ -421,7 +421,7 @@ __device__ __forceinline__ void phase_a_global(const Ctx& C, const Team& T, int 
 }
 
 // Phase A of one branch with the image streamed through shared memory in bands of
-// kBandRows rows (two buffers, one bulk copy each, refilled while the other is read).
+// band_rows() rows (two buffers, one bulk copy each, refilled while the other is read).
 // This block's units (ustart + member + i * size) are taken in groups of 32, one per
 // warp; each group walks all bands, each lane accumulating its ray over the samples
 // that fall in the band (one float-float anchor per band and ray), then finishes the
@@ -441,8 +441,9 @@ __device__ __forceinline__ bool phase_a_banded(const Ctx& C, const Team& T, int 
     const int ustart = row ? 0 : R.nrow * C.nchunk;
     const int total = (row ? R.nrow : R.na) * C.nchunk - ustart;
     const int nu = total > tm ? (total - tm + ts - 1) / ts : 0;
-    const int nb = (M + kBandRows - 1) / kBandRows;
-    const int band_floats = kBandRows * ld;
+    const int BR = band_rows(R.nx, R.ny, ES);
+    const int nb = (M + BR - 1) / BR;
+    const int band_floats = BR * ld;
     const float halfM = 0.5f * (float)(M - 1);
     for (int g0 = 0; g0 < nu; g0 += BNW) {
         const int i = g0 + warp;
@@ -472,24 +473,24 @@ __device__ __forceinline__ bool phase_a_banded(const Ctx& C, const Team& T, int 
         }
         float sum = 0.f, cmp = 0.f;
         if (threadIdx.x == 0) {
-            const int rows0 = M < kBandRows ? M : kBandRows;
+            const int rows0 = M < BR ? M : BR;
             bulk_load(smem, img_base, ES * rows0 * ld, &mbar[0]);
         }
         for (int b = 0; b < nb; ++b) {
             const int bi = b & 1;
             if (threadIdx.x == 0 && b + 1 < nb) {  // the other buffer was released by the last barrier
-                const int rows = min(kBandRows, M - (b + 1) * kBandRows);
+                const int rows = min(BR, M - (b + 1) * BR);
                 bulk_load(smem + (bi ^ 1) * band_floats, img_base + (size_t)(b + 1) * band_floats, ES * rows * ld,
                           &mbar[bi ^ 1]);
             }
             if (!mbar_wait(&mbar[bi], (parity >> bi) & 1u, T.wait_ns, T.err)) return false;
             parity ^= 1u << bi;
-            const int m0 = max(mlo, b * kBandRows), m1 = min(mhi, (b + 1) * kBandRows);
+            const int m0 = max(mlo, b * BR), m1 = min(mhi, (b + 1) * BR);
             if (valid && m0 < m1) {
                 int j0;
                 int q = split_fixed22(ff_add(Ak, ff_mul_f((float)m0 - halfM, r.slope)), j0);
                 const int step = r.slope_q22;
-                const TS* rp = smem + bi * band_floats + (m0 - b * kBandRows) * ld + kPad + j0;
+                const TS* rp = smem + bi * band_floats + (m0 - b * BR) * ld + kPad + j0;
                 float s0 = 0.f, s1 = 0.f;
 #pragma unroll 4
                 for (int m = m0; m < m1; ++m, rp += ld, q += step) {

@@ -304,23 +304,29 @@ cudaError_t launch_persist(const PersistLaunch& L, cudaStream_t st);
 // (a function of the box size alone, so a region's result never depends on where it
 // is solved): 0 = the whole padded image staged in shared memory by one bulk copy
 // (teams read it from global memory instead, with the same arithmetic); 1 = streamed
-// through shared memory in bands of kBandRows rows, double-buffered; 2 = read from
-// global memory.
+// through shared memory in bands of band_rows() rows (as many as two buffers in
+// kStageMaxBytes hold, a multiple of 8, from kBandRowsMin to kBandRowsMax),
+// double-buffered; 2 = read from global memory.
 constexpr size_t kStageMaxBytes = 200 * 1024;
-constexpr int kBandRows = 24;
+constexpr int kBandRowsMin = 24;
+constexpr int kBandRowsMax = 96;
+ROI_HD int band_rows(int nx, int ny, int esz) {
+    const size_t lr = (size_t)padded_ld_e(nx, esz), lc = (size_t)padded_ld_e(ny, esz);
+    size_t rows = kStageMaxBytes / ((size_t)esz * 2 * (lr > lc ? lr : lc)) / 8 * 8;
+    return (int)(rows > (size_t)kBandRowsMax ? (size_t)kBandRowsMax : rows);
+}
 ROI_HD int stage_mode(int nx, int ny, int esz) {
     const size_t lr = (size_t)padded_ld_e(nx, esz), lc = (size_t)padded_ld_e(ny, esz);
     const size_t full = (size_t)esz * (ny * lr > nx * lc ? ny * lr : nx * lc);
     if (full <= kStageMaxBytes) return 0;
-    const size_t band = (size_t)esz * 2 * kBandRows * (lr > lc ? lr : lc);
-    return band <= kStageMaxBytes ? 1 : 2;
+    return band_rows(nx, ny, esz) >= kBandRowsMin ? 1 : 2;
 }
 // Dynamic shared memory the staging of a box of nx x ny (elements of esz bytes) needs.
 ROI_HD size_t stage_bytes(int nx, int ny, int esz) {
     const size_t lr = (size_t)padded_ld_e(nx, esz), lc = (size_t)padded_ld_e(ny, esz);
     const int m = stage_mode(nx, ny, esz);
     if (m == 0) return (size_t)esz * (ny * lr > nx * lc ? ny * lr : nx * lc);
-    if (m == 1) return (size_t)esz * 2 * kBandRows * (lr > lc ? lr : lc);
+    if (m == 1) return (size_t)esz * 2 * band_rows(nx, ny, esz) * (lr > lc ? lr : lc);
     return 0;
 }
 
