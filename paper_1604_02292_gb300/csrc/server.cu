@@ -534,7 +534,7 @@ roi_status roi_server_create(const roi_server_config* cfg_in, roi_server_t* out)
     if (cfg.device_bytes == 0) cfg.device_bytes = (size_t)4 << 30;
     if (cfg.host_bytes == 0) cfg.host_bytes = (size_t)512 << 20;
     if (cfg.ring_slots == 0) cfg.ring_slots = 1024;
-    if (cfg.team_blocks == 0) cfg.team_blocks = 8;
+    if (cfg.team_blocks == 0) cfg.team_blocks = 16;
     if (cfg.large_side == 0) cfg.large_side = 320;
     if (cfg.idle_us == 0) cfg.idle_us = 2000;
     if (cfg.ring_slots < 1 || cfg.ring_slots > (1 << 20) || cfg.team_blocks < 1 || cfg.team_blocks > 1024 ||
