@@ -305,7 +305,8 @@ unsigned long long roi_recon_launch_count(void);
 /* A server solves ROI requests (each the Sec. 1 scheme on one region of one resident
  * sinogram, Sec. 5.5: regions are independent) while more keep arriving.  One
  * cooperative kernel runs while there is work: its blocks form units -- single blocks
- * for small boxes, teams of team_blocks blocks for boxes of side >= large_side -- that
+ * for small boxes, teams of team_blocks blocks for boxes of side >= large_side (and for
+ * small ones while a team is idle, unless no_spill) -- that
  * take requests from rings in page-locked host memory mapped into the device, so a
  * request submitted while others are on the GPU starts as soon as a unit is free,
  * without a launch.  The host side (a progress engine, run by a background thread after
@@ -327,6 +328,9 @@ typedef struct {
     int teams;             /* teams (-1: about 3/4 of the blocks; 0: no team pool) */
     int large_side;        /* box side from which a request goes to the team pool (0: 320) */
     int idle_us;           /* the kernel leaves after this long without work (0: 2000) */
+    int no_spill;          /* 0: a small-box request is admitted to an idle team when no
+                              large one waits for it (faster at light load); 1: small boxes
+                              always go to the single-block pool */
 } roi_server_config;
 
 typedef struct {

@@ -139,6 +139,7 @@ struct Pool {
     unsigned char* ring_d = nullptr;  // its device view
     unsigned long long* head_d = nullptr;
     std::vector<Req*> occupant;
+    int live = 0;  // published and not yet completed
     long long next_ticket = 0;
     std::deque<Req*> pending;
 };
@@ -293,6 +294,7 @@ void complete(roi_server* s, Pool& P, size_t slot, Req* r, roi_status status) {
     r->status = status;
     r->state = 2;
     P.occupant[slot] = nullptr;
+    --P.live;
     if (r->has_dev) {
         s->darena.release(r->dev_off, r->lay.total);
         r->has_dev = false;
@@ -378,15 +380,27 @@ void publish(roi_server* s, int pi, Req* r, size_t slot) {
     r->t_publish = now_ms();
     r->state = 1;
     P.occupant[slot] = r;
+    ++P.live;
     // the slot's contents before the new tail (release, read by the kernel with acquire)
     __atomic_store_n(&s->ctl_h->tail[pi], (unsigned long long)(r->ticket + 1), __ATOMIC_RELEASE);
 }
 
+// Admits pending requests in arrival order per pool while their state fits the budgets.
+// A small-box request goes to the team pool instead when a team is idle there and no
+// large request waits for one (unless no_spill): at light load a request then runs on a
+// team of blocks rather than one block, at heavy load the teams are busy and it stays in
+// its pool.  The result is the same bits either way.
 void admit(roi_server* s) {
     for (int pi = 0; pi < 2; ++pi) {
-        Pool& P = s->pools[pi];
-        while (!P.pending.empty()) {
-            Req* r = P.pending.front();
+        std::deque<Req*>& pend = s->pools[pi].pending;
+        while (!pend.empty()) {
+            Req* r = pend.front();
+            Pool& T = s->pools[1];
+            const int to = (pi == 0 && !s->cfg.no_spill && T.nteams > 0 && T.pending.empty() && T.live < T.nteams &&
+                            !T.occupant[(size_t)(T.next_ticket % T.slots)])
+                               ? 1
+                               : pi;
+            Pool& P = s->pools[to];
             const size_t slot = (size_t)(P.next_ticket % P.slots);
             if (P.occupant[slot]) break;  // ring full at this position
             size_t doff = 0, hoff = 0;
@@ -399,8 +413,9 @@ void admit(roi_server* s) {
             r->host_off = hoff;
             r->has_dev = r->has_host = true;
             r->ticket = P.next_ticket++;
-            P.pending.pop_front();
-            publish(s, pi, r, slot);
+            r->pool = to;
+            pend.pop_front();
+            publish(s, to, r, slot);
         }
     }
 }
@@ -538,7 +553,8 @@ roi_status roi_server_create(const roi_server_config* cfg_in, roi_server_t* out)
     if (cfg.large_side == 0) cfg.large_side = 320;
     if (cfg.idle_us == 0) cfg.idle_us = 2000;
     if (cfg.ring_slots < 1 || cfg.ring_slots > (1 << 20) || cfg.team_blocks < 1 || cfg.team_blocks > 1024 ||
-        cfg.teams < -1 || cfg.large_side < 1 || cfg.idle_us < 1 || cfg.idle_us > 10000000)
+        cfg.teams < -1 || cfg.large_side < 1 || cfg.idle_us < 1 || cfg.idle_us > 10000000 || cfg.no_spill < 0 ||
+        cfg.no_spill > 1)
         return ROI_EINVAL;
     roi_server* s = new (std::nothrow) roi_server;
     if (!s) return ROI_ENOMEM;

@@ -223,6 +223,22 @@ def test_server_argument_errors(sinos):
         assert e.value.status == R.ROI_ESTATE
 
 
+def test_small_requests_spill_to_idle_teams(sinos):
+    """With the teams idle a small-box request is admitted to the team pool (unless
+    no_spill); its result is the same bits as through the single-block pool."""
+    sino, region, prm = CASES[0]  # 48-px box, below large_side
+    got = {}
+    for ns in (0, 1):
+        with make_server(sinos, team_blocks=4, teams=8, large_side=100, no_spill=ns) as s:
+            rid = s.submit(sino, region, prm)
+            s.drain(120000.0)
+            (c,) = s.poll()
+            assert c["status"] == R.ROI_OK
+            assert c["pool"] == (0 if ns else 1)
+            got[ns] = s.take(rid, (c["box"][3], c["box"][2]))
+    assert np.array_equal(got[0], got[1])
+
+
 def test_destroy_with_requests_outstanding(sinos):
     s = make_server(sinos, device_bytes=8 << 20)
     for k in range(24):
@@ -249,7 +265,7 @@ def test_serving_geometry_2048_sampled():
         rr.fbp()
         recons.append(rr)
         sinos_np.append(p)
-    with R.Server(team_blocks=8, teams=12, large_side=320) as s:
+    with R.Server(team_blocks=8, teams=12, large_side=320, no_spill=1) as s:
         for rr in recons:
             s.add(rr)
         ids = {s.submit(sino, reg, prm): k for k, (sino, reg, prm) in enumerate(reqs)}
