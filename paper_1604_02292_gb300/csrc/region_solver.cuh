@@ -47,7 +47,14 @@ constexpr int ACH = 16;      // angles per staging chunk (one per lane of the fi
 // touched is in [0, 24] < SBB.
 constexpr int KOFFB = 12;
 constexpr int SBB = 26;      // staged bins per angle
-constexpr int WARP_STAGE = ACH * SBB + 4 * ACH * 2;  // floats per warp in phase B (bins + consts)
+constexpr int BUFB = ACH * SBB + 8 * ACH;  // one phase B staging buffer: bins + 8 constants per angle
+constexpr int WARP_STAGE = 2 * BUFB;        // floats per warp in phase B (double-buffered)
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 enum PassA { A_SOLVE = 0, A_ROWSUM = 1, A_EXTER = 2 };
 enum PassB { B_SOLVE = 0, B_COLSUM = 1, B_XS = 2 };  // B_XS: x_s^k = W_L^T C_{u_k} p (Sec. 3)
@@ -226,15 +233,6 @@ __device__ __forceinline__ void phase_b(const Ctx& C, const Team& T, int pass, i
     const int lane = threadIdx.x & 31;
     const int nx = R.nx, ny = R.ny;
     const int tiles_x = (nx + TB - 1) / TB, tiles = tiles_x * ((ny + TB - 1) / TB);
-    float* st = wstage;                                            // [ACH][SBB]
-    int* cb = reinterpret_cast<int*>(wstage + ACH * SBB);          // [ACH] base (Q.23)
-    int* cc = cb + ACH;                                            // [ACH] c step
-    int* cs = cc + ACH;                                            // [ACH] s step
-    float* ciw = reinterpret_cast<float*>(cs + ACH);               // [ACH] 1/w
-    int* ckb = reinterpret_cast<int*>(ciw + ACH);                  // [ACH] kbase
-    int* cwd = ckb + ACH;                                          // [ACH] width
-    int* cai = cwd + ACH;                                          // [ACH] sinogram angle index
-    int* cd0 = cai + ACH;                                          // [ACH] first bin of the window
     // B_XS reads the window bins of the filtered sinogram of iteration kiter + 1
     const float* fk = pass == B_XS ? R.fcp + (size_t)kiter * R.na * R.fcp_nd : nullptr;
     const int li = lane >> 1, lj0 = (lane & 1) * RUNB;
@@ -244,12 +242,22 @@ __device__ __forceinline__ void phase_b(const Ctx& C, const Team& T, int pass, i
         const int tile_x0 = (t % tiles_x) * TB, tile_y0 = (t / tiles_x) * TB;
         const float xi_t = (float)tile_x0 + 0.5f * (TB - 1) - 0.5f * (float)(nx - 1);
         const float eta_t = 0.5f * (float)(ny - 1) - ((float)tile_y0 + 0.5f * (TB - 1));
-        float sum[RUNB], cmp[RUNB];
-#pragma unroll
-        for (int p = 0; p < RUNB; ++p) sum[p] = cmp[p] = 0.f;
-        for (int a0 = 0; a0 < R.na; a0 += ACH) {
+        // Chunk a0 .. a0 + ACH - 1 into buffer b: the tile constants of each angle (one lane
+        // per angle), then the window bins by asynchronous copies (zero outside the window),
+        // so the next chunk's bins are in flight while this chunk is gathered.
+        // Buffer layout: bins [ACH][SBB] | base (Q.23) | c step | s step | 1/w | kbase | width |
+        // sinogram angle index | first window bin, ACH each.
+        auto stage = [&](int a0, int b) {
+            float* st = wstage + b * BUFB;
+            int* cb = reinterpret_cast<int*>(st + ACH * SBB);
+            int* cc = cb + ACH;
+            int* cs = cc + ACH;
+            float* ciw = reinterpret_cast<float*>(cs + ACH);
+            int* ckb = reinterpret_cast<int*>(ciw + ACH);
+            int* cwd = ckb + ACH;
+            int* cai = cwd + ACH;
+            int* cd0 = cai + ACH;
             const int nch = min(ACH, R.na - a0);
-            __syncwarp();
             if (lane < nch) {
                 const AngleRec& r = R.rec[a0 + lane];
                 ff kt = ff_add(ff_mul_f(xi_t, r.c), ff_mul_f(eta_t, r.s));
@@ -270,17 +278,38 @@ __device__ __forceinline__ void phase_b(const Ctx& C, const Team& T, int pass, i
             __syncwarp();
             for (int e = lane; e < nch * SBB; e += 32) {
                 const int al = e / SBB, kk = ckb[al] + (e - al * SBB);
-                float v = 0.f;
-                if (kk >= 0 && kk < cwd[al]) {
-                    if (pass == B_COLSUM)
-                        v = 1.f;
-                    else if (pass == B_XS)
-                        v = fk[(size_t)cai[al] * R.fcp_nd + cd0[al] + kk];
-                    else
-                        v = C.b.u[(size_t)(a0 + al) * R.stride + kk];
+                const bool in = kk >= 0 && kk < cwd[al];
+                if (pass == B_COLSUM) {
+                    st[e] = in ? 1.f : 0.f;
+                } else {
+                    const float* row = pass == B_XS ? fk + (size_t)cai[al] * R.fcp_nd + cd0[al]
+                                                    : C.b.u + (size_t)(a0 + al) * R.stride;
+                    cp_async4(st + e, in ? row + kk : row, in);
                 }
-                st[e] = v * ciw[al];  // staged times 1/w: the hat weights below are max(0, 1 - d/w)
             }
+            cp_async_commit();
+        };
+        float sum[RUNB], cmp[RUNB];
+#pragma unroll
+        for (int p = 0; p < RUNB; ++p) sum[p] = cmp[p] = 0.f;
+        __syncwarp();  // the previous tile's reads of both buffers are done
+        stage(0, 0);
+        for (int a0 = 0, b = 0; a0 < R.na; a0 += ACH, b ^= 1) {
+            const int nch = min(ACH, R.na - a0);
+            if (a0 + ACH < R.na) {
+                stage(a0 + ACH, b ^ 1);
+                cp_async_wait_group<1>();  // this chunk's copies have landed (the next may fly)
+            } else {
+                cp_async_wait_group<0>();
+            }
+            __syncwarp();
+            float* st = wstage + b * BUFB;
+            const int* cb = reinterpret_cast<const int*>(st + ACH * SBB);
+            const int* cc = cb + ACH;
+            const int* cs = cc + ACH;
+            const float* ciw = reinterpret_cast<const float*>(cs + ACH);
+            // bins times 1/w of their angle: the hat weights below are then max(0, 1 - d/w)
+            for (int e = lane; e < nch * SBB; e += 32) st[e] *= ciw[e / SBB];
             __syncwarp();
             float acc[RUNB];
 #pragma unroll
@@ -305,6 +334,7 @@ __device__ __forceinline__ void phase_b(const Ctx& C, const Team& T, int pass, i
             }
 #pragma unroll
             for (int p = 0; p < RUNB; ++p) neu_add(sum[p], cmp[p], acc[p]);
+            __syncwarp();  // buffer b is refilled by the chunk after next
         }
         // epilogue for this lane's pixels
         const int gi = tile_y0 + li;
