@@ -6,11 +6,12 @@
 // Chambolle-Pock; the operators W_L, W_L^T of Sec. 2.1):
 //   phase A  every block stages the whole padded image it projects (x for SIRT, xbar
 //            for CP; rows or columns by the branch of its angles) into shared memory
-//            with one TMA bulk copy and runs the ray-driven forward W_L on its share of
-//            (angle, 32-ray) units, fusing  r = p' - W_L x  (SIRT)  or
-//            u <- (u + sigma (W_L xbar - p'))/(1 + sigma/2)  (CP); for CP it also
-//            updates the gradient dual  v <- proj_lambda(v + sigma_v grad xbar)  on its
-//            share of pixels while the copy is in flight;
+//            with four TMA bulk copies (the rows of the four ray segments) and runs the
+//            ray-driven forward W_L on its share of (angle, 32-ray) units, fusing
+//            r = p' - W_L x  (SIRT)  or  u <- (u + sigma (W_L xbar - p'))/(1 + sigma/2)
+//            (CP); for CP eight warps first update the gradient dual
+//            v <- proj_lambda(v + sigma_v grad xbar)  on the block's share of pixels
+//            while the first copies are in flight;
 //   barrier
 //   phase B  every block takes 16 x 16 pixel tiles, stages the window bins the tile's
 //            pixels reach for all angles, gathers W_L^T of r (or u) over all angles and
