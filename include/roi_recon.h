@@ -329,8 +329,9 @@ typedef struct {
     int large_side;        /* box side from which a request goes to the team pool (0: 320) */
     int idle_us;           /* the kernel leaves after this long without work (0: 2000) */
     int no_spill;          /* 0: a small-box request is admitted to an idle team when no
-                              large one waits for it (faster at light load); 1: small boxes
-                              always go to the single-block pool */
+                              large one waits for it, and a lone request on an idle server
+                              runs on one team of all blocks until a queue forms (lower
+                              latency at light load); 1: requests go to their pool by size */
 } roi_server_config;
 
 typedef struct {

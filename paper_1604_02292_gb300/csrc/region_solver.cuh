@@ -760,8 +760,7 @@ __device__ __forceinline__ bool solve_region(const BatchRoi& R, const RegionBufs
         W.nchunk = (R.stride + 31) / 32;
         W.member = SOLO ? 0 : T.member;
         W.gthreads = (SOLO ? 1 : T.size) * BPT;
-        W.stage = stage_mode(R.nx, R.ny, ES);
-        if (W.stage == 0 && !(SOLO || T.size == 1)) W.stage = 2;  // same arithmetic as the staged image
+        W.stage = stage_mode(R.nx, R.ny, ES);  // every block of a team stages the image itself
     }
     __syncthreads();
     const Ctx& C = s_ctx;

@@ -303,7 +303,7 @@ cudaError_t launch_persist(const PersistLaunch& L, cudaStream_t st);
 // ---- how the whole-region solvers read a box image in the forward projection
 // (a function of the box size alone, so a region's result never depends on where it
 // is solved): 0 = the whole padded image staged in shared memory by one bulk copy
-// (teams read it from global memory instead, with the same arithmetic); 1 = streamed
+// (by every block of a team); 1 = streamed
 // through shared memory in bands of band_rows() rows (as many as two buffers in
 // kStageMaxBytes hold, a multiple of 8, from kBandRowsMin to kBandRowsMax),
 // double-buffered; 2 = read from global memory.

@@ -186,6 +186,8 @@ struct roi_server {
     unsigned char* ring_alloc = nullptr;
     // kernel state
     bool running = false;
+    int mode = 0;          // of the running (or next) kernel: 0 the configured pools, 1 solo
+    bool leaving = false;  // the close flag was set to end a solo launch
     cudaEvent_t ev_end = nullptr;
     long long launches = 0;
     // requests
@@ -389,15 +391,19 @@ void publish(roi_server* s, int pi, Req* r, size_t slot) {
 // A small-box request goes to the team pool instead when a team is idle there and no
 // large request waits for one (unless no_spill): at light load a request then runs on a
 // team of blocks rather than one block, at heavy load the teams are busy and it stays in
-// its pool.  The result is the same bits either way.
+// its pool.  While a solo launch runs (and is not leaving), every request goes to the team
+// ring.  The result is the same bits either way.
+constexpr int kSoloQueue = 8;
+
 void admit(roi_server* s) {
     for (int pi = 0; pi < 2; ++pi) {
         std::deque<Req*>& pend = s->pools[pi].pending;
         while (!pend.empty()) {
             Req* r = pend.front();
             Pool& T = s->pools[1];
-            const int to = (pi == 0 && !s->cfg.no_spill && T.nteams > 0 && T.pending.empty() && T.live < T.nteams &&
-                            !T.occupant[(size_t)(T.next_ticket % T.slots)])
+            const int to = ((s->mode == 1 && !s->leaving) ||
+                            (pi == 0 && !s->cfg.no_spill && T.nteams > 0 && T.pending.empty() && T.live < T.nteams &&
+                             !T.occupant[(size_t)(T.next_ticket % T.slots)]))
                                ? 1
                                : pi;
             Pool& P = s->pools[to];
@@ -429,6 +435,8 @@ bool any_published(const roi_server* s) {
 
 roi_status launch(roi_server* s) {
     SCU(s, cudaMemsetAsync(s->ctl_reset_d, 0, s->ctl_reset_bytes, s->st));
+    __atomic_store_n(&s->ctl_h->close, 0, __ATOMIC_RELEASE);  // no kernel runs here
+    s->leaving = false;
     SCU(s, cudaMemsetAsync(s->busy_d, 0, sizeof(int), s->st));
     SCU(s, cudaMemsetAsync(s->last_d, 0, sizeof(unsigned long long), s->st));
     roi::ServeArgs A{};
@@ -445,6 +453,13 @@ roi_status launch(roi_server* s) {
         D.head = P.head_d;
         D.tail = &s->ctl_d->tail[pi];
         D.done = s->done_d[pi];
+    }
+    if (s->mode == 1) {  // solo: no single-block units, one team of every block
+        A.pool[0].nteams = 0;
+        A.pool[1].first_block = 0;
+        A.pool[1].team = s->blocks;
+        A.pool[1].nteams = 1;
+        A.pool[1].team_base = 0;
     }
     A.close = &s->ctl_d->close;
     A.busy = s->busy_d;
@@ -503,7 +518,24 @@ roi_status progress_locked(roi_server* s) {
     }
     if (!s->rings_ready) return st;
     poll_done(s);
+    // Mode of the next launch: a lone request on an idle server runs on one team of every
+    // block (solo: the latency of a whole-GPU solve); otherwise the configured pools.
+    if (!s->running) {
+        size_t pend = 0;
+        for (const Pool& P : s->pools) pend += P.pending.size();
+        s->mode = (!s->cfg.no_spill && s->pools[1].nteams > 0 && s->pools[0].live + s->pools[1].live == 0 &&
+                   pend == 1)
+                      ? 1
+                      : 0;
+    }
     admit(s);
+    // A queue behind a solo launch (more than kSoloQueue requests waiting): let it finish
+    // the request it holds and leave, so the next launch serves the queue with the
+    // configured pools, whose throughput is higher.
+    if (s->running && s->mode == 1 && !s->leaving && s->pools[1].live > kSoloQueue) {
+        __atomic_store_n(&s->ctl_h->close, 1, __ATOMIC_RELEASE);
+        s->leaving = true;
+    }
     if (!s->running && any_published(s)) {
         roi_status l = launch(s);
         if (l != ROI_OK) return l;
