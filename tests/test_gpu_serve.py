@@ -239,6 +239,34 @@ def test_small_requests_spill_to_idle_teams(sinos):
     assert np.array_equal(got[0], got[1])
 
 
+def test_solo_launch_and_leaving_it(sinos):
+    """A lone request on an idle server runs solo (one team of all blocks); when more than
+    eight requests queue behind it, the solo launch finishes the request it holds and leaves,
+    and the queue is served by the configured pools.  Every result equals the batched
+    solver's."""
+    long_req = (1, (130.0, 128.0, 100.0, 50.0), dict(reg=R.ROI_SIRT_NONNEG, iters=200))
+    reqs = [long_req] + [CASES[k % len(CASES)] for k in range(12)]
+    with make_server(sinos, team_blocks=4, teams=8, large_side=100, start=False) as s:
+        ids = [s.submit(*reqs[0])]
+        s.progress()  # solo launch with the lone request
+        ids += [s.submit(*r) for r in reqs[1:]]
+        s.progress()  # twelve wait behind it: the solo launch is asked to leave
+        s.drain(300000.0)
+        comp = {c["id"]: c for c in s.poll()}
+        got = []
+        for rid in ids:
+            c = comp[rid]
+            assert c["status"] == R.ROI_OK
+            got.append(s.take(rid, (c["box"][3], c["box"][2])))
+        assert comp[ids[0]]["pool"] == 1
+        assert s.stats()["kernel_launches"] >= 2
+    for (sino, region, prm), g in zip(reqs, got):
+        rr = sinos[1][sino][0]
+        outs, _ = rr.solve_batch([region], [prm])
+        rr.sync()
+        assert np.array_equal(outs[0].cpu().numpy(), g)
+
+
 def test_destroy_with_requests_outstanding(sinos):
     s = make_server(sinos, device_bytes=8 << 20)
     for k in range(24):
