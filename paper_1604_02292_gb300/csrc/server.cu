@@ -387,14 +387,15 @@ void publish(roi_server* s, int pi, Req* r, size_t slot) {
     __atomic_store_n(&s->ctl_h->tail[pi], (unsigned long long)(r->ticket + 1), __ATOMIC_RELEASE);
 }
 
+// Requests waiting behind a solo launch before it is asked to leave.
+constexpr int kSoloQueue = 8;
+
 // Admits pending requests in arrival order per pool while their state fits the budgets.
 // A small-box request goes to the team pool instead when a team is idle there and no
 // large request waits for one (unless no_spill): at light load a request then runs on a
 // team of blocks rather than one block, at heavy load the teams are busy and it stays in
 // its pool.  While a solo launch runs (and is not leaving), every request goes to the team
 // ring.  The result is the same bits either way.
-constexpr int kSoloQueue = 8;
-
 void admit(roi_server* s) {
     for (int pi = 0; pi < 2; ++pi) {
         std::deque<Req*>& pend = s->pools[pi].pending;
