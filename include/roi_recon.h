@@ -177,6 +177,29 @@ roi_status roi_recon_reproject_exterior(roi_recon_t h, const roi_region* region,
 roi_status roi_recon_solve_local(roi_recon_t h, const roi_region* region, const roi_solve_params* params,
                                  float* out, int out_on_device, roi_solve_info* info);
 
+/* Checkpoint / resume of roi_recon_solve_local (ROI_SIRT_NONNEG and ROI_TV_CP).  After a
+ * solve_local without eval_objective the handle holds the iterate state of that solve:
+ * SIRT x; CP x, xbar, the gradient dual (vx, vy) and the data dual on the window.
+ * roi_recon_state_size gives its size in bytes: a 64-byte header (regularizer, weighting /
+ * precond flag, lambda, box, window layout, iterations done) followed by those arrays,
+ * float32, box-major [box_h][box_w] images and the window [n_angles][window_stride].
+ * roi_recon_state_export copies it to dst (bytes >= the size; device memory when
+ * on_device = 1, host memory otherwise); the call synchronizes.
+ * roi_recon_solve_local_resume runs params->iters further iterations from such a state
+ * (device or host memory) instead of from x = 0; everything else is as for solve_local,
+ * and info->iters_done counts the state's iterations too.  The region must give the
+ * state's box and window layout, and params->reg, weighting / precond and lambda must be
+ * those of the solve that made it.  With the same sinogram and FBP, the result is
+ * bit-identical to one uninterrupted solve of all the iterations (both run the same
+ * operations in the same order).  ROI_ESTATE when the handle holds no state (no solve yet,
+ * or forward_local, back_local, filter_prepare or another solve_local has used the solver
+ * buffers since), ROI_EINVAL for a state that does not match the call. */
+roi_status roi_recon_state_size(roi_recon_t h, size_t* bytes);
+roi_status roi_recon_state_export(roi_recon_t h, void* dst, size_t bytes, int on_device);
+roi_status roi_recon_solve_local_resume(roi_recon_t h, const roi_region* region, const roi_solve_params* params,
+                                        const void* state, size_t bytes, int state_on_device, float* out,
+                                        int out_on_device, roi_solve_info* info);
+
 /* Many local solves in one call (Sec. 5.5: local reconstructions are independent and can
  * be computed in parallel; Sec. 1 scheme for each).  regions[n], params[n] (one per region;
  * SIRT and CP may be mixed; CP must use precond = 1; eval_objective is ignored), outs[n]:

@@ -24,7 +24,7 @@ __all__ = [
     "ROI_OK", "ROI_EINVAL", "ROI_ENOMEM", "ROI_ESTATE", "ROI_ECUDA", "ROI_ETIMEOUT", "ROI_EBUSY",
     "ROI_F32", "ROI_BF16", "ROI_F16", "ROI_SIRT_NONNEG", "ROI_TV_CP", "ROI_FILTER_SIRT", "ROI_FILTER_TV", "ROI_FILTER_ISTA",
     "roi_recon_filter_prepare", "roi_recon_filter_get", "roi_recon_set_sinogram_truncated",
-    "roi_recon_solve_tiled",
+    "roi_recon_solve_tiled", "roi_recon_state_size", "roi_recon_state_export", "roi_recon_solve_local_resume",
     "Geometry", "Region", "SolveParams", "SolveInfo", "RoiError", "lib", "EXPORTS",
     "roi_recon_create", "roi_recon_destroy", "roi_recon_last_error", "roi_recon_set_sinogram",
     "roi_recon_fbp", "roi_recon_reproject_exterior", "roi_recon_solve_local", "roi_recon_plan",
@@ -102,7 +102,7 @@ EXPORTS = [
     "roi_server_progress", "roi_server_poll", "roi_server_take", "roi_server_drain", "roi_server_stats_get",
     "roi_server_last_error", "roi_server_destroy", "roi_server_footprint",
     "roi_recon_filter_prepare", "roi_recon_filter_get", "roi_recon_set_sinogram_truncated",
-    "roi_recon_solve_tiled",
+    "roi_recon_solve_tiled", "roi_recon_state_size", "roi_recon_state_export", "roi_recon_solve_local_resume",
 ]
 
 _lib = None
@@ -134,6 +134,14 @@ def lib() -> ctypes.CDLL:
             L.roi_recon_solve_local.argtypes = [_H, ctypes.POINTER(Region), ctypes.POINTER(SolveParams), _P,
                                                 ctypes.c_int, ctypes.POINTER(SolveInfo)]
             L.roi_recon_solve_local.restype = st
+            L.roi_recon_state_size.argtypes = [_H, ctypes.POINTER(ctypes.c_size_t)]
+            L.roi_recon_state_size.restype = st
+            L.roi_recon_state_export.argtypes = [_H, _P, ctypes.c_size_t, ctypes.c_int]
+            L.roi_recon_state_export.restype = st
+            L.roi_recon_solve_local_resume.argtypes = [_H, ctypes.POINTER(Region), ctypes.POINTER(SolveParams), _P,
+                                                       ctypes.c_size_t, ctypes.c_int, _P, ctypes.c_int,
+                                                       ctypes.POINTER(SolveInfo)]
+            L.roi_recon_solve_local_resume.restype = st
             L.roi_recon_plan.argtypes = [ctypes.POINTER(Geometry), ctypes.POINTER(Region),
                                          ctypes.POINTER(SolveInfo), _P, _P]
             L.roi_recon_plan.restype = st
@@ -232,6 +240,23 @@ def roi_recon_solve_local(h, region: Region, params: SolveParams, out: int, out_
                           info: SolveInfo | None) -> int:
     return lib().roi_recon_solve_local(h, ctypes.byref(region), ctypes.byref(params), out, out_on_device,
                                        ctypes.byref(info) if info is not None else None)
+
+
+def roi_recon_state_size(h) -> tuple[int, int]:
+    n = ctypes.c_size_t(0)
+    st = lib().roi_recon_state_size(h, ctypes.byref(n))
+    return st, n.value
+
+
+def roi_recon_state_export(h, dst: int, nbytes: int, on_device: int) -> int:
+    return lib().roi_recon_state_export(h, dst, nbytes, on_device)
+
+
+def roi_recon_solve_local_resume(h, region: Region, params: SolveParams, state: int, nbytes: int,
+                                 state_on_device: int, out: int, out_on_device: int, info: SolveInfo | None) -> int:
+    return lib().roi_recon_solve_local_resume(h, ctypes.byref(region), ctypes.byref(params), state, nbytes,
+                                              state_on_device, out, out_on_device,
+                                              ctypes.byref(info) if info is not None else None)
 
 
 def roi_recon_plan(geom: Geometry, region: Region, info: SolveInfo, d0: int | None, width: int | None) -> int:
@@ -501,8 +526,10 @@ class RoiRecon:
         return d0
 
     def solve_local(self, region, reg=ROI_SIRT_NONNEG, iters=200, lam=0.0, weighting=0, precond=1,
-                    crop_disk=0, eval_objective=0, out=None, inner_iters=0):
-        """Returns (out, info); out is a CUDA tensor [box_h][box_w] or a host numpy array."""
+                    crop_disk=0, eval_objective=0, out=None, inner_iters=0, resume=None):
+        """Returns (out, info); out is a CUDA tensor [box_h][box_w] or a host numpy array.
+        resume: a state from state() (host numpy uint8 array or CUDA uint8 tensor); the solve
+        then runs `iters` further iterations from it."""
         torch = self._torch
         pl = self.plan(region)
         shape = (pl.box[3], pl.box[2])
@@ -512,14 +539,42 @@ class RoiRecon:
         if out is None:
             out = torch.empty(shape, dtype=torch.float32, device="cuda")
         if isinstance(out, torch.Tensor) and out.is_cuda:
-            s = roi_recon_solve_local(self.h, Region(*map(float, region)), prm, self._dev(out, shape), 1, info)
+            optr, odev = self._dev(out, shape), 1
         else:
             import numpy as np
             if out.dtype != np.float32 or out.shape != shape or not out.flags["C_CONTIGUOUS"]:
                 raise TypeError(f"host output must be C-contiguous float32 of shape {shape}")
-            s = roi_recon_solve_local(self.h, Region(*map(float, region)), prm, out.ctypes.data, 0, info)
+            optr, odev = out.ctypes.data, 0
+        if resume is None:
+            s = roi_recon_solve_local(self.h, Region(*map(float, region)), prm, optr, odev, info)
+        else:
+            if isinstance(resume, torch.Tensor):
+                if not (resume.is_cuda and resume.dtype == torch.uint8 and resume.is_contiguous()):
+                    raise TypeError("a device state must be a contiguous uint8 CUDA tensor")
+                sptr, sn, sdev = resume.data_ptr(), resume.numel(), 1
+            else:
+                import numpy as np
+                if resume.dtype != np.uint8 or not resume.flags["C_CONTIGUOUS"]:
+                    raise TypeError("a host state must be a C-contiguous uint8 numpy array")
+                sptr, sn, sdev = resume.ctypes.data, resume.nbytes, 0
+            s = roi_recon_solve_local_resume(self.h, Region(*map(float, region)), prm, sptr, sn, sdev, optr, odev,
+                                             info)
         self._check(s)
         return out, info
+
+    def state(self, on_device=False):
+        """The iterate state of the last solve_local (checkpoint): a host numpy uint8 array, or a
+        CUDA uint8 tensor when on_device."""
+        st, n = roi_recon_state_size(self.h)
+        self._check(st)
+        if on_device:
+            buf = self._torch.empty(n, dtype=self._torch.uint8, device="cuda")
+            self._check(roi_recon_state_export(self.h, buf.data_ptr(), n, 1))
+        else:
+            import numpy as np
+            buf = np.empty(n, np.uint8)
+            self._check(roi_recon_state_export(self.h, buf.ctypes.data, n, 0))
+        return buf
 
     def solve_batch(self, regions, params, outs=None):
         """Solve many regions in one call.  regions: list of (cx, cy, r, m); params: list of dicts

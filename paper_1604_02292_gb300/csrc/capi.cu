@@ -99,6 +99,14 @@ struct roi_recon {
     DevBuf part;             // angle-group partials of the gather
     double* red = nullptr;   // kRedScratch partials + 4 results
     int exterior_ready = 0;  // p' in `pp` matches the cached plan and FBP
+    // iterate state of the last solve_local (checkpoint / resume)
+    bool state_valid = false;
+    int state_reg = 0, state_flag = 0;
+    double state_lambda = 0.0;
+    long long state_iters = 0;
+    const unsigned char* resume = nullptr;  // state being resumed from, during solve_local_resume
+    int resume_on_device = 0;
+    long long resume_iters = 0;
     // optional kernel timing: event pairs per kernel class (0 forward, 1 back, 2 single-launch solve)
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -235,6 +243,7 @@ roi_status ensure_plan(roi_recon* h, const roi_region* region) {
         return fail(h, ROI_EINVAL, "region: extended box does not intersect the %d x %d grid", h->N, h->N);
     h->plan_valid = false;
     h->exterior_ready = 0;
+    h->state_valid = false;  // the solver buffers belong to another box now
     h->h_loc.resize(h->na);
     h->h_ext.resize(h->na);
     const Rect grid{0, 0, h->N, h->N};
@@ -437,6 +446,47 @@ roi::PersistLaunch persist_base(roi_recon* h, int mode, int iters, int blocks) {
     return L;
 }
 
+// Checkpoint layout: this header, then float32 arrays -- SIRT: x; CP: x, xbar, vx, vy
+// ([box_h][box_w] each) and the data dual u ([n_angles][window_stride]).
+struct StateHeader {
+    char magic[8];
+    int reg, flag;  // regularizer; SIRT weighting / CP precond
+    int box_x0, box_y0, box_w, box_h;
+    int na, stride;
+    long long iters_done;
+    double lambda;
+    int reserved[2];
+};
+static_assert(sizeof(StateHeader) == 64, "the state header is 64 bytes");
+constexpr char kStateMagic[8] = {'R', 'O', 'I', 'S', 'T', 'A', 'T', '1'};
+
+size_t state_bytes_for(int reg, int nx, int ny, int na, int stride) {
+    const size_t nimg = (size_t)nx * ny, nwin = (size_t)na * stride;
+    return sizeof(StateHeader) + sizeof(float) * (reg == ROI_SIRT_NONNEG ? nimg : 4 * nimg + nwin);
+}
+
+// The iterate state being resumed from into the solver buffers (SIRT: x into the padded
+// images; CP: x, vx, vy, u, and xbar into the padded images).
+roi_status resume_load(roi_recon* h, bool cp) {
+    const size_t nimg = (size_t)h->box.w * h->box.h, nwin = (size_t)h->na * h->stride;
+    const cudaMemcpyKind k = h->resume_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const unsigned char* src = h->resume + sizeof(StateHeader);
+    if (cp) {
+        CU(h, cudaMemcpyAsync(h->xc.p, src, sizeof(float) * nimg, k, h->st));
+        src += sizeof(float) * nimg;
+    }
+    CU(h, cudaMemcpyAsync(h->itmp.p, src, sizeof(float) * nimg, k, h->st));  // x (SIRT) or xbar (CP)
+    src += sizeof(float) * nimg;
+    if (cp) {
+        CU(h, cudaMemcpyAsync(h->vx.p, src, sizeof(float) * nimg, k, h->st));
+        src += sizeof(float) * nimg;
+        CU(h, cudaMemcpyAsync(h->vy.p, src, sizeof(float) * nimg, k, h->st));
+        src += sizeof(float) * nimg;
+        CU(h, cudaMemcpyAsync(h->u.p, src, sizeof(float) * nwin, k, h->st));
+    }
+    return load_padded(h, h->itmp.p);
+}
+
 roi_status solve_sirt(roi_recon* h, const roi_solve_params* prm) {
     const int nx = h->box.w, ny = h->box.h;
     const size_t nwin = (size_t)h->na * h->stride;
@@ -450,7 +500,7 @@ roi_status solve_sirt(roi_recon* h, const roi_solve_params* prm) {
         R = h->sig.p;
         C = h->tau.p;
     }
-    roi_status s = clear_padded(h);  // x^0 = 0
+    roi_status s = h->resume ? resume_load(h, false) : clear_padded(h);  // x^0 = 0, or the state's x
     if (s != ROI_OK) return s;
     const float alpha = (float)(1.0 / ((double)h->na * h->nd));
     roi::FwdArgs fa = fwd_local(h, h->u.p);
@@ -530,9 +580,14 @@ roi_status solve_cp(roi_recon* h, const roi_solve_params* prm, double* L_out) {
         *L_out = 1.0;            // marker: read back later
     }
     // x in xc; xbar in the padded xa (+ transpose xaT) that the forward reads
-    for (DevBuf* b : {&h->xc, &h->vx, &h->vy}) roi::launch_fill(b->p, 0.f, nimg, h->st);
-    roi::launch_fill(h->u.p, 0.f, nwin, h->st);
-    roi_status s0 = clear_padded(h);
+    roi_status s0;
+    if (h->resume) {
+        s0 = resume_load(h, true);
+    } else {
+        for (DevBuf* b : {&h->xc, &h->vx, &h->vy}) roi::launch_fill(b->p, 0.f, nimg, h->st);
+        roi::launch_fill(h->u.p, 0.f, nwin, h->st);
+        s0 = clear_padded(h);
+    }
     if (s0 != ROI_OK) return s0;
     const float lam = (float)prm->lambda;
     int blocks = 0;
@@ -1018,6 +1073,7 @@ roi_status roi_recon_reproject_exterior(roi_recon_t h, const roi_region* region,
 roi_status roi_recon_forward_local(roi_recon_t h, const roi_region* region, const float* x, float* y) {
     if (!h || !region) return ROI_EINVAL;
     h->err.clear();
+    h->state_valid = false;
     if (!x || !y) return fail(h, ROI_EINVAL, "forward_local: null pointer");
     roi_status s = ensure_plan(h, region);
     if (s != ROI_OK) return s;
@@ -1031,6 +1087,7 @@ roi_status roi_recon_forward_local(roi_recon_t h, const roi_region* region, cons
 roi_status roi_recon_back_local(roi_recon_t h, const roi_region* region, const float* y, float* x) {
     if (!h || !region) return ROI_EINVAL;
     h->err.clear();
+    h->state_valid = false;
     if (!x || !y) return fail(h, ROI_EINVAL, "back_local: null pointer");
     roi_status s = ensure_plan(h, region);
     if (s != ROI_OK) return s;
@@ -1039,10 +1096,11 @@ roi_status roi_recon_back_local(roi_recon_t h, const roi_region* region, const f
     return ROI_OK;
 }
 
-roi_status roi_recon_solve_local(roi_recon_t h, const roi_region* region, const roi_solve_params* params, float* out,
-                                 int out_on_device, roi_solve_info* info) {
-    if (!h || !region || !params) return ROI_EINVAL;
-    h->err.clear();
+namespace {
+
+roi_status solve_local_impl(roi_recon* h, const roi_region* region, const roi_solve_params* params, float* out,
+                            int out_on_device, roi_solve_info* info) {
+    h->state_valid = false;  // the solver buffers are about to change
     if (!out) return fail(h, ROI_EINVAL, "solve_local: null output");
     if (params->reg == ROI_FILTER_TV || params->reg == ROI_FILTER_ISTA) {  // run in the whole-region solver
         if (params->eval_objective) return fail(h, ROI_EINVAL, "solve_local: no objective for this regularizer");
@@ -1125,18 +1183,126 @@ roi_status roi_recon_solve_local(roi_recon_t h, const roi_region* region, const 
         s = roi_recon_sync(h);
         if (s != ROI_OK) return s;
     }
+    if (!filt && !params->eval_objective) {  // the buffers hold this solve's iterate state
+        h->state_valid = true;
+        h->state_reg = (int)params->reg;
+        h->state_flag = sirt ? params->weighting : params->precond;
+        h->state_lambda = sirt ? 0.0 : params->lambda;
+        h->state_iters = h->resume_iters + params->iters;
+    }
     if (info) {
         fill_info(h, info);
-        info->iters_done = params->iters;
+        info->iters_done = (int)(h->resume_iters + params->iters);
         info->step_L = L;
         info->objective = objective;
     }
     return ROI_OK;
 }
 
+}  // namespace
+
+roi_status roi_recon_solve_local(roi_recon_t h, const roi_region* region, const roi_solve_params* params, float* out,
+                                 int out_on_device, roi_solve_info* info) {
+    if (!h || !region || !params) return ROI_EINVAL;
+    h->err.clear();
+    return solve_local_impl(h, region, params, out, out_on_device, info);
+}
+
+roi_status roi_recon_state_size(roi_recon_t h, size_t* bytes) {
+    if (!h || !bytes) return ROI_EINVAL;
+    h->err.clear();
+    if (!h->state_valid) return fail(h, ROI_ESTATE, "state_size: no solver state (run solve_local first)");
+    *bytes = state_bytes_for(h->state_reg, h->box.w, h->box.h, h->na, h->stride);
+    return ROI_OK;
+}
+
+roi_status roi_recon_state_export(roi_recon_t h, void* dst, size_t bytes, int on_device) {
+    if (!h) return ROI_EINVAL;
+    h->err.clear();
+    if (!dst) return fail(h, ROI_EINVAL, "state_export: null destination");
+    if (!h->state_valid) return fail(h, ROI_ESTATE, "state_export: no solver state (run solve_local first)");
+    const int nx = h->box.w, ny = h->box.h;
+    const size_t need = state_bytes_for(h->state_reg, nx, ny, h->na, h->stride);
+    if (bytes < need) return fail(h, ROI_EINVAL, "state_export: %zu bytes given, %zu needed", bytes, need);
+    StateHeader hd{};
+    std::memcpy(hd.magic, kStateMagic, sizeof hd.magic);
+    hd.reg = h->state_reg;
+    hd.flag = h->state_flag;
+    hd.box_x0 = h->box.x0;
+    hd.box_y0 = h->box.y0;
+    hd.box_w = nx;
+    hd.box_h = ny;
+    hd.na = h->na;
+    hd.stride = h->stride;
+    hd.iters_done = h->state_iters;
+    hd.lambda = h->state_lambda;
+    unsigned char* d = static_cast<unsigned char*>(dst);
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (on_device)
+        CU(h, cudaMemcpyAsync(d, &hd, sizeof hd, cudaMemcpyHostToDevice, h->st));
+    else
+        std::memcpy(d, &hd, sizeof hd);
+    d += sizeof hd;
+    const size_t row = sizeof(float) * nx, img = row * ny;
+    if (h->state_reg == ROI_SIRT_NONNEG) {
+        CU(h, cudaMemcpy2DAsync(d, row, xa0(h), sizeof(float) * lda(h), row, ny, k, h->st));  // x
+    } else {
+        CU(h, cudaMemcpyAsync(d, h->xc.p, img, k, h->st));  // x
+        d += img;
+        CU(h, cudaMemcpy2DAsync(d, row, xa0(h), sizeof(float) * lda(h), row, ny, k, h->st));  // xbar
+        d += img;
+        CU(h, cudaMemcpyAsync(d, h->vx.p, img, k, h->st));
+        d += img;
+        CU(h, cudaMemcpyAsync(d, h->vy.p, img, k, h->st));
+        d += img;
+        CU(h, cudaMemcpyAsync(d, h->u.p, sizeof(float) * (size_t)h->na * h->stride, k, h->st));
+    }
+    CU(h, cudaStreamSynchronize(h->st));
+    return ROI_OK;
+}
+
+roi_status roi_recon_solve_local_resume(roi_recon_t h, const roi_region* region, const roi_solve_params* params,
+                                        const void* state, size_t bytes, int state_on_device, float* out,
+                                        int out_on_device, roi_solve_info* info) {
+    if (!h || !region || !params) return ROI_EINVAL;
+    h->err.clear();
+    if (!state) return fail(h, ROI_EINVAL, "solve_local_resume: null state");
+    if (params->reg != ROI_SIRT_NONNEG && params->reg != ROI_TV_CP)
+        return fail(h, ROI_EINVAL, "solve_local_resume: only SIRT and CP-TV solves resume");
+    if (bytes < sizeof(StateHeader)) return fail(h, ROI_EINVAL, "solve_local_resume: state too short");
+    StateHeader hd{};
+    if (state_on_device) {
+        CU(h, cudaMemcpyAsync(&hd, state, sizeof hd, cudaMemcpyDeviceToHost, h->st));
+        CU(h, cudaStreamSynchronize(h->st));
+    } else {
+        std::memcpy(&hd, state, sizeof hd);
+    }
+    if (std::memcmp(hd.magic, kStateMagic, sizeof hd.magic) != 0)
+        return fail(h, ROI_EINVAL, "solve_local_resume: not a solver state");
+    roi_status s = ensure_plan(h, region);
+    if (s != ROI_OK) return s;
+    const bool sirt = params->reg == ROI_SIRT_NONNEG;
+    if (hd.reg != (int)params->reg || hd.flag != (sirt ? params->weighting : params->precond) ||
+        (!sirt && hd.lambda != params->lambda))
+        return fail(h, ROI_EINVAL, "solve_local_resume: regularizer, weighting / precond or lambda differ from the state's");
+    if (hd.box_x0 != h->box.x0 || hd.box_y0 != h->box.y0 || hd.box_w != h->box.w || hd.box_h != h->box.h ||
+        hd.na != h->na || hd.stride != h->stride || hd.iters_done < 0)
+        return fail(h, ROI_EINVAL, "solve_local_resume: the state's box or window layout differs from the region's");
+    if (bytes < state_bytes_for(hd.reg, hd.box_w, hd.box_h, hd.na, hd.stride))
+        return fail(h, ROI_EINVAL, "solve_local_resume: state too short for its box");
+    h->resume = static_cast<const unsigned char*>(state);
+    h->resume_on_device = state_on_device;
+    h->resume_iters = hd.iters_done;
+    s = solve_local_impl(h, region, params, out, out_on_device, info);
+    h->resume = nullptr;
+    h->resume_iters = 0;
+    return s;
+}
+
 roi_status roi_recon_filter_prepare(roi_recon_t h, int n_iters) {
     if (!h) return ROI_EINVAL;
     h->err.clear();
+    h->state_valid = false;
     if (n_iters < 1 || n_iters > 100000) return fail(h, ROI_EINVAL, "filter_prepare: n_iters out of range");
     if (!h->have_sino) return fail(h, ROI_ESTATE, "filter_prepare: no sinogram (call set_sinogram first)");
     if (h->filt_n < n_iters) {
