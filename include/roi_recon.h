@@ -301,6 +301,15 @@ roi_status roi_recon_set_option(roi_recon_t h, roi_option opt, long long value);
  * itself whenever it synchronizes (host output). */
 roi_status roi_recon_sync(roi_recon_t h);
 
+/* Check build only (the library compiled with -DROI_CHECK; the Python binding loads that
+ * variant when ROI_RECON_CHECK=1): the number of out-of-range indices the hot kernels'
+ * checks have found since the last call -- image columns of ray samples and staged bins of
+ * gathered pixels, each replaced by an in-range index when found -- with the first one's
+ * site (1-2 single-launch solver, 3-5 whole-region solver, 6-7 one-launch-per-operator
+ * projectors) and value in *site / *index (either may be NULL); the reports are cleared.
+ * Waits for the device.  The product build has no checks and returns 0. */
+int roi_recon_check_report(int* site, int* index);
+
 /* --------------------------------------------------------------------------
  * Measurement
  * ------------------------------------------------------------------------ */

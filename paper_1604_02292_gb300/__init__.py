@@ -25,6 +25,7 @@ __all__ = [
     "ROI_F32", "ROI_BF16", "ROI_F16", "ROI_SIRT_NONNEG", "ROI_TV_CP", "ROI_FILTER_SIRT", "ROI_FILTER_TV", "ROI_FILTER_ISTA",
     "roi_recon_filter_prepare", "roi_recon_filter_get", "roi_recon_set_sinogram_truncated",
     "roi_recon_solve_tiled", "roi_recon_state_size", "roi_recon_state_export", "roi_recon_solve_local_resume",
+    "roi_recon_check_report",
     "Geometry", "Region", "SolveParams", "SolveInfo", "RoiError", "lib", "EXPORTS",
     "roi_recon_create", "roi_recon_destroy", "roi_recon_last_error", "roi_recon_set_sinogram",
     "roi_recon_fbp", "roi_recon_reproject_exterior", "roi_recon_solve_local", "roi_recon_plan",
@@ -103,6 +104,7 @@ EXPORTS = [
     "roi_server_last_error", "roi_server_destroy", "roi_server_footprint",
     "roi_recon_filter_prepare", "roi_recon_filter_get", "roi_recon_set_sinogram_truncated",
     "roi_recon_solve_tiled", "roi_recon_state_size", "roi_recon_state_export", "roi_recon_solve_local_resume",
+    "roi_recon_check_report",
 ]
 
 _lib = None
@@ -116,7 +118,7 @@ def lib() -> ctypes.CDLL:
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build()
+            path = _build.build(check=os.environ.get("ROI_RECON_CHECK") == "1")
             L = ctypes.CDLL(path)
             st = ctypes.c_int
             L.roi_recon_create.argtypes = [ctypes.POINTER(Geometry), _P, ctypes.POINTER(_H)]
@@ -134,6 +136,8 @@ def lib() -> ctypes.CDLL:
             L.roi_recon_solve_local.argtypes = [_H, ctypes.POINTER(Region), ctypes.POINTER(SolveParams), _P,
                                                 ctypes.c_int, ctypes.POINTER(SolveInfo)]
             L.roi_recon_solve_local.restype = st
+            L.roi_recon_check_report.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+            L.roi_recon_check_report.restype = ctypes.c_int
             L.roi_recon_state_size.argtypes = [_H, ctypes.POINTER(ctypes.c_size_t)]
             L.roi_recon_state_size.restype = st
             L.roi_recon_state_export.argtypes = [_H, _P, ctypes.c_size_t, ctypes.c_int]
@@ -240,6 +244,13 @@ def roi_recon_solve_local(h, region: Region, params: SolveParams, out: int, out_
                           info: SolveInfo | None) -> int:
     return lib().roi_recon_solve_local(h, ctypes.byref(region), ctypes.byref(params), out, out_on_device,
                                        ctypes.byref(info) if info is not None else None)
+
+
+def roi_recon_check_report() -> tuple[int, int, int]:
+    """(count, site, index) of the check build's out-of-range indices since the last call."""
+    site, index = ctypes.c_int(0), ctypes.c_int(0)
+    n = lib().roi_recon_check_report(ctypes.byref(site), ctypes.byref(index))
+    return n, site.value, index.value
 
 
 def roi_recon_state_size(h) -> tuple[int, int]:

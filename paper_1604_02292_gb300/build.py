@@ -3,7 +3,8 @@
 Each translation unit under ``csrc/`` is compiled in parallel
 (``-gencode arch=compute_103a,code=sm_103a -O3 -lineinfo``) and linked into one
 shared library against the shared CUDA runtime.  The library is rebuilt when
-any source or header is newer than it.
+any source or header is newer than it.  ``build(check=True)`` builds the check variant
+``_lib/libroi_recon_check.so`` (``-DROI_CHECK``: index checks in the hot kernels).
 """
 from __future__ import annotations
 
@@ -41,21 +42,27 @@ def _deps():
         glob.glob(os.path.join(ROOT, "include", "*.h")) + [os.path.abspath(__file__)]
 
 
-def stale() -> bool:
-    if not os.path.exists(LIB):
+LIB_CHECK = os.path.join(LIBDIR, "libroi_recon_check.so")
+
+
+def stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(d) > t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link the library if needed; returns its path."""
-    if not force and not stale():
-        return LIB
+def build(force: bool = False, verbose: bool = False, check: bool = False) -> str:
+    """Compile and link the library (or its check variant) if needed; returns its path."""
+    lib = LIB_CHECK if check else LIB
+    if not force and not stale(lib):
+        return lib
     nvcc = _nvcc()
-    objdir = os.path.join(LIBDIR, "obj")
+    objdir = os.path.join(LIBDIR, "obj_check" if check else "obj")
     os.makedirs(objdir, exist_ok=True)
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", os.path.join(ROOT, "include")]
+    if check:
+        common += ["-DROI_CHECK"]
 
     def compile_one(src):
         obj = os.path.join(objdir, os.path.basename(src) + ".o")
@@ -72,14 +79,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + \
         ["-Xlinker", "-rpath," + _cuda_libdir(nvcc)]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -122,4 +122,6 @@ cudaError_t launch_batch(const BatchArgs& B, int blocks, size_t smem, cudaStream
     return cudaGetLastError();
 }
 
+ROI_CHECK_TU(batch)
+
 }  // namespace roi

@@ -1589,6 +1589,23 @@ roi_status roi_recon_set_option(roi_recon_t h, roi_option opt, long long value) 
     return fail(h, ROI_EINVAL, "set_option: unknown option %d", (int)opt);
 }
 
+int roi_recon_check_report(int* site, int* index) {
+    cudaDeviceSynchronize();
+    roi::CheckReport reps[4];
+    roi::check_take_persist(&reps[0]);
+    roi::check_take_batch(&reps[1]);
+    roi::check_take_serve(&reps[2]);
+    roi::check_take_project(&reps[3]);
+    int total = 0, first = -1;
+    for (int i = 0; i < 4; ++i) {
+        if (reps[i].count > 0 && first < 0) first = i;
+        total += reps[i].count;
+    }
+    if (site) *site = first >= 0 ? reps[first].site : 0;
+    if (index) *index = first >= 0 ? reps[first].index : 0;
+    return total;
+}
+
 roi_status roi_recon_sync(roi_recon_t h) {
     if (!h) return ROI_EINVAL;
     h->err.clear();

@@ -39,6 +39,7 @@
 
 #include <algorithm>
 
+#include "check.cuh"
 #include "dev_common.cuh"
 #include "roi_internal.h"
 
@@ -191,6 +192,7 @@ __device__ __forceinline__ ff ray_segment(const AngleRec& r, int k, int seg, int
         int j0;
         int q = split_fixed22(ff_add(Ak, ff_mul_f((float)m0 - halfM, r.slope)), j0);  // sample m0
         const int mend = min(m0 + SEGA, mhi);
+        const int jlo = -kPad - j0, jhi = ld - 1 - kPad - j0;  // taps j, j + 1 inside the padded row
         // sum of v0 + f (v1 - v0) with f = mf 2^-22: the two parts are summed separately,
         // two samples per packed (f32x2) operation (even and odd samples in the two lanes
         // of the pair, added at the end)
@@ -201,7 +203,7 @@ __device__ __forceinline__ ff ray_segment(const AngleRec& r, int k, int seg, int
 #pragma unroll 2
         for (; m + 1 < mend; m += 2, rp += 2 * ld, q += 2 * step) {
             const int q1 = q + step;
-            const int ja = q >> 22, jb = q1 >> 22;
+            const int ja = chk(q >> 22, jlo, jhi, CHK_PERSIST_RAY), jb = chk(q1 >> 22, jlo, jhi, CHK_PERSIST_RAY);
             const float2 bits = make_float2(__uint_as_float(0x4B000000u | ((unsigned)q & 0x3FFFFFu)),
                                             __uint_as_float(0x4B000000u | ((unsigned)q1 & 0x3FFFFFu)));
             const float2 mf = __fadd2_rn(bits, e23);
@@ -211,7 +213,7 @@ __device__ __forceinline__ ff ray_segment(const AngleRec& r, int k, int seg, int
             S1 = __ffma2_rn(mf, __ffma2_rn(v0, m1, v1), S1);  // v1 - v0 exactly as a subtraction
         }
         if (m < mend) {
-            const int j = q >> 22;
+            const int j = chk(q >> 22, jlo, jhi, CHK_PERSIST_RAY);
             const float mf = frac_int<22>(q);
             const float v0 = rp[j], v1 = rp[j + 1];
             S0.x += v0;
@@ -591,7 +593,8 @@ __global__ void __launch_bounds__(PT, 1) k_persist(PArgs A) {
 #pragma unroll
                     for (int p = 0; p < RUN / 2; ++p) {
                         const int K1 = K + q.c;
-                        const int kl0 = K >> 23, kl1 = K1 >> 23;
+                        const int kl0 = chk(K >> 23, 0, BSB - 1, CHK_PERSIST_GATHER);
+                        const int kl1 = chk(K1 >> 23, 0, BSB - 1, CHK_PERSIST_GATHER);
                         const float2 bits = make_float2(__uint_as_float(0x4B000000u | ((unsigned)K & 0x7FFFFFu)),
                                                         __uint_as_float(0x4B000000u | ((unsigned)K1 & 0x7FFFFFu)));
                         const float2 mf = __fadd2_rn(bits, make_float2(-8388608.0f, -8388608.0f));
@@ -737,6 +740,8 @@ cudaError_t launch_persist(const PersistLaunch& L, cudaStream_t st) {
     count_launches(1);
     return cudaLaunchCooperativeKernel((const void*)k_persist, dim3(L.blocks), dim3(PT), args, smem, st);
 }
+
+ROI_CHECK_TU(persist)
 
 int persist_max_blocks(int na, int nx, int ny, int stride, int device) {
     int sms = 0;

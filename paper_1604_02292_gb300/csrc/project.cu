@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "check.cuh"
 #include "dev_common.cuh"
 #include "roi_internal.h"
 
@@ -103,11 +104,12 @@ __global__ void __launch_bounds__(FWD_RAYS* FWD_MAXSEG) k_forward(const FwdArgs 
             const int mend = min(m0 + SEG, mhi);
             float acc = 0.f;
             const T* rp = src + (size_t)m0 * ld + bi;
+            const int jlo = -kPad - bi, jhi = ld - 1 - kPad - bi;  // taps j, j + 1 inside the padded row
 #pragma unroll 4
             for (int m = m0; m < mend; ++m, rp += ld) {
                 const float q = fmaf((float)(m - m0) - 0.5f * (SEG - 1), slope, bf);
                 const float fl = floorf(q);
-                const int j = (int)fl;
+                const int j = chk((int)fl, jlo, jhi, CHK_FORWARD);
                 const float f = q - fl;
                 float v0 = to_f32<DT>(__ldg(rp + j));
                 float v1 = to_f32<DT>(__ldg(rp + j + 1));
@@ -260,7 +262,7 @@ __global__ void __launch_bounds__(BT_X* BT_Y) k_back(BackArgs A) {
             for (int p = 0; p < PPT; ++p) {
                 const float kap = p == 0 ? k0 : fmaf(-(float)(BT_Y * p), cc.y, k0);
                 const float fl = floorf(kap);
-                const int kl = (int)fl;
+                const int kl = chk((int)fl, 0, SB - 1, CHK_BACK);
                 const float f = kap - fl;
                 const float w0 = fmaxf(0.f, fmaf(-f, iw2, iw));
                 const float w1 = fmaxf(0.f, fmaf(f, iw2, iwm));
@@ -455,5 +457,7 @@ void launch_window_ones(float* win, const AngleRec* rec, int na, int stride, cud
     count_launches(1);
     k_window_ones<<<grid, 128, 0, st>>>(win, rec, na, stride);
 }
+
+ROI_CHECK_TU(project)
 
 }  // namespace roi

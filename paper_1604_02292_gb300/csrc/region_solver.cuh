@@ -30,6 +30,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "check.cuh"
 #include "dev_common.cuh"
 #include "roi_internal.h"
 
@@ -149,11 +150,12 @@ __device__ __forceinline__ ff ray_full(const AngleRec& r, int k, int M, int Mm, 
         int j0;
         int q = split_fixed22(ff_add(Ak, ff_mul_f((float)m0 - halfM, r.slope)), j0);
         const int mend = min(m0 + SEGB, mhi);
+        const int jlo = -kPad - j0, jhi = ld - 1 - kPad - j0;  // taps j, j + 1 inside the padded row
         float s0 = 0.f, s1 = 0.f;
         const typename Stor<DT>::T* rp = img + (size_t)m0 * ld + j0;
 #pragma unroll 4
         for (int m = m0; m < mend; ++m, rp += ld, q += step) {
-            const int j = q >> 22;
+            const int j = chk(q >> 22, jlo, jhi, CHK_REGION_RAY);
             const float mf = frac_int<22>(q);
             const float v0 = to_f32<DT>(rp[j]), v1 = to_f32<DT>(rp[j + 1]);
             s0 += v0;
@@ -324,7 +326,7 @@ __device__ __forceinline__ void phase_b(const Ctx& C, const Team& T, int pass, i
                 const float* srow = st + al * SBB;
 #pragma unroll
                 for (int p = 0; p < RUNB; ++p) {
-                    const int kl = K >> 23;
+                    const int kl = chk(K >> 23, 0, SBB - 1, CHK_REGION_GATHER);
                     const float mf = frac_int<23>(K);
                     const float w0 = fma_sat(mf, niws, 1.f);
                     const float w1 = fma_sat(mf, iws, omiw);
@@ -521,10 +523,11 @@ __device__ __forceinline__ bool phase_a_banded(const Ctx& C, const Team& T, int 
                 int q = split_fixed22(ff_add(Ak, ff_mul_f((float)m0 - halfM, r.slope)), j0);
                 const int step = r.slope_q22;
                 const TS* rp = smem + bi * band_floats + (m0 - b * BR) * ld + kPad + j0;
+                const int jlo = -kPad - j0, jhi = ld - 1 - kPad - j0;
                 float s0 = 0.f, s1 = 0.f;
 #pragma unroll 4
                 for (int m = m0; m < m1; ++m, rp += ld, q += step) {
-                    const int j = q >> 22;
+                    const int j = chk(q >> 22, jlo, jhi, CHK_REGION_BAND);
                     const float mf = frac_int<22>(q);
                     const float v0 = to_f32<DT>(rp[j]), v1 = to_f32<DT>(rp[j + 1]);
                     s0 += v0;

@@ -459,4 +459,16 @@ int sino_view(::roi_recon* h, SinoView* v, std::string* msg);
 size_t batch_smem_bytes(size_t max_stage_bytes);
 cudaError_t launch_batch(const BatchArgs& B, int blocks, size_t smem, cudaStream_t st);
 
+// ---- check build (-DROI_CHECK): index checks of the hot kernels, one report per
+// translation unit; the product build's reports are always empty.
+struct CheckReport {
+    int count;          // indices found out of range
+    int site, index;    // the first one: its site (CheckSite) and value
+    int lo, hi;         // and its range
+};
+void check_take_persist(CheckReport* out);
+void check_take_batch(CheckReport* out);
+void check_take_serve(CheckReport* out);
+void check_take_project(CheckReport* out);
+
 }  // namespace roi

@@ -205,4 +205,6 @@ cudaError_t launch_serve(const ServeArgs& A, int blocks, cudaStream_t st) {
     return cudaLaunchCooperativeKernel((const void*)k_serve, dim3(blocks), dim3(BPT), args, smem, st);
 }
 
+ROI_CHECK_TU(serve)
+
 }  // namespace roi
