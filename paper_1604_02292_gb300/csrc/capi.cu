@@ -1488,7 +1488,7 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
     B.wait_ns = h->opt_wait_ns;
     B.team = team > 1 ? team : 1;
     B.bars = team > 1 ? h->b_bars.p : nullptr;
-    const size_t smem = roi::batch_smem_bytes(max_stage);
+    const size_t smem = roi::batch_smem_bytes(max_stage, h->na);
     cudaError_t e;
     {
         Span sp(h, 2);

@@ -223,8 +223,18 @@ __device__ __forceinline__ float disc_value(const BatchRoi& R, int i, int j) {
     return (x * x + y * y <= 0.25f * (float)R.grid_n * (float)R.grid_n) ? R.disc_g : 0.f;
 }
 
-// Phase B: this block's tiles are member + i * size, warps take i from *counter (preset
-// to BNW); lane = run of 8 pixels.  wstage: this warp's shared area.
+// Phase B: this block's tiles are member + i * size.  Per tile and pixel the gather is the
+// sum, in chunk order with Neumaier compensation, of per-chunk partials (each the FMA chain
+// over the chunk's 16 angles in order), then the pass's update.  Two ways to run it, with
+// the same operations and so the same bits:
+//  - per warp: warps take tiles i from *counter (preset to BNW), lane = run of 8 pixels,
+//    chunks streamed through the warp's double buffer;
+//  - cooperative, when the block has few tiles for its chunks (2 x tiles <= chunks) and the
+//    shared memory holds one tile's partials: all warps of the block share each tile, warp
+//    w taking chunks w, w + 32, ..., their partials meet in shared memory and one thread
+//    per pixel adds them in chunk order (a team of many blocks, e.g. a solo launch, keeps
+//    every warp busy instead of one per tile).
+// wstage: this warp's shared area (WARP_STAGE floats at smem + warp * WARP_STAGE).
 template <bool SOLO, int DT>
 __device__ __forceinline__ void phase_b(const Ctx& C, const Team& T, int pass, int* counter, float* wstage,
                                         int kiter = 0) {
@@ -232,163 +242,207 @@ __device__ __forceinline__ void phase_b(const Ctx& C, const Team& T, int pass, i
     auto* xaT = static_cast<typename Stor<DT>::T*>(C.xaT);
     const int tm = SOLO ? 0 : T.member, ts = SOLO ? 1 : T.size;
     const BatchRoi& R = *C.R;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nx = R.nx, ny = R.ny;
     const int tiles_x = (nx + TB - 1) / TB, tiles = tiles_x * ((ny + TB - 1) / TB);
     // B_XS reads the window bins of the filtered sinogram of iteration kiter + 1
     const float* fk = pass == B_XS ? R.fcp + (size_t)kiter * R.na * R.fcp_nd : nullptr;
     const int li = lane >> 1, lj0 = (lane & 1) * RUNB;
-    for (int i = threadIdx.x >> 5;;) {
+    const int nchunks = (R.na + ACH - 1) / ACH;
+
+    // Chunk a0 .. a0 + ACH - 1 of tile (xi_t, eta_t) into buffer b of this warp: the tile
+    // constants of each angle (one lane per angle), then the window bins by asynchronous
+    // copies (zero outside the window; committed as one group).
+    // Buffer layout: bins [ACH][SBB] | base (Q.23) | c step | s step | 1/w | kbase | width |
+    // sinogram angle index | first window bin, ACH each.
+    auto stage = [&](float xi_t, float eta_t, int a0, int b) {
+        float* st = wstage + b * BUFB;
+        int* cb = reinterpret_cast<int*>(st + ACH * SBB);
+        int* cc = cb + ACH;
+        int* cs = cc + ACH;
+        float* ciw = reinterpret_cast<float*>(cs + ACH);
+        int* ckb = reinterpret_cast<int*>(ciw + ACH);
+        int* cwd = ckb + ACH;
+        int* cai = cwd + ACH;
+        int* cd0 = cai + ACH;
+        const int nch = min(ACH, R.na - a0);
+        if (lane < nch) {
+            const AngleRec& r = R.rec[a0 + lane];
+            ff kt = ff_add(ff_mul_f(xi_t, r.c), ff_mul_f(eta_t, r.s));
+            kt = ff_add(kt, ff{-r.phi.hi, -r.phi.lo});
+            const int kbase = (int)floorf(kt.hi) - KOFFB;
+            kt = ff_add(kt, ff{-(float)kbase, 0.f});
+            kt = ff_add(kt, ff_mul_f(-0.5f * (TB - 1), r.c));
+            kt = ff_add(kt, ff_mul_f(0.5f * (TB - 1), r.s));
+            cb[lane] = to_fixed<23>(kt);
+            cc[lane] = r.c_q23;
+            cs[lane] = r.s_q23;
+            ciw[lane] = r.inv_w;
+            ckb[lane] = kbase;
+            cwd[lane] = r.width;
+            cai[lane] = r.aidx;
+            cd0[lane] = r.d0;
+        }
+        __syncwarp();
+        for (int e = lane; e < nch * SBB; e += 32) {
+            const int al = e / SBB, kk = ckb[al] + (e - al * SBB);
+            const bool in = kk >= 0 && kk < cwd[al];
+            if (pass == B_COLSUM) {
+                st[e] = in ? 1.f : 0.f;
+            } else {
+                const float* row = pass == B_XS ? fk + (size_t)cai[al] * R.fcp_nd + cd0[al]
+                                                : C.b.u + (size_t)(a0 + al) * R.stride;
+                cp_async4(st + e, in ? row + kk : row, in);
+            }
+        }
+        cp_async_commit();
+    };
+    // Partials of chunk a0 (in buffer b, bins landed) for this lane's run of 8 pixels.
+    auto gather = [&](int a0, int b, float* acc) {
+        const int nch = min(ACH, R.na - a0);
+        float* st = wstage + b * BUFB;
+        const int* cb = reinterpret_cast<const int*>(st + ACH * SBB);
+        const int* cc = cb + ACH;
+        const int* cs = cc + ACH;
+        const float* ciw = reinterpret_cast<const float*>(cs + ACH);
+        // bins times 1/w of their angle: the hat weights below are then max(0, 1 - d/w)
+        for (int e = lane; e < nch * SBB; e += 32) st[e] *= ciw[e / SBB];
+        __syncwarp();
+#pragma unroll
+        for (int p = 0; p < RUNB; ++p) acc[p] = 0.f;
+        for (int al = 0; al < nch; ++al) {
+            // weights max(0, 1 - d/w) of the two bins at distances f and 1 - f, f = mf 2^-23,
+            // one saturating FMA each
+            const float iw = ciw[al];
+            const float iws = iw * 1.1920928955078125e-07f, niws = -iws, omiw = 1.f - iw;
+            const int c = cc[al];
+            int K = cb[al] + lj0 * c - li * cs[al];
+            const float* srow = st + al * SBB;
+#pragma unroll
+            for (int p = 0; p < RUNB; ++p) {
+                const int kl = chk(K >> 23, 0, SBB - 1, CHK_REGION_GATHER);
+                const float mf = frac_int<23>(K);
+                const float w0 = fma_sat(mf, niws, 1.f);
+                const float w1 = fma_sat(mf, iws, omiw);
+                acc[p] = fmaf(w0, srow[kl], fmaf(w1, srow[kl + 1], acc[p]));
+                K += c;
+            }
+        }
+    };
+    // The pass's update of box pixel (gi, gj) from its gather acc.
+    auto update = [&](int gi, int gj, float acc) {
+        const int o = gi * nx + gj;
+        if (pass == B_XS) {
+            C.b.vy[o] = acc;  // x_s^k
+        } else if (R.reg >= 3) {  // z = x_s + x_L - alpha W_L^T W_L x_L, disc added (FISTA-TV, Haar-ISTA)
+            C.b.vx[o] = C.b.vy[o] + C.b.x[o] + acc + disc_value(R, gi, gj);
+        } else if (R.reg == 2) {  // Alg. method, x >= 0 on the final image (disc added back)
+            const float xs = C.b.vy[o];
+            const float sv = xs + C.b.x[o] + acc;  // acc = -alpha W_L^T W_L y
+            const float sh = disc_value(R, gi, gj);
+            const float xv = fmaxf(sv + sh, 0.f) - sh;
+            const float yn = xv - xs;
+            C.b.x[o] = yn;
+            C.b.vx[o] = xv;
+            const auto ys = from_f32<DT>(yn);
+            xa[gi * C.lda + gj] = ys;
+            xaT[gj * C.ldaT + gi] = ys;
+        } else if (pass == B_COLSUM) {
+            if (R.reg == 0) {
+                C.b.tau[o] = acc > 1e-3f ? 1.f / acc : 0.f;
+            } else {
+                const int cnt = (gj < nx - 1) + (gj > 0) + (gi < ny - 1) + (gi > 0);
+                C.b.tau[o] = 1.f / (acc + (float)cnt);
+            }
+        } else if (R.reg == 0) {  // x in float; the projector reads its stored copy
+            const float step = R.weighting ? C.b.tau[o] : R.alpha;
+            float xn = fmaf(step, acc, C.b.x[o]);
+            xn = fmaxf(xn, 0.f);
+            C.b.x[o] = xn;
+            const auto xs = from_f32<DT>(xn);
+            xa[gi * C.lda + gj] = xs;
+            xaT[gj * C.ldaT + gi] = xs;
+        } else {
+            float dv = 0.f;
+            if (gj < nx - 1) dv += C.b.vx[o];
+            if (gj > 0) dv -= C.b.vx[o - 1];
+            if (gi < ny - 1) dv += C.b.vy[o];
+            if (gi > 0) dv -= C.b.vy[o - nx];
+            const float xo = C.b.x[o];
+            const float xn = xo - C.b.tau[o] * (acc - dv);
+            C.b.x[o] = xn;
+            const auto xb = from_f32<DT>(2.f * xn - xo);
+            xa[gi * C.lda + gj] = xb;
+            xaT[gj * C.ldaT + gi] = xb;
+        }
+    };
+
+    const int my_tiles = tm < tiles ? (tiles - tm + ts - 1) / ts : 0;
+    unsigned dyn_bytes;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_bytes));
+    const int room = (int)(dyn_bytes / sizeof(float)) - BNW * WARP_STAGE;  // floats past the warp areas
+    if (my_tiles > 0 && 2 * my_tiles <= nchunks && nchunks * TB * TB <= room) {
+        // ---- cooperative: every warp of the block on each of its tiles in turn
+        float* part = wstage - warp * WARP_STAGE + BNW * WARP_STAGE;  // [nchunks][TB * TB]
+        for (int i = 0; i < my_tiles; ++i) {
+            const int t = tm + i * ts;
+            const int tile_x0 = (t % tiles_x) * TB, tile_y0 = (t / tiles_x) * TB;
+            const float xi_t = (float)tile_x0 + 0.5f * (TB - 1) - 0.5f * (float)(nx - 1);
+            const float eta_t = 0.5f * (float)(ny - 1) - ((float)tile_y0 + 0.5f * (TB - 1));
+            for (int c = warp; c < nchunks; c += BNW) {
+                __syncwarp();  // this warp's buffer is free
+                stage(xi_t, eta_t, c * ACH, 0);
+                cp_async_wait_group<0>();
+                __syncwarp();
+                float acc[RUNB];
+                gather(c * ACH, 0, acc);
+#pragma unroll
+                for (int p = 0; p < RUNB; ++p) part[c * (TB * TB) + li * TB + lj0 + p] = acc[p];
+            }
+            __syncthreads();
+            if (threadIdx.x < TB * TB) {  // one thread per pixel: the chunks in order
+                const int px = threadIdx.x;
+                float sum = 0.f, cmp = 0.f;
+                for (int c = 0; c < nchunks; ++c) neu_add(sum, cmp, part[c * (TB * TB) + px]);
+                const int gi = tile_y0 + px / TB, gj = tile_x0 + px % TB;
+                if (gi < ny && gj < nx) update(gi, gj, sum + cmp);
+            }
+            __syncthreads();  // the partials area is reused by the next tile
+        }
+        return;
+    }
+    // ---- per warp
+    for (int i = warp;;) {
         const int t = tm + i * ts;
         if (t >= tiles) break;
         const int tile_x0 = (t % tiles_x) * TB, tile_y0 = (t / tiles_x) * TB;
         const float xi_t = (float)tile_x0 + 0.5f * (TB - 1) - 0.5f * (float)(nx - 1);
         const float eta_t = 0.5f * (float)(ny - 1) - ((float)tile_y0 + 0.5f * (TB - 1));
-        // Chunk a0 .. a0 + ACH - 1 into buffer b: the tile constants of each angle (one lane
-        // per angle), then the window bins by asynchronous copies (zero outside the window),
-        // so the next chunk's bins are in flight while this chunk is gathered.
-        // Buffer layout: bins [ACH][SBB] | base (Q.23) | c step | s step | 1/w | kbase | width |
-        // sinogram angle index | first window bin, ACH each.
-        auto stage = [&](int a0, int b) {
-            float* st = wstage + b * BUFB;
-            int* cb = reinterpret_cast<int*>(st + ACH * SBB);
-            int* cc = cb + ACH;
-            int* cs = cc + ACH;
-            float* ciw = reinterpret_cast<float*>(cs + ACH);
-            int* ckb = reinterpret_cast<int*>(ciw + ACH);
-            int* cwd = ckb + ACH;
-            int* cai = cwd + ACH;
-            int* cd0 = cai + ACH;
-            const int nch = min(ACH, R.na - a0);
-            if (lane < nch) {
-                const AngleRec& r = R.rec[a0 + lane];
-                ff kt = ff_add(ff_mul_f(xi_t, r.c), ff_mul_f(eta_t, r.s));
-                kt = ff_add(kt, ff{-r.phi.hi, -r.phi.lo});
-                const int kbase = (int)floorf(kt.hi) - KOFFB;
-                kt = ff_add(kt, ff{-(float)kbase, 0.f});
-                kt = ff_add(kt, ff_mul_f(-0.5f * (TB - 1), r.c));
-                kt = ff_add(kt, ff_mul_f(0.5f * (TB - 1), r.s));
-                cb[lane] = to_fixed<23>(kt);
-                cc[lane] = r.c_q23;
-                cs[lane] = r.s_q23;
-                ciw[lane] = r.inv_w;
-                ckb[lane] = kbase;
-                cwd[lane] = r.width;
-                cai[lane] = r.aidx;
-                cd0[lane] = r.d0;
-            }
-            __syncwarp();
-            for (int e = lane; e < nch * SBB; e += 32) {
-                const int al = e / SBB, kk = ckb[al] + (e - al * SBB);
-                const bool in = kk >= 0 && kk < cwd[al];
-                if (pass == B_COLSUM) {
-                    st[e] = in ? 1.f : 0.f;
-                } else {
-                    const float* row = pass == B_XS ? fk + (size_t)cai[al] * R.fcp_nd + cd0[al]
-                                                    : C.b.u + (size_t)(a0 + al) * R.stride;
-                    cp_async4(st + e, in ? row + kk : row, in);
-                }
-            }
-            cp_async_commit();
-        };
         float sum[RUNB], cmp[RUNB];
 #pragma unroll
         for (int p = 0; p < RUNB; ++p) sum[p] = cmp[p] = 0.f;
         __syncwarp();  // the previous tile's reads of both buffers are done
-        stage(0, 0);
+        stage(xi_t, eta_t, 0, 0);
         for (int a0 = 0, b = 0; a0 < R.na; a0 += ACH, b ^= 1) {
-            const int nch = min(ACH, R.na - a0);
             if (a0 + ACH < R.na) {
-                stage(a0 + ACH, b ^ 1);
-                cp_async_wait_group<1>();  // this chunk's copies have landed (the next may fly)
+                stage(xi_t, eta_t, a0 + ACH, b ^ 1);  // the next chunk's bins fly while this one is gathered
+                cp_async_wait_group<1>();               // this chunk's copies have landed
             } else {
                 cp_async_wait_group<0>();
             }
             __syncwarp();
-            float* st = wstage + b * BUFB;
-            const int* cb = reinterpret_cast<const int*>(st + ACH * SBB);
-            const int* cc = cb + ACH;
-            const int* cs = cc + ACH;
-            const float* ciw = reinterpret_cast<const float*>(cs + ACH);
-            // bins times 1/w of their angle: the hat weights below are then max(0, 1 - d/w)
-            for (int e = lane; e < nch * SBB; e += 32) st[e] *= ciw[e / SBB];
-            __syncwarp();
             float acc[RUNB];
-#pragma unroll
-            for (int p = 0; p < RUNB; ++p) acc[p] = 0.f;
-            for (int al = 0; al < nch; ++al) {
-                // weights max(0, 1 - d/w) of the two bins at distances f and 1 - f, f = mf 2^-23,
-                // one saturating FMA each
-                const float iw = ciw[al];
-                const float iws = iw * 1.1920928955078125e-07f, niws = -iws, omiw = 1.f - iw;
-                const int c = cc[al];
-                int K = cb[al] + lj0 * c - li * cs[al];
-                const float* srow = st + al * SBB;
-#pragma unroll
-                for (int p = 0; p < RUNB; ++p) {
-                    const int kl = chk(K >> 23, 0, SBB - 1, CHK_REGION_GATHER);
-                    const float mf = frac_int<23>(K);
-                    const float w0 = fma_sat(mf, niws, 1.f);
-                    const float w1 = fma_sat(mf, iws, omiw);
-                    acc[p] = fmaf(w0, srow[kl], fmaf(w1, srow[kl + 1], acc[p]));
-                    K += c;
-                }
-            }
+            gather(a0, b, acc);
 #pragma unroll
             for (int p = 0; p < RUNB; ++p) neu_add(sum[p], cmp[p], acc[p]);
             __syncwarp();  // buffer b is refilled by the chunk after next
         }
-        // epilogue for this lane's pixels
+        // update of this lane's pixels
         const int gi = tile_y0 + li;
 #pragma unroll
         for (int p = 0; p < RUNB; ++p) {
             const int gj = tile_x0 + lj0 + p;
-            if (gi >= ny || gj >= nx) continue;
-            const float acc = sum[p] + cmp[p];
-            const int o = gi * nx + gj;
-            if (pass == B_XS) {
-                C.b.vy[o] = acc;  // x_s^k
-            } else if (R.reg >= 3) {  // z = x_s + x_L - alpha W_L^T W_L x_L, disc added (FISTA-TV, Haar-ISTA)
-                C.b.vx[o] = C.b.vy[o] + C.b.x[o] + acc + disc_value(R, gi, gj);
-            } else if (R.reg == 2) {  // Alg. method, x >= 0 on the final image (disc added back)
-                const float xs = C.b.vy[o];
-                const float sv = xs + C.b.x[o] + acc;  // acc = -alpha W_L^T W_L y
-                const float sh = disc_value(R, gi, gj);
-                const float xv = fmaxf(sv + sh, 0.f) - sh;
-                const float yn = xv - xs;
-                C.b.x[o] = yn;
-                C.b.vx[o] = xv;
-                const auto ys = from_f32<DT>(yn);
-                xa[gi * C.lda + gj] = ys;
-                xaT[gj * C.ldaT + gi] = ys;
-            } else if (pass == B_COLSUM) {
-                if (R.reg == 0) {
-                    C.b.tau[o] = acc > 1e-3f ? 1.f / acc : 0.f;
-                } else {
-                    const int cnt = (gj < nx - 1) + (gj > 0) + (gi < ny - 1) + (gi > 0);
-                    C.b.tau[o] = 1.f / (acc + (float)cnt);
-                }
-            } else if (R.reg == 0) {  // x in float; the projector reads its stored copy
-                const float step = R.weighting ? C.b.tau[o] : R.alpha;
-                float xn = fmaf(step, acc, C.b.x[o]);
-                xn = fmaxf(xn, 0.f);
-                C.b.x[o] = xn;
-                const auto xs = from_f32<DT>(xn);
-                xa[gi * C.lda + gj] = xs;
-                xaT[gj * C.ldaT + gi] = xs;
-            } else {
-                float dv = 0.f;
-                if (gj < nx - 1) dv += C.b.vx[o];
-                if (gj > 0) dv -= C.b.vx[o - 1];
-                if (gi < ny - 1) dv += C.b.vy[o];
-                if (gi > 0) dv -= C.b.vy[o - nx];
-                const float xo = C.b.x[o];
-                const float xn = xo - C.b.tau[o] * (acc - dv);
-                C.b.x[o] = xn;
-                const auto xb = from_f32<DT>(2.f * xn - xo);
-                xa[gi * C.lda + gj] = xb;
-                xaT[gj * C.ldaT + gi] = xb;
-            }
+            if (gi < ny && gj < nx) update(gi, gj, sum[p] + cmp[p]);
         }
         int nxt = 0;
         if (lane == 0) nxt = atomicAdd(counter, 1);

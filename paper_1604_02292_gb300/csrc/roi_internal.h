@@ -456,7 +456,7 @@ struct SinoView {
 
 int sino_view(::roi_recon* h, SinoView* v, std::string* msg);
 
-size_t batch_smem_bytes(size_t max_stage_bytes);
+size_t batch_smem_bytes(size_t max_stage_bytes, int na);
 cudaError_t launch_batch(const BatchArgs& B, int blocks, size_t smem, cudaStream_t st);
 
 // ---- check build (-DROI_CHECK): index checks of the hot kernels, one report per
