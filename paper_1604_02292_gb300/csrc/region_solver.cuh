@@ -12,19 +12,22 @@
 //     phase A  forward W_L: warps take 32-ray units (one angle); a warp sums whole rays
 //              (fixed point along the ray) and fuses the residual (SIRT) or data-dual
 //              (CP) update; CP also updates the gradient dual on every pixel;
-//     phase B  back W_L^T: warps take 16 x 16 pixel tiles; a lane owns a run of 8
-//              pixels, angles are streamed in chunks of 16 (per-warp staging of the
-//              window bins), and the lane applies the primal update to its pixels.
+//     phase B  back W_L^T: 16 x 16 pixel tiles; a lane owns a run of 8 pixels, angles
+//              are streamed in chunks of 16 through per-warp staging buffers, a pixel's
+//              gather is the chunk partials added in chunk order, and the pixel's primal
+//              update follows.  Warps take whole tiles, or, in a block with few tiles,
+//              all warps share each tile by chunks (same operations, same bits).
 // The units and tiles of a phase are dealt round-robin to the blocks of the team and
-// picked up dynamically by the warps of a block.  Every ray and every tile is computed
-// by one warp in a fixed order, so a region's result is bit-identical whatever team
-// solves it, whatever else runs beside it and however the work is dealt.
+// picked up dynamically by the warps of a block.  Every ray and every chunk of a tile is
+// computed by one warp in a fixed order, so a region's result is bit-identical whatever
+// team solves it, whatever else runs beside it and however the work is dealt.
 //
-// A team of one block synchronises with __syncthreads and may stage the box image in
-// shared memory (one TMA bulk copy per branch and iteration); larger teams read the
-// image from global memory and meet at a barrier counter with bounded waits.  Data
-// written by one block of a team and read by another is ordered by that barrier's
-// release / acquire at GPU scope.
+// How phase A reads the box image depends on the box size alone (stage_mode): every block
+// stages it whole in shared memory (one TMA bulk copy per branch and iteration), streams
+// it in bands, or reads it from global memory.  A team of one block synchronises with
+// __syncthreads; larger teams meet at a barrier counter with bounded waits.  Data written
+// by one block of a team and read by another is ordered by that barrier's release /
+// acquire at GPU scope.
 #pragma once
 
 #include <cuda_runtime.h>
