@@ -80,6 +80,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true", help="default workload: skip the serving comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-global", action="store_true", help="default workload: skip the local-vs-global report")
     return ap.parse_args()
 
 
@@ -373,6 +374,36 @@ def run_ours(args):
         e2e = {"value": shard.throughput(ke, ws, te), "unit": "solves/s", "h2d_bytes_per_step": int(p_host.nbytes),
                "d2h_bytes_per_step": int(outs_h[0].nbytes), "steps": ke}
 
+    # ---- local vs global regularized solve inside the ROI disk (reported, not a parity claim):
+    # the same solver, lambda and iterations on a box covering the whole grid
+    local_global = None
+    if rank == 0 and not args.no_global:
+        N = w.N
+        glob_region = (0.5 * (N - 1), 0.5 * (N - 1), 0.7072 * N + 1.0, 0.0)
+        with torch.cuda.stream(stream):
+            rr.set_sinogram(p_dev)
+            rr.fbp()
+            t0 = time.perf_counter()
+            xg, ginfo = rr.solve_local(glob_region, reg, iters=w.iters, lam=w.lam)
+            torch.cuda.synchronize()
+            t_glob = time.perf_counter() - t0
+            xl, linfo = rr.solve_local(regions[0], reg, iters=w.iters, lam=w.lam)
+        torch.cuda.synchronize()
+        xg, xl = xg.cpu().numpy(), xl.cpu().numpy()
+        cx, cy, r, _ = regions[0]
+        ii, jj = np.meshgrid(np.arange(linfo.box_h) + linfo.box_y0, np.arange(linfo.box_w) + linfo.box_x0,
+                             indexing="ij")
+        inside = (jj - cx) ** 2 + (ii - cy) ** 2 <= r * r
+        a = xl[inside].astype(np.float64)
+        b = xg[ii[inside] - ginfo.box_y0, jj[inside] - ginfo.box_x0].astype(np.float64)
+        local_global = {"rel_l2_in_roi": float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)),
+                        "mean_in_roi": [float(a.mean()), float(b.mean())],
+                        "max_abs_in_roi": [float(np.abs(a).max()), float(np.abs(b).max())],
+                        "global_box": [ginfo.box_x0, ginfo.box_y0, ginfo.box_w, ginfo.box_h],
+                        "global_solve_s": t_glob, "solver": w.reg, "iters": w.iters, "lambda": w.lam,
+                        "note": "report only (local, global): at this lambda the data term dominates and "
+                                "both iterates amplify noise, the local one more"}
+
     # ---- serving on the 2048 x 2048 serving workload: continuous batching vs one at a time
     serving = None
     if not args.no_serving:
@@ -418,6 +449,7 @@ def run_ours(args):
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "local_vs_global": local_global,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)
