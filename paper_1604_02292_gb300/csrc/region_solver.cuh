@@ -380,11 +380,13 @@ __device__ __forceinline__ void phase_b(const Ctx& C, const Team& T, int pass, i
         }
     };
 
+    // (the single-block batch kernel, SOLO, keeps the per-warp schedule only: the same bits,
+    // and fewer registers live in its loops)
     const int my_tiles = tm < tiles ? (tiles - tm + ts - 1) / ts : 0;
     unsigned dyn_bytes;
     asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_bytes));
     const int room = (int)(dyn_bytes / sizeof(float)) - BNW * WARP_STAGE;  // floats past the warp areas
-    if (my_tiles > 0 && 2 * my_tiles <= nchunks && nchunks * TB * TB <= room) {
+    if (!SOLO && my_tiles > 0 && 2 * my_tiles <= nchunks && nchunks * TB * TB <= room) {
         // ---- cooperative: every warp of the block on each of its tiles in turn
         float* part = wstage - warp * WARP_STAGE + BNW * WARP_STAGE;  // [nchunks][TB * TB]
         for (int i = 0; i < my_tiles; ++i) {
