@@ -9,7 +9,7 @@
 //            with four TMA bulk copies (the rows of the four ray segments) and runs the
 //            ray-driven forward W_L on its share of (angle, 32-ray) units, fusing
 //            r = p' - W_L x  (SIRT)  or  u <- (u + sigma (W_L xbar - p'))/(1 + sigma/2)
-//            (CP); for CP eight warps first update the gradient dual
+//            (CP); for CP four warps first update the gradient dual
 //            v <- proj_lambda(v + sigma_v grad xbar)  on the block's share of pixels
 //            while the first copies are in flight;
 //   barrier
@@ -52,7 +52,7 @@ constexpr int NWARP = PT / 32;
 constexpr int RAYS = 32;                 // rays per unit (one warp-wide ray group)
 constexpr int FSEG = 4;                  // segments per ray in phase A
 constexpr int CHUNK_UNITS = 16;          // phase A units whose partials are held at once
-constexpr int DG_WARPS = 8;              // warps that update the gradient dual while the others project
+constexpr int DG_WARPS = 4;              // warps that update the gradient dual while the others project
 constexpr int SEGA = 48;                 // samples per float-float anchor
 constexpr int MAXUNITS = 512;            // phase A units per block (checked by the host)
 constexpr int NBUCKET = 512;             // cost classes of the phase A balancing sort
