@@ -81,6 +81,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-global", action="store_true", help="default workload: skip the local-vs-global report")
+    ap.add_argument("--no-batch", action="store_true", help="default workload: skip the batching figure")
+    ap.add_argument("--no-precision", action="store_true", help="default workload: skip the precision figure")
+    ap.add_argument("--rates", default="50,100,150",
+                    help="default workload: arrival rates (requests/s) of the sustainable-rate serving points")
     return ap.parse_args()
 
 
@@ -198,9 +202,9 @@ def bytes_per_launch(pl, w):
 
 # --------------------------------------------------------------------------- oracle arm
 
-def oracle_sample(w, p, region, cp_iters):
-    """Time the FP64 oracle: FBP + exterior + cp_iters CP iterations; returns seconds per
-    whole solve (CP time scaled to w.iters) and the parts."""
+def oracle_solve(w, p, region):
+    """Time one whole FP64 oracle solve: FBP + exterior + all w.iters iterations; returns
+    (seconds, (fbp, exterior, iterations))."""
     import oracle
     g = oracle.Geometry(*w.geometry())
     box = oracle.roi_box(w.N, *region)
@@ -210,12 +214,19 @@ def oracle_sample(w, p, region, cp_iters):
     pp = oracle.exterior(g, box, p.astype(np.float64), xf)
     t2 = time.perf_counter()
     if w.reg == "sirt":
-        oracle.sirt(g, box, pp, cp_iters)
+        oracle.sirt(g, box, pp, w.iters)
     else:
-        oracle.cp_tv(g, box, pp, cp_iters, w.lam, precond=1)
+        oracle.cp_tv(g, box, pp, w.iters, w.lam, precond=1)
     t3 = time.perf_counter()
-    per_solve = (t1 - t0) + (t2 - t1) + (t3 - t2) * (w.iters / cp_iters)
-    return per_solve, (t1 - t0, t2 - t1, t3 - t2)
+    return t3 - t0, (t1 - t0, t2 - t1, t3 - t2)
+
+
+def oracle_warm(w, p, region):
+    """Untimed warm-up of the oracle: FBP and exterior step (threads started, pages touched)."""
+    import oracle
+    g = oracle.Geometry(*w.geometry())
+    xf = oracle.fbp(g, p.astype(np.float64))
+    oracle.exterior(g, oracle.roi_box(w.N, *region), p.astype(np.float64), xf)
 
 
 def omp_threads():
@@ -224,23 +235,28 @@ def omp_threads():
 
 
 def run_reference(args):
+    """The FP64 oracle on the host cores, on our arm's workload: every timed step is one
+    whole local solve (FBP + exterior + all iterations) of one region, measured, nothing
+    scaled; warm-up steps run the oracle's FBP and exterior step only."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
     w = WL.WORKLOADS[args.workload]
     p = WL.sinogram(w, 0)
     regions = [WL.region(w, seed=s) for s in range(N_REGIONS)]
-    cp_iters = 25
     for k in range(args.warmup):
-        oracle_sample(w, p, regions[k % N_REGIONS], 2)
-    times = []
+        oracle_warm(w, p, regions[k % N_REGIONS])
+    times, parts = [], []
     for k in range(args.steps):
-        t, _ = oracle_sample(w, p, regions[k % N_REGIONS], cp_iters)
+        t, pt = oracle_solve(w, p, regions[k % N_REGIONS])
         times.append(t)
+        parts.append(pt)
     total = sum(times)
     value = args.steps / total
-    sample = (f"each step: oracle FBP + exterior + {cp_iters} of {w.iters} CP iterations on one region, "
-              f"CP time scaled by {w.iters}/{cp_iters}")
+    mean = [statistics.mean(x[i] for x in parts) for i in range(3)]
+    sample = (f"each step: one whole oracle solve of one region (FBP {mean[0]:.2f} s + exterior {mean[1]:.2f} s + "
+              f"{w.iters} {'CP' if w.reg == 'tv' else 'SIRT'} iterations {mean[2]:.2f} s, means), measured; "
+              f"warm-up steps: FBP + exterior only")
     line = {
         "impl": "reference", "metric": "roi_solves_per_s", "value": value, "unit": "solves/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
@@ -251,12 +267,43 @@ def run_reference(args):
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": omp_threads(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "timed_s": total,
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
 # ------------------------------------------------------------------------------ our arm
+
+def local_vs_global(rr, w, p_dev, region, reg, stream):
+    """The regularized local solve of `region` against the same solver, lambda and
+    iterations on a box covering the whole grid, inside the ROI disk (report only)."""
+    import torch
+
+    N = w.N
+    glob_region = (0.5 * (N - 1), 0.5 * (N - 1), 0.7072 * N + 1.0, 0.0)
+    with torch.cuda.stream(stream):
+        rr.set_sinogram(p_dev)
+        rr.fbp()
+        t0 = time.perf_counter()
+        xg, ginfo = rr.solve_local(glob_region, reg, iters=w.iters, lam=w.lam)
+        torch.cuda.synchronize()
+        t_glob = time.perf_counter() - t0
+        xl, linfo = rr.solve_local(region, reg, iters=w.iters, lam=w.lam)
+    torch.cuda.synchronize()
+    xg, xl = xg.cpu().numpy(), xl.cpu().numpy()
+    cx, cy, r, _ = region
+    ii, jj = np.meshgrid(np.arange(linfo.box_h) + linfo.box_y0, np.arange(linfo.box_w) + linfo.box_x0,
+                         indexing="ij")
+    inside = (jj - cx) ** 2 + (ii - cy) ** 2 <= r * r
+    a = xl[inside].astype(np.float64)
+    b = xg[ii[inside] - ginfo.box_y0, jj[inside] - ginfo.box_x0].astype(np.float64)
+    return {"rel_l2_in_roi": float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)),
+            "mean_in_roi": [float(a.mean()), float(b.mean())],
+            "max_abs_in_roi": [float(np.abs(a).max()), float(np.abs(b).max())],
+            "global_box": [ginfo.box_x0, ginfo.box_y0, ginfo.box_w, ginfo.box_h],
+            "global_solve_s": t_glob, "solver": w.reg, "iters": w.iters, "lambda": w.lam}
+
 
 def run_ours(args):
     import torch
@@ -375,51 +422,65 @@ def run_ours(args):
                "d2h_bytes_per_step": int(outs_h[0].nbytes), "steps": ke}
 
     # ---- local vs global regularized solve inside the ROI disk (reported, not a parity claim):
-    # the same solver, lambda and iterations on a box covering the whole grid
+    # the same solver, lambda and iterations on a box covering the whole grid; on the noisy
+    # workload sinogram and on the noise-free analytic sinogram of the same phantom
     local_global = None
     if rank == 0 and not args.no_global:
-        N = w.N
-        glob_region = (0.5 * (N - 1), 0.5 * (N - 1), 0.7072 * N + 1.0, 0.0)
-        with torch.cuda.stream(stream):
-            rr.set_sinogram(p_dev)
-            rr.fbp()
-            t0 = time.perf_counter()
-            xg, ginfo = rr.solve_local(glob_region, reg, iters=w.iters, lam=w.lam)
-            torch.cuda.synchronize()
-            t_glob = time.perf_counter() - t0
-            xl, linfo = rr.solve_local(regions[0], reg, iters=w.iters, lam=w.lam)
-        torch.cuda.synchronize()
-        xg, xl = xg.cpu().numpy(), xl.cpu().numpy()
-        cx, cy, r, _ = regions[0]
-        ii, jj = np.meshgrid(np.arange(linfo.box_h) + linfo.box_y0, np.arange(linfo.box_w) + linfo.box_x0,
-                             indexing="ij")
-        inside = (jj - cx) ** 2 + (ii - cy) ** 2 <= r * r
-        a = xl[inside].astype(np.float64)
-        b = xg[ii[inside] - ginfo.box_y0, jj[inside] - ginfo.box_x0].astype(np.float64)
-        local_global = {"rel_l2_in_roi": float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)),
-                        "mean_in_roi": [float(a.mean()), float(b.mean())],
-                        "max_abs_in_roi": [float(np.abs(a).max()), float(np.abs(b).max())],
-                        "global_box": [ginfo.box_x0, ginfo.box_y0, ginfo.box_w, ginfo.box_h],
-                        "global_solve_s": t_glob, "solver": w.reg, "iters": w.iters, "lambda": w.lam,
-                        "note": "report only (local, global): at this lambda the data term dominates and "
-                                "both iterates amplify noise, the local one more"}
+        local_global = local_vs_global(rr, w, p_dev, regions[0], reg, stream)
+        local_global["note"] = ("report only (local, global): at this lambda the data term dominates and "
+                                "both iterates amplify noise, the local one more")
+        p_clean = torch.from_numpy(WL.sinogram(w, seed=rank, noise=False)).cuda()
+        local_global["noise_free"] = local_vs_global(rr, w, p_clean, regions[0], reg, stream)
 
-    # ---- serving on the 2048 x 2048 serving workload: continuous batching vs one at a time
+    # ---- serving on the 2048 x 2048 serving workload: continuous batching vs one at a time,
+    # in overload (the workload's 2000 requests/s) and at sustainable rates
     serving = None
     if not args.no_serving:
         serving = serve_measure(args, args.requests, dist, ws, rank, local, clock=False)
         serving.pop("w")
         serving.pop("clocks")
+        pts = []
+        for r in [float(v) for v in args.rates.split(",") if v.strip()]:
+            m = serve_measure(args, args.requests, dist, ws, rank, local, clock=False, rate=r)
+            pts.append({"rate_per_s": r, "value": m["value"], "latency_ms": m["latency_ms"],
+                        "plain": m["plain"], "kernel_launches": m["server"]["kernel_launches"]})
+        serving["rates"] = pts
 
-    # ---- CPU baseline: the oracle on a bounded sample (rank 0, one GPU only)
+    # ---- batching on the 2048 x 2048 batch workload: all 4096 regions in one persistent launch
+    batch = None
+    if not args.no_batch:
+        wb = WL.BATCHES["roi_batch_2048"]
+        batch = batch_measure(wb, None, 1, 1, dist, ws, rank, local, clock=False)
+        batch.pop("clocks")
+        batch.update({"workload": wb.name, "N": wb.N, "n_angles": wb.n_angles, "n_det": wb.n_det,
+                      "radius": [wb.r_lo, wb.r_hi], "iters": wb.iters, "solvers": "SIRT/TV 50/50",
+                      "timing": "CUDA events around one solve_batch call (one persistent launch)"})
+
+    # ---- precision on the 4096 x 4096 precision workload: one wave of regions (one per team
+    # of 8 blocks), bfloat16 sinogram with float32 images and with bfloat16 images
+    precision = None
+    if rank == 0 and not args.no_precision:
+        wp = WL.PRECISION["roi_precision_4096"]
+        teams = N_SM // 8
+        precision = precision_measure(wp, teams, "bf16", 8, teams, local, clock=False)
+        precision.pop("clocks")
+        precision.update({"workload": wp.name, "N": wp.N, "n_angles": wp.n_angles, "n_det": wp.n_det,
+                          "iters": wp.iters, "solver": "CP-TV", "lambda": wp.lam, "I0": wp.I0})
+
+    # ---- CPU baseline: whole oracle solves, measured (rank 0, one GPU only), until about
+    # ten seconds of work
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cp_iters = 50
-        per_solve, parts = oracle_sample(w, p_host, regions[0], cp_iters)
-        cpu = {"value": 1.0 / per_solve, "unit": "solves/s", "cores": omp_threads(), "kind": "oracle",
-               "sample": (f"one region: FP64 oracle FBP ({parts[0]:.2f} s) + exterior ({parts[1]:.2f} s) + "
-                          f"{cp_iters} of {w.iters} CP iterations ({parts[2]:.2f} s), CP time scaled by "
-                          f"{w.iters}/{cp_iters}")}
+        ts, pts = [], []
+        while not ts or (sum(ts) < 10.0 and len(ts) < N_REGIONS):
+            t, pt = oracle_solve(w, p_host, regions[len(ts)])
+            ts.append(t)
+            pts.append(pt)
+        mean = [statistics.mean(x[i] for x in pts) for i in range(3)]
+        cpu = {"value": len(ts) / sum(ts), "unit": "solves/s", "cores": omp_threads(), "kind": "oracle",
+               "sample": (f"{len(ts)} whole FP64 oracle solve(s) of the workload's regions, measured: FBP "
+                          f"{mean[0]:.2f} s + exterior {mean[1]:.2f} s + {w.iters} iterations {mean[2]:.2f} s "
+                          f"(means)")}
 
     if rank == 0:
         sm = sorted(step_ms)
@@ -451,6 +512,8 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "local_vs_global": local_global,
             "serving": serving,
+            "batch": batch,
+            "precision": precision,
         }
         print(json.dumps(line), flush=True)
     rr.close()
@@ -459,12 +522,65 @@ def run_ours(args):
     return 0
 
 
-def run_batch(args):
-    """Batch workload: one step = roi_recon_solve_batch over the regions (one batched exterior
-    projection + one persistent launch); value = regions solved per second."""
+def batch_measure(w, count, steps, warmup, dist, ws, rank, local, clock=True):
+    """Batched solves: one step = roi_recon_solve_batch over the regions (one persistent
+    launch); the warm-up steps run every region for one iteration (same boxes, so the same
+    device slots).  Returns regions/s over all ranks, the per-step times and the lerps/s of
+    rank 0 against the derived ceiling."""
     import torch
 
     import paper_1604_02292_gb300 as R
+
+    p = WL.sinogram(w, seed=0)
+    all_items = WL.batch_regions(w, seed=0, count=count)
+    share = shard.assign([shard.region_cost(r, prm["iters"], w.n_angles) for r, prm in all_items], ws)[rank]
+    items = [all_items[i] for i in share]
+    regions = [r for r, _ in items]
+    params = [prm for _, prm in items]
+    warm = [dict(prm, iters=1) for prm in params]
+    stream = torch.cuda.Stream()
+    rr = R.RoiRecon(*w.geometry(), stream=stream)
+    outs = None
+    with torch.cuda.stream(stream):
+        rr.set_sinogram(torch.from_numpy(p).cuda())
+        rr.fbp()
+        for _ in range(warmup):
+            outs, _ = rr.solve_batch(regions, warm, outs)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    if dist:
+        dist.barrier()
+    n0 = R.roi_recon_launch_count()
+    with ClockSampler(local if clock else None) as clk:
+        with torch.cuda.stream(stream):
+            for k in range(steps):
+                ev[k][0].record(stream)
+                outs, _ = rr.solve_batch(regions, params, outs)
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    rr.sync()
+    launches = int(R.roi_recon_launch_count() - n0)
+    ms = [a.elapsed_time(b) for a, b in ev]
+    n_lerps = 0
+    for reg, prm in items:
+        pl = rr.plan(reg)
+        nx, ny = pl.box[2], pl.box[3]
+        n_lerps += prm["iters"] * (sum(pl.width) * max(nx, ny) + nx * ny * w.n_angles)
+    rr.close()
+    t_mine = sum(ms) / 1e3
+    t = shard.max_over_ranks(t_mine, dist, device="cuda")
+    pk, pk_src = peaks()
+    peak = N_SM * LERPS_PER_CLK_SM * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e9
+    achieved = n_lerps * steps / t_mine / 1e9
+    return {"value": len(all_items) * steps / t, "unit": "solves/s", "regions": len(all_items), "steps": steps,
+            "ms_per_step": statistics.mean(ms), "gpu_launches": launches,
+            "projector_Glerp_s_rank0": achieved, "lerp_ceiling_Glerp_s": peak, "frac_of_ceiling": achieved / peak,
+            "clocks": clk.summary()}
+
+
+def run_batch(args):
+    """Batch workload line (see batch_measure); value = regions solved per second."""
+    import torch
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -473,54 +589,21 @@ def run_batch(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     w = WL.BATCHES[args.workload]
-    p = WL.sinogram(w, seed=0)
-    all_items = WL.batch_regions(w, seed=0, count=args.batch_count)
-    share = shard.assign([shard.region_cost(r, prm["iters"], w.n_angles) for r, prm in all_items], ws)[rank]
-    items = [all_items[i] for i in share]
-    regions = [r for r, _ in items]
-    params = [prm for _, prm in items]
-    stream = torch.cuda.Stream()
-    rr = R.RoiRecon(*w.geometry(), stream=stream)
-    outs = None
-    with torch.cuda.stream(stream):
-        rr.set_sinogram(torch.from_numpy(p).cuda())
-        rr.fbp()
-        for _ in range(args.warmup):
-            outs, _ = rr.solve_batch(regions, params, outs)
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    n0 = R.roi_recon_launch_count()
-    with ClockSampler(local) as clk:
-        with torch.cuda.stream(stream):
-            for k in range(args.steps):
-                ev[k][0].record(stream)
-                outs, _ = rr.solve_batch(regions, params, outs)
-                ev[k][1].record(stream)
-        torch.cuda.synchronize()
-    rr.sync()
-    ms = [a.elapsed_time(b) for a, b in ev]
-    if dist:
-        dist.barrier()
-    n_lerps = 0
-    for reg, prm in items:
-        pl = rr.plan(reg)
-        nx, ny = pl.box[2], pl.box[3]
-        n_lerps += prm["iters"] * (sum(pl.width) * max(nx, ny) + nx * ny * w.n_angles)
-    t = shard.max_over_ranks(sum(ms) / 1e3, dist, device="cuda")
+    m = batch_measure(w, args.batch_count, args.steps, args.warmup, dist, ws, rank, local)
     line = {
-        "metric": "roi_solves_per_s", "value": len(all_items) * args.steps / t, "unit": "solves/s", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(ms), "higher_is_better": True,
+        "metric": "roi_solves_per_s", "value": m["value"], "unit": "solves/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
         "dtype": "f32", "data": "synthetic",
         "scaling": "strong",
-        "config": {"workload": w.name, "N": w.N, "n_angles": w.n_angles, "n_det": w.n_det, "regions": len(all_items),
+        "config": {"workload": w.name, "N": w.N, "n_angles": w.n_angles, "n_det": w.n_det, "regions": m["regions"],
                    "radius": [w.r_lo, w.r_hi], "iters": w.iters, "solvers": "SIRT/TV 50/50"},
-        "gpu_launches": int(R.roi_recon_launch_count() - n0),
-        "projector_Glerp_s_rank0": n_lerps * args.steps / t / 1e9,
-        "clocks": clk.summary(),
+        "gpu_launches": m["gpu_launches"],
+        "projector_Glerp_s_rank0": m["projector_Glerp_s_rank0"],
+        "frac_of_lerp_ceiling": m["frac_of_ceiling"],
+        "clocks": m["clocks"],
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
-    rr.close()
     if dist:
         dist.destroy_process_group()
     return 0
@@ -534,7 +617,7 @@ def _pct(v, q):
     return v[k]
 
 
-def serve_measure(args, count, dist, ws, rank, local, clock=True):
+def serve_measure(args, count, dist, ws, rank, local, clock=True, rate=None):
     """Serving run on the serving workload: the requests arrive by a seeded Poisson process
     and are submitted to the server (continuous batching over resident sinograms) at their
     arrival times; latency = completion seen on the host - arrival.  The same requests are
@@ -546,8 +629,9 @@ def serve_measure(args, count, dist, ws, rank, local, clock=True):
     import paper_1604_02292_gb300 as R
 
     w = WL.SERVING["roi_serve_2048"] if args.workload not in WL.SERVING else WL.SERVING[args.workload]
+    rate = args.rate if rate is None else rate
     reqs = WL.serve_requests(w, seed=0, count=count)
-    arr = WL.arrivals(w, seed=0, count=count, rate=args.rate)
+    arr = WL.arrivals(w, seed=0, count=count, rate=rate)
     mine = [i for i in range(count) if i % ws == rank]
     recons = []
     for k in range(w.n_sinos):
@@ -626,7 +710,7 @@ def serve_measure(args, count, dist, ws, rank, local, clock=True):
     for rr in recons:
         rr.close()
     return {
-        "workload": w.name, "requests": count, "rate_per_s": args.rate or w.rate, "value": count / t_served,
+        "workload": w.name, "requests": count, "rate_per_s": rate or w.rate, "value": count / t_served,
         "unit": "solves/s", "wall_s": t_served,
         "latency_ms": {"p50": _pct(lat, 50), "p99": _pct(lat, 99), "mean": statistics.mean(lat)},
         "plain": plain,
@@ -671,35 +755,33 @@ def run_serve(args):
     return 0
 
 
-def run_precision(args):
-    """Precision workload: the regions solved through the server (all by teams, submitted at
-    once) with 16-bit storage of the resident sinogram, FBP image and projector images;
-    value = regions/s of that run.  Errors per result, relative L2: against the float32-
-    storage path fed the same quantized sinogram (the error the 16-bit storage adds), and
-    against the float32 path on the unrounded sinogram (adds the rounding of the data)."""
+def precision_measure(w, count, storage, team_blocks, teams, local, clock=True):
+    """Precision workload: `count` regions solved through the server (all by teams of
+    team_blocks blocks, submitted at once) with the sinogram stored in `storage` ("bf16" or
+    "f16"), once with float32 images and once with the FBP and projector images stored in
+    `storage` too; then with float32 storage on the same quantized data and on the
+    unrounded data.  Errors per result, relative L2: each 16-bit run against the float32
+    run fed the same quantized sinogram (the error the storage adds), and against the
+    float32 run on the unrounded data (with the rounding of the data themselves)."""
     import torch
 
     import paper_1604_02292_gb300 as R
     from paper_1604_02292_gb300 import synth
 
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    w = WL.PRECISION[args.workload]
-    count = args.batch_count or 32
     items = WL.precision_regions(w, seed=0, count=count)
     phantom = synth.random_phantom(w.N, w.n_ellipses, texture=w.texture, seed=0)
     p = synth.poisson_noise(synth.analytic_sinogram(phantom, w.n_angles, w.n_det), w.I0, seed=1000).astype(np.float32)
-    st_code = {"f32": R.ROI_F32, "bf16": R.ROI_BF16, "f16": R.ROI_F16}[args.storage]
+    st_code = {"f32": R.ROI_F32, "bf16": R.ROI_BF16, "f16": R.ROI_F16}[storage]
     tdt = {R.ROI_F32: torch.float32, R.ROI_BF16: torch.bfloat16, R.ROI_F16: torch.float16}[st_code]
     p_dev = torch.from_numpy(p).cuda()
     p_q = p_dev.to(tdt)  # the quantized data, as the 16-bit handle stores it
 
-    def serve(storage, sino):
-        rr = R.RoiRecon(*w.geometry(), storage=storage)
+    def serve(sino_st, img_st, sino):
+        rr = R.RoiRecon(*w.geometry(), storage=sino_st, image_storage=img_st)
         rr.set_sinogram(sino)
         rr.fbp()
         torch.cuda.synchronize()
-        srv = R.Server(team_blocks=args.team_blocks or 8, teams=args.teams, large_side=1, idle_us=1000)
+        srv = R.Server(team_blocks=team_blocks, teams=teams, large_side=1, idle_us=1000)
         srv.add(rr)
         srv.submit(0, items[0][0], dict(items[0][1], iters=2))  # warm-up
         srv.drain()
@@ -707,13 +789,15 @@ def run_precision(args):
             srv.take(c["id"], (c["box"][3], c["box"][2]))
         time.sleep(0.05)  # the serving kernel leaves after 1 ms idle: the timed run launches it
         n0 = R.roi_recon_launch_count()
-        with ClockSampler(local) as clk:
+        with ClockSampler(local if clock else None) as clk:
             t0 = time.monotonic()
             ids = {srv.submit(0, reg, prm): k for k, (reg, prm) in enumerate(items)}
             srv.drain(3600e3)
             t = time.monotonic() - t0
         res = {}
         for c in srv.poll():
+            if c["status"] != R.ROI_OK:
+                raise R.RoiError(c["status"], "served request failed")
             res[ids[c["id"]]] = srv.take(c["id"], (c["box"][3], c["box"][2]))
         st = srv.stats()
         srv.close()
@@ -724,30 +808,54 @@ def run_precision(args):
     def rel(a, b):
         return float(np.linalg.norm(a.astype(np.float64) - b) / max(np.linalg.norm(b), 1e-30))
 
-    t16, r16, st16, launches, clocks = serve(st_code, p_dev)
-    t32, r32q, _, _, _ = serve(R.ROI_F32, p_q)        # float32 storage, same quantized data
-    _, r32, _, _, _ = serve(R.ROI_F32, p_dev)          # float32 storage, unrounded data
-    e_store = [rel(r16[k], r32q[k]) for k in range(count)]
-    e_total = [rel(r16[k], r32[k]) for k in range(count)]
+    t_all, r_all, st16, launches, clocks = serve(st_code, st_code, p_dev)
+    t_sino, r_sino, _, launches_s, _ = serve(st_code, R.ROI_F32, p_dev)
+    t32, r32q, _, _, _ = serve(R.ROI_F32, R.ROI_F32, p_q)    # float32 storage, same quantized data
+    _, r32, _, _, _ = serve(R.ROI_F32, R.ROI_F32, p_dev)      # float32 storage, unrounded data
+
+    def errs(r):
+        e_store = [rel(r[k], r32q[k]) for k in range(count)]
+        e_total = [rel(r[k], r32[k]) for k in range(count)]
+        return ({"max": max(e_store), "median": statistics.median(e_store), "per_result": e_store},
+                {"max": max(e_total), "median": statistics.median(e_total)})
+
     pl = R.plan(*w.geometry(), items[0][0])
     nx, ny = pl.box[2], pl.box[3]
     lerps_one = w.iters * (sum(pl.width) * max(nx, ny) + nx * ny * w.n_angles)
+    e_all = errs(r_all)
+    e_sino = errs(r_sino)
+    return {"value": count / t_all, "unit": "solves/s", "regions": count, "box": nx, "wall_s": t_all,
+            "storage": storage, "image_storage": storage,
+            "error_vs_float32_same_data": e_all[0], "error_vs_float32_unrounded_data": e_all[1],
+            "sinogram_only": {"value": count / t_sino, "unit": "solves/s", "image_storage": "f32",
+                              "error_vs_float32_same_data": e_sino[0],
+                              "error_vs_float32_unrounded_data": e_sino[1]},
+            "float32_storage": {"value": count / t32, "unit": "solves/s"},
+            "server": {k: st16[k] for k in ("teams", "team_blocks", "device_peak")},
+            "gpu_launches": launches + launches_s, "projector_Glerp_s": lerps_one * count / t_all / 1e9,
+            "clocks": clocks, "path": "server, teams of blocks, all submitted at once"}
+
+
+def run_precision(args):
+    """Precision workload line (see precision_measure); value = regions/s with 16-bit
+    sinogram and images."""
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    w = WL.PRECISION[args.workload]
+    count = args.batch_count or 32
+    m = precision_measure(w, count, args.storage, args.team_blocks or 8, args.teams, local)
     line = {
-        "metric": "roi_solves_per_s", "value": count / t16, "unit": "solves/s", "n_gpus": ws, "steps": 1,
-        "warmup": 1, "ms_per_step": t16 * 1e3, "higher_is_better": True, "dtype": args.storage + " storage, f32 math",
-        "data": "synthetic", "scaling": "strong",
+        "metric": "roi_solves_per_s", "value": m["value"], "unit": "solves/s", "n_gpus": ws, "steps": 1,
+        "warmup": 1, "ms_per_step": m["wall_s"] * 1e3, "higher_is_better": True,
+        "dtype": args.storage + " storage, f32 math", "data": "synthetic", "scaling": "strong",
         "config": {"workload": w.name, "N": w.N, "n_angles": w.n_angles, "n_det": w.n_det, "regions": count,
-                   "radius": w.radius, "margin": w.margin, "box": nx, "iters": w.iters, "solver": "CP-TV",
-                   "lambda": w.lam, "I0": w.I0, "path": "server, teams of blocks, all submitted at once"},
-        "float32_storage": {"value": count / t32, "unit": "solves/s"},
-        "error_storage_vs_float32_same_data": {"max": max(e_store), "median": statistics.median(e_store),
-                                               "per_result": e_store},
-        "error_vs_float32_unrounded_data": {"max": max(e_total), "median": statistics.median(e_total)},
-        "server": {k: st16[k] for k in ("teams", "team_blocks", "device_peak")},
-        "gpu_launches": launches,
-        "projector_Glerp_s": lerps_one * count / t16 / 1e9,
-        "clocks": clocks,
+                   "radius": w.radius, "margin": w.margin, "box": m["box"], "iters": w.iters, "solver": "CP-TV",
+                   "lambda": w.lam, "I0": w.I0, "path": m["path"]},
     }
+    line.update({k: m[k] for k in ("error_vs_float32_same_data", "error_vs_float32_unrounded_data", "sinogram_only",
+                                   "float32_storage", "server", "gpu_launches", "projector_Glerp_s", "clocks")})
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0

@@ -78,9 +78,14 @@ typedef struct {
     int n_angles;          /* N_theta >= 1                                             */
     int n_det;             /* N_d >= 1                                                 */
     const double* angles;  /* host array of n_angles radians, copied; NULL: a*pi/N_theta */
-    roi_dtype storage;     /* storage of the resident sinogram and FBP image, and of the
-                              projector images of batched / served solves: ROI_F32,
-                              ROI_BF16 or ROI_F16 (arithmetic is float throughout)        */
+    roi_dtype storage;     /* storage of the resident sinogram: ROI_F32, ROI_BF16 or ROI_F16 */
+    roi_dtype image_storage; /* storage of the cached FBP image and of the projector images
+                              of batched / served solves: ROI_F32, ROI_BF16 or ROI_F16.
+                              Arithmetic is float throughout.  A 16-bit sinogram with a
+                              float32 image (image_storage = ROI_F32, the zero value) keeps
+                              every image at full precision: the solve then differs from
+                              the float32 path fed the same rounded data by float rounding
+                              only.  A 16-bit image adds its own rounding to each solve.  */
 } roi_geometry;
 
 /* Region of interest in pixel-index units (see Conventions). */
@@ -118,12 +123,12 @@ typedef struct {
 
 /* Create a handle for geometry *geom, ordering all work on `cuda_stream`
  * (a cudaStream_t; NULL = the legacy default stream) of the current device.
- * Allocates the sinogram, filter and FBP buffers (s N_theta N_d + 4 N_theta N_d + 2 s N^2
- * bytes, s = 4 for ROI_F32, 2 for ROI_BF16 / ROI_F16; 16-bit storage adds a float N^2
- * scratch at the first fbp).  With 16-bit storage every stored value is rounded to
- * nearest even; the ramp filter, projections and solves still compute in float.
- * ROI_EINVAL for non-positive sizes or an unknown storage type, ROI_ENOMEM if the
- * device allocation fails.  *out is NULL on failure. */
+ * Allocates the sinogram, filter and FBP buffers (s N_theta N_d + 4 N_theta N_d + 2 i N^2
+ * bytes, s and i = 4 for ROI_F32, 2 for ROI_BF16 / ROI_F16, of storage and image_storage;
+ * a 16-bit image adds a float N^2 scratch at the first fbp).  With 16-bit storage every
+ * stored value is rounded to nearest even; the ramp filter, projections and solves still
+ * compute in float.  ROI_EINVAL for non-positive sizes or an unknown storage type,
+ * ROI_ENOMEM if the device allocation fails.  *out is NULL on failure. */
 roi_status roi_recon_create(const roi_geometry* geom, void* cuda_stream, roi_recon_t* out);
 
 /* Release every resource of the handle (waits for its stream first).  NULL is ignored. */
@@ -430,7 +435,8 @@ const char* roi_server_last_error(roi_server_t s);
 void roi_server_destroy(roi_server_t s);
 
 /* Host only (no GPU): the device-state and result bytes the server budgets for a request
- * on a sinogram of n_pix / n_angles / n_det with the given storage type, and its box side. */
+ * on a sinogram of n_pix / n_angles / n_det whose handle has image storage type `storage`
+ * (the projector images of a served solve are kept in it), and its box side. */
 roi_status roi_server_footprint(int n_pix, int n_angles, int n_det, roi_dtype storage, const roi_region* region,
                                 size_t* device_bytes, size_t* host_bytes, int* box_side);
 
@@ -444,7 +450,8 @@ roi_status roi_server_footprint(int n_pix, int n_angles, int n_det, roi_dtype st
  * else's fixed budget (a framework's caching allocator, a server that reserves HBM up
  * front) and loops that cannot take the implicit device synchronisation of
  * cudaMalloc / cudaFree.  It calls neither, nor anything that allocates.
- *   geom:    as for roi_recon_create; angles must be NULL (a*pi/N_theta), storage ROI_F32.
+ *   geom:    as for roi_recon_create; angles must be NULL (a*pi/N_theta), storage and
+ *            image_storage ROI_F32.
  *   x:       device [box_h][box_w] float32; y: device [n_angles][window_stride] float32,
  *            sizes from roi_recon_plan; work is ordered on cuda_stream (NULL = legacy
  *            default stream) of the current device.
@@ -452,13 +459,18 @@ roi_status roi_server_footprint(int n_pix, int n_angles, int n_det, roi_dtype st
  * Scratch: a fixed 16 MiB device array inside the library holds the per-angle ray
  * table and two zero-padded copies of the box image (by rows and by columns, each row
  * padded to its length + 4 rounded up to a multiple of 4 floats).  Calls needing more
- * (about 80 bytes per angle plus 8 box_w box_h bytes for large boxes) fail with
- * ROI_EINVAL and say so in err.
- * Every GPU that loads the library keeps this array until the process exits.  The
- * first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.  All
- * calls share the array and it keeps the last call's contents; each call rewrites
- * what it reads, but calls that overlap on the GPU race on it, so serialise them. */
+ * (about 90 bytes per angle plus 8 box_w box_h bytes for large boxes) fail with
+ * ROI_EINVAL and say so in err.  The ray table is the plan roi_recon_plan returns for
+ * the same geometry and region (the same host function makes it), so y has exactly the
+ * window layout the caller sized it for; it reaches the device as kernel parameters.
+ * Every GPU that loads the library keeps this array until the process exits.  With lazy
+ * module loading (the CUDA default) the first call on each device loads the module that
+ * holds the array, which allocates that module's memory and may synchronise; later calls
+ * do neither, so make the first call before any stream capture.  Each call looks up the
+ * array's address (cudaGetSymbolAddress, no allocation) with the caller's device current.
+ * All calls share the array and it keeps the last call's contents; each call rewrites
+ * what it reads, but calls that overlap on the GPU (other streams or host threads) race
+ * on it, so serialise them. */
 roi_status roi_recon_forward_local_noalloc(const roi_geometry* geom, const roi_region* region,
                                            const float* x, float* y, void* cuda_stream,
                                            char* err, int err_len);

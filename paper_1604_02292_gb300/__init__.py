@@ -50,7 +50,8 @@ _STATUS = {0: "ROI_OK", 1: "ROI_EINVAL", 2: "ROI_ENOMEM", 3: "ROI_ESTATE", 4: "R
 
 class Geometry(ctypes.Structure):
     _fields_ = [("n_pix", ctypes.c_int), ("n_angles", ctypes.c_int), ("n_det", ctypes.c_int),
-                ("angles", ctypes.POINTER(ctypes.c_double)), ("storage", ctypes.c_int)]
+                ("angles", ctypes.POINTER(ctypes.c_double)), ("storage", ctypes.c_int),
+                ("image_storage", ctypes.c_int)]
 
 
 class Region(ctypes.Structure):
@@ -412,8 +413,8 @@ class RoiError(RuntimeError):
         self.status = status
 
 
-def _geometry(N, n_angles, n_det, angles=None, storage=ROI_F32):
-    g = Geometry(int(N), int(n_angles), int(n_det), None, int(storage))
+def _geometry(N, n_angles, n_det, angles=None, storage=ROI_F32, image_storage=ROI_F32):
+    g = Geometry(int(N), int(n_angles), int(n_det), None, int(storage), int(image_storage))
     keep = None
     if angles is not None:
         import numpy as np
@@ -453,15 +454,17 @@ class RoiRecon:
     Tensors must be contiguous float32 CUDA tensors on the current device.
     """
 
-    def __init__(self, N, n_angles, n_det, angles=None, stream=None, storage=ROI_F32):
-        """storage: ROI_F32, ROI_BF16 or ROI_F16 -- the type the resident sinogram and FBP
-        image (and the projector images of batched / served solves) are stored in."""
+    def __init__(self, N, n_angles, n_det, angles=None, stream=None, storage=ROI_F32, image_storage=None):
+        """storage: ROI_F32, ROI_BF16 or ROI_F16 -- the type the resident sinogram is stored
+        in; image_storage: the type of the cached FBP image and of the projector images of
+        batched / served solves (None: the same as storage)."""
         import torch
         self._torch = torch
         self.N, self.n_angles, self.n_det = int(N), int(n_angles), int(n_det)
         self.storage = int(storage)
+        self.image_storage = int(storage if image_storage is None else image_storage)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        g, self._angles_keep = _geometry(N, n_angles, n_det, angles, storage)
+        g, self._angles_keep = _geometry(N, n_angles, n_det, angles, storage, self.image_storage)
         s, h = roi_recon_create(g, self.stream.cuda_stream)
         if s != ROI_OK:
             raise RoiError(s, "roi_recon_create failed")

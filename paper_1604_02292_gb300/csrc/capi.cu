@@ -68,16 +68,18 @@ struct roi_recon {
     std::vector<double> angles;
     cudaStream_t st = nullptr;
     std::string err;
-    // resident data, stored as dt (0 float, 1 bfloat16, 2 half; esz bytes an element)
+    // resident data: the sinogram stored as pdt, the FBP image and the projector images of
+    // whole-region solves as dt (0 float, 1 bfloat16, 2 half; pesz / esz bytes an element)
     int dt = 0, esz = 4;
-    void* p = nullptr;       // [na][nd]
+    int pdt = 0, pesz = 4;
+    void* p = nullptr;       // [na][nd], storage pdt
     float* q = nullptr;      // [na][nd] filtered sinogram (float)
     void* xfbp = nullptr;    // [N][N] padded (row stride xld), element (0,0)
     void* xfbpT = nullptr;   // its transpose, padded
     unsigned char* xfbp_base = nullptr;
     unsigned char* xfbpT_base = nullptr;
     int xld = 0;             // padded_ld_e(N, esz)
-    DevBuf fbp32;            // 16-bit storage: the float FBP image before narrowing [N][N]
+    DevBuf fbp32;            // 16-bit image storage: the float FBP image before narrowing [N][N]
     DevBufT<unsigned char> in_tmp;  // set_sinogram input awaiting conversion
     float* hodd = nullptr;   // Ram-Lak odd taps scaled by pi/na, [nd/2 + 1]
     float ctail = 0.f;       // (pi/na) (h0 + 2 sum_{odd m < nd} h_m)
@@ -222,6 +224,8 @@ roi_status check_geometry(const roi_geometry* g) {
     if (g->n_pix < 1 || g->n_angles < 1 || g->n_det < 1) return ROI_EINVAL;
     if (g->n_pix > 65536 || g->n_angles > 65536 || g->n_det > 8192) return ROI_EINVAL;
     if (g->storage != ROI_F32 && g->storage != ROI_BF16 && g->storage != ROI_F16) return ROI_EINVAL;
+    if (g->image_storage != ROI_F32 && g->image_storage != ROI_BF16 && g->image_storage != ROI_F16)
+        return ROI_EINVAL;
     if (g->angles)
         for (int a = 0; a < g->n_angles; ++a)
             if (!std::isfinite(g->angles[a])) return ROI_EINVAL;
@@ -364,6 +368,7 @@ roi_status ensure_residual(roi_recon* h) {
     a.img_ld = h->xld;
     a.imgT_ld = h->xld;
     a.dt = h->dt;
+    a.pdt = h->pdt;
     a.hole = Rect{0, 0, 0, 0};
     a.out = h->resid.p;
     a.p = h->p;
@@ -407,6 +412,7 @@ roi_status run_exterior(roi_recon* h) {
     a.img_ld = h->xld;
     a.imgT_ld = h->xld;
     a.dt = h->dt;
+    a.pdt = h->pdt;
     a.hole = h->box;
     a.out = h->pp.p;
     a.p = h->p;
@@ -731,7 +737,7 @@ roi_status filter_sinogram(roi_recon* h, int n) {
     fw.imgT_ld = ld;
     fw.out = wd.p;
     roi::launch_forward(roi::FWD_PLAIN, fw, h->st);
-    roi::launch_disc_subtract(h->p, h->dt, wd.p, 0.f, h->filt_pd.p, ns, h->st);  // p as float
+    roi::launch_disc_subtract(h->p, h->pdt, wd.p, 0.f, h->filt_pd.p, ns, h->st);  // p as float
     roi::launch_row_sums(h->filt_pd.p, na, nd, sums.p, h->st);
     roi::launch_row_sums(wd.p, na, nd, sums.p + na, h->st);
     LAUNCHED(h, "disc projection");
@@ -744,7 +750,7 @@ roi_status filter_sinogram(roi_recon* h, int n) {
         den += hs[na + a] * hs[na + a];
     }
     h->disc_g = den > 0.0 ? num / den : 0.0;
-    roi::launch_disc_subtract(h->p, h->dt, wd.p, (float)h->disc_g, h->filt_pd.p, ns, h->st);
+    roi::launch_disc_subtract(h->p, h->pdt, wd.p, (float)h->disc_g, h->filt_pd.p, ns, h->st);
     CU(h, h->filt_cp.ensure((size_t)n * ns));
     roi::launch_filter_conv(h->filt_u.p, h->filt_pd.p, h->filt_cp.p, n, na, nd, h->st);
     LAUNCHED(h, "filtered sinograms");
@@ -836,12 +842,14 @@ roi_status roi_recon_create(const roi_geometry* geom, void* cuda_stream, roi_rec
     h->nd = geom->n_det;
     h->angles = make_angles(geom);
     h->st = (cudaStream_t)cuda_stream;
-    h->dt = (int)geom->storage;
+    h->pdt = (int)geom->storage;
+    h->pesz = roi::dt_size(h->pdt);
+    h->dt = (int)geom->image_storage;
     h->esz = roi::dt_size(h->dt);
     h->xld = roi::padded_ld_e(h->N, h->esz);
     const size_t ns = (size_t)h->na * h->nd;
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMalloc(&h->p, (size_t)h->esz * ns);
+    if (e == cudaSuccess) e = cudaMalloc(&h->p, (size_t)h->pesz * ns);
     if (e == cudaSuccess) e = dev_alloc(&h->q, ns);
     const size_t npad_bytes = (size_t)h->esz * h->N * h->xld;
     if (e == cudaSuccess) e = dev_alloc(&h->xfbp_base, npad_bytes);
@@ -936,13 +944,13 @@ roi_status roi_recon_set_sinogram(roi_recon_t h, const void* p, roi_dtype dt, in
     if (dt != ROI_F32 && dt != ROI_BF16 && dt != ROI_F16) return fail(h, ROI_EINVAL, "set_sinogram: unknown dtype");
     const size_t n = (size_t)h->na * h->nd;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    if ((int)dt == h->dt) {
-        CU(h, cudaMemcpyAsync(h->p, p, (size_t)h->esz * n, kind, h->st));
+    if ((int)dt == h->pdt) {
+        CU(h, cudaMemcpyAsync(h->p, p, (size_t)h->pesz * n, kind, h->st));
     } else {  // narrow (or widen) to the storage type on the device
         const size_t in_bytes = (size_t)roi::dt_size((int)dt) * n;
         CU(h, h->in_tmp.ensure(in_bytes));
         CU(h, cudaMemcpyAsync(h->in_tmp.p, p, in_bytes, kind, h->st));
-        roi::launch_convert(h->in_tmp.p, (int)dt, h->p, h->dt, n, h->st);
+        roi::launch_convert(h->in_tmp.p, (int)dt, h->p, h->pdt, n, h->st);
         LAUNCHED(h, "set_sinogram conversion");
     }
     h->have_sino = true;
@@ -966,7 +974,7 @@ roi_status roi_recon_set_sinogram_truncated(roi_recon_t h, const void* p, roi_dt
     CU(h, h->in_tmp.ensure(in_bytes));
     CU(h, cudaMemcpyAsync(h->in_tmp.p, p, in_bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                           h->st));
-    roi::launch_pad_truncated(h->in_tmp.p, (int)dt, n_measured, h->p, h->dt, h->na, h->nd,
+    roi::launch_pad_truncated(h->in_tmp.p, (int)dt, n_measured, h->p, h->pdt, h->na, h->nd,
                               (h->nd - n_measured) / 2, h->st);
     LAUNCHED(h, "set_sinogram_truncated padding");
     h->have_sino = true;
@@ -982,7 +990,7 @@ roi_status roi_recon_ramp_filter(roi_recon_t h, float* q) {
     h->err.clear();
     if (!q) return fail(h, ROI_EINVAL, "ramp_filter: null output");
     if (!h->have_sino) return fail(h, ROI_ESTATE, "ramp_filter: no sinogram (call set_sinogram first)");
-    roi::launch_ramp(h->p, h->dt, h->hodd, q, h->na, h->nd, h->ctail, h->st);
+    roi::launch_ramp(h->p, h->pdt, h->hodd, q, h->na, h->nd, h->ctail, h->st);
     LAUNCHED(h, "ramp filter");
     return ROI_OK;
 }
@@ -991,7 +999,7 @@ roi_status roi_recon_fbp(roi_recon_t h, float* out_or_null) {
     if (!h) return ROI_EINVAL;
     h->err.clear();
     if (!h->have_sino) return fail(h, ROI_ESTATE, "fbp: no sinogram (call set_sinogram first)");
-    roi::launch_ramp(h->p, h->dt, h->hodd, h->q, h->na, h->nd, h->ctail, h->st);
+    roi::launch_ramp(h->p, h->pdt, h->hodd, h->q, h->na, h->nd, h->ctail, h->st);
     roi::BackArgs b{};
     b.rec = h->rec_fbp;
     b.na = h->na;

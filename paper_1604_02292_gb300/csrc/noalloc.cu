@@ -10,13 +10,20 @@
 // front), and loops that cannot take the implicit device synchronisation of
 // cudaMalloc / cudaFree.
 //
+// The ray table is the host plan itself (plan_angles, the function roi_recon_plan uses),
+// so the windows the kernel projects into are the windows the caller sized y with.  It
+// reaches the device as kernel parameters (up to kRecsPerLaunch records per launch of
+// k_put_recs): no host staging buffer, no copy from pageable memory, nothing allocated.
+//
 // Facts a caller must know:
 //   * Every GPU that loads this library holds the array (kNoallocScratchBytes) until
-//     the process exits.
-//   * Host code cannot use the array's name as a device address; the address is
-//     obtained once per device with cudaGetSymbolAddress on the first call made
-//     with that device current.  That first call should come before any stream
-//     capture.
+//     the process exits.  With lazy module loading (the default since CUDA 12.2) the
+//     module, and so the array, is loaded by the first call on each device: that call
+//     may allocate the module's memory and synchronise; later calls do neither.  Make
+//     the first call before any stream capture.
+//   * Host code cannot use the array's name as a device address; every call looks the
+//     address up with cudaGetSymbolAddress (which allocates nothing) with the caller's
+//     device current, so the address stays right after a device reset.
 //   * All calls share the array and it keeps the last call's contents.  Each call
 //     clears and rewrites every scratch byte it reads before reading it (the zero
 //     borders of the padded image copies included), so nothing carries over; but
@@ -26,7 +33,6 @@
 
 #include <cmath>
 #include <cstdio>
-#include <mutex>
 
 #include "roi_recon.h"
 #include "roi_internal.h"
@@ -34,41 +40,21 @@
 namespace {
 
 constexpr size_t kNoallocScratchBytes = size_t(16) << 20;  // 16 MiB per device
-constexpr int kMaxDevices = 64;
+constexpr double kPi = 3.14159265358979323846;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
-std::mutex g_addr_mu;
-void* g_addr[kMaxDevices] = {};
+// A run of host-planned ray records passed by value (kernel parameters, at most 32764
+// bytes on this architecture) and stored at rec[a0 .. a0 + n).
+constexpr int kRecsPerLaunch = 320;
+struct RecChunk {
+    int a0, n;
+    roi::AngleRec r[kRecsPerLaunch];
+};
+static_assert(sizeof(RecChunk) <= 32000, "ray records must fit the kernel parameter space");
 
-// Device-side copy of the host ROI plan for one angle (frame = target = box; see
-// plan.cpp for the derivation of the window of bins whose Joseph rays reach the box).
-__global__ void k_plan_box(roi::AngleRec* rec, int N, int na, int nd, roi::Rect box, int stride) {
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= na) return;
-    const double kPi = 3.14159265358979323846;
-    const double th = a * kPi / na;
-    const double c = cos(th), s = sin(th);
-    const double half = 0.5 * (N - 1), dhalf = 0.5 * (nd - 1);
-    const double Xb = box.x0 + 0.5 * (box.w - 1) - half;
-    const double Yb = half - (box.y0 + 0.5 * (box.h - 1));
-    const int row = fabs(c) >= fabs(s) - 1e-12;
-    const double wd = row ? fabs(c) : fabs(s);
-    const double Tb = Xb * c + Yb * s;
-    const double H = 0.5 * (fabs(c) * (box.w - 1) + fabs(s) * (box.h - 1));
-    long dlo = (long)floor(Tb - H - wd + dhalf - 1e-6) + 1;
-    long dhi = (long)ceil(Tb + H + wd + dhalf + 1e-6) - 1;
-    dlo = dlo < 0 ? 0 : dlo;
-    dhi = dhi > nd - 1 ? nd - 1 : dhi;
-    int d0 = 0, width = 0;
-    if (dhi >= dlo) {
-        d0 = (int)dlo;
-        width = (int)(dhi - dlo + 1);
-    }
-    if (width > stride) width = stride;  // the output row holds `stride` bins
-    roi::AngleRec r;
-    roi::angle_fill(r, a, c, s, row, wd, d0, width, d0 - dhalf - Tb, row ? box.w : box.h);
-    rec[a] = r;
+__global__ void k_put_recs(roi::AngleRec* rec, const RecChunk c) {
+    for (int i = threadIdx.x; i < c.n; i += blockDim.x) rec[c.a0 + i] = c.r[i];
 }
 
 void put_err(char* err, int err_len, const char* msg) {
@@ -86,7 +72,8 @@ extern "C" roi_status roi_recon_forward_local_noalloc(const roi_geometry* geom, 
         return ROI_EINVAL;
     }
     if (geom->n_pix < 1 || geom->n_angles < 1 || geom->n_det < 1 || geom->n_pix > 65536 ||
-        geom->n_angles > 65536 || geom->n_det > 8192 || geom->storage != ROI_F32 || geom->angles != nullptr) {
+        geom->n_angles > 65536 || geom->n_det > 8192 || geom->storage != ROI_F32 || geom->image_storage != ROI_F32 ||
+        geom->angles != nullptr) {
         put_err(err, err_len, "forward_local_noalloc: geometry must be valid, float32, with default angles");
         return ROI_EINVAL;
     }
@@ -99,12 +86,6 @@ extern "C" roi_status roi_recon_forward_local_noalloc(const roi_geometry* geom, 
     roi::Rect box;
     if (!roi::plan_box(geom->n_pix, region->cx, region->cy, region->radius, region->margin, &box)) {
         put_err(err, err_len, "forward_local_noalloc: extended box does not intersect the grid");
-        return ROI_EINVAL;
-    }
-    // The caller sizes y with the host plan's window stride; recompute it here.
-    roi_solve_info info;
-    if (roi_recon_plan(geom, region, &info, nullptr, nullptr) != ROI_OK) {
-        put_err(err, err_len, "forward_local_noalloc: planning failed");
         return ROI_EINVAL;
     }
     const int na = geom->n_angles;
@@ -121,27 +102,16 @@ extern "C" roi_status roi_recon_forward_local_noalloc(const roi_geometry* geom, 
         put_err(err, err_len, msg);
         return ROI_EINVAL;
     }
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        put_err(err, err_len, "forward_local_noalloc: no usable current CUDA device");
-        return ROI_ECUDA;
-    }
     void* base = nullptr;
     {
-        std::lock_guard<std::mutex> lk(g_addr_mu);
-        if (!g_addr[dev]) {
-            void* p = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-            if (e != cudaSuccess || !p) {
-                char msg[256];
-                std::snprintf(msg, sizeof msg, "forward_local_noalloc: cudaGetSymbolAddress failed: %s",
-                              cudaGetErrorString(e));
-                put_err(err, err_len, msg);
-                return ROI_ECUDA;
-            }
-            g_addr[dev] = p;
+        cudaError_t e = cudaGetSymbolAddress(&base, g_noalloc_scratch);
+        if (e != cudaSuccess || !base) {
+            char msg[256];
+            std::snprintf(msg, sizeof msg, "forward_local_noalloc: cudaGetSymbolAddress failed: %s",
+                          cudaGetErrorString(e));
+            put_err(err, err_len, msg);
+            return ROI_ECUDA;
         }
-        base = g_addr[dev];
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
     roi::AngleRec* rec = (roi::AngleRec*)base;
@@ -151,14 +121,30 @@ extern "C" roi_status roi_recon_forward_local_noalloc(const roi_geometry* geom, 
         put_err(err, err_len, "forward_local_noalloc: clearing the scratch failed");
         return ROI_ECUDA;
     }
-    roi::count_launches(1);
-    k_plan_box<<<(na + 127) / 128, 128, 0, st>>>(rec, geom->n_pix, na, geom->n_det, box, info.window_stride);
+    // The ray table: the host plan of roi_recon_plan (default angles a pi / N_theta), made
+    // and sent a chunk of angles at a time; its widest window gives the stride of y.
+    int wmax = 0;
+    {
+        RecChunk chunk;
+        double ang[kRecsPerLaunch];
+        for (int a0 = 0; a0 < na; a0 += kRecsPerLaunch) {
+            const int n = na - a0 < kRecsPerLaunch ? na - a0 : kRecsPerLaunch;
+            for (int i = 0; i < n; ++i) ang[i] = (a0 + i) * kPi / na;
+            const int w = roi::plan_angles(geom->n_pix, n, geom->n_det, ang, box, box, false, chunk.r);
+            wmax = w > wmax ? w : wmax;
+            for (int i = 0; i < n; ++i) chunk.r[i].aidx = a0 + i;
+            chunk.a0 = a0;
+            chunk.n = n;
+            roi::count_launches(1);
+            k_put_recs<<<1, 128, 0, st>>>(rec, chunk);
+        }
+    }
     roi::launch_copy_pad(x, box.w, xr + roi::kPad, roi::padded_ld(box.w), box.h, box.w, st);
     roi::launch_transpose(x, box.w, xc + roi::kPad, roi::padded_ld(box.h), box.h, box.w, st);
     roi::FwdArgs a{};
     a.rec = rec;
     a.na = na;
-    a.stride = info.window_stride;
+    a.stride = roi::round_stride(wmax);  // = roi_recon_plan's window_stride
     a.nx = box.w;
     a.ny = box.h;
     a.img = xr + roi::kPad;

@@ -52,9 +52,10 @@ constexpr int TARGET_THREADS = 152 * 2048;
 // Positions: each 16-sample segment is anchored in float-float, then offsets
 // |m - anchor| <= 8 are formed in float.  Sums: float within a segment, Neumaier
 // carry across segments, float-float across the S threads of a ray.
-template <int MODE, int DT>
+template <int MODE, int DT, int PDT = DT>
 __global__ void __launch_bounds__(FWD_RAYS* FWD_MAXSEG) k_forward(const FwdArgs A) {
-    using T = typename Stor<DT>::T;  // element of the frame image (and of p): float or 16-bit
+    using T = typename Stor<DT>::T;   // element of the frame image: float or 16-bit
+    using TP = typename Stor<PDT>::T;  // element of p (FWD_EXTERIOR)
     __shared__ float red_s[FWD_MAXSEG][FWD_RAYS];
     __shared__ float red_c[FWD_MAXSEG][FWD_RAYS];
     const int a = blockIdx.y;
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(FWD_RAYS* FWD_MAXSEG) k_forward(const FwdArgs 
     }
     tot = ff_mul_f(r.inv_w, tot);
     if (MODE == FWD_EXTERIOR) {  // p - sum, with the float-float sum
-        const float pv = to_f32<DT>(__ldg(static_cast<const T*>(A.p) + (size_t)r.aidx * A.nd + r.d0 + k));
+        const float pv = to_f32<PDT>(__ldg(static_cast<const TP*>(A.p) + (size_t)r.aidx * A.nd + r.d0 + k));
         const ff d = two_sum(pv, -tot.hi);
         *out = d.hi + (d.lo - tot.lo);
         return;
@@ -395,13 +396,18 @@ void launch_forward(FwdMode mode, const FwdArgs& a0, cudaStream_t st) {
     count_launches(1);
     switch (mode) {
         case FWD_PLAIN: k_forward<FWD_PLAIN, 0><<<grid, block, 0, st>>>(a); break;
-        case FWD_EXTERIOR:
-            if (a.dt == 1)
-                k_forward<FWD_EXTERIOR, 1><<<grid, block, 0, st>>>(a);
-            else if (a.dt == 2)
-                k_forward<FWD_EXTERIOR, 2><<<grid, block, 0, st>>>(a);
-            else
-                k_forward<FWD_EXTERIOR, 0><<<grid, block, 0, st>>>(a);
+        case FWD_EXTERIOR:  // image storage x sinogram storage
+            switch (3 * a.dt + a.pdt) {
+                case 1: k_forward<FWD_EXTERIOR, 0, 1><<<grid, block, 0, st>>>(a); break;
+                case 2: k_forward<FWD_EXTERIOR, 0, 2><<<grid, block, 0, st>>>(a); break;
+                case 3: k_forward<FWD_EXTERIOR, 1, 0><<<grid, block, 0, st>>>(a); break;
+                case 4: k_forward<FWD_EXTERIOR, 1, 1><<<grid, block, 0, st>>>(a); break;
+                case 5: k_forward<FWD_EXTERIOR, 1, 2><<<grid, block, 0, st>>>(a); break;
+                case 6: k_forward<FWD_EXTERIOR, 2, 0><<<grid, block, 0, st>>>(a); break;
+                case 7: k_forward<FWD_EXTERIOR, 2, 1><<<grid, block, 0, st>>>(a); break;
+                case 8: k_forward<FWD_EXTERIOR, 2, 2><<<grid, block, 0, st>>>(a); break;
+                default: k_forward<FWD_EXTERIOR, 0, 0><<<grid, block, 0, st>>>(a); break;
+            }
             break;
         case FWD_SIRT: k_forward<FWD_SIRT, 0><<<grid, block, 0, st>>>(a); break;
         case FWD_CP: k_forward<FWD_CP, 0><<<grid, block, 0, st>>>(a); break;

@@ -163,12 +163,13 @@ struct FwdArgs {
     const void* img;       // frame image [ny][img_ld], padded (float, or dt for FWD_EXTERIOR)
     const void* imgT;      // its transpose [nx][imgT_ld], padded
     int img_ld, imgT_ld;
-    int dt;                // FWD_EXTERIOR: storage of img, imgT and p (0 float, 1 bfloat16, 2 half)
+    int dt;                // FWD_EXTERIOR: storage of img and imgT (0 float, 1 bfloat16, 2 half)
+    int pdt;               // FWD_EXTERIOR: storage of p
     int seg_len;           // set by launch_forward
     Rect hole;             // FWD_EXTERIOR: frame pixels treated as zero (w = 0: none)
     float* out;            // [na][stride]
     // FWD_EXTERIOR: out = p[a][d0 + k] - W_F x
-    const void* p;         // [na][nd], storage dt
+    const void* p;         // [na][nd], storage pdt
     int nd;
     // FWD_SIRT: out = (pp - W x) * (R ? R[a][k] : 1)
     // FWD_CP:   out = (out + sig (W x - pp)) / (1 + sig / 2), sig = R ? R[a][k] : sig_scalar

@@ -98,11 +98,13 @@ def batch_regions(w: BatchWorkload, seed: int = 0, count: int | None = None):
     return out
 
 
-def sinogram(w, seed: int = 0) -> np.ndarray:
-    """Noisy analytic sinogram of the seeded phantom, float32 [n_angles][n_det]."""
+def sinogram(w, seed: int = 0, noise: bool = True) -> np.ndarray:
+    """Analytic sinogram of the seeded phantom, float32 [n_angles][n_det], with the
+    workload's Poisson noise (noise=False: the noise-free line integrals)."""
     ph = synth.random_phantom(w.N, w.n_ellipses, texture=getattr(w, "texture", False), seed=seed)
     p = synth.analytic_sinogram(ph, w.n_angles, w.n_det)
-    p = synth.poisson_noise(p, w.I0, seed=seed + 1000)
+    if noise:
+        p = synth.poisson_noise(p, w.I0, seed=seed + 1000)
     return p.astype(np.float32)
 
 

@@ -79,7 +79,11 @@ def test_plan_rejects_bad_geometry():
     assert R.roi_recon_plan(g, R.Region(1, 1, 1, 0), info, None, None) == R.ROI_EINVAL
     g = R.Geometry(128, 64, 128, None, 7)  # unknown storage type
     assert R.roi_recon_plan(g, R.Region(1, 1, 1, 0), info, None, None) == R.ROI_EINVAL
+    g = R.Geometry(128, 64, 128, None, R.ROI_F32, 5)  # unknown image storage type
+    assert R.roi_recon_plan(g, R.Region(1, 1, 1, 0), info, None, None) == R.ROI_EINVAL
     g = R.Geometry(128, 64, 128, None, R.ROI_BF16)  # 16-bit storage plans like float32
+    assert R.roi_recon_plan(g, R.Region(64, 64, 8, 4), info, None, None) == R.ROI_OK
+    g = R.Geometry(128, 64, 128, None, R.ROI_BF16, R.ROI_F16)  # any sinogram / image pair
     assert R.roi_recon_plan(g, R.Region(64, 64, 8, 4), info, None, None) == R.ROI_OK
 
 

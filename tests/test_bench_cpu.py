@@ -30,6 +30,7 @@ def test_reference_arm_prints_the_contract_line():
     assert d["value"] > 0 and d["config"]["workload"] == "roi_sirt_128"
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert "scaled" not in cb["sample"] and "measured" in cb["sample"]  # whole solves, timed
     e = d["e2e"]
     assert e["value"] == d["value"] and e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
 
