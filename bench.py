@@ -275,6 +275,50 @@ def run_reference(args):
 
 # ------------------------------------------------------------------------------ our arm
 
+def large_box_measure(reps=3):
+    """Lone large regions through roi_recon_solve_local on the 2048 x 2048 / 180-angle serving
+    geometry: radius 128 and 256 px (boxes 384 and 768), SIRT and CP-TV, 200 iterations,
+    solved by the whole-region solver as one team of every block (the default) and by one
+    launch per operator (ROI_OPT_SINGLE_LAUNCH = 0); CUDA-event time per solve and the
+    projector lerps/s (forward window rays x box side + gather pixels x angles, per iteration)."""
+    import torch
+
+    import paper_1604_02292_gb300 as R
+
+    w = WL.SERVING["roi_serve_2048"]
+    stream = torch.cuda.Stream()
+    rr = R.RoiRecon(*w.geometry(), stream=stream)
+    c = (w.N - 1) / 2.0
+    out = []
+    with torch.cuda.stream(stream):
+        rr.set_sinogram(torch.from_numpy(WL.sinogram(w, 0)).cuda())
+        rr.fbp()
+        for r in (128.0, 256.0):
+            region = (c + 100.0, c - 150.0, r, r / 2.0)
+            pl = rr.plan(region)
+            nx, ny = pl.box[2], pl.box[3]
+            lerps = w.iters * (sum(pl.width) * max(nx, ny) + nx * ny * w.n_angles)
+            for reg, lam in ((R.ROI_SIRT_NONNEG, 0.0), (R.ROI_TV_CP, w.lam)):
+                row = {"radius": r, "box": nx, "solver": "sirt" if reg == R.ROI_SIRT_NONNEG else "tv",
+                       "iters": w.iters}
+                for key, single in (("team", 1), ("per_operator", 0)):
+                    rr.set_option(R.ROI_OPT_SINGLE_LAUNCH, single)
+                    rr.solve_local(region, reg, iters=w.iters, lam=lam)  # warm-up (allocations)
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    for _ in range(reps):
+                        rr.solve_local(region, reg, iters=w.iters, lam=lam)
+                    b.record(stream)
+                    torch.cuda.synchronize()
+                    ms = a.elapsed_time(b) / reps
+                    row[key] = {"ms": ms, "solves_per_s": 1e3 / ms, "Glerp_s": lerps / (ms * 1e-3) / 1e9}
+                rr.set_option(R.ROI_OPT_SINGLE_LAUNCH, 1)
+                row["speedup"] = row["per_operator"]["ms"] / row["team"]["ms"]
+                out.append(row)
+    rr.close()
+    return out
+
+
 def local_vs_global(rr, w, p_dev, region, reg, stream):
     """The regularized local solve of `region` against the same solver, lambda and
     iterations on a box covering the whole grid, inside the ROI disk (report only)."""
@@ -446,6 +490,11 @@ def run_ours(args):
                         "plain": m["plain"], "kernel_launches": m["server"]["kernel_launches"]})
         serving["rates"] = pts
 
+    # ---- lone large boxes (beyond the single-launch solver): team of all blocks vs per operator
+    large = None
+    if rank == 0 and not args.no_batch:
+        large = large_box_measure()
+
     # ---- batching on the 2048 x 2048 batch workload: all 4096 regions in one persistent launch
     batch = None
     if not args.no_batch:
@@ -514,6 +563,7 @@ def run_ours(args):
             "serving": serving,
             "batch": batch,
             "precision": precision,
+            "large_box": large,
         }
         print(json.dumps(line), flush=True)
     rr.close()

@@ -53,7 +53,8 @@ typedef enum {
     ROI_ESTATE = 3,
     ROI_ECUDA = 4,
     ROI_ETIMEOUT = 5,
-    ROI_EBUSY = 6
+    ROI_EBUSY = 6,
+    ROI_ECANCELED = 7
 } roi_status;
 
 typedef enum { ROI_F32 = 0, ROI_BF16 = 1, ROI_F16 = 2 } roi_dtype;
@@ -190,6 +191,8 @@ roi_status roi_recon_solve_local(roi_recon_t h, const roi_region* region, const 
  * float32, box-major [box_h][box_w] images and the window [n_angles][window_stride].
  * roi_recon_state_export copies it to dst (bytes >= the size; device memory when
  * on_device = 1, host memory otherwise); the call synchronizes.
+ * A large box solved by the whole-region solver (see ROI_OPT_SINGLE_LAUNCH) leaves no
+ * state: set ROI_OPT_SINGLE_LAUNCH = 0 for solves that are to be checkpointed.
  * roi_recon_solve_local_resume runs params->iters further iterations from such a state
  * (device or host memory) instead of from x = 0; everything else is as for solve_local,
  * and info->iters_done counts the state's iterations too.  The region must give the
@@ -286,15 +289,24 @@ roi_status roi_recon_ramp_filter(roi_recon_t h, float* q);
  * ------------------------------------------------------------------------ */
 
 typedef enum {
-    /* 1 (default): run each solve as one cooperative launch when the box's padded image
-     * fits in a block's shared memory (all iterations in one kernel, grid barriers
-     * between phases); 0: one launch per operator per iteration. */
+    /* 1 (default): run each SIRT / CP-TV solve_local as one cooperative launch.  When the
+     * box's padded image fits in a block's shared memory (sides up to about 216 px): the
+     * single-launch solver (all iterations in one kernel, grid barriers between phases).
+     * Larger boxes: the whole-region solver of roi_recon_solve_batch, one team of every
+     * co-resident block, exterior step p' = (p - W x_fbp) + W_L x_fbp (bit-identical to
+     * solve_batch's result for the region; such a solve keeps no resumable state, and
+     * eval_objective, CP with precond = 0 and resumed solves take the per-operator path).
+     * 0: one launch per operator per iteration for every box. */
     ROI_OPT_SINGLE_LAUNCH = 0,
     /* time limit of one grid-barrier wait in a single-launch solve, microseconds
      * (default 1,000,000); a wait that runs out aborts the solve (see roi_recon_sync). */
     ROI_OPT_WAIT_LIMIT_US = 1,
-    /* testing only: number of participants the grid barrier waits for beyond the blocks
-     * launched (default 0).  Any value > 0 makes every single-launch solve time out. */
+    /* testing only: number of participants every grid or team barrier waits for beyond the
+     * blocks launched (default 0).  Any value > 0 makes every cooperative solve time out:
+     * single-launch solves, batched solves run by teams (few regions), large boxes of
+     * solve_local, and (roi_server_set_option) requests solved by a team of a server.  For
+     * a server, -1 keeps the team leaders away instead, so that the members' waits for
+     * the leader's claim (the team mailbox) run out. */
     ROI_OPT_TEST_ABSENT_BLOCKS = 2
 } roi_option;
 
@@ -335,6 +347,12 @@ roi_status roi_recon_kernel_times(roi_recon_t h, int kernel, int* launches, doub
 /* Number of CUDA kernels this library has launched in this process (all handles). */
 unsigned long long roi_recon_launch_count(void);
 
+/* Testing only (process-wide, no GPU needed): the nth device or page-locked host allocation
+ * the library makes from now on fails as if memory had run out, without allocating (the
+ * call making it returns ROI_ENOMEM and leaves its handle or server usable); the later ones
+ * succeed again.  nth = 0 turns it off.  ROI_EINVAL for nth < 0. */
+roi_status roi_recon_test_fail_alloc(int nth);
+
 /* --------------------------------------------------------------------------
  * Serving: continuous batching of ROI requests over resident sinograms
  * ------------------------------------------------------------------------ */
@@ -373,7 +391,8 @@ typedef struct {
 
 typedef struct {
     long long id;          /* as returned by roi_server_submit */
-    roi_status status;     /* ROI_OK, or ROI_ETIMEOUT when a device wait gave up */
+    roi_status status;     /* ROI_OK; ROI_ETIMEOUT when a device wait gave up; ROI_ECANCELED
+                              after roi_server_cancel */
     int sino;
     int box_x0, box_y0, box_w, box_h;
     int pool;              /* 0: one block, 1: a team */
@@ -387,6 +406,7 @@ typedef struct {
     long long kernel_launches;
     size_t device_in_use, device_peak, host_in_use, host_peak;
     int blocks, single_units, teams, team_blocks;
+    long long cancelled;   /* requests removed from the queue by roi_server_cancel */
 } roi_server_stats;
 
 /* Creates a server on the current device (it owns a non-blocking stream).  cfg may be
@@ -422,6 +442,19 @@ int roi_server_poll(roi_server_t s, roi_server_completion* out, int max);
  * dst (may be NULL to discard) and releases it.  ROI_EBUSY if not complete yet,
  * ROI_EINVAL for an unknown id, the request's own status if it failed. */
 roi_status roi_server_take(roi_server_t s, long long id, float* dst);
+
+/* Removes request id from the queue if it is still waiting there (not yet admitted to the
+ * device): it then completes at once with status ROI_ECANCELED (reported by poll; take
+ * releases it and returns ROI_ECANCELED).  ROI_EBUSY if it is already on the device (it
+ * runs to completion), ROI_EINVAL for an unknown or completed id. */
+roi_status roi_server_cancel(roi_server_t s, long long id);
+
+/* Server options, read at the next launch of the serving kernel: ROI_OPT_WAIT_LIMIT_US
+ * (limit of the team barrier and mailbox waits, default 2 s) and ROI_OPT_TEST_ABSENT_BLOCKS
+ * (testing only, see roi_option).  When a wait runs out the kernel leaves, the requests
+ * it held complete with ROI_ETIMEOUT, and the server relaunches for the rest.  ROI_EINVAL
+ * for ROI_OPT_SINGLE_LAUNCH or a value out of range. */
+roi_status roi_server_set_option(roi_server_t s, roi_option opt, long long value);
 
 /* Waits (running progress itself when the thread is not started) until every submitted
  * request has completed or timeout_ms has passed (ROI_EBUSY then). */

@@ -21,7 +21,7 @@ from dataclasses import dataclass
 from . import build as _build
 
 __all__ = [
-    "ROI_OK", "ROI_EINVAL", "ROI_ENOMEM", "ROI_ESTATE", "ROI_ECUDA", "ROI_ETIMEOUT", "ROI_EBUSY",
+    "ROI_OK", "ROI_EINVAL", "ROI_ENOMEM", "ROI_ESTATE", "ROI_ECUDA", "ROI_ETIMEOUT", "ROI_EBUSY", "ROI_ECANCELED",
     "ROI_F32", "ROI_BF16", "ROI_F16", "ROI_SIRT_NONNEG", "ROI_TV_CP", "ROI_FILTER_SIRT", "ROI_FILTER_TV", "ROI_FILTER_ISTA",
     "roi_recon_filter_prepare", "roi_recon_filter_get", "roi_recon_set_sinogram_truncated",
     "roi_recon_solve_tiled", "roi_recon_state_size", "roi_recon_state_export", "roi_recon_solve_local_resume",
@@ -37,15 +37,16 @@ __all__ = [
     "roi_server_create", "roi_server_destroy", "roi_server_add_sinogram", "roi_server_submit",
     "roi_server_start", "roi_server_stop", "roi_server_progress", "roi_server_poll", "roi_server_take",
     "roi_server_drain", "roi_server_stats_get", "roi_server_last_error", "roi_server_footprint",
+    "roi_server_cancel", "roi_server_set_option", "roi_recon_test_fail_alloc",
 ]
 
-ROI_OK, ROI_EINVAL, ROI_ENOMEM, ROI_ESTATE, ROI_ECUDA, ROI_ETIMEOUT, ROI_EBUSY = range(7)
+ROI_OK, ROI_EINVAL, ROI_ENOMEM, ROI_ESTATE, ROI_ECUDA, ROI_ETIMEOUT, ROI_EBUSY, ROI_ECANCELED = range(8)
 ROI_F32, ROI_BF16, ROI_F16 = range(3)
 ROI_SIRT_NONNEG, ROI_TV_CP, ROI_FILTER_SIRT, ROI_FILTER_TV, ROI_FILTER_ISTA = range(5)
 ROI_OPT_SINGLE_LAUNCH, ROI_OPT_WAIT_LIMIT_US, ROI_OPT_TEST_ABSENT_BLOCKS = range(3)
 
 _STATUS = {0: "ROI_OK", 1: "ROI_EINVAL", 2: "ROI_ENOMEM", 3: "ROI_ESTATE", 4: "ROI_ECUDA",
-           5: "ROI_ETIMEOUT", 6: "ROI_EBUSY"}
+           5: "ROI_ETIMEOUT", 6: "ROI_EBUSY", 7: "ROI_ECANCELED"}
 
 
 class Geometry(ctypes.Structure):
@@ -90,7 +91,7 @@ class ServerStats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_longlong), ("device_in_use", ctypes.c_size_t),
                 ("device_peak", ctypes.c_size_t), ("host_in_use", ctypes.c_size_t), ("host_peak", ctypes.c_size_t),
                 ("blocks", ctypes.c_int), ("single_units", ctypes.c_int), ("teams", ctypes.c_int),
-                ("team_blocks", ctypes.c_int)]
+                ("team_blocks", ctypes.c_int), ("cancelled", ctypes.c_longlong)]
 
 
 # every symbol declared in include/roi_recon.h
@@ -105,7 +106,7 @@ EXPORTS = [
     "roi_server_last_error", "roi_server_destroy", "roi_server_footprint",
     "roi_recon_filter_prepare", "roi_recon_filter_get", "roi_recon_set_sinogram_truncated",
     "roi_recon_solve_tiled", "roi_recon_state_size", "roi_recon_state_export", "roi_recon_solve_local_resume",
-    "roi_recon_check_report",
+    "roi_recon_check_report", "roi_server_cancel", "roi_server_set_option", "roi_recon_test_fail_alloc",
 ]
 
 _lib = None
@@ -209,6 +210,12 @@ def lib() -> ctypes.CDLL:
                                                ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
                                                ctypes.POINTER(ctypes.c_int)]
             L.roi_server_footprint.restype = st
+            L.roi_server_cancel.argtypes = [_H, ctypes.c_longlong]
+            L.roi_server_cancel.restype = st
+            L.roi_server_set_option.argtypes = [_H, ctypes.c_int, ctypes.c_longlong]
+            L.roi_server_set_option.restype = st
+            L.roi_recon_test_fail_alloc.argtypes = [ctypes.c_int]
+            L.roi_recon_test_fail_alloc.restype = st
             _lib = L
     return _lib
 
@@ -396,6 +403,18 @@ def roi_server_stats_get(s, out: ServerStats) -> int:
 
 def roi_server_last_error(s) -> str:
     return (lib().roi_server_last_error(s) or b"").decode()
+
+
+def roi_server_cancel(s, rid: int) -> int:
+    return lib().roi_server_cancel(s, int(rid))
+
+
+def roi_server_set_option(s, opt: int, value: int) -> int:
+    return lib().roi_server_set_option(s, int(opt), int(value))
+
+
+def roi_recon_test_fail_alloc(nth: int) -> int:
+    return lib().roi_recon_test_fail_alloc(int(nth))
 
 
 def roi_server_footprint(n_pix: int, n_angles: int, n_det: int, storage: int, region: Region):
@@ -772,6 +791,14 @@ class Server:
 
     def drain(self, timeout_ms: float = 600000.0):
         self._check(roi_server_drain(self.s, timeout_ms))
+
+    def cancel(self, rid: int):
+        """Removes a queued request (its completion then reports ROI_ECANCELED); RoiError with
+        ROI_EBUSY once it is on the device."""
+        self._check(roi_server_cancel(self.s, rid))
+
+    def set_option(self, opt: int, value: int):
+        self._check(roi_server_set_option(self.s, opt, value))
 
     def stats(self) -> dict:
         st = ServerStats()

@@ -73,7 +73,8 @@ __global__ void __launch_bounds__(BPT, 1) k_batch_team(BatchArgs B) {
     if (tid == 0) {
         mbar_init(&s_mbar[0], 1);
         mbar_init(&s_mbar[1], 1);
-        s_team = rs::Team{(int)(blockIdx.x % B.team), B.team, B.bars + team_id, 0u, B.err, B.wait_ns};
+        s_team = rs::Team{(int)(blockIdx.x % B.team), B.team, B.bars + team_id, 0u, B.err, B.wait_ns,
+                          B.absent > 0 ? (unsigned)(B.team + B.absent) : 0u};
         const size_t slot = team_id;
         s_bufs.pp = B.slot_pp + slot * B.win_cap;
         s_bufs.u = B.slot_u + slot * B.win_cap;

@@ -25,6 +25,27 @@ namespace roi {
 static std::atomic<unsigned long long> g_launches{0};
 void count_launches(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 unsigned long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
+
+// Allocation failure injection (testing): > 0 counts down the allocations still to succeed
+// plus one; the allocation that brings it to zero fails without allocating.
+static std::atomic<long long> g_fail_alloc{0};
+static bool injected_failure() {
+    long long v = g_fail_alloc.load(std::memory_order_relaxed);
+    while (v > 0) {
+        if (g_fail_alloc.compare_exchange_weak(v, v - 1, std::memory_order_relaxed)) return v == 1;
+    }
+    return false;
+}
+cudaError_t dev_malloc(void** p, size_t bytes) {
+    *p = nullptr;
+    if (injected_failure()) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, bytes);
+}
+cudaError_t pinned_alloc(void** p, size_t bytes, unsigned flags) {
+    *p = nullptr;
+    if (injected_failure()) return cudaErrorMemoryAllocation;
+    return cudaHostAlloc(p, bytes, flags);
+}
 }  // namespace roi
 
 namespace {
@@ -36,7 +57,7 @@ template <class T>
 cudaError_t dev_alloc(T** p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
-    return cudaMalloc((void**)p, sizeof(T) * count);
+    return roi::dev_malloc((void**)p, sizeof(T) * count);
 }
 
 // Grow-only device buffer.
@@ -103,6 +124,7 @@ struct roi_recon {
     int exterior_ready = 0;  // p' in `pp` matches the cached plan and FBP
     // iterate state of the last solve_local (checkpoint / resume)
     bool state_valid = false;
+    bool state_region_path = false;  // the last solve_local ran in the whole-region solver
     int state_reg = 0, state_flag = 0;
     double state_lambda = 0.0;
     long long state_iters = 0;
@@ -248,6 +270,7 @@ roi_status ensure_plan(roi_recon* h, const roi_region* region) {
     h->plan_valid = false;
     h->exterior_ready = 0;
     h->state_valid = false;  // the solver buffers belong to another box now
+    h->state_region_path = false;
     h->h_loc.resize(h->na);
     h->h_ext.resize(h->na);
     const Rect grid{0, 0, h->N, h->N};
@@ -849,7 +872,7 @@ roi_status roi_recon_create(const roi_geometry* geom, void* cuda_stream, roi_rec
     h->xld = roi::padded_ld_e(h->N, h->esz);
     const size_t ns = (size_t)h->na * h->nd;
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMalloc(&h->p, (size_t)h->pesz * ns);
+    if (e == cudaSuccess) e = roi::dev_malloc(&h->p, (size_t)h->pesz * ns);
     if (e == cudaSuccess) e = dev_alloc(&h->q, ns);
     const size_t npad_bytes = (size_t)h->esz * h->N * h->xld;
     if (e == cudaSuccess) e = dev_alloc(&h->xfbp_base, npad_bytes);
@@ -1082,6 +1105,7 @@ roi_status roi_recon_forward_local(roi_recon_t h, const roi_region* region, cons
     if (!h || !region) return ROI_EINVAL;
     h->err.clear();
     h->state_valid = false;
+    h->state_region_path = false;
     if (!x || !y) return fail(h, ROI_EINVAL, "forward_local: null pointer");
     roi_status s = ensure_plan(h, region);
     if (s != ROI_OK) return s;
@@ -1096,6 +1120,7 @@ roi_status roi_recon_back_local(roi_recon_t h, const roi_region* region, const f
     if (!h || !region) return ROI_EINVAL;
     h->err.clear();
     h->state_valid = false;
+    h->state_region_path = false;
     if (!x || !y) return fail(h, ROI_EINVAL, "back_local: null pointer");
     roi_status s = ensure_plan(h, region);
     if (s != ROI_OK) return s;
@@ -1106,9 +1131,13 @@ roi_status roi_recon_back_local(roi_recon_t h, const roi_region* region, const f
 
 namespace {
 
+roi_status solve_batch_impl(roi_recon* h, int n, const roi_region* regions, const roi_solve_params* params,
+                            float* const* outs, int out_on_device, roi_solve_info* infos, int team_req);
+
 roi_status solve_local_impl(roi_recon* h, const roi_region* region, const roi_solve_params* params, float* out,
                             int out_on_device, roi_solve_info* info) {
     h->state_valid = false;  // the solver buffers are about to change
+    h->state_region_path = false;
     if (!out) return fail(h, ROI_EINVAL, "solve_local: null output");
     if (params->reg == ROI_FILTER_TV || params->reg == ROI_FILTER_ISTA) {  // run in the whole-region solver
         if (params->eval_objective) return fail(h, ROI_EINVAL, "solve_local: no objective for this regularizer");
@@ -1131,6 +1160,17 @@ roi_status solve_local_impl(roi_recon* h, const roi_region* region, const roi_so
     }
     roi_status s = ensure_plan(h, region);
     if (s != ROI_OK) return s;
+    int pblocks = 0;
+    if (!filt && h->opt_persistent && params->iters > 0 && !persist_ok(h, &pblocks) && !h->resume &&
+        !params->eval_objective && (params->reg == ROI_SIRT_NONNEG || params->precond)) {
+        // a box too large for the single-launch solver: the whole-region solver, one
+        // cooperative team of every co-resident block, exterior step p' = r + W_L x_fbp
+        // (Eq. locouter with the residual r = p - W x_fbp of the FBP)
+        float* outs[1] = {out};
+        s = solve_batch_impl(h, 1, region, params, outs, out_on_device, info, -1);
+        if (s == ROI_OK) h->state_region_path = true;
+        return s;
+    }
     double L_flag = 0.0;
     if (filt) {
         s = solve_filter(h, params);
@@ -1219,6 +1259,10 @@ roi_status roi_recon_solve_local(roi_recon_t h, const roi_region* region, const 
 roi_status roi_recon_state_size(roi_recon_t h, size_t* bytes) {
     if (!h || !bytes) return ROI_EINVAL;
     h->err.clear();
+    if (!h->state_valid && h->state_region_path)
+        return fail(h, ROI_ESTATE,
+                    "state_size: the last solve ran in the whole-region solver, which keeps no resumable state "
+                    "(ROI_OPT_SINGLE_LAUNCH = 0 keeps one for large boxes)");
     if (!h->state_valid) return fail(h, ROI_ESTATE, "state_size: no solver state (run solve_local first)");
     *bytes = state_bytes_for(h->state_reg, h->box.w, h->box.h, h->na, h->stride);
     return ROI_OK;
@@ -1228,6 +1272,10 @@ roi_status roi_recon_state_export(roi_recon_t h, void* dst, size_t bytes, int on
     if (!h) return ROI_EINVAL;
     h->err.clear();
     if (!dst) return fail(h, ROI_EINVAL, "state_export: null destination");
+    if (!h->state_valid && h->state_region_path)
+        return fail(h, ROI_ESTATE,
+                    "state_export: the last solve ran in the whole-region solver, which keeps no resumable state "
+                    "(ROI_OPT_SINGLE_LAUNCH = 0 keeps one for large boxes)");
     if (!h->state_valid) return fail(h, ROI_ESTATE, "state_export: no solver state (run solve_local first)");
     const int nx = h->box.w, ny = h->box.h;
     const size_t need = state_bytes_for(h->state_reg, nx, ny, h->na, h->stride);
@@ -1311,6 +1359,7 @@ roi_status roi_recon_filter_prepare(roi_recon_t h, int n_iters) {
     if (!h) return ROI_EINVAL;
     h->err.clear();
     h->state_valid = false;
+    h->state_region_path = false;
     if (n_iters < 1 || n_iters > 100000) return fail(h, ROI_EINVAL, "filter_prepare: n_iters out of range");
     if (!h->have_sino) return fail(h, ROI_ESTATE, "filter_prepare: no sinogram (call set_sinogram first)");
     if (h->filt_n < n_iters) {
@@ -1335,10 +1384,13 @@ roi_status roi_recon_filter_get(roi_recon_t h, int n_filters, float* u_out, doub
     return ROI_OK;
 }
 
-roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions, const roi_solve_params* params,
-                                 float* const* outs, int out_on_device, roi_solve_info* infos) {
-    if (!h) return ROI_EINVAL;
-    h->err.clear();
+namespace {
+
+// roi_recon_solve_batch with a choice of launch: team_req = 0 picks it from the number of
+// regions (one block per region, or teams of up to 16 blocks for few regions); team_req < 0
+// makes one team of every co-resident block (a lone large region).
+roi_status solve_batch_impl(roi_recon* h, int n, const roi_region* regions, const roi_solve_params* params,
+                            float* const* outs, int out_on_device, roi_solve_info* infos, int team_req) {
     if (n < 0 || (n > 0 && (!regions || !params || !outs))) return fail(h, ROI_EINVAL, "solve_batch: bad arguments");
     if (n == 0) return ROI_OK;
     bool need_fbp = false;
@@ -1400,16 +1452,20 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
     if (!out_on_device) CU(h, h->b_out.ensure(out_total));
     // few regions: teams of blocks per region (co-resident: at most one block per SM)
     int blocks = std::max(1, h->sms);
-    const int team = std::min(16, blocks / n);
+    int team = std::min(16, blocks / n);
+    if (team_req < 0) team = std::min(blocks, roi::serve_max_blocks(h->device));
     if (team > 1) {
         blocks = std::min(blocks, roi::serve_max_blocks(h->device));
+        team = std::min(team, blocks);
         blocks = (blocks / team) * team;
         CU(h, h->b_bars.ensure((size_t)blocks / team));
     }
-    for (DevBuf* b : {&h->s_pp, &h->s_u, &h->s_sig}) CU(h, b->ensure(win_cap * blocks));
-    for (DevBuf* b : {&h->s_x, &h->s_vx, &h->s_vy, &h->s_tau}) CU(h, b->ensure(img_cap * blocks));
-    for (DevBuf* b : {&h->s_xa, &h->s_xaT}) CU(h, b->ensure(pad_cap * blocks));
-    if (need_fgp) CU(h, h->s_fgp.ensure(5 * img_cap * blocks));
+    // one slot of buffers per block, or per team of blocks
+    const size_t slots = team > 1 ? (size_t)blocks / team : (size_t)blocks;
+    for (DevBuf* b : {&h->s_pp, &h->s_u, &h->s_sig}) CU(h, b->ensure(win_cap * slots));
+    for (DevBuf* b : {&h->s_x, &h->s_vx, &h->s_vy, &h->s_tau}) CU(h, b->ensure(img_cap * slots));
+    for (DevBuf* b : {&h->s_xa, &h->s_xaT}) CU(h, b->ensure(pad_cap * slots));
+    if (need_fgp) CU(h, h->s_fgp.ensure(5 * img_cap * slots));
     // ---- page-locked staging: tables, descriptors, order
     const size_t tab_bytes = sizeof(AngleRec) * (size_t)n * na;
     const size_t roi_bytes = sizeof(roi::BatchRoi) * (size_t)n;
@@ -1420,7 +1476,7 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
         if (h->pin) cudaFreeHost(h->pin);
         h->pin = nullptr;
         h->pin_cap = 0;
-        CU(h, cudaMallocHost((void**)&h->pin, pin_need));
+        CU(h, roi::pinned_alloc((void**)&h->pin, pin_need, cudaHostAllocDefault));
         h->pin_cap = pin_need;
     }
     AngleRec* ptab = reinterpret_cast<AngleRec*>(h->pin);
@@ -1496,6 +1552,7 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
     B.wait_ns = h->opt_wait_ns;
     B.team = team > 1 ? team : 1;
     B.bars = team > 1 ? h->b_bars.p : nullptr;
+    B.absent = h->opt_phantoms;
     const size_t smem = roi::batch_smem_bytes(max_stage, h->na);
     cudaError_t e;
     {
@@ -1516,6 +1573,15 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
         }
     }
     return ROI_OK;
+}
+
+}  // namespace
+
+roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions, const roi_solve_params* params,
+                                 float* const* outs, int out_on_device, roi_solve_info* infos) {
+    if (!h) return ROI_EINVAL;
+    h->err.clear();
+    return solve_batch_impl(h, n, regions, params, outs, out_on_device, infos, 0);
 }
 
 roi_status roi_recon_solve_tiled(roi_recon_t h, int tile, int margin, const roi_solve_params* params, float* out) {
@@ -1643,5 +1709,11 @@ roi_status roi_recon_kernel_times(roi_recon_t h, int kernel, int* launches, doub
 }
 
 unsigned long long roi_recon_launch_count(void) { return roi::launches_total(); }
+
+roi_status roi_recon_test_fail_alloc(int nth) {
+    if (nth < 0) return ROI_EINVAL;
+    roi::g_fail_alloc.store(nth, std::memory_order_relaxed);
+    return ROI_OK;
+}
 
 }  // extern "C"

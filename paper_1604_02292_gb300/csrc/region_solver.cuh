@@ -70,6 +70,8 @@ struct Team {
     unsigned nbar;             // barriers passed by this block (thread 0's copy is used)
     int* err;
     unsigned long long wait_ns;
+    unsigned expect;           // arrivals a barrier waits for: 0 = size; testing only: size plus
+                               // participants that never arrive, so every barrier runs out
 };
 
 // Team barrier.  false: a wait gave up (error flag set) and the caller must leave.
@@ -82,7 +84,7 @@ __device__ __forceinline__ bool team_sync(Team& T) {
     if (threadIdx.x == 0) {
         int ok = 1;
         ++T.nbar;
-        const unsigned target = T.nbar * (unsigned)T.size;
+        const unsigned target = T.nbar * (T.expect ? T.expect : (unsigned)T.size);
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(T.bar) : "memory");
         unsigned long long t0 = 0;
         for (unsigned polls = 1;; ++polls) {

@@ -134,6 +134,12 @@ int round_stride(int wmax);
 // aidx = sinogram index; *nrow = their count; returns the largest window width.
 int plan_region_table(int N, int na, int nd, const double* angles, Rect box, AngleRec* out, int* nrow);
 
+// ---------------------------------------------------------------- allocation
+// Every device and page-locked host allocation of the library goes through these two, so
+// that a test can make the n-th one fail as if memory had run out (roi_recon_test_fail_alloc).
+cudaError_t dev_malloc(void** p, size_t bytes);
+cudaError_t pinned_alloc(void** p, size_t bytes, unsigned flags);
+
 // ----------------------------------------------------------------- launchers
 // Process-wide count of kernels launched by the library.
 void count_launches(unsigned n);
@@ -383,6 +389,7 @@ struct BatchArgs {
     unsigned long long wait_ns;
     int team;              // blocks per region: 1, or > 1 for a cooperative launch of teams
     unsigned* bars;        // team > 1: one barrier counter per team (zeroed by the launcher)
+    int absent;            // testing only: barrier participants per team that never arrive
 };
 // Device buffers of one whole-region solve: windows [na][stride]; box arrays [ny][nx];
 // padded images from row 0 column -kPad, row strides padded_ld(nx) / padded_ld(ny).
@@ -434,6 +441,9 @@ struct ServeArgs {
     unsigned long long cap_ns;     // longest poll of one block
     int* err;
     unsigned long long wait_ns;
+    // testing only: > 0 barrier participants per team that never arrive; < 0 the team
+    // leaders stay away (members' mailbox waits run out)
+    int absent;
 };
 size_t serve_smem_bytes();
 int serve_max_blocks(int device);  // co-resident blocks of the serving kernel

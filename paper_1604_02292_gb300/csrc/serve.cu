@@ -119,7 +119,9 @@ __global__ void __launch_bounds__(BPT, 1) k_serve(const ServeArgs A) {
         const int rel = b - P.first_block;
         const int team_id = rel / P.team;
         s_pool = (rel < 0 || team_id >= P.nteams) ? -1 : pi;  // -1: not part of a unit
-        s_team = rs::Team{rel - team_id * P.team, P.team, A.bars + P.team_base + team_id, 0u, A.err, A.wait_ns};
+        s_team = rs::Team{rel - team_id * P.team, P.team, A.bars + P.team_base + team_id, 0u, A.err, A.wait_ns,
+                          (A.absent > 0 && P.team > 1) ? (unsigned)(P.team + A.absent) : 0u};
+        if (A.absent < 0 && P.team > 1 && s_team.member == 0) s_pool = -1;  // testing: an absent leader
         s_mail = 0;
         mbar_init(&s_mbar[0], 1);
         mbar_init(&s_mbar[1], 1);

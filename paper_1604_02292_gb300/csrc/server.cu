@@ -190,6 +190,9 @@ struct roi_server {
     bool leaving = false;  // the close flag was set to end a solo launch
     cudaEvent_t ev_end = nullptr;
     long long launches = 0;
+    // options (roi_server_set_option), read at each launch
+    unsigned long long opt_wait_ns = 2000000000ull;  // team barrier / mailbox wait limit
+    int opt_absent = 0;                               // testing only: absent participants / leaders
     // requests
     std::mutex mu;
     std::thread worker;
@@ -198,7 +201,7 @@ struct roi_server {
     long long next_id = 1;
     std::unordered_map<long long, Req*> reqs;
     std::deque<roi_server_completion> completed;
-    long long n_submitted = 0, n_completed = 0, n_failed = 0, n_outstanding = 0;
+    long long n_submitted = 0, n_completed = 0, n_failed = 0, n_outstanding = 0, n_cancelled = 0;
 };
 
 namespace {
@@ -259,8 +262,9 @@ roi_status ensure_rings(roi_server* s) {
         P.occupant.assign(P.slots, nullptr);
         ring_total += P.nteams > 0 ? slot_bytes * P.slots : 0;
     }
-    SCU(s, cudaHostAlloc((void**)&s->ring_alloc, std::max<size_t>(ring_total, kAlign),
-                         cudaHostAllocMapped | cudaHostAllocPortable));
+    if (!s->ring_alloc)  // (kept when a later allocation here failed and submit is retried)
+        SCU(s, roi::pinned_alloc((void**)&s->ring_alloc, std::max<size_t>(ring_total, kAlign),
+                                 cudaHostAllocMapped | cudaHostAllocPortable));
     size_t off = 0;
     for (Pool& P : s->pools) {
         if (P.nteams == 0) continue;
@@ -270,7 +274,8 @@ roi_status ensure_rings(roi_server* s) {
         SCU(s, cudaHostGetDevicePointer(&d, P.ring_h, 0));
         P.ring_d = (unsigned char*)d;
     }
-    SCU(s, cudaMalloc((void**)&s->rec_slots_d, sizeof(AngleRec) * (size_t)s->max_na * s->blocks));
+    if (!s->rec_slots_d)
+        SCU(s, roi::dev_malloc((void**)&s->rec_slots_d, sizeof(AngleRec) * (size_t)s->max_na * s->blocks));
     s->rings_ready = true;
     return ROI_OK;
 }
@@ -471,9 +476,12 @@ roi_status launch(roi_server* s) {
     A.rec_slots = s->rec_slots_d;
     A.max_na = s->max_na;
     A.idle_ns = (unsigned long long)s->cfg.idle_us * 1000ull;
-    A.cap_ns = 60ull * 1000000000ull;
+    // a unit polls for work at most 60 s; with absent leaders (testing) their members'
+    // mailbox waits, bounded by this plus the wait limit, run out soon
+    A.cap_ns = s->opt_absent < 0 ? s->opt_wait_ns : 60ull * 1000000000ull;
     A.err = s->err_d;
-    A.wait_ns = 2000000000ull;
+    A.wait_ns = s->opt_wait_ns;
+    A.absent = s->opt_absent;
     cudaError_t e = roi::launch_serve(A, s->blocks, s->st);
     if (e != cudaSuccess) return scuda(s, e, "serving kernel launch");
     SCU(s, cudaEventRecord(s->ev_end, s->st));
@@ -626,7 +634,7 @@ roi_status roi_server_create(const roi_server_config* cfg_in, roi_server_t* out)
     const size_t bars_b = sizeof(unsigned) * (size_t)nteam_total, mseq_b = bars_b;
     const size_t mval_off = round_up(fixed + bars_b + mseq_b);
     const size_t ctl_bytes = mval_off + sizeof(long long) * (size_t)nteam_total;
-    if (e == cudaSuccess) e = cudaMalloc((void**)&s->dctl, ctl_bytes);
+    if (e == cudaSuccess) e = roi::dev_malloc((void**)&s->dctl, ctl_bytes);
     if (e == cudaSuccess) e = cudaMemset(s->dctl, 0, ctl_bytes);
     if (e == cudaSuccess) {
         s->busy_d = reinterpret_cast<int*>(s->dctl);
@@ -641,9 +649,10 @@ roi_status roi_server_create(const roi_server_config* cfg_in, roi_server_t* out)
         s->ctl_reset_bytes = bars_b + mseq_b;
         if (s->ctl_reset_bytes == 0) s->ctl_reset_bytes = 4;
     }
-    if (e == cudaSuccess) e = cudaMalloc((void**)&s->arena_d, cfg.device_bytes);
+    if (e == cudaSuccess) e = roi::dev_malloc((void**)&s->arena_d, cfg.device_bytes);
     if (e == cudaSuccess) s->darena.init(cfg.device_bytes);
-    if (e == cudaSuccess) e = cudaHostAlloc((void**)&s->out_h, cfg.host_bytes, cudaHostAllocMapped | cudaHostAllocPortable);
+    if (e == cudaSuccess)
+        e = roi::pinned_alloc((void**)&s->out_h, cfg.host_bytes, cudaHostAllocMapped | cudaHostAllocPortable);
     if (e == cudaSuccess) {
         void* d = nullptr;
         e = cudaHostGetDevicePointer(&d, s->out_h, 0);
@@ -653,8 +662,8 @@ roi_status roi_server_create(const roi_server_config* cfg_in, roi_server_t* out)
     // control words and completion words, page-locked
     const size_t done_b = sizeof(unsigned long long) * (size_t)cfg.ring_slots;
     if (e == cudaSuccess)
-        e = cudaHostAlloc((void**)&s->ctl_h, round_up(sizeof(Ctl)) + 2 * round_up(done_b),
-                          cudaHostAllocMapped | cudaHostAllocPortable);
+        e = roi::pinned_alloc((void**)&s->ctl_h, round_up(sizeof(Ctl)) + 2 * round_up(done_b),
+                              cudaHostAllocMapped | cudaHostAllocPortable);
     if (e == cudaSuccess) {
         std::memset(s->ctl_h, 0, round_up(sizeof(Ctl)) + 2 * round_up(done_b));
         void* d = nullptr;
@@ -837,7 +846,47 @@ roi_status roi_server_stats_get(roi_server_t s, roi_server_stats* out) {
     out->single_units = s->pools[0].nteams;
     out->teams = s->pools[1].nteams;
     out->team_blocks = s->pools[1].team;
+    out->cancelled = s->n_cancelled;
     return ROI_OK;
+}
+
+roi_status roi_server_cancel(roi_server_t s, long long id) {
+    if (!s) return ROI_EINVAL;
+    std::lock_guard<std::mutex> g(s->mu);
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end()) return sfail(s, ROI_EINVAL, "cancel: unknown request %lld", id);
+    Req* r = it->second;
+    if (r->state == 1) return sfail(s, ROI_EBUSY, "cancel: request %lld is already on the device", id);
+    if (r->state == 2) return sfail(s, ROI_EINVAL, "cancel: request %lld has completed", id);
+    std::deque<Req*>& pend = s->pools[r->pool].pending;
+    auto q = std::find(pend.begin(), pend.end(), r);
+    if (q == pend.end()) return sfail(s, ROI_EINVAL, "cancel: request %lld is not queued", id);
+    pend.erase(q);
+    r->t_done = now_ms();
+    r->status = ROI_ECANCELED;
+    r->state = 2;
+    --s->n_outstanding;
+    ++s->n_cancelled;
+    push_completion(s, r);
+    return ROI_OK;
+}
+
+roi_status roi_server_set_option(roi_server_t s, roi_option opt, long long value) {
+    if (!s) return ROI_EINVAL;
+    std::lock_guard<std::mutex> g(s->mu);
+    switch (opt) {
+        case ROI_OPT_WAIT_LIMIT_US:
+            if (value < 1 || value > 600000000LL) return sfail(s, ROI_EINVAL, "set_option: wait limit out of range");
+            s->opt_wait_ns = (unsigned long long)value * 1000ull;
+            return ROI_OK;
+        case ROI_OPT_TEST_ABSENT_BLOCKS:
+            if (value < -1 || value > 1024) return sfail(s, ROI_EINVAL, "set_option: absent blocks out of range");
+            s->opt_absent = (int)value;
+            return ROI_OK;
+        default:
+            break;
+    }
+    return sfail(s, ROI_EINVAL, "set_option: option %d does not apply to a server", (int)opt);
 }
 
 const char* roi_server_last_error(roi_server_t s) { return s ? s->err.c_str() : "null server"; }

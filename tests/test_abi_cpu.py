@@ -133,3 +133,10 @@ def test_server_footprint_rejects_bad_input():
         R.server_footprint(0, 96, 272, (100.0, 100.0, 5.0, 1.0))
     with pytest.raises(R.RoiError):
         R.server_footprint(256, 96, 272, (100.0, 100.0, 5.0, 1.0), storage=9)
+
+
+def test_alloc_failure_hook_arguments():
+    """The allocation-failure hook is host-only: negative counts are refused, 0 turns it off."""
+    assert R.roi_recon_test_fail_alloc(-1) == R.ROI_EINVAL
+    assert R.roi_recon_test_fail_alloc(3) == R.ROI_OK
+    assert R.roi_recon_test_fail_alloc(0) == R.ROI_OK
