@@ -243,6 +243,7 @@ def test_injected_allocation_failures_leave_handles_usable():
         for nth in range(1, 64):
             R.roi_recon_test_fail_alloc(nth)
             st, h = R.roi_recon_create(g, 0)
+            R.roi_recon_test_fail_alloc(0)  # disarm: the countdown may not have run out
             if st == R.ROI_OK:
                 R.roi_recon_destroy(h)
                 break
@@ -277,11 +278,14 @@ def test_injected_allocation_failures_leave_handles_usable():
         for nth in range(1, 32):
             R.roi_recon_test_fail_alloc(nth)
             try:
-                R.Server(start=False).close()
-                break
+                srv = R.Server(start=False)
             except R.RoiError as e:
                 assert e.status == R.ROI_ENOMEM
                 n_srv += 1
+                continue
+            R.roi_recon_test_fail_alloc(0)
+            srv.close()
+            break
         assert n_srv >= 3
     finally:
         R.roi_recon_test_fail_alloc(0)
