@@ -159,13 +159,16 @@ roi_status roi_recon_set_sinogram_truncated(roi_recon_t h, const void* p, roi_dt
                                            int n_measured);
 
 /* Global filtered backprojection FBP(p, h) = W^T C_h p (Eq. fbp), Ram-Lak filter
- * scaled by pi/N_theta, on the whole N x N grid; the result is cached in the
- * handle (in its storage type) for the exterior step.  out_or_null: optional device
+ * scaled by pi/N_theta, on the whole N x N grid; the result is cached in the handle (in
+ * its image storage type) for the exterior step, restricted to the field of view: pixels
+ * whose centre lies farther than min(N, N_d)/2 from the rotation axis are set to 0 (the
+ * detector misses them at some angles, so their FBP value is not determined by the data
+ * and would make the reprojected exterior inconsistent).  out_or_null: optional device
  * [N][N] float32 copy of the cached image.  ROI_ESTATE before set_sinogram. */
 roi_status roi_recon_fbp(roi_recon_t h, float* out_or_null);
 
 /* Exterior subtraction (Sec. 1; Eq. locouter): p' = p - W M_F x_fbp on every ray that
- * reaches the extended box of *region.  window_out_or_null: optional device buffer
+ * reaches the extended box of *region (x_fbp: the cached image, inside its field of view).  window_out_or_null: optional device buffer
  * [n_angles][window_stride] float32 receiving p'; entry [a][k] belongs to bin
  * d0[a] + k, entries past the angle's width are 0.  d0_out_or_null: optional host
  * int[n_angles] receiving d0 (the call then synchronizes).  Sizes come from

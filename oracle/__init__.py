@@ -57,6 +57,7 @@ def _load():
             lib.orc_ramp.argtypes = [_I, _I, _D, _D]
             lib.orc_fbp.argtypes = [_I, _I, _I, _D, _D, _D]
             lib.orc_exterior.argtypes = [_I, _I, _I, _D] + i7 + [_D, _D, _D]
+            lib.orc_fov.argtypes = [_I, _I, _D]
             lib.orc_rowcol_sums.argtypes = [_I, _I, _I, _D] + i7 + [_D, _D]
             lib.orc_sirt.argtypes = [_I, _I, _I, _D] + i7 + [_D, _I, ctypes.c_double, _I, _I, _D]
             lib.orc_cp.argtypes = [_I, _I, _I, _D] + i7 + [_D, _I, ctypes.c_double, _I, ctypes.c_double, _D]
@@ -146,8 +147,16 @@ def fbp(g: Geometry, p) -> np.ndarray:
     return out
 
 
+def fov(g: Geometry, x) -> np.ndarray:
+    """x (N x N) with the pixels outside the field of view -- centre farther than
+    min(N, N_d)/2 from the rotation axis -- set to 0 (a copy)."""
+    x = _f64(x).reshape(g.N, g.N).copy()
+    _load().orc_fov(g.N, g.nd, _p(x))
+    return x
+
+
 def exterior(g: Geometry, box, p, xfbp) -> np.ndarray:
-    """p' = p - W M_F x_fbp over the whole sinogram."""
+    """p' = p - W M_F M_V x_fbp over the whole sinogram (M_V: the field of view, see fov)."""
     p = _f64(p).reshape(g.na, g.nd)
     xfbp = _f64(xfbp).reshape(g.N, g.N)
     out = np.empty_like(p)

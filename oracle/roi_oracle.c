@@ -39,6 +39,12 @@
  *   - FBP uses the spatial Ram-Lak filter h[0] = 1/4, h[odd k] = -1/(pi^2 k^2),
  *     h[even k != 0] = 0, applied as a linear zero-padded convolution of length
  *     2 N_d - 1, scaled by pi / N_theta.
+ *   - The exterior step reprojects the global reconstruction only inside its field of
+ *     view: the pixels whose centre lies within min(N, N_d)/2 of the rotation axis (for
+ *     N_d >= N the disc of diameter N that Sec. 3.3 takes as the object's support).
+ *     Outside it the detector misses the pixel at some angles, the FBP value there is
+ *     not determined by the data, and its reprojection would make p' inconsistent
+ *     (Sec. 1 warns that a poor global reconstruction causes artifacts in the ROI).
  *   - TV is isotropic, forward differences with a zero last difference (Neumann).
  *   - Chambolle-Pock uses the diagonal preconditioning of Pock & Chambolle (2011,
  *     alpha = 1) or scalar steps 0.99/||K|| from a power iteration.
@@ -201,12 +207,33 @@ void orc_fbp(int N, int na, int nd, const double* ang, const double* p, double* 
     free(q);
 }
 
-/* Exterior subtraction (Sec. 1): p' = p - W M_F x_fbp, every bin of the sinogram. */
+/* Field of view of the global reconstruction: pixel (i, j) lies in it when its centre
+ * is within D/2 of the rotation axis, D = min(N, N_d); in doubled coordinates
+ * (2 x_j, 2 y_i) = (2j - (N-1), (N-1) - 2i) the test is exact in integers. */
+static int in_fov(int N, int nd, int i, int j) {
+    const long long X = 2LL * j - (N - 1), Y = (long long)(N - 1) - 2LL * i;
+    const long long D = N < nd ? N : nd;
+    return X * X + Y * Y <= D * D;
+}
+
+/* x (N x N) restricted to the field of view: pixels outside it set to 0. */
+void orc_fov(int N, int nd, double* x) {
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j)
+            if (!in_fov(N, nd, i, j)) x[(size_t)i * N + j] = 0.0;
+}
+
+/* Exterior subtraction (Sec. 1): p' = p - W M_F M_V x_fbp, every bin of the sinogram,
+ * M_V the field of view of the global reconstruction (orc_fov). */
 void orc_exterior(int N, int na, int nd, const double* ang,
                   int bx0, int by0, int bw, int bh,
                   const double* p, const double* xfbp, double* pprime) {
-    orc_forward(N, na, nd, ang, 0, 0, N, N, xfbp, bx0, by0, bw, bh, pprime);
+    double* xv = (double*)malloc(sizeof(double) * (size_t)N * N);
+    memcpy(xv, xfbp, sizeof(double) * (size_t)N * N);
+    orc_fov(N, nd, xv);
+    orc_forward(N, na, nd, ang, 0, 0, N, N, xv, bx0, by0, bw, bh, pprime);
     for (long r = 0; r < (long)na * nd; ++r) pprime[r] = p[r] - pprime[r];
+    free(xv);
 }
 
 /* Row sums W_L 1 (per ray) and column sums W_L^T 1 (per box pixel). */

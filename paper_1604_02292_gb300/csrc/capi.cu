@@ -1031,6 +1031,10 @@ roi_status roi_recon_fbp(roi_recon_t h, float* out_or_null) {
     b.ny = h->N;
     b.win = h->q;
     b.part = nullptr;  // the whole grid has enough tiles for one angle group
+    // the cached global reconstruction is kept inside its field of view only: outside the
+    // disc of diameter min(N, N_d) some angles miss the pixel, its FBP value is not set by
+    // the data, and reprojecting it in the exterior step would make p' inconsistent
+    b.fov_d = std::min(h->N, h->nd);
     if (h->dt == 0) {  // straight into the padded image and its transpose
         b.out = static_cast<float*>(h->xfbp);
         b.out_ld = h->xld;

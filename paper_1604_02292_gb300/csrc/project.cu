@@ -185,6 +185,10 @@ __device__ __forceinline__ float back_epilogue(const BackArgs& A, int li, int lj
     const size_t o = (size_t)li * A.nx + lj;                  // unpadded [ny][nx] arrays
     float* xo = A.out + (size_t)li * A.out_ld + lj;
     if (MODE == BACK_PLAIN) {
+        if (A.fov_d > 0) {  // doubled centre coordinates, exact in integers
+            const long long X = 2LL * lj - (A.nx - 1), Y = (long long)(A.ny - 1) - 2LL * li;
+            if (X * X + Y * Y > (long long)A.fov_d * A.fov_d) acc = 0.f;
+        }
         *xo = acc;
         return acc;
     } else if (MODE == BACK_SIRT) {

@@ -203,6 +203,9 @@ struct BackArgs {
     const float* vy;
     float* xbar;           // BACK_CP: row stride xbar_ld (its transpose goes to outT)
     int xbar_ld;
+    // BACK_PLAIN on the whole grid (frame = grid): > 0 restricts the result to the field of
+    // view, the pixels whose centre lies within fov_d / 2 of the rotation axis (others 0)
+    int fov_d;
 };
 
 // Work splits chosen from the sizes alone (results never depend on other work).

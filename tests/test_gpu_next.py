@@ -38,7 +38,7 @@ def test_truncated_data_with_constant_padding(sino):
     xg = torch.empty((N, N), device="cuda")
     rr.fbp(xg)
     xg = xg.cpu().numpy()
-    assert rel_l2(xg, oracle.fbp(g, padded)) <= 1e-5
+    assert rel_l2(xg, oracle.fov(g, oracle.fbp(g, padded))) <= 1e-5
     # padding reduces the truncation error inside the measured disk (against the full data)
     full = oracle.fbp(g, sino.astype(np.float64))
     zero = oracle.fbp(g, np.pad(pt.astype(np.float64), ((0, 0), (off, off))))

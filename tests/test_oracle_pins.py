@@ -418,16 +418,49 @@ def test_cp_tv_matches_independent_admm():
 # ------------------------------------------------------------------- pipeline
 
 
-def test_exterior_is_p_minus_outer_projection():
-    N, na, nd = 64, 32, 64
+def _fov_mask(N, nd):
+    """Field of view by direct distance: pixel centre within min(N, N_d)/2 of the axis."""
+    jj, ii = _centres(N)
+    return np.hypot(jj, ii) <= min(N, nd) / 2.0
+
+
+@pytest.mark.parametrize("N,nd", [(64, 64), (64, 80), (63, 50)])
+def test_exterior_is_p_minus_outer_projection(N, nd):
+    """Eq. locouter on the global reconstruction inside its field of view:
+    p - p' + W_L (x_V on the box) = W x_V with x_V = M_V x_fbp."""
+    na = 32
     g = oracle.Geometry(N, na, nd)
     box = oracle.roi_box(N, 30.0, 34.0, 8, 4)
     xf = np.random.default_rng(6).random((N, N))
     p = np.random.default_rng(7).random((na, nd))
     pp = oracle.exterior(g, box, p, xf)
+    xv = np.where(_fov_mask(N, nd), xf, 0.0)
     x0, y0, w, h = box
-    np.testing.assert_allclose(p - pp + oracle.forward(g, xf[y0:y0 + h, x0:x0 + w], rect=box),
-                               oracle.forward(g, xf), rtol=0, atol=1e-11)
+    np.testing.assert_allclose(p - pp + oracle.forward(g, xv[y0:y0 + h, x0:x0 + w], rect=box),
+                               oracle.forward(g, xv), rtol=0, atol=1e-11)
+
+
+def test_fov_restriction():
+    """The field of view: the disc of diameter min(N, N_d) on the rotation axis.  An image
+    outside it reprojects to nothing in the exterior step (p' = p); inside it, the exterior
+    step is the plain p - W M_F x; the pixel count of the disc is the lattice-point count of
+    a brute-force enumeration."""
+    for N, nd in [(16, 16), (16, 12), (15, 40), (7, 7)]:
+        g = oracle.Geometry(N, 8, nd)
+        m = _fov_mask(N, nd)
+        count = sum(1 for i in range(N) for j in range(N)
+                    if (2 * j - (N - 1)) ** 2 + ((N - 1) - 2 * i) ** 2 <= min(N, nd) ** 2)
+        assert int(m.sum()) == count
+        x = np.random.default_rng(N + nd).random((N, N)) + 0.5
+        xv = oracle.fov(g, x)
+        assert np.array_equal(xv != 0.0, m)
+        p = np.random.default_rng(3).random((8, nd))
+        box = (N // 3, N // 3, 3, 2)
+        outside = np.where(m, 0.0, x)
+        assert np.array_equal(oracle.exterior(g, box, p, outside), p)
+        inside = np.where(m, x, 0.0)
+        np.testing.assert_allclose(oracle.exterior(g, box, p, inside),
+                                   p - oracle.forward(g, inside, hole=box), rtol=0, atol=1e-12)
 
 
 def test_roi_box_rule():
