@@ -83,6 +83,7 @@ def parse():
     ap.add_argument("--no-global", action="store_true", help="default workload: skip the local-vs-global report")
     ap.add_argument("--no-batch", action="store_true", help="default workload: skip the batching figure")
     ap.add_argument("--no-precision", action="store_true", help="default workload: skip the precision figure")
+    ap.add_argument("--autotune", action="store_true", help="batch workloads: autotune the tile shapes first")
     ap.add_argument("--rates", default="50,100,150",
                     help="default workload: arrival rates (requests/s) of the sustainable-rate serving points")
     return ap.parse_args()
@@ -499,7 +500,7 @@ def run_ours(args):
     batch = None
     if not args.no_batch:
         wb = WL.BATCHES["roi_batch_2048"]
-        batch = batch_measure(wb, None, 1, 1, dist, ws, rank, local, clock=False)
+        batch = batch_measure(wb, None, 1, 1, dist, ws, rank, local, clock=False, tune=True)
         batch.pop("clocks")
         batch.update({"workload": wb.name, "N": wb.N, "n_angles": wb.n_angles, "n_det": wb.n_det,
                       "radius": [wb.r_lo, wb.r_hi], "iters": wb.iters, "solvers": "SIRT/TV 50/50",
@@ -572,11 +573,13 @@ def run_ours(args):
     return 0
 
 
-def batch_measure(w, count, steps, warmup, dist, ws, rank, local, clock=True):
+def batch_measure(w, count, steps, warmup, dist, ws, rank, local, clock=True, tune=False):
     """Batched solves: one step = roi_recon_solve_batch over the regions (one persistent
     launch); the warm-up steps run every region for one iteration (same boxes, so the same
     device slots).  Returns regions/s over all ranks, the per-step times and the lerps/s of
-    rank 0 against the derived ceiling."""
+    rank 0 against the derived ceiling.  tune: the phase B tile shapes are first chosen by
+    roi_recon_autotune on this sinogram (timed apart), and the default table (16 x 16 for
+    every box size) is measured as well."""
     import torch
 
     import paper_1604_02292_gb300 as R
@@ -597,20 +600,33 @@ def batch_measure(w, count, steps, warmup, dist, ws, rank, local, clock=True):
         for _ in range(warmup):
             outs, _ = rr.solve_batch(regions, warm, outs)
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+
+    def timed_steps():
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        with torch.cuda.stream(stream):
+            for k in range(steps):
+                ev[k][0].record(stream)
+                rr.solve_batch(regions, params, outs)
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        rr.sync()
+        return [a.elapsed_time(b) for a, b in ev]
+
+    tuning = None
+    if tune:
+        default_ms = timed_steps()  # the default table: 16 x 16 tiles for every box size
+        t0 = time.perf_counter()
+        shapes, tms = rr.autotune()
+        tuning = {"shapes_per_class": [list(R.TILE_SHAPES[sh]) for sh in shapes],
+                  "classes": ["box side <= 96", "97..216", "217..384"], "trial_ms": tms,
+                  "autotune_s": time.perf_counter() - t0,
+                  "default_solves_per_s": len(all_items) * steps / (sum(default_ms) / 1e3)}
     if dist:
         dist.barrier()
     n0 = R.roi_recon_launch_count()
     with ClockSampler(local if clock else None) as clk:
-        with torch.cuda.stream(stream):
-            for k in range(steps):
-                ev[k][0].record(stream)
-                outs, _ = rr.solve_batch(regions, params, outs)
-                ev[k][1].record(stream)
-        torch.cuda.synchronize()
-    rr.sync()
+        ms = timed_steps()
     launches = int(R.roi_recon_launch_count() - n0)
-    ms = [a.elapsed_time(b) for a, b in ev]
     n_lerps = 0
     for reg, prm in items:
         pl = rr.plan(reg)
@@ -625,7 +641,7 @@ def batch_measure(w, count, steps, warmup, dist, ws, rank, local, clock=True):
     return {"value": len(all_items) * steps / t, "unit": "solves/s", "regions": len(all_items), "steps": steps,
             "ms_per_step": statistics.mean(ms), "gpu_launches": launches,
             "projector_Glerp_s_rank0": achieved, "lerp_ceiling_Glerp_s": peak, "frac_of_ceiling": achieved / peak,
-            "clocks": clk.summary()}
+            "autotune": tuning, "clocks": clk.summary()}
 
 
 def run_batch(args):
@@ -639,7 +655,7 @@ def run_batch(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     w = WL.BATCHES[args.workload]
-    m = batch_measure(w, args.batch_count, args.steps, args.warmup, dist, ws, rank, local)
+    m = batch_measure(w, args.batch_count, args.steps, args.warmup, dist, ws, rank, local, tune=args.autotune)
     line = {
         "metric": "roi_solves_per_s", "value": m["value"], "unit": "solves/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
@@ -650,6 +666,7 @@ def run_batch(args):
         "gpu_launches": m["gpu_launches"],
         "projector_Glerp_s_rank0": m["projector_Glerp_s_rank0"],
         "frac_of_lerp_ceiling": m["frac_of_ceiling"],
+        "autotune": m["autotune"],
         "clocks": m["clocks"],
     }
     if rank == 0:

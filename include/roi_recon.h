@@ -310,10 +310,37 @@ typedef enum {
      * solve_local, and (roi_server_set_option) requests solved by a team of a server.  For
      * a server, -1 keeps the team leaders away instead, so that the members' waits for
      * the leader's claim (the team mailbox) run out. */
-    ROI_OPT_TEST_ABSENT_BLOCKS = 2
+    ROI_OPT_TEST_ABSENT_BLOCKS = 2,
+    /* -1 (default): the phase B tile shape of each whole-region solve (solve_batch, large
+     * boxes of solve_local, and requests served from this handle's sinogram) is taken from
+     * the handle's tile table by box size (roi_recon_autotune); 0, 1, 2: that shape for
+     * every region.  Shapes: 0 = 16 x 16 pixels per warp (runs of 8 pixels per lane),
+     * 1 = 8 x 8 (runs of 2), 2 = 16 x 8 (runs of 4).  The shape changes how a pixel's
+     * angles are grouped into partial sums, so results of different shapes agree to
+     * rounding, not bit for bit; with one shape they are bit-identical wherever solved. */
+    ROI_OPT_TILE_SHAPE = 3
 } roi_option;
 
 roi_status roi_recon_set_option(roi_recon_t h, roi_option opt, long long value);
+
+/* Autotuner of the batching tier's tile shapes (Sec. 5.5: many independent local solves).
+ * For each box-size class -- sides 48..96, 97..216 (image staged whole), 217..384 (image
+ * streamed in bands), clipped to the grid -- it solves one batch of regions_per_class
+ * seeded regions of that class (0: two per SM; SIRT and CP-TV alternating, iters
+ * iterations, 0: 20) on this handle's sinogram with each tile shape (a warm-up, then the
+ * best of two timed runs, CUDA events on the handle's stream), and keeps the fastest shape
+ * per class in the handle's tile table.  The table is also kept per geometry (grid,
+ * angles, detector, image storage) for handles created later in the process.
+ * shapes_out (optional, int[3]): the chosen shape per class; ms_out (optional,
+ * double[3][3]): milliseconds per class and shape (0 for a class the grid cannot hold).
+ * Synchronizes.  ROI_ESTATE before fbp. */
+roi_status roi_recon_autotune(roi_recon_t h, int regions_per_class, int iters, int* shapes_out, double* ms_out);
+
+/* The handle's tile table (int[3], one shape per box-size class, see ROI_OPT_TILE_SHAPE):
+ * set it (ROI_EINVAL for an unknown shape) or read it.  A server reads the table of each
+ * sinogram's handle when the sinogram is added. */
+roi_status roi_recon_set_tile_shapes(roi_recon_t h, const int* shapes);
+roi_status roi_recon_get_tile_shapes(roi_recon_t h, int* shapes);
 
 /* Wait for all work on the handle's stream, then report device-side failures: ROI_ETIMEOUT
  * if a single-launch solve gave up at a grid barrier since the last report (its output is

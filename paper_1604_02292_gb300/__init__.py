@@ -38,12 +38,15 @@ __all__ = [
     "roi_server_start", "roi_server_stop", "roi_server_progress", "roi_server_poll", "roi_server_take",
     "roi_server_drain", "roi_server_stats_get", "roi_server_last_error", "roi_server_footprint",
     "roi_server_cancel", "roi_server_set_option", "roi_recon_test_fail_alloc",
+    "ROI_OPT_TILE_SHAPE", "TILE_SHAPES", "roi_recon_autotune", "roi_recon_set_tile_shapes",
+    "roi_recon_get_tile_shapes",
 ]
 
 ROI_OK, ROI_EINVAL, ROI_ENOMEM, ROI_ESTATE, ROI_ECUDA, ROI_ETIMEOUT, ROI_EBUSY, ROI_ECANCELED = range(8)
 ROI_F32, ROI_BF16, ROI_F16 = range(3)
 ROI_SIRT_NONNEG, ROI_TV_CP, ROI_FILTER_SIRT, ROI_FILTER_TV, ROI_FILTER_ISTA = range(5)
-ROI_OPT_SINGLE_LAUNCH, ROI_OPT_WAIT_LIMIT_US, ROI_OPT_TEST_ABSENT_BLOCKS = range(3)
+ROI_OPT_SINGLE_LAUNCH, ROI_OPT_WAIT_LIMIT_US, ROI_OPT_TEST_ABSENT_BLOCKS, ROI_OPT_TILE_SHAPE = range(4)
+TILE_SHAPES = {0: (16, 16), 1: (8, 8), 2: (16, 8)}   # phase B tile shape: (x, y) pixels per warp
 
 _STATUS = {0: "ROI_OK", 1: "ROI_EINVAL", 2: "ROI_ENOMEM", 3: "ROI_ESTATE", 4: "ROI_ECUDA",
            5: "ROI_ETIMEOUT", 6: "ROI_EBUSY", 7: "ROI_ECANCELED"}
@@ -107,6 +110,7 @@ EXPORTS = [
     "roi_recon_filter_prepare", "roi_recon_filter_get", "roi_recon_set_sinogram_truncated",
     "roi_recon_solve_tiled", "roi_recon_state_size", "roi_recon_state_export", "roi_recon_solve_local_resume",
     "roi_recon_check_report", "roi_server_cancel", "roi_server_set_option", "roi_recon_test_fail_alloc",
+    "roi_recon_autotune", "roi_recon_set_tile_shapes", "roi_recon_get_tile_shapes",
 ]
 
 _lib = None
@@ -216,6 +220,13 @@ def lib() -> ctypes.CDLL:
             L.roi_server_set_option.restype = st
             L.roi_recon_test_fail_alloc.argtypes = [ctypes.c_int]
             L.roi_recon_test_fail_alloc.restype = st
+            L.roi_recon_autotune.argtypes = [_H, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                             ctypes.POINTER(ctypes.c_double)]
+            L.roi_recon_autotune.restype = st
+            L.roi_recon_set_tile_shapes.argtypes = [_H, ctypes.POINTER(ctypes.c_int)]
+            L.roi_recon_set_tile_shapes.restype = st
+            L.roi_recon_get_tile_shapes.argtypes = [_H, ctypes.POINTER(ctypes.c_int)]
+            L.roi_recon_get_tile_shapes.restype = st
             _lib = L
     return _lib
 
@@ -415,6 +426,25 @@ def roi_server_set_option(s, opt: int, value: int) -> int:
 
 def roi_recon_test_fail_alloc(nth: int) -> int:
     return lib().roi_recon_test_fail_alloc(int(nth))
+
+
+def roi_recon_autotune(h, regions_per_class: int, iters: int):
+    """(status, shapes [3], ms [3][3])."""
+    shapes = (ctypes.c_int * 3)()
+    ms = (ctypes.c_double * 9)()
+    st = lib().roi_recon_autotune(h, int(regions_per_class), int(iters), shapes, ms)
+    return st, list(shapes), [list(ms[3 * c:3 * c + 3]) for c in range(3)]
+
+
+def roi_recon_set_tile_shapes(h, shapes) -> int:
+    arr = (ctypes.c_int * 3)(*[int(v) for v in shapes])
+    return lib().roi_recon_set_tile_shapes(h, arr)
+
+
+def roi_recon_get_tile_shapes(h):
+    arr = (ctypes.c_int * 3)()
+    st = lib().roi_recon_get_tile_shapes(h, arr)
+    return st, list(arr)
 
 
 def roi_server_footprint(n_pix: int, n_angles: int, n_det: int, storage: int, region: Region):
@@ -685,6 +715,23 @@ class RoiRecon:
 
     def set_option(self, opt: int, value: int):
         self._check(roi_recon_set_option(self.h, opt, value))
+
+    def autotune(self, regions_per_class: int = 0, iters: int = 0):
+        """Pick the phase B tile shape per box-size class by timing (roi_recon_autotune);
+        returns (shapes, ms) -- ms[class][shape] in milliseconds."""
+        st, shapes, ms = roi_recon_autotune(self.h, regions_per_class, iters)
+        self._check(st)
+        return shapes, ms
+
+    @property
+    def tile_shapes(self):
+        st, shapes = roi_recon_get_tile_shapes(self.h)
+        self._check(st)
+        return shapes
+
+    @tile_shapes.setter
+    def tile_shapes(self, shapes):
+        self._check(roi_recon_set_tile_shapes(self.h, shapes))
 
     def sync(self):
         """Wait for the handle's stream; raises RoiError(ROI_ETIMEOUT) if a device wait gave up."""

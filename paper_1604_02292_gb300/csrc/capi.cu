@@ -11,8 +11,12 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <array>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "roi_recon.h"
@@ -84,6 +88,27 @@ using DevBuf = DevBufT<float>;
 
 }  // namespace
 
+namespace {
+// Tile tables found by roi_recon_autotune, per geometry (grid, angles, detector, image
+// storage), for the handles created afterwards.
+struct TuneKey {
+    int N, na, nd, dt;
+    unsigned long long angles;  // FNV-1a of the angle array
+    bool operator<(const TuneKey& o) const {
+        return std::tie(N, na, nd, dt, angles) < std::tie(o.N, o.na, o.nd, o.dt, o.angles);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::array<int, roi::kShapeClasses>> g_tune;
+
+unsigned long long fnv_doubles(const std::vector<double>& v) {
+    unsigned long long h = 1469598103934665603ull;
+    const unsigned char* b = reinterpret_cast<const unsigned char*>(v.data());
+    for (size_t i = 0; i < v.size() * sizeof(double); ++i) h = (h ^ b[i]) * 1099511628211ull;
+    return h;
+}
+}  // namespace
+
 struct roi_recon {
     int N = 0, na = 0, nd = 0;
     std::vector<double> angles;
@@ -141,6 +166,8 @@ struct roi_recon {
     int* d_err = nullptr;
     int device = 0;
     int opt_persistent = 1;
+    int opt_tile_shape = -1;              // >= 0: phase B tile shape for every region
+    int tile_shape[roi::kShapeClasses] = {0, 0, 0};  // per box-size class (roi_recon_autotune)
     unsigned long long opt_wait_ns = 1000000000ull;
     int opt_phantoms = 0;
     size_t max_smem_optin = 0;
@@ -848,6 +875,7 @@ int sino_view(roi_recon* h, SinoView* v, std::string* msg) {
     v->fcp = h->filt_cp.p;
     v->fcp_n = h->fcp_n;
     v->disc_g = (float)h->disc_g;
+    for (int c = 0; c < kShapeClasses; ++c) v->shape[c] = h->opt_tile_shape >= 0 ? h->opt_tile_shape : h->tile_shape[c];
     return ROI_OK;
 }
 }  // namespace roi
@@ -921,6 +949,12 @@ roi_status roi_recon_create(const roi_geometry* geom, void* cuda_stream, roi_rec
     if (e != cudaSuccess) {
         roi_recon_destroy(h);
         return e == cudaErrorMemoryAllocation ? ROI_ENOMEM : ROI_ECUDA;
+    }
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tune.find(TuneKey{h->N, h->na, h->nd, h->dt, fnv_doubles(h->angles)});
+        if (it != g_tune.end())
+            for (int c = 0; c < roi::kShapeClasses; ++c) h->tile_shape[c] = it->second[c];
     }
     *out = h;
     return ROI_OK;
@@ -1514,6 +1548,7 @@ roi_status solve_batch_impl(roi_recon* h, int n, const roi_region* regions, cons
         filter_inputs(h, R);
         R.n_fgp = P.inner_iters ? P.inner_iters : 100;
         R.lam_f = (float)(0.5 * P.lambda / ((double)na * h->nd));
+        R.shape = h->opt_tile_shape >= 0 ? h->opt_tile_shape : h->tile_shape[roi::shape_class(std::max(box.w, box.h))];
         ooff += (size_t)box.w * box.h;
         pord[i] = i;
         if (infos) {
@@ -1638,6 +1673,118 @@ roi_status roi_recon_solve_tiled(roi_recon_t h, int tile, int margin, const roi_
     return ROI_OK;
 }
 
+roi_status roi_recon_autotune(roi_recon_t h, int regions_per_class, int iters, int* shapes_out, double* ms_out) {
+    if (!h) return ROI_EINVAL;
+    h->err.clear();
+    if (!h->have_fbp) return fail(h, ROI_ESTATE, "autotune: no FBP image (call fbp first)");
+    if (regions_per_class < 0 || regions_per_class > 100000 || iters < 0 || iters > 100000)
+        return fail(h, ROI_EINVAL, "autotune: regions_per_class or iters out of range");
+    const int n = regions_per_class ? regions_per_class : 2 * std::max(h->sms, 1);
+    const int it = iters ? iters : 20;
+    // box sides of the classes (side = 2 ceil(1.5 r) with margin r / 2)
+    const int side_lo[roi::kShapeClasses] = {48, 97, 217}, side_hi[roi::kShapeClasses] = {96, 216, 384};
+    unsigned long long rng = 0x9E3779B97F4A7C15ull;  // splitmix64, seeded the same every call
+    auto uni = [&rng]() {
+        unsigned long long z = (rng += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return (double)((z ^ (z >> 31)) >> 11) * (1.0 / 9007199254740992.0);
+    };
+    const int keep = h->opt_tile_shape;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CU(h, cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(h, ce, "autotune events");
+    }
+    roi_status st = ROI_OK;
+    DevBuf outb;
+    for (int c = 0; c < roi::kShapeClasses && st == ROI_OK; ++c) {
+        const int hi = std::min(side_hi[c], h->N);
+        if (hi < side_lo[c]) {  // the grid has no box of this class
+            for (int sh = 0; sh < roi::kTileShapes; ++sh)
+                if (ms_out) ms_out[c * roi::kTileShapes + sh] = 0.0;
+            continue;
+        }
+        std::vector<roi_region> regs(n);
+        std::vector<roi_solve_params> prms(n);
+        std::vector<float*> outs(n);
+        size_t total = 0;
+        std::vector<size_t> off(n);
+        for (int i = 0; i < n; ++i) {
+            const int side = side_lo[c] + (int)(uni() * (hi - side_lo[c] + 1));
+            const double r = std::max(1.0, (side / 2 - 0.5) / 1.5);  // box 2 ceil(1.5 r) = side (even)
+            const double ext = std::ceil(1.5 * r);
+            const double span = std::max(0.0, h->N - 2.0 * ext);
+            regs[i] = roi_region{ext + uni() * span, ext + uni() * span, r, 0.5 * r};
+            prms[i] = roi_solve_params{};
+            prms[i].reg = (i & 1) ? ROI_TV_CP : ROI_SIRT_NONNEG;
+            prms[i].lambda = (i & 1) ? 0.01 : 0.0;
+            prms[i].iters = it;
+            prms[i].precond = 1;
+            Rect box;
+            roi::plan_box(h->N, regs[i].cx, regs[i].cy, regs[i].radius, regs[i].margin, &box);
+            off[i] = total;
+            total += (size_t)box.w * box.h;
+        }
+        st = outb.ensure(total) == cudaSuccess ? ROI_OK : fail(h, ROI_ENOMEM, "autotune: output buffer");
+        if (st != ROI_OK) break;
+        for (int i = 0; i < n; ++i) outs[i] = outb.p + off[i];
+        double best = 0.0;
+        int best_sh = 0;
+        for (int sh = 0; sh < roi::kTileShapes && st == ROI_OK; ++sh) {
+            h->opt_tile_shape = sh;
+            double ms = 0.0;
+            for (int rep = 0; rep < 3 && st == ROI_OK; ++rep) {  // a warm-up, then the best of two
+                cudaEventRecord(e0, h->st);
+                st = solve_batch_impl(h, n, regs.data(), prms.data(), outs.data(), 1, nullptr, 0);
+                cudaEventRecord(e1, h->st);
+                if (st == ROI_OK) st = roi_recon_sync(h);
+                float t = 0.f;
+                if (st == ROI_OK && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess && rep > 0)
+                    ms = rep == 1 ? t : std::min(ms, (double)t);
+            }
+            if (ms_out) ms_out[c * roi::kTileShapes + sh] = ms;
+            if (st == ROI_OK && (sh == 0 || ms < best)) {
+                best = ms;
+                best_sh = sh;
+            }
+        }
+        if (st == ROI_OK) h->tile_shape[c] = best_sh;
+    }
+    outb.release();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->opt_tile_shape = keep;
+    h->state_valid = false;
+    h->state_region_path = false;
+    if (st != ROI_OK) return st;
+    if (shapes_out)
+        for (int c = 0; c < roi::kShapeClasses; ++c) shapes_out[c] = h->tile_shape[c];
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto& t = g_tune[TuneKey{h->N, h->na, h->nd, h->dt, fnv_doubles(h->angles)}];
+    for (int c = 0; c < roi::kShapeClasses; ++c) t[c] = h->tile_shape[c];
+    return ROI_OK;
+}
+
+roi_status roi_recon_set_tile_shapes(roi_recon_t h, const int* shapes) {
+    if (!h) return ROI_EINVAL;
+    h->err.clear();
+    if (!shapes) return fail(h, ROI_EINVAL, "set_tile_shapes: null argument");
+    for (int c = 0; c < roi::kShapeClasses; ++c)
+        if (shapes[c] < 0 || shapes[c] >= roi::kTileShapes)
+            return fail(h, ROI_EINVAL, "set_tile_shapes: unknown shape %d", shapes[c]);
+    for (int c = 0; c < roi::kShapeClasses; ++c) h->tile_shape[c] = shapes[c];
+    return ROI_OK;
+}
+
+roi_status roi_recon_get_tile_shapes(roi_recon_t h, int* shapes) {
+    if (!h || !shapes) return ROI_EINVAL;
+    for (int c = 0; c < roi::kShapeClasses; ++c) shapes[c] = h->tile_shape[c];
+    return ROI_OK;
+}
+
 roi_status roi_recon_set_timing(roi_recon_t h, int enable) {
     if (!h) return ROI_EINVAL;
     h->err.clear();
@@ -1663,19 +1810,24 @@ roi_status roi_recon_set_option(roi_recon_t h, roi_option opt, long long value) 
             if (value < 0 || value > 1024) return fail(h, ROI_EINVAL, "set_option: absent blocks out of range");
             h->opt_phantoms = (int)value;
             return ROI_OK;
+        case ROI_OPT_TILE_SHAPE:
+            if (value < -1 || value >= roi::kTileShapes) return fail(h, ROI_EINVAL, "set_option: unknown tile shape");
+            h->opt_tile_shape = (int)value;
+            return ROI_OK;
     }
     return fail(h, ROI_EINVAL, "set_option: unknown option %d", (int)opt);
 }
 
 int roi_recon_check_report(int* site, int* index) {
     cudaDeviceSynchronize();
-    roi::CheckReport reps[4];
+    roi::CheckReport reps[5];
     roi::check_take_persist(&reps[0]);
     roi::check_take_batch(&reps[1]);
-    roi::check_take_serve(&reps[2]);
-    roi::check_take_project(&reps[3]);
+    roi::check_take_batch_team(&reps[2]);
+    roi::check_take_serve(&reps[3]);
+    roi::check_take_project(&reps[4]);
     int total = 0, first = -1;
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 5; ++i) {
         if (reps[i].count > 0 && first < 0) first = i;
         total += reps[i].count;
     }

@@ -43,16 +43,39 @@ namespace rs {
 constexpr int BPT = 1024;
 constexpr int BNW = BPT / 32;
 constexpr int SEGB = 48;     // samples per float-float anchor (Q.22 drift < 6e-6 px)
-constexpr int TB = 16;       // tile side
-constexpr int RUNB = 8;      // pixels per lane
 constexpr int ACH = 16;      // angles per staging chunk (one per lane of the first half-warp)
-// Tile pixels lie within sqrt(7.5^2 + 7.5^2) = 10.61 bins of the tile centre; the hat
-// reaches one bin further, so with kbase = floor(kappa_centre) - 12 every staged index
-// touched is in [0, 24] < SBB.
-constexpr int KOFFB = 12;
-constexpr int SBB = 26;      // staged bins per angle
-constexpr int BUFB = ACH * SBB + 8 * ACH;  // one phase B staging buffer: bins + 8 constants per angle
-constexpr int WARP_STAGE = 2 * BUFB;        // floats per warp in phase B (double-buffered)
+
+// Phase B tile shapes: X x Y pixels per warp, a lane owning a run of RUN pixels along a
+// tile row (X / RUN lanes per row, 32 lanes = Y rows).  Shape 0 (16 x 16, runs of 8) is
+// the default; 1 (8 x 8, runs of 2) and 2 (16 x 8, runs of 4) give more tiles per box,
+// so more warps are busy on small boxes and in teams, at a higher per-angle cost per
+// pixel.  The shape of a region is chosen by the host (a function of its box size and of
+// the handle's tile table, so a region gets the same bits wherever it is solved).
+constexpr int kShapes = 3;
+template <int SH> struct Shape;
+template <> struct Shape<0> { static constexpr int X = 16, Y = 16, RUN = 8; };
+template <> struct Shape<1> { static constexpr int X = 8, Y = 8, RUN = 2; };
+template <> struct Shape<2> { static constexpr int X = 16, Y = 8, RUN = 4; };
+// Tile pixels lie within h = sqrt((X-1)^2 + (Y-1)^2) / 2 bins of the tile centre in window
+// coordinates and the hat reaches one bin further, so with kbase = floor(kappa_centre) -
+// KOFF, KOFF = ceil(h) + 1, every staged index touched is in [1, 2 ceil(h) + 2] < SB.
+constexpr int ceil_half_diag(int x, int y) {
+    int c = 0;
+    while (4 * c * c < (x - 1) * (x - 1) + (y - 1) * (y - 1)) ++c;
+    return c;
+}
+template <int SH> struct ShapeStage {
+    static constexpr int X = Shape<SH>::X, Y = Shape<SH>::Y, RUN = Shape<SH>::RUN;
+    static constexpr int LPR = X / RUN;                    // lanes per tile row
+    static_assert(LPR * Y == 32, "a tile is one warp");
+    static constexpr int KOFF = ceil_half_diag(X, Y) + 1;  // 16 x 16: 12
+    static constexpr int SB = 2 * KOFF + 2;                // staged bins per angle (16 x 16: 26)
+    static constexpr int BUF = ACH * SB + 8 * ACH;          // one buffer: bins + 8 constants per angle
+};
+// floats per warp in phase B (double-buffered), the largest shape's
+constexpr int WARP_STAGE = 2 * ShapeStage<0>::BUF;
+static_assert(2 * ShapeStage<1>::BUF <= WARP_STAGE && 2 * ShapeStage<2>::BUF <= WARP_STAGE, "warp area");
+constexpr int TB = 16;       // largest tile side (cooperative partial areas are sized by X Y <= TB TB)
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
@@ -228,31 +251,35 @@ __device__ __forceinline__ float disc_value(const BatchRoi& R, int i, int j) {
     return (x * x + y * y <= 0.25f * (float)R.grid_n * (float)R.grid_n) ? R.disc_g : 0.f;
 }
 
-// Phase B: this block's tiles are member + i * size.  Per tile and pixel the gather is the
-// sum, in chunk order with Neumaier compensation, of per-chunk partials (each the FMA chain
-// over the chunk's 16 angles in order), then the pass's update.  Two ways to run it, with
-// the same operations and so the same bits:
-//  - per warp: warps take tiles i from *counter (preset to BNW), lane = run of 8 pixels,
+// Phase B with tile shape SH: this block's tiles are member + i * size.  Per tile and pixel
+// the gather is the sum, in chunk order with Neumaier compensation, of per-chunk partials
+// (each the FMA chain over the chunk's 16 angles in order), then the pass's update.  Two
+// ways to run it, with the same operations and so the same bits:
+//  - per warp: warps take tiles i from *counter (preset to BNW), lane = run of RUN pixels,
 //    chunks streamed through the warp's double buffer;
-//  - cooperative, when the block has few tiles for its chunks (2 x tiles <= chunks) and the
-//    shared memory holds one tile's partials: all warps of the block share each tile, warp
-//    w taking chunks w, w + 32, ..., their partials meet in shared memory and one thread
-//    per pixel adds them in chunk order (a team of many blocks, e.g. a solo launch, keeps
-//    every warp busy instead of one per tile).
+//  - cooperative, in a team block with fewer tiles than warps when the shared memory past
+//    the warp areas holds at least one tile's partials: the block's tiles go in groups,
+//    the (tile, chunk) items of a group are dealt over all warps, their partials meet in
+//    shared memory and one thread per pixel adds them in chunk order (a team of many
+//    blocks, e.g. a lone large box or a solo launch, keeps every warp busy instead of one
+//    per tile).
 // wstage: this warp's shared area (WARP_STAGE floats at smem + warp * WARP_STAGE).
-template <bool SOLO, int DT>
-__device__ __forceinline__ void phase_b(const Ctx& C, const Team& T, int pass, int* counter, float* wstage,
-                                        int kiter = 0) {
+template <bool SOLO, int DT, int SH>
+__device__ __forceinline__ void phase_b_s(const Ctx& C, const Team& T, int pass, int* counter, float* wstage,
+                                          int kiter) {
+    using SS = ShapeStage<SH>;
+    constexpr int TX = SS::X, TY = SS::Y, RUNB = SS::RUN, SBB = SS::SB, KOFFB = SS::KOFF, BUFB = SS::BUF;
+    constexpr int TP = TX * TY;
     auto* xa = static_cast<typename Stor<DT>::T*>(C.xa);
     auto* xaT = static_cast<typename Stor<DT>::T*>(C.xaT);
     const int tm = SOLO ? 0 : T.member, ts = SOLO ? 1 : T.size;
     const BatchRoi& R = *C.R;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nx = R.nx, ny = R.ny;
-    const int tiles_x = (nx + TB - 1) / TB, tiles = tiles_x * ((ny + TB - 1) / TB);
+    const int tiles_x = (nx + TX - 1) / TX, tiles = tiles_x * ((ny + TY - 1) / TY);
     // B_XS reads the window bins of the filtered sinogram of iteration kiter + 1
     const float* fk = pass == B_XS ? R.fcp + (size_t)kiter * R.na * R.fcp_nd : nullptr;
-    const int li = lane >> 1, lj0 = (lane & 1) * RUNB;
+    const int li = lane / SS::LPR, lj0 = (lane % SS::LPR) * RUNB;
     const int nchunks = (R.na + ACH - 1) / ACH;
 
     // Chunk a0 .. a0 + ACH - 1 of tile (xi_t, eta_t) into buffer b of this warp: the tile
@@ -277,8 +304,8 @@ __device__ __forceinline__ void phase_b(const Ctx& C, const Team& T, int pass, i
             kt = ff_add(kt, ff{-r.phi.hi, -r.phi.lo});
             const int kbase = (int)floorf(kt.hi) - KOFFB;
             kt = ff_add(kt, ff{-(float)kbase, 0.f});
-            kt = ff_add(kt, ff_mul_f(-0.5f * (TB - 1), r.c));
-            kt = ff_add(kt, ff_mul_f(0.5f * (TB - 1), r.s));
+            kt = ff_add(kt, ff_mul_f(-0.5f * (TX - 1), r.c));
+            kt = ff_add(kt, ff_mul_f(0.5f * (TY - 1), r.s));
             cb[lane] = to_fixed<23>(kt);
             cc[lane] = r.c_q23;
             cs[lane] = r.s_q23;
@@ -388,15 +415,22 @@ __device__ __forceinline__ void phase_b(const Ctx& C, const Team& T, int pass, i
     unsigned dyn_bytes;
     asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_bytes));
     const int room = (int)(dyn_bytes / sizeof(float)) - BNW * WARP_STAGE;  // floats past the warp areas
-    if (!SOLO && my_tiles > 0 && 2 * my_tiles <= nchunks && nchunks * TB * TB <= room) {
-        // ---- cooperative: every warp of the block on each of its tiles in turn
-        float* part = wstage - warp * WARP_STAGE + BNW * WARP_STAGE;  // [nchunks][TB * TB]
-        for (int i = 0; i < my_tiles; ++i) {
-            const int t = tm + i * ts;
-            const int tile_x0 = (t % tiles_x) * TB, tile_y0 = (t / tiles_x) * TB;
-            const float xi_t = (float)tile_x0 + 0.5f * (TB - 1) - 0.5f * (float)(nx - 1);
-            const float eta_t = 0.5f * (float)(ny - 1) - ((float)tile_y0 + 0.5f * (TB - 1));
-            for (int c = warp; c < nchunks; c += BNW) {
+    const int per_tile = nchunks * TP;                                     // one tile's chunk partials
+    if (!SOLO && my_tiles > 0 && my_tiles < BNW && per_tile <= room) {
+        // ---- cooperative: fewer tiles than warps.  The block's tiles are taken in groups
+        // whose partials fit the shared memory past the warp areas; the (tile, chunk) items
+        // of a group are dealt over all warps, and one thread per pixel adds a tile's chunk
+        // partials in chunk order.
+        float* part = wstage - warp * WARP_STAGE + BNW * WARP_STAGE;  // [group][nchunks][TP]
+        const int G = min(my_tiles, room / per_tile);
+        for (int g0 = 0; g0 < my_tiles; g0 += G) {
+            const int gn = min(G, my_tiles - g0);
+            for (int item = warp; item < gn * nchunks; item += BNW) {
+                const int gt = item / nchunks, c = item - gt * nchunks;
+                const int t = tm + (g0 + gt) * ts;
+                const int tile_x0 = (t % tiles_x) * TX, tile_y0 = (t / tiles_x) * TY;
+                const float xi_t = (float)tile_x0 + 0.5f * (TX - 1) - 0.5f * (float)(nx - 1);
+                const float eta_t = 0.5f * (float)(ny - 1) - ((float)tile_y0 + 0.5f * (TY - 1));
                 __syncwarp();  // this warp's buffer is free
                 stage(xi_t, eta_t, c * ACH, 0);
                 cp_async_wait_group<0>();
@@ -404,17 +438,19 @@ __device__ __forceinline__ void phase_b(const Ctx& C, const Team& T, int pass, i
                 float acc[RUNB];
                 gather(c * ACH, 0, acc);
 #pragma unroll
-                for (int p = 0; p < RUNB; ++p) part[c * (TB * TB) + li * TB + lj0 + p] = acc[p];
+                for (int p = 0; p < RUNB; ++p) part[(gt * nchunks + c) * TP + li * TX + lj0 + p] = acc[p];
             }
             __syncthreads();
-            if (threadIdx.x < TB * TB) {  // one thread per pixel: the chunks in order
-                const int px = threadIdx.x;
+            for (int e = threadIdx.x; e < gn * TP; e += BPT) {  // one thread per pixel: the chunks in order
+                const int gt = e / TP, px = e - gt * TP;
+                const int t = tm + (g0 + gt) * ts;
+                const int tile_x0 = (t % tiles_x) * TX, tile_y0 = (t / tiles_x) * TY;
                 float sum = 0.f, cmp = 0.f;
-                for (int c = 0; c < nchunks; ++c) neu_add(sum, cmp, part[c * (TB * TB) + px]);
-                const int gi = tile_y0 + px / TB, gj = tile_x0 + px % TB;
+                for (int c = 0; c < nchunks; ++c) neu_add(sum, cmp, part[(gt * nchunks + c) * TP + px]);
+                const int gi = tile_y0 + px / TX, gj = tile_x0 + px % TX;
                 if (gi < ny && gj < nx) update(gi, gj, sum + cmp);
             }
-            __syncthreads();  // the partials area is reused by the next tile
+            __syncthreads();  // the partials area is reused by the next group
         }
         return;
     }
@@ -422,9 +458,9 @@ __device__ __forceinline__ void phase_b(const Ctx& C, const Team& T, int pass, i
     for (int i = warp;;) {
         const int t = tm + i * ts;
         if (t >= tiles) break;
-        const int tile_x0 = (t % tiles_x) * TB, tile_y0 = (t / tiles_x) * TB;
-        const float xi_t = (float)tile_x0 + 0.5f * (TB - 1) - 0.5f * (float)(nx - 1);
-        const float eta_t = 0.5f * (float)(ny - 1) - ((float)tile_y0 + 0.5f * (TB - 1));
+        const int tile_x0 = (t % tiles_x) * TX, tile_y0 = (t / tiles_x) * TY;
+        const float xi_t = (float)tile_x0 + 0.5f * (TX - 1) - 0.5f * (float)(nx - 1);
+        const float eta_t = 0.5f * (float)(ny - 1) - ((float)tile_y0 + 0.5f * (TY - 1));
         float sum[RUNB], cmp[RUNB];
 #pragma unroll
         for (int p = 0; p < RUNB; ++p) sum[p] = cmp[p] = 0.f;
@@ -455,6 +491,18 @@ __device__ __forceinline__ void phase_b(const Ctx& C, const Team& T, int pass, i
         if (lane == 0) nxt = atomicAdd(counter, 1);
         i = __shfl_sync(0xffffffffu, nxt, 0);
     }
+}
+
+// Phase B with the region's tile shape.
+template <bool SOLO, int DT>
+__device__ __forceinline__ void phase_b(const Ctx& C, const Team& T, int pass, int* counter, float* wstage,
+                                        int kiter = 0) {
+    if (C.R->shape == 1)
+        phase_b_s<SOLO, DT, 1>(C, T, pass, counter, wstage, kiter);
+    else if (C.R->shape == 2)
+        phase_b_s<SOLO, DT, 2>(C, T, pass, counter, wstage, kiter);
+    else
+        phase_b_s<SOLO, DT, 0>(C, T, pass, counter, wstage, kiter);
 }
 
 __device__ __forceinline__ void fill_team(const Ctx& C, float* p, size_t n, float v) {

@@ -340,6 +340,12 @@ ROI_HD size_t stage_bytes(int nx, int ny, int esz) {
     return 0;
 }
 
+// ---- phase B tile shapes of the whole-region solvers, chosen per box-size class: boxes
+// of side <= 96, <= 216 (padded image staged whole), and larger (band-streamed)
+constexpr int kTileShapes = 3;
+constexpr int kShapeClasses = 3;
+ROI_HD int shape_class(int side) { return side <= 96 ? 0 : (side <= 216 ? 1 : 2); }
+
 // ---- whole-region solves by one block (batched) or a team of blocks (serving)
 struct BatchRoi {
     const AngleRec* rec;   // box-frame table, per-row-branch angles first
@@ -368,6 +374,7 @@ struct BatchRoi {
     // reg = 3, Alg. methodfista: FGP iterations and weight (lam_f = alpha lambda / 2)
     int n_fgp;
     float lam_f;
+    int shape;             // phase B tile shape (0: 16 x 16, 1: 8 x 8, 2: 16 x 8)
 };
 
 struct BatchArgs {
@@ -466,12 +473,14 @@ struct SinoView {
     int dt;
     const float* resid;
     int resid_ld;
+    int shape[kShapeClasses];  // tile shape per box-size class (the handle's table)
 };
 
 int sino_view(::roi_recon* h, SinoView* v, std::string* msg);
 
 size_t batch_smem_bytes(size_t max_stage_bytes, int na);
 cudaError_t launch_batch(const BatchArgs& B, int blocks, size_t smem, cudaStream_t st);
+cudaError_t launch_batch_team(const BatchArgs& B, int blocks, size_t smem, cudaStream_t st);
 
 // ---- check build (-DROI_CHECK): index checks of the hot kernels, one report per
 // translation unit; the product build's reports are always empty.
@@ -482,6 +491,7 @@ struct CheckReport {
 };
 void check_take_persist(CheckReport* out);
 void check_take_batch(CheckReport* out);
+void check_take_batch_team(CheckReport* out);
 void check_take_serve(CheckReport* out);
 void check_take_project(CheckReport* out);
 

@@ -369,6 +369,7 @@ void publish(roi_server* s, int pi, Req* r, size_t slot) {
     R.fcp_nd = v.nd;
     R.disc_g = v.disc_g;
     R.grid_n = v.N;
+    R.shape = v.shape[roi::shape_class(std::max(r->box.w, r->box.h))];
     unsigned char* base = s->arena_d + r->dev_off;
     roi::RegionBufs& B = hdr.bufs;
     B.pp = reinterpret_cast<float*>(base + r->lay.pp);
