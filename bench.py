@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--team-blocks", type=int, default=0, help="serving: blocks per team (0: library default)")
     ap.add_argument("--teams", type=int, default=-1, help="serving: teams (-1: library default)")
     ap.add_argument("--large-side", type=int, default=0, help="serving: box side served by teams (0: default)")
+    ap.add_argument("--solo-queue-ms", type=int, default=0,
+                    help="serving: queued work (ms) that ends a solo launch (0: library default)")
     ap.add_argument("--no-plain", action="store_true", help="serving: skip the one-at-a-time comparison")
     ap.add_argument("--no-serving", action="store_true", help="default workload: skip the serving comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -707,7 +709,8 @@ def serve_measure(args, count, dist, ws, rank, local, clock=True, rate=None):
         rr.fbp()
         recons.append(rr)
     torch.cuda.synchronize()
-    srv = R.Server(team_blocks=args.team_blocks, teams=args.teams, large_side=args.large_side)
+    srv = R.Server(team_blocks=args.team_blocks, teams=args.teams, large_side=args.large_side,
+                   solo_queue_ms=args.solo_queue_ms)
     for rr in recons:
         srv.add(rr)
     # warm-up: a few short requests through both paths (first launch, ring allocation)

@@ -414,9 +414,13 @@ typedef struct {
     int large_side;        /* box side from which a request goes to the team pool (0: 320) */
     int idle_us;           /* the kernel leaves after this long without work (0: 2000) */
     int no_spill;          /* 0: a small-box request is admitted to an idle team when no
-                              large one waits for it, and a lone request on an idle server
-                              runs on one team of all blocks until a queue forms (lower
-                              latency at light load); 1: requests go to their pool by size */
+                              large one waits for it, and requests arriving at an idle server
+                              run one at a time on one team of all blocks (a solo launch)
+                              until a queue forms (lower latency at light load); 1: requests
+                              go to their pool by size */
+    int solo_queue_ms;     /* a solo launch leaves (and the pools take over) when the work
+                              queued behind it exceeds this many milliseconds of estimated
+                              whole-GPU solve time (0: 250) */
 } roi_server_config;
 
 typedef struct {

@@ -78,7 +78,7 @@ class SolveInfo(ctypes.Structure):
 class ServerConfig(ctypes.Structure):
     _fields_ = [("device_bytes", ctypes.c_size_t), ("host_bytes", ctypes.c_size_t), ("ring_slots", ctypes.c_int),
                 ("team_blocks", ctypes.c_int), ("teams", ctypes.c_int), ("large_side", ctypes.c_int),
-                ("idle_us", ctypes.c_int), ("no_spill", ctypes.c_int)]
+                ("idle_us", ctypes.c_int), ("no_spill", ctypes.c_int), ("solo_queue_ms", ctypes.c_int)]
 
 
 class ServerCompletion(ctypes.Structure):
@@ -775,9 +775,9 @@ class Server:
     """
 
     def __init__(self, device_bytes=0, host_bytes=0, ring_slots=0, team_blocks=0, teams=-1, large_side=0,
-                 idle_us=0, no_spill=0, start=True):
+                 idle_us=0, no_spill=0, start=True, solo_queue_ms=0):
         cfg = ServerConfig(int(device_bytes), int(host_bytes), int(ring_slots), int(team_blocks), int(teams),
-                           int(large_side), int(idle_us), int(no_spill))
+                           int(large_side), int(idle_us), int(no_spill), int(solo_queue_ms))
         st, s = roi_server_create(cfg)
         if st != ROI_OK:
             raise RoiError(st, "roi_server_create failed")

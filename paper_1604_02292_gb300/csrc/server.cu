@@ -127,6 +127,7 @@ struct Req {
     bool has_dev = false, has_host = false;
     long long ticket = -1;
     double t_submit = 0, t_publish = 0, t_done = 0;
+    double est_ms = 0;  // estimated time of a solve on every block (the solo launch)
     roi_status status = ROI_OK;
     int state = 0;  // 0 pending, 1 published, 2 done
 };
@@ -393,8 +394,22 @@ void publish(roi_server* s, int pi, Req* r, size_t slot) {
     __atomic_store_n(&s->ctl_h->tail[pi], (unsigned long long)(r->ticket + 1), __ATOMIC_RELEASE);
 }
 
-// Requests waiting behind a solo launch before it is asked to leave.
-constexpr int kSoloQueue = 8;
+// A solo launch serves the queue one request at a time on every block (the latency of a
+// whole-GPU solve, the plain one-at-a-time throughput).  It is asked to leave when the work
+// queued behind it, estimated in solo milliseconds, exceeds cfg.solo_queue_ms (or more than
+// kSoloQueue requests wait): the pools' throughput is then worth more than the solo latency.
+constexpr int kSoloQueue = 64;
+// Estimated solo time of a request: its projector work at a whole-GPU rate, but no less than
+// a fixed cost per iteration (a small box is latency-bound on a team of every block).
+constexpr double kSoloLerpsPerMs = 1.1e9;
+constexpr double kSoloIterMs = 0.012;
+
+double solo_ms_live(const roi_server* s) {
+    double w = 0.0;
+    for (const Req* r : s->pools[1].occupant)
+        if (r && r->state == 1) w += r->est_ms;
+    return w;
+}
 
 // Admits pending requests in arrival order per pool while their state fits the budgets.
 // A small-box request goes to the team pool instead when a team is idle there and no
@@ -532,17 +547,22 @@ roi_status progress_locked(roi_server* s) {
     // block (solo: the latency of a whole-GPU solve); otherwise the configured pools.
     if (!s->running) {
         size_t pend = 0;
-        for (const Pool& P : s->pools) pend += P.pending.size();
+        double work = 0.0;
+        for (const Pool& P : s->pools) {
+            pend += P.pending.size();
+            for (const Req* r : P.pending) work += r->est_ms;
+        }
         s->mode = (!s->cfg.no_spill && s->pools[1].nteams > 0 && s->pools[0].live + s->pools[1].live == 0 &&
-                   pend == 1)
+                   pend >= 1 && pend <= (size_t)kSoloQueue && work <= s->cfg.solo_queue_ms)
                       ? 1
                       : 0;
     }
     admit(s);
-    // A queue behind a solo launch (more than kSoloQueue requests waiting): let it finish
-    // the request it holds and leave, so the next launch serves the queue with the
-    // configured pools, whose throughput is higher.
-    if (s->running && s->mode == 1 && !s->leaving && s->pools[1].live > kSoloQueue) {
+    // A queue behind a solo launch (more queued work than solo_queue_ms, or more than
+    // kSoloQueue requests): let it finish the request it holds and leave, so the next launch
+    // serves the queue with the configured pools, whose throughput is higher.
+    if (s->running && s->mode == 1 && !s->leaving &&
+        (solo_ms_live(s) > s->cfg.solo_queue_ms || s->pools[1].live > kSoloQueue)) {
         __atomic_store_n(&s->ctl_h->close, 1, __ATOMIC_RELEASE);
         s->leaving = true;
     }
@@ -594,9 +614,10 @@ roi_status roi_server_create(const roi_server_config* cfg_in, roi_server_t* out)
     if (cfg.team_blocks == 0) cfg.team_blocks = 16;
     if (cfg.large_side == 0) cfg.large_side = 320;
     if (cfg.idle_us == 0) cfg.idle_us = 2000;
+    if (cfg.solo_queue_ms == 0) cfg.solo_queue_ms = 250;
     if (cfg.ring_slots < 1 || cfg.ring_slots > (1 << 20) || cfg.team_blocks < 1 || cfg.team_blocks > 1024 ||
         cfg.teams < -1 || cfg.large_side < 1 || cfg.idle_us < 1 || cfg.idle_us > 10000000 || cfg.no_spill < 0 ||
-        cfg.no_spill > 1)
+        cfg.no_spill > 1 || cfg.solo_queue_ms < 0 || cfg.solo_queue_ms > 3600000)
         return ROI_EINVAL;
     roi_server* s = new (std::nothrow) roi_server;
     if (!s) return ROI_ENOMEM;
@@ -732,6 +753,13 @@ roi_status roi_server_submit(roi_server_t s, int sino_id, const roi_region* regi
     }
     r->lay = state_layout(v.na, r->stride, r->box.w, r->box.h, roi::dt_size(v.dt), P.reg >= ROI_FILTER_TV);
     r->host_bytes = sizeof(float) * (size_t)r->box.w * r->box.h;
+    {
+        double lerps = 0.0;  // per iteration: window rays x box side, then pixels x angles
+        for (const AngleRec& a : r->rec) lerps += (double)a.width * std::max(r->box.w, r->box.h);
+        lerps += (double)r->box.w * r->box.h * v.na;
+        const double it = std::max(P.iters, 1);
+        r->est_ms = std::max(it * lerps / kSoloLerpsPerMs, it * kSoloIterMs);
+    }
     if (round_up(r->lay.total) > s->darena.size || round_up(r->host_bytes) > s->harena.size) {
         const size_t need = r->lay.total;
         delete r;
