@@ -553,7 +553,7 @@ roi_status progress_locked(roi_server* s) {
             for (const Req* r : P.pending) work += r->est_ms;
         }
         s->mode = (!s->cfg.no_spill && s->pools[1].nteams > 0 && s->pools[0].live + s->pools[1].live == 0 &&
-                   pend >= 1 && pend <= (size_t)kSoloQueue && work <= s->cfg.solo_queue_ms)
+                   (pend == 1 || (pend > 1 && pend <= (size_t)kSoloQueue && work <= s->cfg.solo_queue_ms)))
                       ? 1
                       : 0;
     }

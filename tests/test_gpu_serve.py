@@ -240,13 +240,13 @@ def test_small_requests_spill_to_idle_teams(sinos):
 
 
 def test_solo_launch_and_leaving_it(sinos):
-    """A lone request on an idle server runs solo (one team of all blocks); when more than
-    eight requests queue behind it, the solo launch finishes the request it holds and leaves,
-    and the queue is served by the configured pools.  Every result equals the batched
-    solver's."""
+    """A lone request on an idle server runs solo (one team of all blocks); when the work
+    queued behind it exceeds solo_queue_ms (here 1 ms of estimated whole-GPU time), the solo
+    launch finishes the request it holds and leaves, and the queue is served by the
+    configured pools.  Every result equals the batched solver's."""
     long_req = (1, (130.0, 128.0, 100.0, 50.0), dict(reg=R.ROI_SIRT_NONNEG, iters=200))
     reqs = [long_req] + [CASES[k % len(CASES)] for k in range(12)]
-    with make_server(sinos, team_blocks=4, teams=8, large_side=100, start=False) as s:
+    with make_server(sinos, team_blocks=4, teams=8, large_side=100, start=False, solo_queue_ms=1) as s:
         ids = [s.submit(*reqs[0])]
         s.progress()  # solo launch with the lone request
         ids += [s.submit(*r) for r in reqs[1:]]
