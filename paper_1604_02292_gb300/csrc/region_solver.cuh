@@ -153,17 +153,14 @@ struct Ctx {
 // This thread's index over the team.
 __device__ __forceinline__ int team_tid(const Ctx& C) { return C.member * BPT + (int)threadIdx.x; }
 
-// Whole-ray Joseph sum of ray k (fixed point along the ray).  Samples whose minor
-// coordinate lies in [-1.5, Mm + 0.5] are visited, so both taps stay inside the padded
-// row; every SEGB samples the position is re-anchored from float-float as an integer
-// column plus a Q.22 offset from it (the offset stays below 2^31 whatever the box size).
-template <int DT>
-__device__ __forceinline__ ff ray_full(const AngleRec& r, int k, int M, int Mm, const typename Stor<DT>::T* img,
-                                       int ld) {
-    float sum = 0.f, cmp = 0.f;
+// Samples [mlo, mhi) of ray k whose minor coordinate lies in [-1.5, Mm + 0.5] (the others
+// contribute 0, so both taps stay inside the padded row), and the ray's coordinate Ak at
+// the major-axis centre.
+__device__ __forceinline__ ff ray_span(const AngleRec& r, int k, int M, int Mm, int& mlo, int& mhi) {
     const float halfM = 0.5f * (float)(M - 1);
     const ff Ak = ff_add(r.A0, ff_mul_f((float)k, r.a_scale));
-    int mlo = 0, mhi = M;
+    mlo = 0;
+    mhi = M;
     if (!r.flat) {
         const float ma = (-1.5f - Ak.hi) * r.inv_slope + halfM;
         const float mb = ((float)Mm + 0.5f - Ak.hi) * r.inv_slope + halfM;
@@ -173,33 +170,84 @@ __device__ __forceinline__ ff ray_full(const AngleRec& r, int k, int M, int Mm, 
     } else if (!(Ak.hi >= -1.5f && Ak.hi <= (float)Mm + 0.5f)) {
         mhi = 0;
     }
+    return Ak;
+}
+
+// The ray's samples [m0, min(m0 + SEGB, mhi)) from one float-float anchor at m0: an integer
+// column plus a Q.22 offset from it, stepped per sample (the offset stays below 2^31
+// whatever the box size); returns s0 + s1 2^-22 (the values and their interpolated
+// differences, summed apart).
+template <int DT>
+__device__ __forceinline__ float ray_anchor(const AngleRec& r, ff Ak, int m0, int mhi, int M,
+                                            const typename Stor<DT>::T* img, int ld) {
+    const float halfM = 0.5f * (float)(M - 1);
+    int j0;
+    int q = split_fixed22(ff_add(Ak, ff_mul_f((float)m0 - halfM, r.slope)), j0);
     const int step = r.slope_q22;
-    for (int m0 = mlo; m0 < mhi; m0 += SEGB) {
-        int j0;
-        int q = split_fixed22(ff_add(Ak, ff_mul_f((float)m0 - halfM, r.slope)), j0);
-        const int mend = min(m0 + SEGB, mhi);
-        const int jlo = -kPad - j0, jhi = ld - 1 - kPad - j0;  // taps j, j + 1 inside the padded row
-        float s0 = 0.f, s1 = 0.f;
-        const typename Stor<DT>::T* rp = img + (size_t)m0 * ld + j0;
+    const int mend = min(m0 + SEGB, mhi);
+    const int jlo = -kPad - j0, jhi = ld - 1 - kPad - j0;  // taps j, j + 1 inside the padded row
+    float s0 = 0.f, s1 = 0.f;
+    const typename Stor<DT>::T* rp = img + (size_t)m0 * ld + j0;
 #pragma unroll 4
-        for (int m = m0; m < mend; ++m, rp += ld, q += step) {
-            const int j = chk(q >> 22, jlo, jhi, CHK_REGION_RAY);
-            const float mf = frac_int<22>(q);
-            const float v0 = to_f32<DT>(rp[j]), v1 = to_f32<DT>(rp[j + 1]);
-            s0 += v0;
-            s1 = fmaf(mf, v1 - v0, s1);
-        }
-        neu_add(sum, cmp, fmaf(s1, 2.384185791015625e-07f, s0));
+    for (int m = m0; m < mend; ++m, rp += ld, q += step) {
+        const int j = chk(q >> 22, jlo, jhi, CHK_REGION_RAY);
+        const float mf = frac_int<22>(q);
+        const float v0 = to_f32<DT>(rp[j]), v1 = to_f32<DT>(rp[j + 1]);
+        s0 += v0;
+        s1 = fmaf(mf, v1 - v0, s1);
     }
+    return fmaf(s1, 2.384185791015625e-07f, s0);
+}
+
+// Whole-ray Joseph sum of ray k (fixed point along the ray): the anchors' values every SEGB
+// samples, added in order with Neumaier compensation.
+template <int DT>
+__device__ __forceinline__ ff ray_full(const AngleRec& r, int k, int M, int Mm, const typename Stor<DT>::T* img,
+                                       int ld) {
+    float sum = 0.f, cmp = 0.f;
+    int mlo, mhi;
+    const ff Ak = ray_span(r, k, M, Mm, mlo, mhi);
+    for (int m0 = mlo; m0 < mhi; m0 += SEGB) neu_add(sum, cmp, ray_anchor<DT>(r, Ak, m0, mhi, M, img, ld));
     return two_sum(sum, cmp);
+}
+
+// The pass's use of the sum tot of window ray (a, k) (angle a of the table).
+__device__ __forceinline__ void finish_ray(const Ctx& C, const AngleRec& r, int a, int k, ff tot, int pass) {
+    const BatchRoi& R = *C.R;
+    tot = ff_mul_f(r.inv_w, tot);
+    const size_t o = (size_t)a * R.stride + k;
+    if (pass == A_EXTER) {  // p' = (p - W x_fbp) + W_L x_fbp
+        const ff d = two_sum(R.resid[(size_t)r.aidx * R.resid_ld + r.d0 + k], tot.hi);
+        C.b.pp[o] = d.hi + (d.lo + tot.lo);
+        return;
+    }
+    const float acc = tot.hi + tot.lo;
+    if (pass == A_ROWSUM) {
+        const float thr = R.reg == 0 ? 1e-3f : 1e-6f;
+        C.b.sig[o] = acc > thr ? 1.f / acc : 0.f;
+    } else if (R.reg == 0) {
+        float res = C.b.pp[o] - acc;
+        if (R.weighting) res *= C.b.sig[o];
+        C.b.u[o] = res;
+    } else if (R.reg >= 2) {
+        C.b.u[o] = -R.alpha * acc;
+    } else {
+        const float sg = C.b.sig[o];
+        C.b.u[o] = (C.b.u[o] + sg * (acc - C.b.pp[o])) / (1.f + 0.5f * sg);
+    }
 }
 
 // Phase A over the units of one branch (row = 1: per-row sampling; the table lists those
 // angles first).  This block's units are ustart + member + i * size; warps take i from
-// *counter (preset to BNW by the caller, warp w starting at i = w).
+// *counter (preset to BNW by the caller, warp w starting at i = w) and sum whole rays.  A
+// team block with fewer units than warps splits the rays at their float-float anchors
+// instead when `part` (part_floats floats of shared memory) holds every anchor value of its
+// units: the (unit, anchor) items go round-robin over all warps, each writes its anchor
+// value, and one warp per unit adds a ray's anchor values in order -- the same operations
+// as the whole-ray sum, so the same bits.
 template <bool SOLO, int DT>
 __device__ __forceinline__ void phase_a_branch(const Ctx& C, const Team& T, int row, const void* img_v, int ld,
-                                               int pass, int* counter) {
+                                               int pass, int* counter, float* part = nullptr, int part_floats = 0) {
     const auto* img = static_cast<const typename Stor<DT>::T*>(img_v);
     const int tm = SOLO ? 0 : T.member, ts = SOLO ? 1 : T.size;
     const BatchRoi& R = *C.R;
@@ -207,36 +255,51 @@ __device__ __forceinline__ void phase_a_branch(const Ctx& C, const Team& T, int 
     const int M = row ? R.ny : R.nx, Mm = row ? R.nx : R.ny;
     const int ustart = row ? 0 : R.nrow * C.nchunk;
     const int uend = (row ? R.nrow : R.na) * C.nchunk;
+    if (!SOLO) {
+        const int total = uend - ustart;
+        const int nu = total > tm ? (total - tm + ts - 1) / ts : 0;
+        const int J = (M + SEGB - 1) / SEGB;  // anchors of the longest ray
+        if (nu > 0 && nu < BNW && part && nu * J * 32 <= part_floats) {
+            for (int item = warp; item < nu * J; item += BNW) {
+                const int i = item / J, j = item - i * J;
+                const int unit = ustart + tm + i * ts;
+                const int a = unit / C.nchunk;
+                const int k = (unit - a * C.nchunk) * 32 + lane;
+                const AngleRec& r = R.rec[a];
+                float v = 0.f;
+                if (k < r.width) {
+                    int mlo, mhi;
+                    const ff Ak = ray_span(r, k, M, Mm, mlo, mhi);
+                    const int m0 = mlo + j * SEGB;
+                    if (m0 < mhi) v = ray_anchor<DT>(r, Ak, m0, mhi, M, img, ld);
+                }
+                part[item * 32 + lane] = v;
+            }
+            __syncthreads();
+            for (int i = warp; i < nu; i += BNW) {
+                const int unit = ustart + tm + i * ts;
+                const int a = unit / C.nchunk;
+                const int k = (unit - a * C.nchunk) * 32 + lane;
+                const AngleRec& r = R.rec[a];
+                if (k < r.width) {
+                    int mlo, mhi;
+                    ray_span(r, k, M, Mm, mlo, mhi);
+                    const int n_anchor = mhi > mlo ? (mhi - mlo + SEGB - 1) / SEGB : 0;
+                    float sum = 0.f, cmp = 0.f;
+                    for (int j = 0; j < n_anchor; ++j) neu_add(sum, cmp, part[(i * J + j) * 32 + lane]);
+                    finish_ray(C, r, a, k, two_sum(sum, cmp), pass);
+                }
+            }
+            return;
+        }
+    }
     for (int i = warp;;) {
         const int unit = ustart + tm + i * ts;
         if (unit >= uend) break;
         const int a = unit / C.nchunk;
         const int k = (unit - a * C.nchunk) * 32 + lane;
         const AngleRec& r = R.rec[a];
-        if (k < r.width) {
-            ff tot = ray_full<DT>(r, k, M, Mm, img, ld);
-            tot = ff_mul_f(r.inv_w, tot);
-            const size_t o = (size_t)a * R.stride + k;
-            if (pass == A_EXTER) {  // p' = (p - W x_fbp) + W_L x_fbp
-                const ff d = two_sum(R.resid[(size_t)r.aidx * R.resid_ld + r.d0 + k], tot.hi);
-                C.b.pp[o] = d.hi + (d.lo + tot.lo);
-            } else {
-                const float acc = tot.hi + tot.lo;
-                if (pass == A_ROWSUM) {
-                    const float thr = R.reg == 0 ? 1e-3f : 1e-6f;
-                    C.b.sig[o] = acc > thr ? 1.f / acc : 0.f;
-                } else if (R.reg == 0) {
-                    float res = C.b.pp[o] - acc;
-                    if (R.weighting) res *= C.b.sig[o];
-                    C.b.u[o] = res;
-                } else if (R.reg >= 2) {
-                    C.b.u[o] = -R.alpha * acc;
-                } else {
-                    const float sg = C.b.sig[o];
-                    C.b.u[o] = (C.b.u[o] + sg * (acc - C.b.pp[o])) / (1.f + 0.5f * sg);
-                }
-            }
-        }
+        if (k < r.width) finish_ray(C, r, a, k, ray_full<DT>(r, k, M, Mm, img, ld), pass);
         int nxt = 0;
         if (lane == 0) nxt = atomicAdd(counter, 1);
         i = __shfl_sync(0xffffffffu, nxt, 0);
@@ -550,13 +613,22 @@ __device__ __forceinline__ void load_fbp_box(const Ctx& C) {
     }
 }
 
-// Both branches of phase A reading the images from global memory.
+// Floats of dynamic shared memory of this launch.
+__device__ __forceinline__ int dyn_smem_floats() {
+    unsigned dyn_bytes;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_bytes));
+    return (int)(dyn_bytes / sizeof(float));
+}
+
+// Both branches of phase A reading the images from global memory (the dynamic shared
+// memory, unused meanwhile, holds the anchor values of a split phase A).
 template <bool SOLO, int DT>
-__device__ __forceinline__ void phase_a_global(const Ctx& C, const Team& T, int pass, int* s_cnt) {
+__device__ __forceinline__ void phase_a_global(const Ctx& C, const Team& T, int pass, int* s_cnt, float* smem) {
     for (int row = 1; row >= 0; --row) {
         if (threadIdx.x == 0) *s_cnt = BNW;
         __syncthreads();
-        phase_a_branch<SOLO, DT>(C, T, row, row ? C.xa : C.xaT, row ? C.lda : C.ldaT, pass, s_cnt);
+        phase_a_branch<SOLO, DT>(C, T, row, row ? C.xa : C.xaT, row ? C.lda : C.ldaT, pass, s_cnt, smem,
+                                 dyn_smem_floats());
         __syncthreads();
     }
 }
@@ -879,6 +951,9 @@ __device__ __forceinline__ bool solve_region(const BatchRoi& R, const RegionBufs
     const size_t nimg = (size_t)R.nx * R.ny, nwin = (size_t)R.na * R.stride;
     const unsigned bytes_row = (unsigned)(ES * (size_t)R.ny * C.lda);
     const unsigned bytes_col = (unsigned)(ES * (size_t)R.nx * C.ldaT);
+    // floats of the whole staged image (stage mode 0), 16-byte aligned: a split phase A keeps
+    // its anchor values past it
+    const int img_floats = (int)((stage_bytes(R.nx, R.ny, ES) + 15) / 16 * 4);
 
     // ---- exterior: p' on the window rays, zero state
     fill_team(C, C.b.u, nwin, 0.f);
@@ -888,14 +963,14 @@ __device__ __forceinline__ bool solve_region(const BatchRoi& R, const RegionBufs
     if (R.reg < 2) {  // the paper's own method (reg 2, 3) needs no exterior step
         load_fbp_box<DT>(C);
         if (!team_sync<SOLO>(T)) return false;
-        phase_a_global<SOLO, DT>(C, T, A_EXTER, s_cnt);
+        phase_a_global<SOLO, DT>(C, T, A_EXTER, s_cnt, smem);
     }
     // ---- set-up: preconditioners / weights from the row and column sums
     if (R.reg == 1 || R.weighting) {
         if (!team_sync<SOLO>(T)) return false;  // the exterior pass has read the images
         set_images<DT>(C, 1.f);
         if (!team_sync<SOLO>(T)) return false;
-        phase_a_global<SOLO, DT>(C, T, A_ROWSUM, s_cnt);
+        phase_a_global<SOLO, DT>(C, T, A_ROWSUM, s_cnt, smem);
         if (tid == 0) *s_cnt = BNW;
         __syncthreads();
         phase_b<SOLO, DT>(C, T, B_COLSUM, s_cnt, smem + warp * WARP_STAGE);
@@ -917,7 +992,7 @@ __device__ __forceinline__ bool solve_region(const BatchRoi& R, const RegionBufs
                 parity ^= 1u;
                 __syncthreads();
                 phase_a_branch<SOLO, DT>(C, T, row, reinterpret_cast<TS*>(smem) + kPad, row ? C.lda : C.ldaT,
-                                         A_SOLVE, s_cnt);
+                                         A_SOLVE, s_cnt, smem + img_floats, dyn_smem_floats() - img_floats);
                 __syncthreads();
             }
         } else if (C.stage == 1) {
@@ -928,7 +1003,7 @@ __device__ __forceinline__ bool solve_region(const BatchRoi& R, const RegionBufs
                     return false;
         } else {
             if (R.reg == 1) dual_grad<DT>(C);
-            phase_a_global<SOLO, DT>(C, T, A_SOLVE, s_cnt);
+            phase_a_global<SOLO, DT>(C, T, A_SOLVE, s_cnt, smem);
         }
         if (!team_sync<SOLO>(T)) return false;  // u, v of this iteration complete
         if (R.reg >= 2) {  // x_s^k first (tiles stay with their block, so a block barrier suffices)
