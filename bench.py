@@ -66,12 +66,16 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=sorted(WL.WORKLOADS) + sorted(WL.BATCHES) + sorted(WL.SERVING) + sorted(WL.PRECISION))
+                    choices=sorted(WL.WORKLOADS) + sorted(WL.BATCHES) + sorted(WL.SERVING) + sorted(WL.PRECISION)
+                    + ["roi_large_2048"])
     ap.add_argument("--storage", default="bf16", choices=["f32", "bf16", "f16"],
                     help="precision workloads: storage type measured against float32 storage")
     ap.add_argument("--batch-count", type=int, default=None,
                     help="batch workloads: solve this many of the regions per step (default: all)")
     ap.add_argument("--requests", type=int, default=256, help="serving workloads: requests in the run")
+    ap.add_argument("--iters", type=int, default=0,
+                    help="batch and large-box workloads: iterations per region (0: the workload's)")
+    ap.add_argument("--radius", type=float, default=128.0, help="large-box workload: ROI radius (margin r/2)")
     ap.add_argument("--rate", type=float, default=None, help="serving workloads: arrival rate (default: workload's)")
     ap.add_argument("--team-blocks", type=int, default=0, help="serving: blocks per team (0: library default)")
     ap.add_argument("--teams", type=int, default=-1, help="serving: teams (-1: library default)")
@@ -575,7 +579,7 @@ def run_ours(args):
     return 0
 
 
-def batch_measure(w, count, steps, warmup, dist, ws, rank, local, clock=True, tune=False):
+def batch_measure(w, count, steps, warmup, dist, ws, rank, local, clock=True, tune=False, iters=0):
     """Batched solves: one step = roi_recon_solve_batch over the regions (one persistent
     launch); the warm-up steps run every region for one iteration (same boxes, so the same
     device slots).  Returns regions/s over all ranks, the per-step times and the lerps/s of
@@ -588,6 +592,8 @@ def batch_measure(w, count, steps, warmup, dist, ws, rank, local, clock=True, tu
 
     p = WL.sinogram(w, seed=0)
     all_items = WL.batch_regions(w, seed=0, count=count)
+    if iters:
+        all_items = [(r, dict(prm, iters=iters)) for r, prm in all_items]
     share = shard.assign([shard.region_cost(r, prm["iters"], w.n_angles) for r, prm in all_items], ws)[rank]
     items = [all_items[i] for i in share]
     regions = [r for r, _ in items]
@@ -657,14 +663,15 @@ def run_batch(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     w = WL.BATCHES[args.workload]
-    m = batch_measure(w, args.batch_count, args.steps, args.warmup, dist, ws, rank, local, tune=args.autotune)
+    m = batch_measure(w, args.batch_count, args.steps, args.warmup, dist, ws, rank, local, tune=args.autotune,
+                      iters=args.iters)
     line = {
         "metric": "roi_solves_per_s", "value": m["value"], "unit": "solves/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
         "dtype": "f32", "data": "synthetic",
         "scaling": "strong",
         "config": {"workload": w.name, "N": w.N, "n_angles": w.n_angles, "n_det": w.n_det, "regions": m["regions"],
-                   "radius": [w.r_lo, w.r_hi], "iters": w.iters, "solvers": "SIRT/TV 50/50"},
+                   "radius": [w.r_lo, w.r_hi], "iters": args.iters or w.iters, "solvers": "SIRT/TV 50/50"},
         "gpu_launches": m["gpu_launches"],
         "projector_Glerp_s_rank0": m["projector_Glerp_s_rank0"],
         "frac_of_lerp_ceiling": m["frac_of_ceiling"],
@@ -1107,6 +1114,62 @@ def run_tile(args):
     rr.close()
     return 0
 
+def run_large(args):
+    """Lone large regions through roi_recon_solve_local on the 2048 x 2048 / 180-angle serving
+    geometry (one region of radius --radius, margin r/2, CP-TV, --iters iterations): the
+    whole-region solver as one team of every block; one step = one solve, CUDA events."""
+    import torch
+
+    import paper_1604_02292_gb300 as R
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    w = WL.SERVING["roi_serve_2048"]
+    iters = args.iters or w.iters
+    c = (w.N - 1) / 2.0
+    region = (c + 100.0, c - 150.0, args.radius, args.radius / 2.0)
+    stream = torch.cuda.Stream()
+    rr = R.RoiRecon(*w.geometry(), stream=stream)
+    with torch.cuda.stream(stream):
+        rr.set_sinogram(torch.from_numpy(WL.sinogram(w, 0)).cuda())
+        rr.fbp()
+        for _ in range(args.warmup):
+            rr.solve_local(region, R.ROI_TV_CP, iters=iters, lam=w.lam)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    n0 = R.roi_recon_launch_count()
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                ev[k][0].record(stream)
+                rr.solve_local(region, R.ROI_TV_CP, iters=iters, lam=w.lam)
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    rr.sync()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    pl = rr.plan(region)
+    nx, ny = pl.box[2], pl.box[3]
+    lerps = iters * (sum(pl.width) * max(nx, ny) + nx * ny * w.n_angles)
+    pk, _ = peaks()
+    peak = N_SM * LERPS_PER_CLK_SM * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e9
+    glerps = lerps / (statistics.mean(ms) * 1e-3) / 1e9
+    line = {
+        "metric": "roi_solves_per_s", "value": args.steps / (sum(ms) / 1e3), "unit": "solves/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(ms), "higher_is_better": True,
+        "dtype": "f32", "data": "synthetic", "scaling": "weak",
+        "config": {"workload": "roi_large_2048", "N": w.N, "n_angles": w.n_angles, "n_det": w.n_det,
+                   "radius": args.radius, "box": nx, "iters": iters, "solver": "CP-TV",
+                   "path": "solve_local, whole-region solver, one team of every block"},
+        "gpu_launches": int(R.roi_recon_launch_count() - n0),
+        "projector_Glerp_s": glerps, "frac_of_lerp_ceiling": glerps / peak,
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    rr.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1121,6 +1184,8 @@ def main():
         return run_serve(args)
     if args.workload in WL.PRECISION:
         return run_precision(args)
+    if args.workload == "roi_large_2048":
+        return run_large(args)
     return run_ours(args)
 
 

@@ -410,8 +410,8 @@ typedef struct {
     size_t host_bytes;     /* page-locked result area (0: 512 MiB) */
     int ring_slots;        /* request slots per unit pool (0: 1024) */
     int team_blocks;       /* blocks per team of the large-box pool (0: 16) */
-    int teams;             /* teams (-1: about 3/4 of the blocks; 0: no team pool) */
-    int large_side;        /* box side from which a request goes to the team pool (0: 320) */
+    int teams;             /* teams (-1: every block but 24 in teams; 0: no team pool) */
+    int large_side;        /* box side from which a request goes to the team pool (0: 256) */
     int idle_us;           /* the kernel leaves after this long without work (0: 2000) */
     int no_spill;          /* 0: a small-box request is admitted to an idle team when no
                               large one waits for it, and requests arriving at an idle server

@@ -394,6 +394,9 @@ void publish(roi_server* s, int pi, Req* r, size_t slot) {
     __atomic_store_n(&s->ctl_h->tail[pi], (unsigned long long)(r->ticket + 1), __ATOMIC_RELEASE);
 }
 
+// Single-block units left by the default pool split (the rest of the blocks form teams).
+constexpr int kSingleUnits = 24;
+
 // A solo launch serves the queue one request at a time on every block (the latency of a
 // whole-GPU solve, the plain one-at-a-time throughput).  It is asked to leave when the work
 // queued behind it, estimated in solo milliseconds, exceeds cfg.solo_queue_ms (or more than
@@ -612,7 +615,7 @@ roi_status roi_server_create(const roi_server_config* cfg_in, roi_server_t* out)
     if (cfg.host_bytes == 0) cfg.host_bytes = (size_t)512 << 20;
     if (cfg.ring_slots == 0) cfg.ring_slots = 1024;
     if (cfg.team_blocks == 0) cfg.team_blocks = 16;
-    if (cfg.large_side == 0) cfg.large_side = 320;
+    if (cfg.large_side == 0) cfg.large_side = 256;
     if (cfg.idle_us == 0) cfg.idle_us = 2000;
     if (cfg.solo_queue_ms == 0) cfg.solo_queue_ms = 250;
     if (cfg.ring_slots < 1 || cfg.ring_slots > (1 << 20) || cfg.team_blocks < 1 || cfg.team_blocks > 1024 ||
@@ -634,7 +637,9 @@ roi_status roi_server_create(const roi_server_config* cfg_in, roi_server_t* out)
     }
     if (e == cudaSuccess) {
         // pool split: teams of team_blocks from the top, single blocks below
-        int teams = cfg.teams < 0 ? (s->blocks * 3 / 4) / cfg.team_blocks : cfg.teams;
+        // default: every block but kSingleUnits in teams (boxes of side >= large_side carry
+        // most of the work of a log-uniform radius mix)
+        int teams = cfg.teams < 0 ? std::max(s->blocks - kSingleUnits, 0) / cfg.team_blocks : cfg.teams;
         teams = std::min(teams, (s->blocks - 1) / cfg.team_blocks);  // keep at least one single block
         teams = std::max(teams, 0);
         Pool& P0 = s->pools[0];
