@@ -62,11 +62,13 @@ __global__ void __launch_bounds__(BPT, 1) k_batch(BatchArgs B) {
 
 }  // namespace
 
-size_t batch_smem_bytes(size_t max_stage_bytes, int na) {
-    // the per-warp phase-B areas and one tile's chunk partials (cooperative phase B)
+size_t batch_smem_bytes(size_t max_stage_bytes, int na, bool banded) {
+    // the per-warp phase-B areas and one tile's chunk partials (cooperative phase B); with a
+    // band-streamed region, the partial sums of a pass over more units than warps
     const size_t chunks = (size_t)(na + rs::ACH - 1) / rs::ACH;
     const size_t phase_b = sizeof(float) * ((size_t)rs::BNW * rs::WARP_STAGE + chunks * rs::TB * rs::TB);
-    return std::min(std::max(max_stage_bytes, phase_b), std::max(max_stage_bytes, (size_t)kStageMaxBytes));
+    const size_t s = std::min(std::max(max_stage_bytes, phase_b), std::max(max_stage_bytes, (size_t)kStageMaxBytes));
+    return banded ? s + kBandStateBytes : s;
 }
 
 cudaError_t launch_batch(const BatchArgs& B, int blocks, size_t smem, cudaStream_t st) {

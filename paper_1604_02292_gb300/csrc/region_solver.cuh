@@ -635,11 +635,16 @@ __device__ __forceinline__ void phase_a_global(const Ctx& C, const Team& T, int 
 
 // Phase A of one branch with the image streamed through shared memory in bands of
 // band_rows() rows (two buffers, one bulk copy each, refilled while the other is read).
-// This block's units (ustart + member + i * size) are taken in groups of 32, one per
-// warp; each group walks all bands, each lane accumulating its ray over the samples
-// that fall in the band (one float-float anchor per band and ray), then finishes the
-// ray as phase_a_branch does.  mbar[0..1]: the buffers' barriers, parity: their phase
-// bits (bit b for buffer b).  false: a wait gave up.
+// This block's units (ustart + member + i * size) go in passes; each pass walks all bands,
+// each ray accumulating the samples that fall in the band (one float-float anchor per band
+// and ray, added in band order with Neumaier compensation), then finishes its rays as
+// phase_a_branch does.  A pass covers 32 units (one per warp, sums in registers), or, when
+// the block has more units than warps and the shared memory past the band buffers holds
+// their partial sums, up to that many (warps take the pass's units round-robin in every
+// band, the sums live in shared memory): the image then crosses from L2 once per pass of
+// up to kBandStateBytes / 256 units instead of once per 32.  Both give the same bits.
+// mbar[0..1]: the buffers' barriers, parity: their phase bits (bit b for buffer b).
+// false: a wait gave up.
 template <bool SOLO, int DT>
 __device__ __forceinline__ bool phase_a_banded(const Ctx& C, const Team& T, int row, const void* img_base_v, int ld,
                                                float* smem_f, uint64_t* mbar, unsigned& parity) {
@@ -658,33 +663,54 @@ __device__ __forceinline__ bool phase_a_banded(const Ctx& C, const Team& T, int 
     const int nb = (M + BR - 1) / BR;
     const int band_floats = BR * ld;
     const float halfM = 0.5f * (float)(M - 1);
-    for (int g0 = 0; g0 < nu; g0 += BNW) {
-        const int i = g0 + warp;
-        int a = 0, k = 0;
-        bool valid = i < nu;
-        if (valid) {
-            const int unit = ustart + tm + i * ts;
-            a = unit / C.nchunk;
-            k = (unit - a * C.nchunk) * 32 + lane;
-            valid = k < R.rec[a].width;
+    // units per pass: the partial sums (two floats per ray) past the band buffers
+    const int state_off = (int)((stage_bytes(R.nx, R.ny, ES) + 15) / 16 * 4);
+    const int cap = (dyn_smem_floats() - state_off) / 64 / BNW * BNW;
+    const int per_pass = (nu > BNW && cap >= 2 * BNW) ? cap : BNW;
+    float* st_sum = smem_f + state_off;          // [per_pass][32]
+    float* st_cmp = st_sum + (size_t)per_pass * 32;
+    // This lane's ray of pass unit i: angle a, ray k; false when it carries no samples.
+    auto ray_of = [&](int i, int& a, int& k) {
+        const int unit = ustart + tm + i * ts;
+        a = unit / C.nchunk;
+        k = (unit - a * C.nchunk) * 32 + lane;
+        return k < R.rec[a].width;
+    };
+    // The value of ray (a, k) over band b (rows [b BR, (b + 1) BR) of the image in buffer bi).
+    auto band_value = [&](const AngleRec& r, ff Ak, int mlo, int mhi, int b, int bi, bool& any) {
+        const int m0 = max(mlo, b * BR), m1 = min(mhi, (b + 1) * BR);
+        any = m0 < m1;
+        if (!any) return 0.f;
+        int j0;
+        int q = split_fixed22(ff_add(Ak, ff_mul_f((float)m0 - halfM, r.slope)), j0);
+        const int step = r.slope_q22;
+        const TS* rp = smem + bi * band_floats + (m0 - b * BR) * ld + kPad + j0;
+        const int jlo = -kPad - j0, jhi = ld - 1 - kPad - j0;
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll 4
+        for (int m = m0; m < m1; ++m, rp += ld, q += step) {
+            const int j = chk(q >> 22, jlo, jhi, CHK_REGION_BAND);
+            const float mf = frac_int<22>(q);
+            const float v0 = to_f32<DT>(rp[j]), v1 = to_f32<DT>(rp[j + 1]);
+            s0 += v0;
+            s1 = fmaf(mf, v1 - v0, s1);
         }
-        const AngleRec& r = R.rec[a];
+        return fmaf(s1, 2.384185791015625e-07f, s0);
+    };
+    for (int g0 = 0; g0 < nu; g0 += per_pass) {
+        const int np = min(per_pass, nu - g0);
+        const bool in_smem = per_pass > BNW;
+        // one unit per warp: its ray in registers
+        int a = 0, k = 0, mlo = 0, mhi = 0;
         ff Ak{0.f, 0.f};
-        int mlo = 0, mhi = 0;
-        if (valid) {
-            Ak = ff_add(r.A0, ff_mul_f((float)k, r.a_scale));
-            mhi = M;
-            if (!r.flat) {
-                const float ma = (-1.5f - Ak.hi) * r.inv_slope + halfM;
-                const float mb = ((float)Mm + 0.5f - Ak.hi) * r.inv_slope + halfM;
-                const float lo = fminf(ma, mb), hi = fmaxf(ma, mb);
-                mlo = (int)fminf(fmaxf(0.f, ceilf(lo)), (float)M);
-                mhi = (int)fmaxf(fminf((float)M, floorf(hi) + 1.f), 0.f);
-            } else if (!(Ak.hi >= -1.5f && Ak.hi <= (float)Mm + 0.5f)) {
-                mhi = 0;
-            }
-        }
+        bool valid = false;
         float sum = 0.f, cmp = 0.f;
+        if (!in_smem) {
+            if (warp < np) valid = ray_of(g0 + warp, a, k);
+            if (valid) Ak = ray_span(R.rec[a], k, M, Mm, mlo, mhi);
+        } else {
+            for (int e = threadIdx.x; e < np * 32; e += BPT) st_sum[e] = st_cmp[e] = 0.f;
+        }
         if (threadIdx.x == 0) {
             const int rows0 = M < BR ? M : BR;
             bulk_load(smem, img_base, ES * rows0 * ld, &mbar[0]);
@@ -698,40 +724,35 @@ __device__ __forceinline__ bool phase_a_banded(const Ctx& C, const Team& T, int 
             }
             if (!mbar_wait(&mbar[bi], (parity >> bi) & 1u, T.wait_ns, T.err)) return false;
             parity ^= 1u << bi;
-            const int m0 = max(mlo, b * BR), m1 = min(mhi, (b + 1) * BR);
-            if (valid && m0 < m1) {
-                int j0;
-                int q = split_fixed22(ff_add(Ak, ff_mul_f((float)m0 - halfM, r.slope)), j0);
-                const int step = r.slope_q22;
-                const TS* rp = smem + bi * band_floats + (m0 - b * BR) * ld + kPad + j0;
-                const int jlo = -kPad - j0, jhi = ld - 1 - kPad - j0;
-                float s0 = 0.f, s1 = 0.f;
-#pragma unroll 4
-                for (int m = m0; m < m1; ++m, rp += ld, q += step) {
-                    const int j = chk(q >> 22, jlo, jhi, CHK_REGION_BAND);
-                    const float mf = frac_int<22>(q);
-                    const float v0 = to_f32<DT>(rp[j]), v1 = to_f32<DT>(rp[j + 1]);
-                    s0 += v0;
-                    s1 = fmaf(mf, v1 - v0, s1);
+            if (!in_smem) {
+                if (valid) {
+                    bool any;
+                    const float v = band_value(R.rec[a], Ak, mlo, mhi, b, bi, any);
+                    if (any) neu_add(sum, cmp, v);
                 }
-                neu_add(sum, cmp, fmaf(s1, 2.384185791015625e-07f, s0));
+            } else {
+                for (int i = warp; i < np; i += BNW) {
+                    int ai, ki;
+                    if (!ray_of(g0 + i, ai, ki)) continue;
+                    const AngleRec& r = R.rec[ai];
+                    int lo, hi;
+                    const ff Aki = ray_span(r, ki, M, Mm, lo, hi);
+                    bool any;
+                    const float v = band_value(r, Aki, lo, hi, b, bi, any);
+                    if (any) neu_add(st_sum[i * 32 + lane], st_cmp[i * 32 + lane], v);
+                }
             }
             __syncthreads();
         }
-        if (valid) {
-            ff tot = ff_mul_f(r.inv_w, two_sum(sum, cmp));
-            const float acc = tot.hi + tot.lo;
-            const size_t o = (size_t)a * R.stride + k;
-            if (R.reg == 0) {
-                float res = C.b.pp[o] - acc;
-                if (R.weighting) res *= C.b.sig[o];
-                C.b.u[o] = res;
-            } else if (R.reg >= 2) {
-                C.b.u[o] = -R.alpha * acc;
-            } else {
-                const float sg = C.b.sig[o];
-                C.b.u[o] = (C.b.u[o] + sg * (acc - C.b.pp[o])) / (1.f + 0.5f * sg);
+        if (!in_smem) {
+            if (valid) finish_ray(C, R.rec[a], a, k, two_sum(sum, cmp), A_SOLVE);
+        } else {
+            for (int i = warp; i < np; i += BNW) {
+                int ai, ki;
+                if (ray_of(g0 + i, ai, ki))
+                    finish_ray(C, R.rec[ai], ai, ki, two_sum(st_sum[i * 32 + lane], st_cmp[i * 32 + lane]), A_SOLVE);
             }
+            __syncthreads();  // the partial sums are reused by the next pass
         }
     }
     return true;

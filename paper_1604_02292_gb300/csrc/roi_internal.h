@@ -318,6 +318,9 @@ cudaError_t launch_persist(const PersistLaunch& L, cudaStream_t st);
 // kStageMaxBytes hold, a multiple of 8, from kBandRowsMin to kBandRowsMax),
 // double-buffered; 2 = read from global memory.
 constexpr size_t kStageMaxBytes = 200 * 1024;
+// Shared memory past the band buffers for the per-ray partial sums of band-streamed phase A
+// when a block has more ray units than warps (up to kBandStateBytes / 256 units per pass).
+constexpr size_t kBandStateBytes = 24 * 1024;
 constexpr int kBandRowsMin = 24;
 constexpr int kBandRowsMax = 96;
 ROI_HD int band_rows(int nx, int ny, int esz) {
@@ -478,7 +481,7 @@ struct SinoView {
 
 int sino_view(::roi_recon* h, SinoView* v, std::string* msg);
 
-size_t batch_smem_bytes(size_t max_stage_bytes, int na);
+size_t batch_smem_bytes(size_t max_stage_bytes, int na, bool banded);
 cudaError_t launch_batch(const BatchArgs& B, int blocks, size_t smem, cudaStream_t st);
 cudaError_t launch_batch_team(const BatchArgs& B, int blocks, size_t smem, cudaStream_t st);
 

@@ -183,9 +183,10 @@ __global__ void __launch_bounds__(BPT, 1) k_serve(const ServeArgs A) {
 }  // namespace
 
 size_t serve_smem_bytes() {
-    // any request's staging (at most kStageMaxBytes) and the per-warp phase-B areas
+    // any request's staging (at most kStageMaxBytes) and the per-warp phase-B areas, then
+    // the per-ray partial sums of band-streamed phase A passes
     const size_t phase_b = sizeof(float) * (size_t)rs::BNW * rs::WARP_STAGE;
-    return kStageMaxBytes > phase_b ? kStageMaxBytes : phase_b;
+    return (kStageMaxBytes > phase_b ? kStageMaxBytes : phase_b) + kBandStateBytes;
 }
 
 int serve_max_blocks(int device) {
