@@ -326,6 +326,45 @@ def large_box_measure(reps=3):
     return out
 
 
+def small_measure(steps=20, warmup=3):
+    """The 128 x 128 workload (64 angles, 128 bins, ROI radius 16 + margin 8: box 48 x 48,
+    200 nonnegative SIRT iterations): one step = set sinogram + FBP + exterior + solve, like
+    the default line's step; CUDA events around each step; steps cycle over 8 regions."""
+    import torch
+
+    import paper_1604_02292_gb300 as R
+
+    w = WL.WORKLOADS["roi_sirt_128"]
+    p_dev = torch.from_numpy(WL.sinogram(w, 0)).cuda()
+    regions = [WL.region(w, seed=s) for s in range(N_REGIONS)]
+    stream = torch.cuda.Stream()
+    rr = R.RoiRecon(*w.geometry(), stream=stream)
+    plans = [rr.plan(r) for r in regions]
+    outs = [torch.empty((pl.box[3], pl.box[2]), dtype=torch.float32, device="cuda") for pl in plans]
+
+    def step(k):
+        rr.set_sinogram(p_dev)
+        rr.fbp()
+        rr.solve_local(regions[k % N_REGIONS], R.ROI_SIRT_NONNEG, iters=w.iters, out=outs[k % N_REGIONS])
+
+    with torch.cuda.stream(stream):
+        for k in range(warmup):
+            step(k)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for k in range(steps):
+            ev[k][0].record(stream)
+            step(k)
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    rr.close()
+    return {"workload": w.name, "value": steps / (sum(ms) / 1e3), "unit": "solves/s",
+            "ms_per_step": statistics.mean(ms), "box": plans[0].box[2], "iters": w.iters, "solver": w.reg,
+            "path": "single cooperative launch per solve (k_persist)"}
+
+
 def local_vs_global(rr, w, p_dev, region, reg, stream):
     """The regularized local solve of `region` against the same solver, lambda and
     iterations on a box covering the whole grid, inside the ROI disk (report only)."""
@@ -497,6 +536,11 @@ def run_ours(args):
                         "plain": m["plain"], "kernel_launches": m["server"]["kernel_launches"]})
         serving["rates"] = pts
 
+    # ---- the 128 x 128 workload (box 48, 200 SIRT iterations)
+    small = None
+    if rank == 0 and not args.no_batch:
+        small = small_measure()
+
     # ---- lone large boxes (beyond the single-launch solver): team of all blocks vs per operator
     large = None
     if rank == 0 and not args.no_batch:
@@ -571,6 +615,7 @@ def run_ours(args):
             "batch": batch,
             "precision": precision,
             "large_box": large,
+            "small_box": small,
         }
         print(json.dumps(line), flush=True)
     rr.close()

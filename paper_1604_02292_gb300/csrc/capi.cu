@@ -1445,7 +1445,7 @@ roi_status solve_batch_impl(roi_recon* h, int n, const roi_region* regions, cons
     std::vector<Rect> boxes(n);
     std::vector<int> strides(n);
     size_t out_total = 0, win_cap = 0, img_cap = 0, pad_cap = 0, max_stage = 0;
-    bool any_banded = false;
+    size_t max_banded_units = 0;  // ray units of the largest band-streamed region
     std::vector<double> cost(n);
     std::vector<AngleRec> loc(na);
     for (int i = 0; i < n; ++i) {
@@ -1477,7 +1477,8 @@ roi_status solve_batch_impl(roi_recon* h, int n, const roi_region* regions, cons
         const size_t pc = (size_t)box.w * roi::padded_ld_e(box.h, h->esz) * h->esz;
         pad_cap = std::max(pad_cap, (std::max(pr, pc) + 15) / 16 * 4);
         max_stage = std::max(max_stage, roi::stage_bytes(box.w, box.h, h->esz));
-        any_banded = any_banded || roi::stage_mode(box.w, box.h, h->esz) == 1;
+        if (roi::stage_mode(box.w, box.h, h->esz) == 1)
+            max_banded_units = std::max(max_banded_units, (size_t)na * ((strides[i] + 31) / 32));
         cost[i] = (double)box.w * box.h * na * (double)std::max(P.iters, 1);
     }
     if (need_fbp) {
@@ -1594,7 +1595,9 @@ roi_status solve_batch_impl(roi_recon* h, int n, const roi_region* regions, cons
     B.team = team > 1 ? team : 1;
     B.bars = team > 1 ? h->b_bars.p : nullptr;
     B.absent = h->opt_phantoms;
-    const size_t smem = roi::batch_smem_bytes(max_stage, h->na, any_banded);
+    // partial-sum room for band-streamed passes when a block gets 128 or more units of a region
+    const size_t per_block = (max_banded_units + (team > 1 ? team : 1) - 1) / (team > 1 ? team : 1);
+    const size_t smem = roi::batch_smem_bytes(max_stage, h->na, per_block >= 128);
     cudaError_t e;
     {
         Span sp(h, 2);

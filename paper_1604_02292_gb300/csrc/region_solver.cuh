@@ -633,18 +633,93 @@ __device__ __forceinline__ void phase_a_global(const Ctx& C, const Team& T, int 
     }
 }
 
+// Band-streamed phase A of a block with many units (as phase_a_banded, same bits): passes
+// of up to per_pass units, each pass walking all bands once; in every band the warps take the
+// pass's units round-robin and add each ray's band value to its partial sums, kept in shared
+// memory past the band buffers (st_sum, st_cmp: [per_pass][32]).  The image then crosses from
+// L2 once per pass instead of once per 32 units.
+template <bool SOLO, int DT>
+__device__ __noinline__ bool phase_a_banded_passes(const Ctx& C, const Team& T, int row, const void* img_base_v,
+                                                   int ld, float* smem_f, uint64_t* mbar, unsigned& parity,
+                                                   int nu, int per_pass, float* st_sum, float* st_cmp) {
+    using TS = typename Stor<DT>::T;
+    constexpr unsigned ES = sizeof(TS);
+    const TS* img_base = static_cast<const TS*>(img_base_v);
+    TS* smem = reinterpret_cast<TS*>(smem_f);
+    const BatchRoi& R = *C.R;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tm = SOLO ? 0 : T.member, ts = SOLO ? 1 : T.size;
+    const int M = row ? R.ny : R.nx, Mm = row ? R.nx : R.ny;
+    const int ustart = row ? 0 : R.nrow * C.nchunk;
+    const int BR = band_rows(R.nx, R.ny, ES);
+    const int nb = (M + BR - 1) / BR;
+    const int band_floats = BR * ld;
+    const float halfM = 0.5f * (float)(M - 1);
+    for (int g0 = 0; g0 < nu; g0 += per_pass) {
+        const int np = min(per_pass, nu - g0);
+        for (int e = threadIdx.x; e < np * 32; e += BPT) st_sum[e] = st_cmp[e] = 0.f;
+        if (threadIdx.x == 0) {
+            const int rows0 = M < BR ? M : BR;
+            bulk_load(smem, img_base, ES * rows0 * ld, &mbar[0]);
+        }
+        for (int b = 0; b < nb; ++b) {
+            const int bi = b & 1;
+            if (threadIdx.x == 0 && b + 1 < nb) {  // the other buffer was released by the last barrier
+                const int rows = min(BR, M - (b + 1) * BR);
+                bulk_load(smem + (bi ^ 1) * band_floats, img_base + (size_t)(b + 1) * band_floats, ES * rows * ld,
+                          &mbar[bi ^ 1]);
+            }
+            if (!mbar_wait(&mbar[bi], (parity >> bi) & 1u, T.wait_ns, T.err)) return false;
+            parity ^= 1u << bi;
+            for (int i = warp; i < np; i += BNW) {
+                const int unit = ustart + tm + (g0 + i) * ts;
+                const int a = unit / C.nchunk;
+                const int k = (unit - a * C.nchunk) * 32 + lane;
+                const AngleRec& r = R.rec[a];
+                if (k >= r.width) continue;
+                int mlo, mhi;
+                const ff Ak = ray_span(r, k, M, Mm, mlo, mhi);
+                const int m0 = max(mlo, b * BR), m1 = min(mhi, (b + 1) * BR);
+                if (m0 >= m1) continue;
+                int j0;
+                int q = split_fixed22(ff_add(Ak, ff_mul_f((float)m0 - halfM, r.slope)), j0);
+                const int step = r.slope_q22;
+                const TS* rp = smem + bi * band_floats + (m0 - b * BR) * ld + kPad + j0;
+                const int jlo = -kPad - j0, jhi = ld - 1 - kPad - j0;
+                float s0 = 0.f, s1 = 0.f;
+#pragma unroll 4
+                for (int m = m0; m < m1; ++m, rp += ld, q += step) {
+                    const int j = chk(q >> 22, jlo, jhi, CHK_REGION_BAND);
+                    const float mf = frac_int<22>(q);
+                    const float v0 = to_f32<DT>(rp[j]), v1 = to_f32<DT>(rp[j + 1]);
+                    s0 += v0;
+                    s1 = fmaf(mf, v1 - v0, s1);
+                }
+                neu_add(st_sum[i * 32 + lane], st_cmp[i * 32 + lane], fmaf(s1, 2.384185791015625e-07f, s0));
+            }
+            __syncthreads();
+        }
+        for (int i = warp; i < np; i += BNW) {
+            const int unit = ustart + tm + (g0 + i) * ts;
+            const int a = unit / C.nchunk;
+            const int k = (unit - a * C.nchunk) * 32 + lane;
+            const AngleRec& r = R.rec[a];
+            if (k < r.width) finish_ray(C, r, a, k, two_sum(st_sum[i * 32 + lane], st_cmp[i * 32 + lane]), A_SOLVE);
+        }
+        __syncthreads();  // the partial sums are reused by the next pass
+    }
+    return true;
+}
+
 // Phase A of one branch with the image streamed through shared memory in bands of
 // band_rows() rows (two buffers, one bulk copy each, refilled while the other is read).
-// This block's units (ustart + member + i * size) go in passes; each pass walks all bands,
-// each ray accumulating the samples that fall in the band (one float-float anchor per band
-// and ray, added in band order with Neumaier compensation), then finishes its rays as
-// phase_a_branch does.  A pass covers 32 units (one per warp, sums in registers), or, when
-// the block has more units than warps and the shared memory past the band buffers holds
-// their partial sums, up to that many (warps take the pass's units round-robin in every
-// band, the sums live in shared memory): the image then crosses from L2 once per pass of
-// up to kBandStateBytes / 256 units instead of once per 32.  Both give the same bits.
-// mbar[0..1]: the buffers' barriers, parity: their phase bits (bit b for buffer b).
-// false: a wait gave up.
+// This block's units (ustart + member + i * size) are taken in groups of 32, one per
+// warp; each group walks all bands, each lane accumulating its ray over the samples
+// that fall in the band (one float-float anchor per band and ray), then finishes the
+// ray as phase_a_branch does.  A block with at least 128 units goes by passes instead
+// (phase_a_banded_passes) when the shared memory past the band buffers holds the partial
+// sums of 64 or more units.  mbar[0..1]: the buffers' barriers, parity: their phase bits
+// (bit b for buffer b).  false: a wait gave up.
 template <bool SOLO, int DT>
 __device__ __forceinline__ bool phase_a_banded(const Ctx& C, const Team& T, int row, const void* img_base_v, int ld,
                                                float* smem_f, uint64_t* mbar, unsigned& parity) {
@@ -659,58 +734,46 @@ __device__ __forceinline__ bool phase_a_banded(const Ctx& C, const Team& T, int 
     const int ustart = row ? 0 : R.nrow * C.nchunk;
     const int total = (row ? R.nrow : R.na) * C.nchunk - ustart;
     const int nu = total > tm ? (total - tm + ts - 1) / ts : 0;
+    if (nu >= 4 * BNW) {  // many units: passes with the partial sums in shared memory
+        const int state_off = (int)((stage_bytes(R.nx, R.ny, ES) + 15) / 16 * 4);
+        const int cap = (dyn_smem_floats() - state_off) / 64 / BNW * BNW;
+        if (cap >= 2 * BNW) {
+            float* st = smem_f + state_off;
+            return phase_a_banded_passes<SOLO, DT>(C, T, row, img_base_v, ld, smem_f, mbar, parity, nu, cap, st,
+                                                   st + (size_t)cap * 32);
+        }
+    }
     const int BR = band_rows(R.nx, R.ny, ES);
     const int nb = (M + BR - 1) / BR;
     const int band_floats = BR * ld;
     const float halfM = 0.5f * (float)(M - 1);
-    // units per pass: the partial sums (two floats per ray) past the band buffers
-    const int state_off = (int)((stage_bytes(R.nx, R.ny, ES) + 15) / 16 * 4);
-    const int cap = (dyn_smem_floats() - state_off) / 64 / BNW * BNW;
-    const int per_pass = (nu > BNW && cap >= 2 * BNW) ? cap : BNW;
-    float* st_sum = smem_f + state_off;          // [per_pass][32]
-    float* st_cmp = st_sum + (size_t)per_pass * 32;
-    // This lane's ray of pass unit i: angle a, ray k; false when it carries no samples.
-    auto ray_of = [&](int i, int& a, int& k) {
-        const int unit = ustart + tm + i * ts;
-        a = unit / C.nchunk;
-        k = (unit - a * C.nchunk) * 32 + lane;
-        return k < R.rec[a].width;
-    };
-    // The value of ray (a, k) over band b (rows [b BR, (b + 1) BR) of the image in buffer bi).
-    auto band_value = [&](const AngleRec& r, ff Ak, int mlo, int mhi, int b, int bi, bool& any) {
-        const int m0 = max(mlo, b * BR), m1 = min(mhi, (b + 1) * BR);
-        any = m0 < m1;
-        if (!any) return 0.f;
-        int j0;
-        int q = split_fixed22(ff_add(Ak, ff_mul_f((float)m0 - halfM, r.slope)), j0);
-        const int step = r.slope_q22;
-        const TS* rp = smem + bi * band_floats + (m0 - b * BR) * ld + kPad + j0;
-        const int jlo = -kPad - j0, jhi = ld - 1 - kPad - j0;
-        float s0 = 0.f, s1 = 0.f;
-#pragma unroll 4
-        for (int m = m0; m < m1; ++m, rp += ld, q += step) {
-            const int j = chk(q >> 22, jlo, jhi, CHK_REGION_BAND);
-            const float mf = frac_int<22>(q);
-            const float v0 = to_f32<DT>(rp[j]), v1 = to_f32<DT>(rp[j + 1]);
-            s0 += v0;
-            s1 = fmaf(mf, v1 - v0, s1);
+    for (int g0 = 0; g0 < nu; g0 += BNW) {
+        const int i = g0 + warp;
+        int a = 0, k = 0;
+        bool valid = i < nu;
+        if (valid) {
+            const int unit = ustart + tm + i * ts;
+            a = unit / C.nchunk;
+            k = (unit - a * C.nchunk) * 32 + lane;
+            valid = k < R.rec[a].width;
         }
-        return fmaf(s1, 2.384185791015625e-07f, s0);
-    };
-    for (int g0 = 0; g0 < nu; g0 += per_pass) {
-        const int np = min(per_pass, nu - g0);
-        const bool in_smem = per_pass > BNW;
-        // one unit per warp: its ray in registers
-        int a = 0, k = 0, mlo = 0, mhi = 0;
+        const AngleRec& r = R.rec[a];
         ff Ak{0.f, 0.f};
-        bool valid = false;
-        float sum = 0.f, cmp = 0.f;
-        if (!in_smem) {
-            if (warp < np) valid = ray_of(g0 + warp, a, k);
-            if (valid) Ak = ray_span(R.rec[a], k, M, Mm, mlo, mhi);
-        } else {
-            for (int e = threadIdx.x; e < np * 32; e += BPT) st_sum[e] = st_cmp[e] = 0.f;
+        int mlo = 0, mhi = 0;
+        if (valid) {
+            Ak = ff_add(r.A0, ff_mul_f((float)k, r.a_scale));
+            mhi = M;
+            if (!r.flat) {
+                const float ma = (-1.5f - Ak.hi) * r.inv_slope + halfM;
+                const float mb = ((float)Mm + 0.5f - Ak.hi) * r.inv_slope + halfM;
+                const float lo = fminf(ma, mb), hi = fmaxf(ma, mb);
+                mlo = (int)fminf(fmaxf(0.f, ceilf(lo)), (float)M);
+                mhi = (int)fmaxf(fminf((float)M, floorf(hi) + 1.f), 0.f);
+            } else if (!(Ak.hi >= -1.5f && Ak.hi <= (float)Mm + 0.5f)) {
+                mhi = 0;
+            }
         }
+        float sum = 0.f, cmp = 0.f;
         if (threadIdx.x == 0) {
             const int rows0 = M < BR ? M : BR;
             bulk_load(smem, img_base, ES * rows0 * ld, &mbar[0]);
@@ -724,35 +787,40 @@ __device__ __forceinline__ bool phase_a_banded(const Ctx& C, const Team& T, int 
             }
             if (!mbar_wait(&mbar[bi], (parity >> bi) & 1u, T.wait_ns, T.err)) return false;
             parity ^= 1u << bi;
-            if (!in_smem) {
-                if (valid) {
-                    bool any;
-                    const float v = band_value(R.rec[a], Ak, mlo, mhi, b, bi, any);
-                    if (any) neu_add(sum, cmp, v);
+            const int m0 = max(mlo, b * BR), m1 = min(mhi, (b + 1) * BR);
+            if (valid && m0 < m1) {
+                int j0;
+                int q = split_fixed22(ff_add(Ak, ff_mul_f((float)m0 - halfM, r.slope)), j0);
+                const int step = r.slope_q22;
+                const TS* rp = smem + bi * band_floats + (m0 - b * BR) * ld + kPad + j0;
+                const int jlo = -kPad - j0, jhi = ld - 1 - kPad - j0;
+                float s0 = 0.f, s1 = 0.f;
+#pragma unroll 4
+                for (int m = m0; m < m1; ++m, rp += ld, q += step) {
+                    const int j = chk(q >> 22, jlo, jhi, CHK_REGION_BAND);
+                    const float mf = frac_int<22>(q);
+                    const float v0 = to_f32<DT>(rp[j]), v1 = to_f32<DT>(rp[j + 1]);
+                    s0 += v0;
+                    s1 = fmaf(mf, v1 - v0, s1);
                 }
-            } else {
-                for (int i = warp; i < np; i += BNW) {
-                    int ai, ki;
-                    if (!ray_of(g0 + i, ai, ki)) continue;
-                    const AngleRec& r = R.rec[ai];
-                    int lo, hi;
-                    const ff Aki = ray_span(r, ki, M, Mm, lo, hi);
-                    bool any;
-                    const float v = band_value(r, Aki, lo, hi, b, bi, any);
-                    if (any) neu_add(st_sum[i * 32 + lane], st_cmp[i * 32 + lane], v);
-                }
+                neu_add(sum, cmp, fmaf(s1, 2.384185791015625e-07f, s0));
             }
             __syncthreads();
         }
-        if (!in_smem) {
-            if (valid) finish_ray(C, R.rec[a], a, k, two_sum(sum, cmp), A_SOLVE);
-        } else {
-            for (int i = warp; i < np; i += BNW) {
-                int ai, ki;
-                if (ray_of(g0 + i, ai, ki))
-                    finish_ray(C, R.rec[ai], ai, ki, two_sum(st_sum[i * 32 + lane], st_cmp[i * 32 + lane]), A_SOLVE);
+        if (valid) {
+            ff tot = ff_mul_f(r.inv_w, two_sum(sum, cmp));
+            const float acc = tot.hi + tot.lo;
+            const size_t o = (size_t)a * R.stride + k;
+            if (R.reg == 0) {
+                float res = C.b.pp[o] - acc;
+                if (R.weighting) res *= C.b.sig[o];
+                C.b.u[o] = res;
+            } else if (R.reg >= 2) {
+                C.b.u[o] = -R.alpha * acc;
+            } else {
+                const float sg = C.b.sig[o];
+                C.b.u[o] = (C.b.u[o] + sg * (acc - C.b.pp[o])) / (1.f + 0.5f * sg);
             }
-            __syncthreads();  // the partial sums are reused by the next pass
         }
     }
     return true;
