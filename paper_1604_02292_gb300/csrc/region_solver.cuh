@@ -146,6 +146,10 @@ struct Ctx {
     int nchunk;
     int member, gthreads; // this block's index in the team, threads of the team
     int stage;            // stage_mode of the box (0 whole image, 1 bands, 2 global)
+    // phase A of the iterations in a team of two or more blocks: the blocks are split between
+    // the two branches in proportion to their units, so each stages one image; this block's
+    // branch (1 rows, 0 columns; -1: both, in turn) and its index / count within it
+    int arow, amember, asize;
 };
 // (A Ctx lives in shared memory: it is uniform over the block, and keeping it out of
 // registers leaves them to the inner loops.)
@@ -1034,6 +1038,20 @@ __device__ __forceinline__ bool solve_region(const BatchRoi& R, const RegionBufs
         W.member = SOLO ? 0 : T.member;
         W.gthreads = (SOLO ? 1 : T.size) * BPT;
         W.stage = stage_mode(R.nx, R.ny, ES);  // every block of a team stages the image itself
+        W.arow = -1;
+        W.amember = W.member;
+        W.asize = SOLO ? 1 : T.size;
+        if (!SOLO && T.size > 1) {
+            const long ur = (long)R.nrow * W.nchunk, uc = (long)(R.na - R.nrow) * W.nchunk;
+            int gr = (int)((ur * T.size + (ur + uc) / 2) / max(ur + uc, 1L));
+            if (ur > 0 && gr < 1) gr = 1;
+            if (uc > 0 && gr > T.size - 1) gr = T.size - 1;
+            if (uc == 0) gr = T.size;
+            if (ur == 0) gr = 0;
+            W.arow = T.member < gr ? 1 : 0;
+            W.amember = W.arow ? T.member : T.member - gr;
+            W.asize = W.arow ? gr : T.size - gr;
+        }
     }
     __syncthreads();
     const Ctx& C = s_ctx;
@@ -1072,24 +1090,31 @@ __device__ __forceinline__ bool solve_region(const BatchRoi& R, const RegionBufs
     float fista_t = 1.f;  // FISTA sequence t_{k-1} (reg 3)
     if (R.reg >= 3) fill_team(C, C.b.tau, nimg, 0.f);  // x^0 = 0
     for (int it = 0; it < R.iters; ++it) {
+        // a team block works on its branch only (C.arow), as a member of that branch's blocks
+        Team TA = T;
+        TA.member = C.amember;
+        TA.size = C.asize;
         if (C.stage == 0) {
             for (int row = 1; row >= 0; --row) {
+                if (C.arow >= 0 && row != C.arow) continue;
                 if (tid == 0) bulk_load(smem, row ? bufs.xa_base : bufs.xaT_base, row ? bytes_row : bytes_col, mbar);
-                if (row == 1 && R.reg == 1) dual_grad<DT>(C);  // reads xbar^k while the copy runs
+                if (row == (C.arow >= 0 ? C.arow : 1) && R.reg == 1) dual_grad<DT>(C);  // reads xbar^k while the copy runs
                 if (tid == 0) *s_cnt = BNW;
                 if (!mbar_wait(mbar, parity & 1u, T.wait_ns, T.err)) return false;
                 parity ^= 1u;
                 __syncthreads();
-                phase_a_branch<SOLO, DT>(C, T, row, reinterpret_cast<TS*>(smem) + kPad, row ? C.lda : C.ldaT,
+                phase_a_branch<SOLO, DT>(C, TA, row, reinterpret_cast<TS*>(smem) + kPad, row ? C.lda : C.ldaT,
                                          A_SOLVE, s_cnt, smem + img_floats, dyn_smem_floats() - img_floats);
                 __syncthreads();
             }
         } else if (C.stage == 1) {
             if (R.reg == 1) dual_grad<DT>(C);
-            for (int row = 1; row >= 0; --row)
-                if (!phase_a_banded<SOLO, DT>(C, T, row, row ? bufs.xa_base : bufs.xaT_base, row ? C.lda : C.ldaT,
+            for (int row = 1; row >= 0; --row) {
+                if (C.arow >= 0 && row != C.arow) continue;
+                if (!phase_a_banded<SOLO, DT>(C, TA, row, row ? bufs.xa_base : bufs.xaT_base, row ? C.lda : C.ldaT,
                                               smem, mbar, parity))
                     return false;
+            }
         } else {
             if (R.reg == 1) dual_grad<DT>(C);
             phase_a_global<SOLO, DT>(C, T, A_SOLVE, s_cnt, smem);
