@@ -252,9 +252,21 @@ roi_status roi_recon_solve_tiled(roi_recon_t h, int tile, int margin, const roi_
  *  2. Disc subtraction (Sec. 3.3): p_d = p - g W D, D the disc of diameter N on the axis,
  *     g minimising the squared norm of the per-angle sums of p_d.
  *  3. The filtered sinograms C_{u_k} p_d for every k (4 n_iters N_theta N_d bytes), reused
- *     by every region of this sinogram.
+ *     by every region of this sinogram; computed as in roi_recon_filter_conv (the filters
+ *     packed for the tensor cores once per filter set: 32 n' N_theta 8 ceil((2 N_d - 1)/8)
+ *     bytes, n' = n_iters rounded up to 16).  ROI_ETIMEOUT if a device wait gave up.
  * ROI_ESTATE before set_sinogram, ROI_EINVAL for n_iters < 1 or > 100000. */
 roi_status roi_recon_filter_prepare(roi_recon_t h, int n_iters);
+
+/* The filtered sinograms of Sec. 3.1 (Eq. sirtapp: iteration k of Alg. method filters the
+ * sinogram with u_k) as one operator on caller data:
+ *     out[k][a][d] = sum_{e < n_det} u[k][a][d - e + n_det - 1] p[a][e],  k < n,
+ * u device [n][n_angles][2 n_det - 1], p device [n_angles][n_det], out device
+ * [n][n_angles][n_det], float32, caller-owned (out must not overlap u or p).  Path as
+ * ROI_OPT_FILTER_CONV says; the tensor-core path packs u into handle scratch first (see
+ * filter_prepare for its size).  Synchronizes.  ROI_EINVAL for n < 1 or a NULL pointer,
+ * ROI_ETIMEOUT if a device wait gave up. */
+roi_status roi_recon_filter_conv(roi_recon_t h, int n, const float* u, const float* p, float* out);
 
 /* After filter_prepare: the filters into device u_out [k][n_angles][2 n_det - 1] float32
  * (the first k = min(n_filters, prepared) of them; NULL to skip) and the disc grey value
@@ -318,7 +330,13 @@ typedef enum {
      * 1 = 8 x 8 (runs of 2), 2 = 16 x 8 (runs of 4).  The shape changes how a pixel's
      * angles are grouped into partial sums, so results of different shapes agree to
      * rounding, not bit for bit; with one shape they are bit-identical wherever solved. */
-    ROI_OPT_TILE_SHAPE = 3
+    ROI_OPT_TILE_SHAPE = 3,
+    /* path of the filtered sinograms (filter_prepare step 3, roi_recon_filter_conv):
+     * 0 (default) the tensor cores (tcgen05 kind::tf32, each operand split into a tf32 head
+     * and remainder, three products accumulated in fp32 in tensor memory) whenever a
+     * detector row's expansion fits in shared memory (n_det up to about 2600), else the
+     * FMA pipe; 1: the FMA pipe (fp32 direct sums).  The two agree to float rounding. */
+    ROI_OPT_FILTER_CONV = 4
 } roi_option;
 
 roi_status roi_recon_set_option(roi_recon_t h, roi_option opt, long long value);
@@ -353,7 +371,7 @@ roi_status roi_recon_sync(roi_recon_t h);
  * checks have found since the last call -- image columns of ray samples and staged bins of
  * gathered pixels, each replaced by an in-range index when found -- with the first one's
  * site (1-2 single-launch solver, 3-5 whole-region solver, 6-7 one-launch-per-operator
- * projectors) and value in *site / *index (either may be NULL); the reports are cleared.
+ * projectors, 8 tensor-core filtered sinograms) and value in *site / *index (either may be NULL); the reports are cleared.
  * Waits for the device.  The product build has no checks and returns 0. */
 int roi_recon_check_report(int* site, int* index);
 
@@ -363,14 +381,17 @@ int roi_recon_check_report(int* site, int* index);
 
 /* Kernel timing for profiling.  enable = 1 starts recording CUDA events around every
  * launch of the projector kernels and of the single-launch solver made by
- * roi_recon_solve_local (and clears earlier records); enable = 0 stops.  Recording adds host work per launch, so
+ * roi_recon_solve_local, of the batched solver, and of the filtered-sinogram kernel (and
+ * clears earlier records); enable = 0 stops.  Recording adds host work per launch, so
  * time whole steps with it off. */
 roi_status roi_recon_set_timing(roi_recon_t h, int enable);
 
 /* Launch count and summed device time (milliseconds, from the recorded events) of
  * kernel class `kernel` since timing was enabled: 0 = forward projector W_L
  * (ray-driven, fused dual/residual update), 1 = backprojector W_L^T (pixel gather,
- * fused primal update), 2 = single-launch solve (all iterations of one solve).
+ * fused primal update), 2 = single-launch solve (all iterations of one solve) or batched
+ * solve (one launch), 3 = filtered sinograms (filter_prepare step 3, roi_recon_filter_conv;
+ * the packing of the filter bank excluded).
  * Synchronizes the handle's stream. */
 roi_status roi_recon_kernel_times(roi_recon_t h, int kernel, int* launches, double* total_ms);
 

@@ -39,13 +39,13 @@ __all__ = [
     "roi_server_drain", "roi_server_stats_get", "roi_server_last_error", "roi_server_footprint",
     "roi_server_cancel", "roi_server_set_option", "roi_recon_test_fail_alloc",
     "ROI_OPT_TILE_SHAPE", "TILE_SHAPES", "roi_recon_autotune", "roi_recon_set_tile_shapes",
-    "roi_recon_get_tile_shapes",
+    "roi_recon_get_tile_shapes", "ROI_OPT_FILTER_CONV", "roi_recon_filter_conv",
 ]
 
 ROI_OK, ROI_EINVAL, ROI_ENOMEM, ROI_ESTATE, ROI_ECUDA, ROI_ETIMEOUT, ROI_EBUSY, ROI_ECANCELED = range(8)
 ROI_F32, ROI_BF16, ROI_F16 = range(3)
 ROI_SIRT_NONNEG, ROI_TV_CP, ROI_FILTER_SIRT, ROI_FILTER_TV, ROI_FILTER_ISTA = range(5)
-ROI_OPT_SINGLE_LAUNCH, ROI_OPT_WAIT_LIMIT_US, ROI_OPT_TEST_ABSENT_BLOCKS, ROI_OPT_TILE_SHAPE = range(4)
+ROI_OPT_SINGLE_LAUNCH, ROI_OPT_WAIT_LIMIT_US, ROI_OPT_TEST_ABSENT_BLOCKS, ROI_OPT_TILE_SHAPE, ROI_OPT_FILTER_CONV = range(5)
 TILE_SHAPES = {0: (16, 16), 1: (8, 8), 2: (16, 8)}   # phase B tile shape: (x, y) pixels per warp
 
 _STATUS = {0: "ROI_OK", 1: "ROI_EINVAL", 2: "ROI_ENOMEM", 3: "ROI_ESTATE", 4: "ROI_ECUDA",
@@ -110,7 +110,7 @@ EXPORTS = [
     "roi_recon_filter_prepare", "roi_recon_filter_get", "roi_recon_set_sinogram_truncated",
     "roi_recon_solve_tiled", "roi_recon_state_size", "roi_recon_state_export", "roi_recon_solve_local_resume",
     "roi_recon_check_report", "roi_server_cancel", "roi_server_set_option", "roi_recon_test_fail_alloc",
-    "roi_recon_autotune", "roi_recon_set_tile_shapes", "roi_recon_get_tile_shapes",
+    "roi_recon_autotune", "roi_recon_set_tile_shapes", "roi_recon_get_tile_shapes", "roi_recon_filter_conv",
 ]
 
 _lib = None
@@ -187,6 +187,8 @@ def lib() -> ctypes.CDLL:
             L.roi_recon_filter_prepare.restype = st
             L.roi_recon_filter_get.argtypes = [_H, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_double)]
             L.roi_recon_filter_get.restype = st
+            L.roi_recon_filter_conv.argtypes = [_H, ctypes.c_int, _P, _P, _P]
+            L.roi_recon_filter_conv.restype = st
             L.roi_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(_H)]
             L.roi_server_create.restype = st
             L.roi_server_add_sinogram.argtypes = [_H, _H, ctypes.POINTER(ctypes.c_int)]
@@ -359,6 +361,10 @@ def roi_recon_filter_get(h, n_filters: int, u_out: int | None):
     g = ctypes.c_double(0.0)
     s = lib().roi_recon_filter_get(h, int(n_filters), u_out or None, ctypes.byref(g))
     return s, g.value
+
+
+def roi_recon_filter_conv(h, n: int, u: int, p: int, out: int) -> int:
+    return lib().roi_recon_filter_conv(h, int(n), u, p, out)
 
 
 def roi_server_create(cfg: ServerConfig | None):
@@ -712,6 +718,18 @@ class RoiRecon:
         s, g = roi_recon_filter_get(self.h, n_filters, u.data_ptr())
         self._check(s)
         return u, g
+
+    def filter_conv(self, u, p, out=None):
+        """out[k][a][d] = sum_e u[k][a][d - e + n_det - 1] p[a][e] (roi_recon_filter_conv):
+        u CUDA float32 [n][n_angles][2 n_det - 1], p [n_angles][n_det]; returns out [n][n_angles][n_det]."""
+        n = int(u.shape[0])
+        # u and p stay referenced here until the call returns (their memory must not be reused for out)
+        u_ptr = self._dev(u, (n, self.n_angles, 2 * self.n_det - 1))
+        p_ptr = self._dev(p, (self.n_angles, self.n_det))
+        if out is None:
+            out = self._torch.empty((n, self.n_angles, self.n_det), dtype=self._torch.float32, device="cuda")
+        self._check(roi_recon_filter_conv(self.h, n, u_ptr, p_ptr, self._dev(out, (n, self.n_angles, self.n_det))))
+        return out
 
     def set_option(self, opt: int, value: int):
         self._check(roi_recon_set_option(self.h, opt, value))

@@ -160,7 +160,7 @@ struct roi_recon {
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spans[3];
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spans[4];
     // single-launch solver: barrier words, device error flag, options
     unsigned* d_bar = nullptr;
     int* d_err = nullptr;
@@ -170,6 +170,7 @@ struct roi_recon {
     int tile_shape[roi::kShapeClasses] = {0, 0, 0};  // per box-size class (roi_recon_autotune)
     unsigned long long opt_wait_ns = 1000000000ull;
     int opt_phantoms = 0;
+    int opt_filter_fma = 0;               // 1: filtered sinograms on the FMA pipe (not the tensor cores)
     size_t max_smem_optin = 0;
     int sms = 0;
     // batched solves: per-region tables / windows / descriptors, per-block slots, pinned staging
@@ -193,6 +194,9 @@ struct roi_recon {
     int fcp_n = 0;                  // filtered sinograms C_{u_k} p_d, k = 1..fcp_n, in filt_cp
     DevBuf filt_cp;                 // [fcp_n][na][nd]
     DevBuf filt_pd;                 // disc-subtracted sinogram [na][nd]
+    DevBuf filt_ug;                 // filt_u packed for the tensor cores (filt_ug_n filters)
+    int filt_ug_n = 0;
+    DevBuf op_ug;                   // scratch of roi_recon_filter_conv
     double disc_g = 0.0;
     unsigned char* pin = nullptr;  // page-locked staging of the uploads
     size_t pin_cap = 0;
@@ -757,6 +761,40 @@ roi_status filter_compute(roi_recon* h, int n) {
     for (DevBuf* b : {&c, &cT, &hc, &wc, &g}) b->release();
     hq.release();
     h->filt_n = n;
+    h->filt_ug_n = 0;  // the packed bank is of the previous filters
+    return ROI_OK;
+}
+
+// C_{u_k} p for k < n (u: [>= n][na][2 nd - 1], p: [na][nd], out: [n][na][nd]): on the
+// tensor cores when the detector row fits in shared memory (the bank packed first unless
+// `packed` already holds these n filters), else on the FMA pipe.  Synchronizes and reports
+// a device wait that ran out.
+roi_status filter_conv(roi_recon* h, int n, const float* u, const float* p, float* out, DevBuf* packed,
+                       int* packed_n) {
+    const int na = h->na, nd = h->nd;
+    if (!h->opt_filter_fma && roi::filter_conv_tc_fits(n, nd)) {
+        if (*packed_n != n) {
+            *packed_n = 0;
+            CU(h, packed->ensure(roi::filter_pack_tc_floats(n, na, nd)));
+            roi::launch_filter_pack_tc(u, packed->p, n, na, nd, h->st);
+            LAUNCHED(h, "filter bank packing");
+            *packed_n = n;
+        }
+        Span sp(h, 3);
+        CU(h, roi::launch_filter_conv_tc(packed->p, p, out, n, na, nd, std::max(1, h->sms), h->d_err, h->opt_wait_ns,
+                                         h->st));
+    } else {
+        Span sp(h, 3);
+        roi::launch_filter_conv(u, p, out, n, na, nd, h->st);
+    }
+    LAUNCHED(h, "filtered sinograms");
+    CU(h, cudaStreamSynchronize(h->st));
+    int flag = 0;
+    CU(h, cudaMemcpy(&flag, h->d_err, sizeof flag, cudaMemcpyDeviceToHost));
+    if (flag) {
+        CU(h, cudaMemset(h->d_err, 0, sizeof(int)));
+        return fail(h, ROI_ETIMEOUT, "filtered sinograms: a device-side wait gave up; the result is invalid");
+    }
     return ROI_OK;
 }
 
@@ -802,9 +840,8 @@ roi_status filter_sinogram(roi_recon* h, int n) {
     h->disc_g = den > 0.0 ? num / den : 0.0;
     roi::launch_disc_subtract(h->p, h->pdt, wd.p, (float)h->disc_g, h->filt_pd.p, ns, h->st);
     CU(h, h->filt_cp.ensure((size_t)n * ns));
-    roi::launch_filter_conv(h->filt_u.p, h->filt_pd.p, h->filt_cp.p, n, na, nd, h->st);
-    LAUNCHED(h, "filtered sinograms");
-    CU(h, cudaStreamSynchronize(h->st));
+    const roi_status s = filter_conv(h, n, h->filt_u.p, h->filt_pd.p, h->filt_cp.p, &h->filt_ug, &h->filt_ug_n);
+    if (s != ROI_OK) return s;
     D.release();
     DT.release();
     wd.release();
@@ -967,7 +1004,7 @@ void roi_recon_destroy(roi_recon_t h) {
         if (b) cudaFree(b);
     h->fbp32.release();
     h->in_tmp.release();
-    for (DevBuf* b : {&h->filt_u, &h->filt_cp, &h->filt_pd}) b->release();
+    for (DevBuf* b : {&h->filt_u, &h->filt_cp, &h->filt_pd, &h->filt_ug, &h->op_ug}) b->release();
     if (h->rec_filt) cudaFree(h->rec_filt);
     for (AngleRec* b : {h->rec_fbp, h->rec_loc, h->rec_ext})
         if (b) cudaFree(b);
@@ -1409,6 +1446,14 @@ roi_status roi_recon_filter_prepare(roi_recon_t h, int n_iters) {
     return ROI_OK;
 }
 
+roi_status roi_recon_filter_conv(roi_recon_t h, int n, const float* u, const float* p, float* out) {
+    if (!h) return ROI_EINVAL;
+    h->err.clear();
+    if (n < 1 || n > 100000 || !u || !p || !out) return fail(h, ROI_EINVAL, "filter_conv: bad arguments");
+    int packed = -1;  // the caller's filters: always packed afresh
+    return filter_conv(h, n, u, p, out, &h->op_ug, &packed);
+}
+
 roi_status roi_recon_filter_get(roi_recon_t h, int n_filters, float* u_out, double* disc_grey) {
     if (!h) return ROI_EINVAL;
     h->err.clear();
@@ -1819,20 +1864,25 @@ roi_status roi_recon_set_option(roi_recon_t h, roi_option opt, long long value) 
             if (value < -1 || value >= roi::kTileShapes) return fail(h, ROI_EINVAL, "set_option: unknown tile shape");
             h->opt_tile_shape = (int)value;
             return ROI_OK;
+        case ROI_OPT_FILTER_CONV:
+            if (value < 0 || value > 1) return fail(h, ROI_EINVAL, "set_option: filter convolution path is 0 or 1");
+            h->opt_filter_fma = (int)value;
+            return ROI_OK;
     }
     return fail(h, ROI_EINVAL, "set_option: unknown option %d", (int)opt);
 }
 
 int roi_recon_check_report(int* site, int* index) {
     cudaDeviceSynchronize();
-    roi::CheckReport reps[5];
+    roi::CheckReport reps[6];
     roi::check_take_persist(&reps[0]);
     roi::check_take_batch(&reps[1]);
     roi::check_take_batch_team(&reps[2]);
     roi::check_take_serve(&reps[3]);
     roi::check_take_project(&reps[4]);
+    roi::check_take_filterconv_tc(&reps[5]);
     int total = 0, first = -1;
-    for (int i = 0; i < 5; ++i) {
+    for (int i = 0; i < 6; ++i) {
         if (reps[i].count > 0 && first < 0) first = i;
         total += reps[i].count;
     }
@@ -1855,7 +1905,7 @@ roi_status roi_recon_sync(roi_recon_t h) {
 }
 
 roi_status roi_recon_kernel_times(roi_recon_t h, int kernel, int* launches, double* total_ms) {
-    if (!h || kernel < 0 || kernel > 2 || !launches || !total_ms) return ROI_EINVAL;
+    if (!h || kernel < 0 || kernel > 3 || !launches || !total_ms) return ROI_EINVAL;
     h->err.clear();
     CU(h, cudaStreamSynchronize(h->st));
     double ms = 0.0;

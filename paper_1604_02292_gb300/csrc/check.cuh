@@ -48,7 +48,8 @@ enum CheckSite {
     CHK_REGION_BAND = 4,     // whole-region solver: image column of a banded sample
     CHK_REGION_GATHER = 5,   // whole-region solver: staged bin of a gathered pixel
     CHK_FORWARD = 6,         // k_forward: image column of a ray sample (global memory)
-    CHK_BACK = 7             // k_back: staged bin of a gathered pixel
+    CHK_BACK = 7,            // k_back: staged bin of a gathered pixel
+    CHK_FILTER_TC = 8        // k_filter_conv_tc: first row of a sinogram tile's descriptor
 };
 
 }  // namespace roi

@@ -267,6 +267,15 @@ void launch_filter_accum(const float* hc, double* hq, float* uk, int na, int nd,
                          cudaStream_t st);
 void launch_axpy_padded(float* c, float* cT, int ld, const float* g, float alpha, int N, cudaStream_t st);
 void launch_filter_conv(const float* u, const float* pd, float* Cp, int n, int na, int nd, cudaStream_t st);
+// The same on the tensor cores (filterconv_tc.cu): the filter bank packed once into its
+// tf32 head/remainder core-matrix layout (filter_pack_tc_floats floats), then one launch of
+// at most `sms` blocks.  filter_conv_tc_fits: the sinogram row's expansion and two stages
+// fit in shared memory (N_d up to about 2600).  A device wait that runs out sets *err.
+bool filter_conv_tc_fits(int n, int nd);
+size_t filter_pack_tc_floats(int n, int na, int nd);
+void launch_filter_pack_tc(const float* u, float* ug, int n, int na, int nd, cudaStream_t st);
+cudaError_t launch_filter_conv_tc(const float* ug, const float* pd, float* Cp, int n, int na, int nd, int sms,
+                                  int* err, unsigned long long wait_ns, cudaStream_t st);
 void launch_window_gather(const float* Cp_k, int nd, const AngleRec* rec, int na, int stride, float* win,
                           cudaStream_t st);
 void launch_filter_update(const float* xs, const float* g, float* y, float* x, const float* shift, float lo, float hi,
@@ -497,5 +506,6 @@ void check_take_batch(CheckReport* out);
 void check_take_batch_team(CheckReport* out);
 void check_take_serve(CheckReport* out);
 void check_take_project(CheckReport* out);
+void check_take_filterconv_tc(CheckReport* out);
 
 }  // namespace roi

@@ -1,7 +1,8 @@
 """The check build (the library compiled with -DROI_CHECK: index checks on every ray-sample
 column and every staged gather bin of the hot kernels) over the paths the parity tests
 cover: single-launch SIRT and CP solves, one launch per operator, batches solved by single
-blocks and by teams with whole-staged and band-streamed images, and served requests.  No
+blocks and by teams with whole-staged and band-streamed images, served requests, and the
+filtered sinograms on the tensor cores (first rows of the sinogram tiles).  No
 index may leave its range, and every result equals the product build's bit for bit (the
 checks only read the indices)."""
 import hashlib
@@ -54,6 +55,10 @@ outs, _ = big.solve_batch(many + regions, [dict(reg=R.ROI_TV_CP, iters=3, lam=0.
 for k, o in enumerate(outs):
     res[f"single{k}"] = o
 big.sync()
+rng = np.random.default_rng(9)
+fu = torch.from_numpy(rng.standard_normal((40, NA, 2 * ND - 1)).astype(np.float32)).cuda()
+fp = torch.from_numpy(rng.standard_normal((NA, ND)).astype(np.float32)).cuda()
+res["filter_conv"] = big.filter_conv(fu, fp)  # tensor cores (Toeplitz tiles of the sinogram rows)
 with R.Server(team_blocks=8, teams=4, large_side=200) as s:
     s.add(big)
     ids = {s.submit(0, r, prm): k for k, (r, prm) in enumerate(zip(regions, params))}
