@@ -39,7 +39,6 @@ constexpr int TC_THREADS = 192;  // warps 0-3: epilogue (TMEM lanes 0-127); 4: b
 constexpr int TC_M = 128;        // output bins per tile
 constexpr int TC_TILES = 2;      // tiles per work item, at TMEM columns 0 and 256
 constexpr int TC_COLS = 512;     // TMEM columns allocated
-constexpr int TC_S = 2;          // tap groups per stage
 constexpr int TC_YPAD = 128;     // zero rows of Y below s = 0
 constexpr int TC_MAX_STAGES = 6;
 constexpr int TC_NB_MAX = 256;   // filters per block (N of one MMA)
@@ -52,6 +51,7 @@ struct TcGeom {
     int t1n;       // tap groups of 8 (the last one zero-padded past 2 N_d - 1)
     int yr;        // rows of Y
     int passes;    // work items per (angle, filter block): 256 output bins each
+    int S;         // tap groups per stage: 4 where two such stages fit, else 2
     int stages;
     size_t smem;
 };
@@ -66,10 +66,14 @@ TcGeom tc_geom(int n, int nd) {
     g.yr = round_up(nd + 262, 8);
     g.passes = (nd + TC_TILES * TC_M - 1) / (TC_TILES * TC_M);
     const size_t ybytes = (size_t)64 * g.yr;
-    const size_t stage = (size_t)4 * TC_S * g.nb * 16;
     const size_t room = TC_SMEM_MAX > ybytes + TC_SMEM_RESERVE ? TC_SMEM_MAX - ybytes - TC_SMEM_RESERVE : 0;
-    g.stages = (int)std::min<size_t>(TC_MAX_STAGES, room / stage);
-    g.smem = ybytes + (size_t)g.stages * stage + TC_SMEM_RESERVE;
+    for (const int S : {4, 2}) {  // fewer, longer stages cost fewer barrier round trips
+        const size_t stage = (size_t)4 * S * g.nb * 16;
+        g.S = S;
+        g.stages = (int)std::min<size_t>(TC_MAX_STAGES, room / stage);
+        g.smem = ybytes + (size_t)g.stages * stage + TC_SMEM_RESERVE;
+        if (g.stages >= 2) break;
+    }
     return g;
 }
 
@@ -158,8 +162,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_filter_conv_tc(TcArgs A) {
     float* Y = reinterpret_cast<float*>(base);
     const unsigned y_addr = smem_addr(base);
     const unsigned y_plane = (unsigned)g.yr * 16;
-    const unsigned stage_bytes = 4u * TC_S * g.nb * 16;
-    const unsigned stage_plane = (unsigned)TC_S * g.nb * 16;
+    const int S = g.S;
+    const unsigned stage_bytes = 4u * S * g.nb * 16;
+    const unsigned stage_plane = (unsigned)S * g.nb * 16;
     const unsigned st_addr = y_addr + 4 * y_plane;
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
@@ -203,7 +208,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_filter_conv_tc(TcArgs A) {
                 t1b = max(t1b, hi[q]);
             }
         }
-        const int nchunks = (t1b - t1a + TC_S) / TC_S;
+        const int nchunks = (t1b - t1a + S) / S;
         // ---- Y[plane = 2 hl + h][y][c] = head (hl = 0) / remainder (hl = 1) of p[y - 128 - 4h - c]
         const float* prow = A.pd + (size_t)a * nd;
         for (int idx = tid; idx < 2 * g.yr; idx += TC_THREADS) {
@@ -226,7 +231,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_filter_conv_tc(TcArgs A) {
         __syncthreads();
         tc_fence_after();
         if (warp == 4) {
-            if (lane == 0) {  // ---- bulk copies of the filter bank, tap groups t1a.., TC_S per stage
+            if (lane == 0) {  // ---- bulk copies of the filter bank, tap groups t1a.., S per stage
                 const float* ub = A.ug + (size_t)(a * g.kb_count + kb) * 4 * g.t1n * g.nb * 4;
                 for (int c = 0; c < nchunks; ++c, ++gc) {
                     const int s = gc % NS;
@@ -234,8 +239,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_filter_conv_tc(TcArgs A) {
                         s_abort = 1;
                         break;
                     }
-                    const int t1c = t1a + c * TC_S;
-                    const int steps = min(TC_S, t1b + 1 - t1c);
+                    const int t1c = t1a + c * S;
+                    const int steps = min(S, t1b + 1 - t1c);
                     const unsigned piece = (unsigned)steps * g.nb * 16;
                     mbar_expect(&full[s], 4 * piece);
                     for (int pl = 0; pl < 4; ++pl)
@@ -256,8 +261,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_filter_conv_tc(TcArgs A) {
                     }
                     tc_fence_after();
                     const unsigned sb = st_addr + s * stage_bytes;
-                    for (int j = 0; j < TC_S; ++j) {
-                        const int t1 = t1a + c * TC_S + j;
+                    for (int j = 0; j < S; ++j) {
+                        const int t1 = t1a + c * S + j;
                         if (t1 > t1b) break;
                         const unsigned b_hi = sb + j * g.nb * 16, b_lo = b_hi + 2 * stage_plane;
                         const uint64_t dbh = kmajor_desc(b_hi, stage_plane), dbl = kmajor_desc(b_lo, stage_plane);
