@@ -321,7 +321,9 @@ typedef enum {
      * single-launch solves, batched solves run by teams (few regions), large boxes of
      * solve_local, and (roi_server_set_option) requests solved by a team of a server.  For
      * a server, -1 keeps the team leaders away instead, so that the members' waits for
-     * the leader's claim (the team mailbox) run out. */
+     * the leader's claim (the team mailbox) run out.  On a handle, > 0 also makes the
+     * tensor-core filtered sinograms (filter_prepare, roi_recon_filter_conv) wait for
+     * filter-bank bytes that never arrive: the call returns ROI_ETIMEOUT. */
     ROI_OPT_TEST_ABSENT_BLOCKS = 2,
     /* -1 (default): the phase B tile shape of each whole-region solve (solve_batch, large
      * boxes of solve_local, and requests served from this handle's sinogram) is taken from
@@ -334,8 +336,9 @@ typedef enum {
     /* path of the filtered sinograms (filter_prepare step 3, roi_recon_filter_conv):
      * 0 (default) the tensor cores (tcgen05 kind::tf32, each operand split into a tf32 head
      * and remainder, three products accumulated in fp32 in tensor memory) whenever a
-     * detector row's expansion fits in shared memory (n_det up to about 2600), else the
-     * FMA pipe; 1: the FMA pipe (fp32 direct sums).  The two agree to float rounding. */
+     * detector row's expansion fits in shared memory (n_det up to about 2500 with 200
+     * filters), else the FMA pipe; 1: the FMA pipe (fp32 direct sums).  The two agree to
+     * float rounding. */
     ROI_OPT_FILTER_CONV = 4
 } roi_option;
 

@@ -782,7 +782,7 @@ roi_status filter_conv(roi_recon* h, int n, const float* u, const float* p, floa
         }
         Span sp(h, 3);
         CU(h, roi::launch_filter_conv_tc(packed->p, p, out, n, na, nd, std::max(1, h->sms), h->d_err, h->opt_wait_ns,
-                                         h->st));
+                                         h->opt_phantoms > 0 ? 16u : 0u, h->st));
     } else {
         Span sp(h, 3);
         roi::launch_filter_conv(u, p, out, n, na, nd, h->st);

@@ -85,6 +85,7 @@ struct TcArgs {
     TcGeom g;
     int* err;
     unsigned long long wait_ns;
+    unsigned test_extra_tx;  // testing only: bytes each stage waits for beyond those copied
 };
 
 __device__ __forceinline__ float tf32_head(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
@@ -242,7 +243,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_filter_conv_tc(TcArgs A) {
                     const int t1c = t1a + c * S;
                     const int steps = min(S, t1b + 1 - t1c);
                     const unsigned piece = (unsigned)steps * g.nb * 16;
-                    mbar_expect(&full[s], 4 * piece);
+                    mbar_expect(&full[s], 4 * piece + A.test_extra_tx);
                     for (int pl = 0; pl < 4; ++pl)
                         bulk_copy_tx(st_addr + s * stage_bytes + pl * stage_plane,
                                      ub + ((size_t)pl * g.t1n + t1c) * g.nb * 4, piece, &full[s]);
@@ -380,7 +381,7 @@ void launch_filter_pack_tc(const float* u, float* ug, int n, int na, int nd, cud
 }
 
 cudaError_t launch_filter_conv_tc(const float* ug, const float* pd, float* Cp, int n, int na, int nd, int sms,
-                                  int* err, unsigned long long wait_ns, cudaStream_t st) {
+                                  int* err, unsigned long long wait_ns, unsigned test_extra_tx, cudaStream_t st) {
     TcArgs A{};
     A.ug = ug;
     A.pd = pd;
@@ -391,6 +392,7 @@ cudaError_t launch_filter_conv_tc(const float* ug, const float* pd, float* Cp, i
     A.g = tc_geom(n, nd);
     A.err = err;
     A.wait_ns = wait_ns;
+    A.test_extra_tx = test_extra_tx;
     if (A.g.stages < 2) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_filter_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)A.g.smem);
     if (e != cudaSuccess) return e;

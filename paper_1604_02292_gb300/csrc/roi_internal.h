@@ -270,12 +270,14 @@ void launch_filter_conv(const float* u, const float* pd, float* Cp, int n, int n
 // The same on the tensor cores (filterconv_tc.cu): the filter bank packed once into its
 // tf32 head/remainder core-matrix layout (filter_pack_tc_floats floats), then one launch of
 // at most `sms` blocks.  filter_conv_tc_fits: the sinogram row's expansion and two stages
-// fit in shared memory (N_d up to about 2600).  A device wait that runs out sets *err.
+// fit in shared memory (N_d up to about 2500 with 200 filters).  A device wait that runs out sets *err;
+// test_extra_tx > 0 (testing only) makes every stage wait for that many bytes more than
+// are copied, so the waits run out.
 bool filter_conv_tc_fits(int n, int nd);
 size_t filter_pack_tc_floats(int n, int na, int nd);
 void launch_filter_pack_tc(const float* u, float* ug, int n, int na, int nd, cudaStream_t st);
 cudaError_t launch_filter_conv_tc(const float* ug, const float* pd, float* Cp, int n, int na, int nd, int sms,
-                                  int* err, unsigned long long wait_ns, cudaStream_t st);
+                                  int* err, unsigned long long wait_ns, unsigned test_extra_tx, cudaStream_t st);
 void launch_window_gather(const float* Cp_k, int nd, const AngleRec* rec, int na, int stride, float* win,
                           cudaStream_t st);
 void launch_filter_update(const float* xs, const float* g, float* y, float* x, const float* shift, float lo, float hi,

@@ -118,3 +118,26 @@ def test_filter_conv_rejects_bad_arguments():
     assert R.roi_recon_filter_conv(rr.h, 2, 0, 1, 1) == R.ROI_EINVAL
     assert R.roi_recon_set_option(rr.h, R.ROI_OPT_FILTER_CONV, 2) == R.ROI_EINVAL
     rr.close()
+
+
+def test_tensor_core_waits_run_out_and_the_handle_recovers():
+    """Failure detection without a fault: with ROI_OPT_TEST_ABSENT_BLOCKS the stage barriers
+    wait for 16 bytes that no copy delivers, the bounded waits (20 ms here) run out, the call
+    returns ROI_ETIMEOUT, and the same handle then computes the right result."""
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need CUDA")
+    na, nd, n = 4, 257, 40
+    u, p = _case(na, nd, n, seed=5)
+    exp, bound = _oracle(na, nd, u, p)
+    rr = R.RoiRecon(nd, na, nd)
+    ud, pd = torch.from_numpy(u).cuda(), torch.from_numpy(p).cuda()
+    out = torch.empty((n, na, nd), dtype=torch.float32, device="cuda")
+    rr.set_option(R.ROI_OPT_WAIT_LIMIT_US, 20000)
+    rr.set_option(R.ROI_OPT_TEST_ABSENT_BLOCKS, 1)
+    st = R.roi_recon_filter_conv(rr.h, n, ud.data_ptr(), pd.data_ptr(), out.data_ptr())
+    assert st == R.ROI_ETIMEOUT, st
+    rr.set_option(R.ROI_OPT_TEST_ABSENT_BLOCKS, 0)
+    got = rr.filter_conv(ud, pd)
+    torch.cuda.synchronize()
+    _check(got.cpu().numpy().astype(np.float64), exp, bound, nd)
+    rr.close()
