@@ -141,3 +141,24 @@ def test_tensor_core_waits_run_out_and_the_handle_recovers():
     torch.cuda.synchronize()
     _check(got.cpu().numpy().astype(np.float64), exp, bound, nd)
     rr.close()
+
+
+def test_full_size_filter_workload_sampled_filters():
+    """The 1024 filter workload's full launch (256 angles, 1024 bins, 200 filters: 152 blocks,
+    four tap groups per stage, two stages) on seeded random filters and rows; the oracle
+    computes four of the 200 filtered sinograms whole (first, last and two inside)."""
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need CUDA")
+    na, nd, n = 256, 1024, 200
+    u, p = _case(na, nd, n, seed=2024)
+    rr = R.RoiRecon(1024, na, nd)
+    got = rr.filter_conv(torch.from_numpy(u).cuda(), torch.from_numpy(p).cuda())
+    torch.cuda.synchronize()
+    rr.close()
+    g = oracle.Geometry(1024, na, nd)
+    pd = p.astype(np.float64)
+    for k in (0, 57, 133, 199):
+        exp = oracle.filter_conv(g, u[k].astype(np.float64), pd)
+        bound = oracle.filter_conv(g, np.abs(u[k]).astype(np.float64), np.abs(pd))
+        worst, rel = _check(got[k].cpu().numpy().astype(np.float64)[None], exp[None], bound[None], nd)
+        print(f"filter_conv full size, filter {k}: max err / sum|u||p| {worst:.2e}, rel L2 {rel:.2e}")
