@@ -490,22 +490,33 @@ __device__ __forceinline__ void phase_b_s(const Ctx& C, const Team& T, int pass,
         // partials in chunk order.
         float* part = wstage - warp * WARP_STAGE + BNW * WARP_STAGE;  // [group][nchunks][TP]
         const int G = min(my_tiles, room / per_tile);
+        // the window bins of a warp's next item are copied while it gathers the current one
+        auto stage_item = [&](int g0, int item, int b) {
+            const int gt = item / nchunks, c = item - gt * nchunks;
+            const int t = tm + (g0 + gt) * ts;
+            const int tile_x0 = (t % tiles_x) * TX, tile_y0 = (t / tiles_x) * TY;
+            const float xi_t = (float)tile_x0 + 0.5f * (TX - 1) - 0.5f * (float)(nx - 1);
+            const float eta_t = 0.5f * (float)(ny - 1) - ((float)tile_y0 + 0.5f * (TY - 1));
+            stage(xi_t, eta_t, c * ACH, b);
+        };
         for (int g0 = 0; g0 < my_tiles; g0 += G) {
-            const int gn = min(G, my_tiles - g0);
-            for (int item = warp; item < gn * nchunks; item += BNW) {
-                const int gt = item / nchunks, c = item - gt * nchunks;
-                const int t = tm + (g0 + gt) * ts;
-                const int tile_x0 = (t % tiles_x) * TX, tile_y0 = (t / tiles_x) * TY;
-                const float xi_t = (float)tile_x0 + 0.5f * (TX - 1) - 0.5f * (float)(nx - 1);
-                const float eta_t = 0.5f * (float)(ny - 1) - ((float)tile_y0 + 0.5f * (TY - 1));
-                __syncwarp();  // this warp's buffer is free
-                stage(xi_t, eta_t, c * ACH, 0);
-                cp_async_wait_group<0>();
+            const int gn = min(G, my_tiles - g0), nitems = gn * nchunks;
+            __syncwarp();  // this warp's buffers are free
+            if (warp < nitems) stage_item(g0, warp, 0);
+            for (int item = warp, b = 0; item < nitems; item += BNW, b ^= 1) {
+                if (item + BNW < nitems) {
+                    stage_item(g0, item + BNW, b ^ 1);
+                    cp_async_wait_group<1>();  // this item's copies have landed
+                } else {
+                    cp_async_wait_group<0>();
+                }
                 __syncwarp();
+                const int gt = item / nchunks, c = item - gt * nchunks;
                 float acc[RUNB];
-                gather(c * ACH, 0, acc);
+                gather(c * ACH, b, acc);
 #pragma unroll
                 for (int p = 0; p < RUNB; ++p) part[(gt * nchunks + c) * TP + li * TX + lj0 + p] = acc[p];
+                __syncwarp();  // buffer b is refilled by the item after next
             }
             __syncthreads();
             for (int e = threadIdx.x; e < gn * TP; e += BPT) {  // one thread per pixel: the chunks in order
