@@ -738,7 +738,11 @@ def batch_measure(w, count, steps, warmup, dist, ws, rank, local, clock=True, tu
         tuning = {"shapes_per_class": [list(R.TILE_SHAPES[sh]) for sh in shapes],
                   "classes": ["box side <= 96", "97..216", "217..384"], "trial_ms": tms,
                   "autotune_s": time.perf_counter() - t0,
-                  "default_solves_per_s": len(all_items) * steps / (sum(default_ms) / 1e3)}
+                  "default_solves_per_s": len(all_items) * steps / (sum(default_ms) / 1e3),
+                  "team_caps_per_class": rr.team_caps, "team_cap_candidates": list(R.TEAM_CAPS),
+                  "team_trial_ms": rr.team_caps_ms(),
+                  "team_note": "team size of few-region batches (8 regions of the class); the 4096-region "
+                               "batch itself runs one block per region"}
     if dist:
         dist.barrier()
     n0 = R.roi_recon_launch_count()

@@ -350,7 +350,8 @@ roi_status roi_recon_set_option(roi_recon_t h, roi_option opt, long long value);
  * seeded regions of that class (0: two per SM; SIRT and CP-TV alternating, iters
  * iterations, 0: 20) on this handle's sinogram with each tile shape (a warm-up, then the
  * best of two timed runs, CUDA events on the handle's stream), and keeps the fastest shape
- * per class in the handle's tile table.  The table is also kept per geometry (grid,
+ * per class in the handle's tile table; then, per class, the team size of few-region
+ * batches (roi_recon_get_team_caps).  Both tables are also kept per geometry (grid,
  * angles, detector, image storage) for handles created later in the process.
  * shapes_out (optional, int[3]): the chosen shape per class; ms_out (optional,
  * double[3][3]): milliseconds per class and shape (0 for a class the grid cannot hold).
@@ -362,6 +363,18 @@ roi_status roi_recon_autotune(roi_recon_t h, int regions_per_class, int iters, i
  * sinogram's handle when the sinogram is added. */
 roi_status roi_recon_set_tile_shapes(roi_recon_t h, const int* shapes);
 roi_status roi_recon_get_tile_shapes(roi_recon_t h, int* shapes);
+
+/* The handle's team table (int[3], per box-size class as above): a batch of fewer regions
+ * than half the blocks solves each region on a team of up to caps[c] blocks, c the class of
+ * the batch's largest box (default 16; also bounded by the blocks per region).  A region's
+ * result is the same bits for every team size.  roi_recon_autotune also times, per class,
+ * a batch of 8 of its regions with caps 4, 8, 16 and 32 (with the class's chosen tile shape)
+ * and keeps the fastest; it is cached with the tile table.  set: ROI_EINVAL for a cap
+ * outside [1, 1024].  get: ms_out (optional, double[3][4]) receives the autotuner's
+ * milliseconds per class and candidate (0 before it ran or for a class the grid cannot
+ * hold). */
+roi_status roi_recon_set_team_caps(roi_recon_t h, const int* caps);
+roi_status roi_recon_get_team_caps(roi_recon_t h, int* caps, double* ms_out);
 
 /* Wait for all work on the handle's stream, then report device-side failures: ROI_ETIMEOUT
  * if a single-launch solve gave up at a grid barrier since the last report (its output is

@@ -39,7 +39,8 @@ __all__ = [
     "roi_server_drain", "roi_server_stats_get", "roi_server_last_error", "roi_server_footprint",
     "roi_server_cancel", "roi_server_set_option", "roi_recon_test_fail_alloc",
     "ROI_OPT_TILE_SHAPE", "TILE_SHAPES", "roi_recon_autotune", "roi_recon_set_tile_shapes",
-    "roi_recon_get_tile_shapes", "ROI_OPT_FILTER_CONV", "roi_recon_filter_conv",
+    "roi_recon_get_tile_shapes", "ROI_OPT_FILTER_CONV", "roi_recon_filter_conv", "roi_recon_set_team_caps",
+    "roi_recon_get_team_caps", "TEAM_CAPS",
 ]
 
 ROI_OK, ROI_EINVAL, ROI_ENOMEM, ROI_ESTATE, ROI_ECUDA, ROI_ETIMEOUT, ROI_EBUSY, ROI_ECANCELED = range(8)
@@ -47,6 +48,7 @@ ROI_F32, ROI_BF16, ROI_F16 = range(3)
 ROI_SIRT_NONNEG, ROI_TV_CP, ROI_FILTER_SIRT, ROI_FILTER_TV, ROI_FILTER_ISTA = range(5)
 ROI_OPT_SINGLE_LAUNCH, ROI_OPT_WAIT_LIMIT_US, ROI_OPT_TEST_ABSENT_BLOCKS, ROI_OPT_TILE_SHAPE, ROI_OPT_FILTER_CONV = range(5)
 TILE_SHAPES = {0: (16, 16), 1: (8, 8), 2: (16, 8)}   # phase B tile shape: (x, y) pixels per warp
+TEAM_CAPS = (4, 8, 16, 32)                             # team sizes the autotuner tries
 
 _STATUS = {0: "ROI_OK", 1: "ROI_EINVAL", 2: "ROI_ENOMEM", 3: "ROI_ESTATE", 4: "ROI_ECUDA",
            5: "ROI_ETIMEOUT", 6: "ROI_EBUSY", 7: "ROI_ECANCELED"}
@@ -111,6 +113,7 @@ EXPORTS = [
     "roi_recon_solve_tiled", "roi_recon_state_size", "roi_recon_state_export", "roi_recon_solve_local_resume",
     "roi_recon_check_report", "roi_server_cancel", "roi_server_set_option", "roi_recon_test_fail_alloc",
     "roi_recon_autotune", "roi_recon_set_tile_shapes", "roi_recon_get_tile_shapes", "roi_recon_filter_conv",
+    "roi_recon_set_team_caps", "roi_recon_get_team_caps",
 ]
 
 _lib = None
@@ -189,6 +192,10 @@ def lib() -> ctypes.CDLL:
             L.roi_recon_filter_get.restype = st
             L.roi_recon_filter_conv.argtypes = [_H, ctypes.c_int, _P, _P, _P]
             L.roi_recon_filter_conv.restype = st
+            L.roi_recon_set_team_caps.argtypes = [_H, ctypes.POINTER(ctypes.c_int)]
+            L.roi_recon_set_team_caps.restype = st
+            L.roi_recon_get_team_caps.argtypes = [_H, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+            L.roi_recon_get_team_caps.restype = st
             L.roi_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(_H)]
             L.roi_server_create.restype = st
             L.roi_server_add_sinogram.argtypes = [_H, _H, ctypes.POINTER(ctypes.c_int)]
@@ -361,6 +368,18 @@ def roi_recon_filter_get(h, n_filters: int, u_out: int | None):
     g = ctypes.c_double(0.0)
     s = lib().roi_recon_filter_get(h, int(n_filters), u_out or None, ctypes.byref(g))
     return s, g.value
+
+
+def roi_recon_set_team_caps(h, caps) -> int:
+    arr = (ctypes.c_int * 3)(*[int(c) for c in caps])
+    return lib().roi_recon_set_team_caps(h, arr)
+
+
+def roi_recon_get_team_caps(h):
+    caps = (ctypes.c_int * 3)()
+    ms = (ctypes.c_double * 12)()
+    s = lib().roi_recon_get_team_caps(h, caps, ms)
+    return s, list(caps), [list(ms[4 * c:4 * c + 4]) for c in range(3)]
 
 
 def roi_recon_filter_conv(h, n: int, u: int, p: int, out: int) -> int:
@@ -751,6 +770,23 @@ class RoiRecon:
     def tile_shapes(self, shapes):
         self._check(roi_recon_set_tile_shapes(self.h, shapes))
 
+    @property
+    def team_caps(self):
+        """Largest team per region of a few-region batch, per box-size class (roi_recon_get_team_caps)."""
+        st, caps, _ = roi_recon_get_team_caps(self.h)
+        self._check(st)
+        return caps
+
+    @team_caps.setter
+    def team_caps(self, caps):
+        self._check(roi_recon_set_team_caps(self.h, caps))
+
+    def team_caps_ms(self):
+        """The autotuner's milliseconds per class for team caps TEAM_CAPS (zeros before it ran)."""
+        st, _, ms = roi_recon_get_team_caps(self.h)
+        self._check(st)
+        return ms
+
     def sync(self):
         """Wait for the handle's stream; raises RoiError(ROI_ETIMEOUT) if a device wait gave up."""
         self._check(roi_recon_sync(self.h))
@@ -759,7 +795,8 @@ class RoiRecon:
         self._check(roi_recon_set_timing(self.h, int(enable)))
 
     def kernel_times(self, kernel: int):
-        """(launches, total device ms) of kernel class 0 (forward), 1 (back) or 2 (single-launch solve)."""
+        """(launches, total device ms) of kernel class 0 (forward), 1 (back), 2 (single-launch or
+        batched solve) or 3 (filtered sinograms)."""
         s, n, ms = roi_recon_kernel_times(self.h, kernel)
         self._check(s)
         return n, ms

@@ -98,8 +98,12 @@ struct TuneKey {
         return std::tie(N, na, nd, dt, angles) < std::tie(o.N, o.na, o.nd, o.dt, o.angles);
     }
 };
+struct TuneVal {
+    std::array<int, roi::kShapeClasses> shape;  // phase B tile shape per box-size class
+    std::array<int, roi::kShapeClasses> team;   // largest team of a few-region batch, per class
+};
 std::mutex g_tune_mu;
-std::map<TuneKey, std::array<int, roi::kShapeClasses>> g_tune;
+std::map<TuneKey, TuneVal> g_tune;
 
 unsigned long long fnv_doubles(const std::vector<double>& v) {
     unsigned long long h = 1469598103934665603ull;
@@ -168,6 +172,8 @@ struct roi_recon {
     int opt_persistent = 1;
     int opt_tile_shape = -1;              // >= 0: phase B tile shape for every region
     int tile_shape[roi::kShapeClasses] = {0, 0, 0};  // per box-size class (roi_recon_autotune)
+    int team_cap[roi::kShapeClasses] = {16, 16, 16};  // largest team per region of a few-region batch
+    double team_ms[roi::kShapeClasses][4] = {};       // the autotuner's timings of the team candidates
     unsigned long long opt_wait_ns = 1000000000ull;
     int opt_phantoms = 0;
     int opt_filter_fma = 0;               // 1: filtered sinograms on the FMA pipe (not the tensor cores)
@@ -991,7 +997,10 @@ roi_status roi_recon_create(const roi_geometry* geom, void* cuda_stream, roi_rec
         std::lock_guard<std::mutex> g(g_tune_mu);
         auto it = g_tune.find(TuneKey{h->N, h->na, h->nd, h->dt, fnv_doubles(h->angles)});
         if (it != g_tune.end())
-            for (int c = 0; c < roi::kShapeClasses; ++c) h->tile_shape[c] = it->second[c];
+            for (int c = 0; c < roi::kShapeClasses; ++c) {
+                h->tile_shape[c] = it->second.shape[c];
+                h->team_cap[c] = it->second.team[c];
+            }
     }
     *out = h;
     return ROI_OK;
@@ -1491,6 +1500,7 @@ roi_status solve_batch_impl(roi_recon* h, int n, const roi_region* regions, cons
     std::vector<int> strides(n);
     size_t out_total = 0, win_cap = 0, img_cap = 0, pad_cap = 0, max_stage = 0;
     size_t max_banded_units = 0;  // ray units of the largest band-streamed region
+    int max_side = 0;             // the largest box side (its class sets the team size of few regions)
     std::vector<double> cost(n);
     std::vector<AngleRec> loc(na);
     for (int i = 0; i < n; ++i) {
@@ -1525,6 +1535,7 @@ roi_status solve_batch_impl(roi_recon* h, int n, const roi_region* regions, cons
         if (roi::stage_mode(box.w, box.h, h->esz) == 1)
             max_banded_units = std::max(max_banded_units, (size_t)na * ((strides[i] + 31) / 32));
         cost[i] = (double)box.w * box.h * na * (double)std::max(P.iters, 1);
+        max_side = std::max(max_side, std::max(box.w, box.h));
     }
     if (need_fbp) {
         roi_status s0 = ensure_residual(h);
@@ -1538,7 +1549,7 @@ roi_status solve_batch_impl(roi_recon* h, int n, const roi_region* regions, cons
     if (!out_on_device) CU(h, h->b_out.ensure(out_total));
     // few regions: teams of blocks per region (co-resident: at most one block per SM)
     int blocks = std::max(1, h->sms);
-    int team = std::min(16, blocks / n);
+    int team = std::min(h->team_cap[roi::shape_class(max_side)], blocks / n);
     if (team_req < 0) team = std::min(blocks, roi::serve_max_blocks(h->device));
     if (team > 1) {
         blocks = std::min(blocks, roi::serve_max_blocks(h->device));
@@ -1755,6 +1766,7 @@ roi_status roi_recon_autotune(roi_recon_t h, int regions_per_class, int iters, i
         if (hi < side_lo[c]) {  // the grid has no box of this class
             for (int sh = 0; sh < roi::kTileShapes; ++sh)
                 if (ms_out) ms_out[c * roi::kTileShapes + sh] = 0.0;
+            for (int k = 0; k < 4; ++k) h->team_ms[c][k] = 0.0;
             continue;
         }
         std::vector<roi_region> regs(n);
@@ -1802,6 +1814,33 @@ roi_status roi_recon_autotune(roi_recon_t h, int regions_per_class, int iters, i
             }
         }
         if (st == ROI_OK) h->tile_shape[c] = best_sh;
+        // the team size of a few-region batch (8 regions of the class, the chosen shape):
+        // results are the same bits for every team size, only the time differs
+        h->opt_tile_shape = -1;
+        const int nf = std::min(n, 8);
+        static const int caps[4] = {4, 8, 16, 32};
+        double best_t = 0.0;
+        int best_cap = h->team_cap[c];
+        const int keep_cap = h->team_cap[c];
+        for (int k = 0; k < 4 && st == ROI_OK; ++k) {
+            h->team_cap[c] = caps[k];
+            double ms = 0.0;
+            for (int rep = 0; rep < 3 && st == ROI_OK; ++rep) {
+                cudaEventRecord(e0, h->st);
+                st = solve_batch_impl(h, nf, regs.data(), prms.data(), outs.data(), 1, nullptr, 0);
+                cudaEventRecord(e1, h->st);
+                if (st == ROI_OK) st = roi_recon_sync(h);
+                float t = 0.f;
+                if (st == ROI_OK && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess && rep > 0)
+                    ms = rep == 1 ? t : std::min(ms, (double)t);
+            }
+            h->team_ms[c][k] = ms;
+            if (st == ROI_OK && (k == 0 || ms < best_t)) {
+                best_t = ms;
+                best_cap = caps[k];
+            }
+        }
+        h->team_cap[c] = st == ROI_OK ? best_cap : keep_cap;
     }
     outb.release();
     cudaEventDestroy(e0);
@@ -1814,7 +1853,10 @@ roi_status roi_recon_autotune(roi_recon_t h, int regions_per_class, int iters, i
         for (int c = 0; c < roi::kShapeClasses; ++c) shapes_out[c] = h->tile_shape[c];
     std::lock_guard<std::mutex> g(g_tune_mu);
     auto& t = g_tune[TuneKey{h->N, h->na, h->nd, h->dt, fnv_doubles(h->angles)}];
-    for (int c = 0; c < roi::kShapeClasses; ++c) t[c] = h->tile_shape[c];
+    for (int c = 0; c < roi::kShapeClasses; ++c) {
+        t.shape[c] = h->tile_shape[c];
+        t.team[c] = h->team_cap[c];
+    }
     return ROI_OK;
 }
 
@@ -1832,6 +1874,26 @@ roi_status roi_recon_set_tile_shapes(roi_recon_t h, const int* shapes) {
 roi_status roi_recon_get_tile_shapes(roi_recon_t h, int* shapes) {
     if (!h || !shapes) return ROI_EINVAL;
     for (int c = 0; c < roi::kShapeClasses; ++c) shapes[c] = h->tile_shape[c];
+    return ROI_OK;
+}
+
+roi_status roi_recon_set_team_caps(roi_recon_t h, const int* caps) {
+    if (!h) return ROI_EINVAL;
+    h->err.clear();
+    if (!caps) return fail(h, ROI_EINVAL, "set_team_caps: null argument");
+    for (int c = 0; c < roi::kShapeClasses; ++c)
+        if (caps[c] < 1 || caps[c] > 1024) return fail(h, ROI_EINVAL, "set_team_caps: team size %d out of range", caps[c]);
+    for (int c = 0; c < roi::kShapeClasses; ++c) h->team_cap[c] = caps[c];
+    return ROI_OK;
+}
+
+roi_status roi_recon_get_team_caps(roi_recon_t h, int* caps, double* ms_out) {
+    if (!h || !caps) return ROI_EINVAL;
+    for (int c = 0; c < roi::kShapeClasses; ++c) {
+        caps[c] = h->team_cap[c];
+        if (ms_out)
+            for (int k = 0; k < 4; ++k) ms_out[c * 4 + k] = h->team_ms[c][k];
+    }
     return ROI_OK;
 }
 

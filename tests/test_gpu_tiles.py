@@ -133,6 +133,38 @@ def test_autotune_picks_a_shape_per_class_and_batches_use_it(data):
     assert rr.tile_shapes == [0, 0, 0]
     with pytest.raises(R.RoiError):
         rr.tile_shapes = [0, 3, 0]
+    # team sizes of few-region batches: one of the candidates per class, the fastest measured
+    caps, cms = rr.team_caps, rr.team_caps_ms()
+    for c in range(3):
+        assert caps[c] in R.TEAM_CAPS
+        assert all(t > 0 for t in cms[c]), cms
+        assert cms[c][R.TEAM_CAPS.index(caps[c])] == min(cms[c])
+    rr.team_caps = [16, 16, 16]
+    with pytest.raises(R.RoiError):
+        rr.team_caps = [16, 0, 16]
+
+
+def test_few_region_batch_is_bit_identical_for_every_team_size(data):
+    """A batch of fewer regions than half the blocks runs on teams; the team size (the
+    handle's team table) changes the time, never the bits."""
+    rr, exp = data
+    regions = [r for r, _ in REGIONS]
+    params = [p for _, p in REGIONS]
+    keep = rr.team_caps
+    try:
+        res = []
+        for cap in R.TEAM_CAPS + (1, 38):
+            rr.team_caps = [cap] * 3
+            outs, _ = rr.solve_batch(regions, params)
+            rr.sync()
+            res.append([o.cpu().numpy() for o in outs])
+        for other in res[1:]:
+            for a, b in zip(res[0], other):
+                assert np.array_equal(a, b)
+        for o, x in zip(res[0], exp):
+            assert rel_l2(o, x) <= SOLVE_TOL
+    finally:
+        rr.team_caps = keep
 
 
 @pytest.mark.parametrize("shape", sorted(R.TILE_SHAPES))
