@@ -66,9 +66,13 @@ cudaError_t dev_alloc(T** p, size_t count) {
 
 // Grow-only device buffer.
 template <class T>
-struct DevBufT {  // grow-only device array of T
+struct DevBufT {  // grow-only device array of T, freed when it goes out of scope
     T* p = nullptr;
     size_t cap = 0;
+    DevBufT() = default;
+    DevBufT(const DevBufT&) = delete;
+    DevBufT& operator=(const DevBufT&) = delete;
+    ~DevBufT() { release(); }
     cudaError_t ensure(size_t n) {
         if (n <= cap) return cudaSuccess;
         if (p) cudaFree(p);
