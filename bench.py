@@ -365,6 +365,9 @@ def small_measure(steps=20, warmup=3):
             "path": "single cooperative launch per solve (k_persist)"}
 
 
+FCONV_SRCS = ["paper_1604_02292_gb300/csrc/filterconv_tc.cu", "paper_1604_02292_gb300/csrc/dev_common.cuh"]
+
+
 def tc_issued_flops(n, na, nd):
     """Tensor-pipe FLOPs of one launch of the tensor-core filtered-sinogram kernel: per work
     item (angle, 256 output bins), each 128-bin tile runs 3 tf32 MMAs (hi*hi, hi*lo, lo*hi)
@@ -419,7 +422,9 @@ def filter_conv_measure(reps=3):
                              "achieved": issued / t / 1e12, "peak": tf32_peak, "frac": issued / t / 1e12 / tf32_peak,
                              "algorithmic_TFLOP_s": alg / t / 1e12,
                              "peak_source": f"tf32 dense = {src} bf16 burst x 1.1/2.25 (nominal ratio)",
-                             "achieved_counts": "tf32 MMA FLOPs issued (3 split products, padded tiles)"}})
+                             "achieved_counts": "tf32 MMA FLOPs issued (3 split products, padded tiles)",
+                             "traffic": profile_traffic(FCONV_SRCS, "profiles/k_filter_conv_tc_filter_1024.md"),
+                             "traffic_unit": "DRAM bytes per launch (ncu, profiles/)"}})
     rr.close()
     return out
 
