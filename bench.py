@@ -619,7 +619,7 @@ def run_ours(args):
     batch = None
     if not args.no_batch:
         wb = WL.BATCHES["roi_batch_2048"]
-        batch = batch_measure(wb, None, 1, 1, dist, ws, rank, local, clock=False, tune=True)
+        batch = batch_measure(wb, None, 1, 1, dist, ws, rank, local, clock=False, tune=True, graph=True)
         batch.pop("clocks")
         batch.update({"workload": wb.name, "N": wb.N, "n_angles": wb.n_angles, "n_det": wb.n_det,
                       "radius": [wb.r_lo, wb.r_hi], "iters": wb.iters, "solvers": "SIRT/TV 50/50",
@@ -694,13 +694,14 @@ def run_ours(args):
     return 0
 
 
-def batch_measure(w, count, steps, warmup, dist, ws, rank, local, clock=True, tune=False, iters=0):
+def batch_measure(w, count, steps, warmup, dist, ws, rank, local, clock=True, tune=False, iters=0, graph=False):
     """Batched solves: one step = roi_recon_solve_batch over the regions (one persistent
     launch); the warm-up steps run every region for one iteration (same boxes, so the same
     device slots).  Returns regions/s over all ranks, the per-step times and the lerps/s of
     rank 0 against the derived ceiling.  tune: the phase B tile shapes are first chosen by
     roi_recon_autotune on this sinogram (timed apart), and the default table (16 x 16 for
-    every box size) is measured as well."""
+    every box size) is measured as well.  graph: the same batch is then planned once
+    (roi_recon_batch_plan_create) and one step replayed as its captured CUDA graph."""
     import torch
 
     import paper_1604_02292_gb300 as R
@@ -754,6 +755,24 @@ def batch_measure(w, count, steps, warmup, dist, ws, rank, local, clock=True, tu
     with ClockSampler(local if clock else None) as clk:
         ms = timed_steps()
     launches = int(R.roi_recon_launch_count() - n0)
+    graph_out = None
+    if graph:
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            plan = rr.batch_plan(regions, params, outs)
+        t_plan = time.perf_counter() - t0
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            plan.launch()
+            b.record(stream)
+        torch.cuda.synchronize()
+        g_ms = a.elapsed_time(b)
+        plan.close()
+        graph_out = {"value": len(items) / (g_ms / 1e3), "unit": "solves/s", "ms": g_ms,
+                     "plan_create_s": t_plan,
+                     "note": "the batch planned once (tables, descriptors and order uploaded) and replayed "
+                             "as one captured CUDA graph: the queue reset and the persistent kernel"}
     n_lerps = 0
     for reg, prm in items:
         pl = rr.plan(reg)
@@ -768,7 +787,7 @@ def batch_measure(w, count, steps, warmup, dist, ws, rank, local, clock=True, tu
     return {"value": len(all_items) * steps / t, "unit": "solves/s", "regions": len(all_items), "steps": steps,
             "ms_per_step": statistics.mean(ms), "gpu_launches": launches,
             "projector_Glerp_s_rank0": achieved, "lerp_ceiling_Glerp_s": peak, "frac_of_ceiling": achieved / peak,
-            "autotune": tuning, "clocks": clk.summary()}
+            "autotune": tuning, "graph": graph_out, "clocks": clk.summary()}
 
 
 def run_batch(args):

@@ -45,6 +45,7 @@ extern "C" {
 #endif
 
 typedef struct roi_recon* roi_recon_t;
+typedef struct roi_batch_plan* roi_batch_plan_t;
 
 typedef enum {
     ROI_OK = 0,
@@ -227,6 +228,25 @@ roi_status roi_recon_solve_local_resume(roi_recon_t h, const roi_region* region,
  * offending region. */
 roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions, const roi_solve_params* params,
                                  float* const* outs, int out_on_device, roi_solve_info* infos);
+
+/* A batch planned once and launched as one captured CUDA graph (Sec. 5.5; many local solves
+ * in one persistent launch): create plans the batch exactly as roi_recon_solve_batch does
+ * (same arguments; outs must be device pointers; SIRT and CP-TV regions only, ROI_EINVAL
+ * otherwise), uploads the angle tables and region descriptors into device buffers of the
+ * plan's own, and captures the launch -- the reset of the launch's queue or team barriers
+ * and the persistent kernel -- into an instantiated CUDA graph (it synchronizes; options
+ * such as the tile table, team table and wait limit are read then).  launch replays the
+ * graph on the handle's stream after recomputing the residual p - W x_fbp if the sinogram
+ * or FBP changed: a new sinogram of the same geometry (set_sinogram + fbp) is solved on the
+ * same regions without host planning, and each result is bit-identical to solve_batch's on
+ * that sinogram.  The outs and the handle must outlive the plan; destroy (or
+ * roi_recon_destroy) waits for the handle's stream and frees the plan.  ROI_ESTATE for
+ * launch before fbp; ROI_EINVAL for a plan of another handle. */
+roi_status roi_recon_batch_plan_create(roi_recon_t h, int n, const roi_region* regions,
+                                       const roi_solve_params* params, float* const* outs, roi_solve_info* infos,
+                                       roi_batch_plan_t* out);
+roi_status roi_recon_batch_plan_launch(roi_recon_t h, roi_batch_plan_t plan);
+roi_status roi_recon_batch_plan_destroy(roi_recon_t h, roi_batch_plan_t plan);
 
 /* Tiling (Sec. 5.5): the whole N x N image as non-overlapping tile x tile local
  * reconstructions placed next to each other.  Tile (ti, tj) covers rows [ti tile, (ti+1)

@@ -40,7 +40,8 @@ __all__ = [
     "roi_server_cancel", "roi_server_set_option", "roi_recon_test_fail_alloc",
     "ROI_OPT_TILE_SHAPE", "TILE_SHAPES", "roi_recon_autotune", "roi_recon_set_tile_shapes",
     "roi_recon_get_tile_shapes", "ROI_OPT_FILTER_CONV", "roi_recon_filter_conv", "roi_recon_set_team_caps",
-    "roi_recon_get_team_caps", "TEAM_CAPS",
+    "roi_recon_get_team_caps", "TEAM_CAPS", "roi_recon_batch_plan_create", "roi_recon_batch_plan_launch",
+    "roi_recon_batch_plan_destroy", "BatchPlan",
 ]
 
 ROI_OK, ROI_EINVAL, ROI_ENOMEM, ROI_ESTATE, ROI_ECUDA, ROI_ETIMEOUT, ROI_EBUSY, ROI_ECANCELED = range(8)
@@ -75,6 +76,43 @@ class SolveInfo(ctypes.Structure):
     _fields_ = [("box_x0", ctypes.c_int), ("box_y0", ctypes.c_int), ("box_w", ctypes.c_int),
                 ("box_h", ctypes.c_int), ("window_max", ctypes.c_int), ("window_stride", ctypes.c_int),
                 ("iters_done", ctypes.c_int), ("step_L", ctypes.c_double), ("objective", ctypes.c_double)]
+
+
+
+class BatchPlan:
+    """A batch of SIRT / CP-TV regions planned once on a handle and launched as one captured
+    CUDA graph; launch() after set_sinogram + fbp solves the same regions on the new data
+    (bit-identical to RoiRecon.solve_batch there).  close() (or the handle's close) frees it."""
+
+    def __init__(self, rr, regions, params, outs=None):
+        torch = rr._torch
+        n = len(regions)
+        if isinstance(params, dict):
+            params = [params] * n
+        regs = (Region * n)(*[Region(*map(float, r)) for r in regions])
+        prms = (SolveParams * n)()
+        for i, p in enumerate(params):
+            prms[i] = _params(p)
+        if outs is None:
+            outs = [torch.empty((rr.plan(r).box[3], rr.plan(r).box[2]), dtype=torch.float32, device="cuda")
+                    for r in regions]
+        ptrs = (ctypes.c_void_p * n)()
+        for i, o in enumerate(outs):
+            ptrs[i] = rr._dev(o)
+        self.infos = (SolveInfo * n)()
+        self.rr, self.outs, self.h = rr, outs, None
+        s, h = roi_recon_batch_plan_create(rr.h, regs, prms, ptrs, self.infos)
+        rr._check(s)
+        self.h = h
+
+    def launch(self):
+        self.rr._check(roi_recon_batch_plan_launch(self.rr.h, self.h))
+        return self.outs
+
+    def close(self):
+        if self.h is not None and self.rr.h:
+            roi_recon_batch_plan_destroy(self.rr.h, self.h)
+        self.h = None
 
 
 class ServerConfig(ctypes.Structure):
@@ -113,7 +151,8 @@ EXPORTS = [
     "roi_recon_solve_tiled", "roi_recon_state_size", "roi_recon_state_export", "roi_recon_solve_local_resume",
     "roi_recon_check_report", "roi_server_cancel", "roi_server_set_option", "roi_recon_test_fail_alloc",
     "roi_recon_autotune", "roi_recon_set_tile_shapes", "roi_recon_get_tile_shapes", "roi_recon_filter_conv",
-    "roi_recon_set_team_caps", "roi_recon_get_team_caps",
+    "roi_recon_set_team_caps", "roi_recon_get_team_caps", "roi_recon_batch_plan_create",
+    "roi_recon_batch_plan_launch", "roi_recon_batch_plan_destroy",
 ]
 
 _lib = None
@@ -192,6 +231,14 @@ def lib() -> ctypes.CDLL:
             L.roi_recon_filter_get.restype = st
             L.roi_recon_filter_conv.argtypes = [_H, ctypes.c_int, _P, _P, _P]
             L.roi_recon_filter_conv.restype = st
+            L.roi_recon_batch_plan_create.argtypes = [_H, ctypes.c_int, ctypes.POINTER(Region),
+                                                      ctypes.POINTER(SolveParams), ctypes.POINTER(ctypes.c_void_p),
+                                                      ctypes.POINTER(SolveInfo), ctypes.POINTER(_H)]
+            L.roi_recon_batch_plan_create.restype = st
+            L.roi_recon_batch_plan_launch.argtypes = [_H, _H]
+            L.roi_recon_batch_plan_launch.restype = st
+            L.roi_recon_batch_plan_destroy.argtypes = [_H, _H]
+            L.roi_recon_batch_plan_destroy.restype = st
             L.roi_recon_set_team_caps.argtypes = [_H, ctypes.POINTER(ctypes.c_int)]
             L.roi_recon_set_team_caps.restype = st
             L.roi_recon_get_team_caps.argtypes = [_H, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
@@ -350,6 +397,21 @@ def roi_recon_solve_batch(h, regions, params, outs, out_on_device: int, infos=No
     """regions, params: ctypes arrays (Region * n, SolveParams * n); outs: (c_void_p * n) pointers."""
     n = len(regions)
     return lib().roi_recon_solve_batch(h, n, regions, params, outs, int(out_on_device), infos)
+
+
+def roi_recon_batch_plan_create(h, regions, params, outs, infos=None):
+    """regions, params: ctypes arrays; outs: (c_void_p * n) device pointers.  Returns (status, plan)."""
+    plan = _H()
+    s = lib().roi_recon_batch_plan_create(h, len(regions), regions, params, outs, infos, ctypes.byref(plan))
+    return s, plan.value
+
+
+def roi_recon_batch_plan_launch(h, plan) -> int:
+    return lib().roi_recon_batch_plan_launch(h, plan)
+
+
+def roi_recon_batch_plan_destroy(h, plan) -> int:
+    return lib().roi_recon_batch_plan_destroy(h, plan)
 
 
 def roi_recon_set_sinogram_truncated(h, p: int, dtype: int, on_device: int, n_measured: int) -> int:
@@ -697,6 +759,12 @@ class RoiRecon:
             raise TypeError("outs must be all CUDA tensors or all host arrays")
         self._check(roi_recon_solve_batch(self.h, regs, prms, ptrs, on_device, infos))
         return outs, list(infos)
+
+    def batch_plan(self, regions, params, outs=None):
+        """A batch planned once and replayed as a captured CUDA graph (roi_recon_batch_plan_*):
+        returns a BatchPlan whose launch() solves the regions on the handle's current sinogram
+        into its outs (CUDA tensors, allocated here unless given)."""
+        return BatchPlan(self, regions, params, outs)
 
     def forward_local(self, region, x, y=None):
         pl = self.plan(region)

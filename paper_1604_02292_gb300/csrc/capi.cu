@@ -90,6 +90,20 @@ struct DevBufT {  // grow-only device array of T, freed when it goes out of scop
 };
 using DevBuf = DevBufT<float>;
 
+// Device buffers of a batched launch: per-region angle tables, descriptors and order, the
+// launch's queue and team barriers, one slot of solver state per block (or per team).  The
+// handle has one set; a batch plan owns another, so that its captured launch never sees the
+// buffers of a later batch.
+struct BatchBufs {
+    DevBufT<AngleRec> tab;
+    DevBuf out;
+    DevBufT<roi::BatchRoi> rois;
+    DevBufT<int> order;
+    DevBufT<int> queue;
+    DevBufT<unsigned> bars;
+    DevBuf pp, u, sig, x, vx, vy, tau, xa, xaT, fgp;
+};
+
 }  // namespace
 
 namespace {
@@ -184,13 +198,8 @@ struct roi_recon {
     size_t max_smem_optin = 0;
     int sms = 0;
     // batched solves: per-region tables / windows / descriptors, per-block slots, pinned staging
-    DevBufT<AngleRec> b_tab;
-    DevBuf b_out;
-    DevBufT<roi::BatchRoi> b_rois;
-    DevBufT<int> b_order;
-    DevBufT<int> b_queue;
-    DevBufT<unsigned> b_bars;
-    DevBuf s_pp, s_u, s_sig, s_x, s_vx, s_vy, s_tau, s_xa, s_xaT, s_fgp;
+    BatchBufs bb;
+    std::vector<roi_batch_plan*> plans;  // live batch plans (destroyed with the handle)
     // residual p - W x_fbp over every ray, [na][resid_ld] (exterior step of the
     // whole-region solvers, Eq. locouter); valid while resid_ready
     DevBuf resid;
@@ -1013,6 +1022,7 @@ roi_status roi_recon_create(const roi_geometry* geom, void* cuda_stream, roi_rec
 void roi_recon_destroy(roi_recon_t h) {
     if (!h) return;
     cudaStreamSynchronize(h->st);
+    while (!h->plans.empty()) roi_recon_batch_plan_destroy(h, h->plans.back());
     for (void* b : {h->p, (void*)h->q, (void*)h->xfbp_base, (void*)h->xfbpT_base, (void*)h->hodd})
         if (b) cudaFree(b);
     h->fbp32.release();
@@ -1024,14 +1034,7 @@ void roi_recon_destroy(roi_recon_t h) {
     if (h->red) cudaFree(h->red);
     if (h->d_bar) cudaFree(h->d_bar);
     if (h->d_err) cudaFree(h->d_err);
-    h->b_tab.release();
-    h->b_rois.release();
-    h->b_order.release();
-    h->b_queue.release();
-    h->b_bars.release();
-    for (DevBuf* b : {&h->b_out, &h->s_pp, &h->s_u, &h->s_sig, &h->s_x, &h->s_vx, &h->s_vy, &h->s_tau, &h->s_xa,
-                      &h->s_xaT, &h->resid, &h->s_fgp})
-        b->release();
+    h->resid.release();  // the batch buffers (h->bb) are freed with the handle
     if (h->pin) cudaFreeHost(h->pin);
     if (h->pin_free) cudaEventDestroy(h->pin_free);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
@@ -1220,7 +1223,8 @@ roi_status roi_recon_back_local(roi_recon_t h, const roi_region* region, const f
 namespace {
 
 roi_status solve_batch_impl(roi_recon* h, int n, const roi_region* regions, const roi_solve_params* params,
-                            float* const* outs, int out_on_device, roi_solve_info* infos, int team_req);
+                            float* const* outs, int out_on_device, roi_solve_info* infos, int team_req,
+                            BatchBufs* own = nullptr, cudaGraphExec_t* capture = nullptr);
 
 roi_status solve_local_impl(roi_recon* h, const roi_region* region, const roi_solve_params* params, float* out,
                             int out_on_device, roi_solve_info* info) {
@@ -1486,7 +1490,9 @@ namespace {
 // regions (one block per region, or teams of up to 16 blocks for few regions); team_req < 0
 // makes one team of every co-resident block (a lone large region).
 roi_status solve_batch_impl(roi_recon* h, int n, const roi_region* regions, const roi_solve_params* params,
-                            float* const* outs, int out_on_device, roi_solve_info* infos, int team_req) {
+                            float* const* outs, int out_on_device, roi_solve_info* infos, int team_req,
+                            BatchBufs* own, cudaGraphExec_t* capture) {
+    BatchBufs& bb = own ? *own : h->bb;
     if (n < 0 || (n > 0 && (!regions || !params || !outs))) return fail(h, ROI_EINVAL, "solve_batch: bad arguments");
     if (n == 0) return ROI_OK;
     bool need_fbp = false;
@@ -1546,11 +1552,11 @@ roi_status solve_batch_impl(roi_recon* h, int n, const roi_region* regions, cons
         if (s0 != ROI_OK) return s0;
     }
     // ---- device storage
-    CU(h, h->b_tab.ensure((size_t)n * na));
-    CU(h, h->b_rois.ensure(n));
-    CU(h, h->b_order.ensure(n));
-    CU(h, h->b_queue.ensure(1));
-    if (!out_on_device) CU(h, h->b_out.ensure(out_total));
+    CU(h, bb.tab.ensure((size_t)n * na));
+    CU(h, bb.rois.ensure(n));
+    CU(h, bb.order.ensure(n));
+    CU(h, bb.queue.ensure(1));
+    if (!out_on_device) CU(h, bb.out.ensure(out_total));
     // few regions: teams of blocks per region (co-resident: at most one block per SM)
     int blocks = std::max(1, h->sms);
     int team = std::min(h->team_cap[roi::shape_class(max_side)], blocks / n);
@@ -1559,14 +1565,14 @@ roi_status solve_batch_impl(roi_recon* h, int n, const roi_region* regions, cons
         blocks = std::min(blocks, roi::serve_max_blocks(h->device));
         team = std::min(team, blocks);
         blocks = (blocks / team) * team;
-        CU(h, h->b_bars.ensure((size_t)blocks / team));
+        CU(h, bb.bars.ensure((size_t)blocks / team));
     }
     // one slot of buffers per block, or per team of blocks
     const size_t slots = team > 1 ? (size_t)blocks / team : (size_t)blocks;
-    for (DevBuf* b : {&h->s_pp, &h->s_u, &h->s_sig}) CU(h, b->ensure(win_cap * slots));
-    for (DevBuf* b : {&h->s_x, &h->s_vx, &h->s_vy, &h->s_tau}) CU(h, b->ensure(img_cap * slots));
-    for (DevBuf* b : {&h->s_xa, &h->s_xaT}) CU(h, b->ensure(pad_cap * slots));
-    if (need_fgp) CU(h, h->s_fgp.ensure(5 * img_cap * slots));
+    for (DevBuf* b : {&bb.pp, &bb.u, &bb.sig}) CU(h, b->ensure(win_cap * slots));
+    for (DevBuf* b : {&bb.x, &bb.vx, &bb.vy, &bb.tau}) CU(h, b->ensure(img_cap * slots));
+    for (DevBuf* b : {&bb.xa, &bb.xaT}) CU(h, b->ensure(pad_cap * slots));
+    if (need_fgp) CU(h, bb.fgp.ensure(5 * img_cap * slots));
     // ---- page-locked staging: tables, descriptors, order
     const size_t tab_bytes = sizeof(AngleRec) * (size_t)n * na;
     const size_t roi_bytes = sizeof(roi::BatchRoi) * (size_t)n;
@@ -1591,8 +1597,8 @@ roi_status solve_batch_impl(roi_recon* h, int n, const roi_region* regions, cons
         const roi_solve_params& P = params[i];
         roi::BatchRoi& R = prois[i];
         R = roi::BatchRoi{};
-        R.rec = h->b_tab.p + (size_t)i * na;
-        R.out = out_on_device ? outs[i] : h->b_out.p + ooff;
+        R.rec = bb.tab.p + (size_t)i * na;
+        R.out = out_on_device ? outs[i] : bb.out.p + ooff;
         R.na = na;
         R.nrow = nr;
         R.nx = box.w;
@@ -1627,38 +1633,57 @@ roi_status solve_batch_impl(roi_recon* h, int n, const roi_region* regions, cons
         }
     }
     std::stable_sort(pord, pord + n, [&](int a, int b) { return cost[a] > cost[b]; });
-    CU(h, cudaMemcpyAsync(h->b_tab.p, ptab, tab_bytes, cudaMemcpyHostToDevice, h->st));
-    CU(h, cudaMemcpyAsync(h->b_rois.p, prois, roi_bytes, cudaMemcpyHostToDevice, h->st));
-    CU(h, cudaMemcpyAsync(h->b_order.p, pord, ord_bytes, cudaMemcpyHostToDevice, h->st));
+    CU(h, cudaMemcpyAsync(bb.tab.p, ptab, tab_bytes, cudaMemcpyHostToDevice, h->st));
+    CU(h, cudaMemcpyAsync(bb.rois.p, prois, roi_bytes, cudaMemcpyHostToDevice, h->st));
+    CU(h, cudaMemcpyAsync(bb.order.p, pord, ord_bytes, cudaMemcpyHostToDevice, h->st));
     CU(h, cudaEventRecord(h->pin_free, h->st));
     // ---- all solves, exterior steps included, in one persistent launch
     roi::BatchArgs B{};
-    B.rois = h->b_rois.p;
-    B.order = h->b_order.p;
+    B.rois = bb.rois.p;
+    B.order = bb.order.p;
     B.nroi = n;
-    B.queue = h->b_queue.p;
-    B.slot_pp = h->s_pp.p;
-    B.slot_u = h->s_u.p;
-    B.slot_sig = h->s_sig.p;
+    B.queue = bb.queue.p;
+    B.slot_pp = bb.pp.p;
+    B.slot_u = bb.u.p;
+    B.slot_sig = bb.sig.p;
     B.win_cap = win_cap;
-    B.slot_x = h->s_x.p;
-    B.slot_vx = h->s_vx.p;
-    B.slot_vy = h->s_vy.p;
-    B.slot_tau = h->s_tau.p;
+    B.slot_x = bb.x.p;
+    B.slot_vx = bb.vx.p;
+    B.slot_vy = bb.vy.p;
+    B.slot_tau = bb.tau.p;
     B.img_cap = img_cap;
-    B.slot_xa = h->s_xa.p;
-    B.slot_xaT = h->s_xaT.p;
+    B.slot_xa = bb.xa.p;
+    B.slot_xaT = bb.xaT.p;
     B.pad_cap = pad_cap;
-    B.slot_fgp = need_fgp ? h->s_fgp.p : nullptr;
+    B.slot_fgp = need_fgp ? bb.fgp.p : nullptr;
     B.err = h->d_err;
     B.wait_ns = h->opt_wait_ns;
     B.team = team > 1 ? team : 1;
-    B.bars = team > 1 ? h->b_bars.p : nullptr;
+    B.bars = team > 1 ? bb.bars.p : nullptr;
     B.absent = h->opt_phantoms;
     // partial-sum room for band-streamed passes when a block gets 128 or more units of a region
     const size_t per_block = (max_banded_units + (team > 1 ? team : 1) - 1) / (team > 1 ? team : 1);
     const size_t smem = roi::batch_smem_bytes(max_stage, h->na, per_block >= 128);
     cudaError_t e;
+    if (capture) {  // a batch plan: the uploads done, the launch alone captured into a graph
+        // (on a private stream: the handle's stream may be the legacy default stream, which
+        // cannot be captured; the graph is replayed on the handle's stream)
+        CU(h, cudaStreamSynchronize(h->st));
+        cudaStream_t cs = nullptr;
+        CU(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            e = roi::launch_batch(B, blocks, smem, cs);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+            if (e == cudaSuccess) e = e2;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(capture, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+        }
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) return cuda_fail(h, e, "batch plan capture");
+        return ROI_OK;
+    }
     {
         Span sp(h, 2);
         e = roi::launch_batch(B, blocks, smem, h->st);
@@ -1666,7 +1691,7 @@ roi_status solve_batch_impl(roi_recon* h, int n, const roi_region* regions, cons
     if (e != cudaSuccess) return cuda_fail(h, e, "batched solve launch");
     if (!out_on_device) {
         std::vector<float> all(out_total);
-        CU(h, cudaMemcpyAsync(all.data(), h->b_out.p, sizeof(float) * out_total, cudaMemcpyDeviceToHost, h->st));
+        CU(h, cudaMemcpyAsync(all.data(), bb.out.p, sizeof(float) * out_total, cudaMemcpyDeviceToHost, h->st));
         roi_status s = roi_recon_sync(h);
         if (s != ROI_OK) return s;
         size_t o = 0;
@@ -1686,6 +1711,64 @@ roi_status roi_recon_solve_batch(roi_recon_t h, int n, const roi_region* regions
     if (!h) return ROI_EINVAL;
     h->err.clear();
     return solve_batch_impl(h, n, regions, params, outs, out_on_device, infos, 0);
+}
+
+// A batch planned once and launched as one captured CUDA graph (config 3's persistent launch):
+// its own copy of the batch buffers, the graph of the launch (the queue or team-barrier reset
+// and the kernel).
+struct roi_batch_plan {
+    roi_recon* h = nullptr;
+    BatchBufs bb;
+    cudaGraphExec_t exec = nullptr;
+};
+
+roi_status roi_recon_batch_plan_create(roi_recon_t h, int n, const roi_region* regions,
+                                       const roi_solve_params* params, float* const* outs, roi_solve_info* infos,
+                                       roi_batch_plan_t* out) {
+    if (!h || !out) return ROI_EINVAL;
+    h->err.clear();
+    *out = nullptr;
+    if (n < 1 || !regions || !params || !outs) return fail(h, ROI_EINVAL, "batch_plan_create: bad arguments");
+    for (int i = 0; i < n; ++i)
+        if (params[i].reg != ROI_SIRT_NONNEG && params[i].reg != ROI_TV_CP)
+            return fail(h, ROI_EINVAL, "batch_plan_create: region %d: plans take SIRT and CP-TV regions", i);
+    roi_batch_plan* P = new (std::nothrow) roi_batch_plan;
+    if (!P) return fail(h, ROI_ENOMEM, "batch_plan_create: host memory");
+    P->h = h;
+    const roi_status s = solve_batch_impl(h, n, regions, params, outs, 1, infos, 0, &P->bb, &P->exec);
+    if (s != ROI_OK) {
+        cudaStreamSynchronize(h->st);
+        if (P->exec) cudaGraphExecDestroy(P->exec);
+        delete P;
+        return s;
+    }
+    h->plans.push_back(P);
+    *out = P;
+    return ROI_OK;
+}
+
+roi_status roi_recon_batch_plan_launch(roi_recon_t h, roi_batch_plan_t plan) {
+    if (!h || !plan || plan->h != h) return ROI_EINVAL;
+    h->err.clear();
+    if (!h->have_fbp) return fail(h, ROI_ESTATE, "batch_plan_launch: no FBP image (call fbp first)");
+    const roi_status s = ensure_residual(h);  // this sinogram's residual, on the handle's stream
+    if (s != ROI_OK) return s;
+    Span sp(h, 2);
+    CU(h, cudaGraphLaunch(plan->exec, h->st));
+    h->state_valid = false;
+    h->state_region_path = false;
+    return ROI_OK;
+}
+
+roi_status roi_recon_batch_plan_destroy(roi_recon_t h, roi_batch_plan_t plan) {
+    if (!h || !plan) return ROI_EINVAL;
+    auto it = std::find(h->plans.begin(), h->plans.end(), plan);
+    if (it == h->plans.end()) return ROI_EINVAL;
+    cudaStreamSynchronize(h->st);  // no launch of the plan in flight when its buffers go
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    h->plans.erase(it);
+    delete plan;
+    return ROI_OK;
 }
 
 roi_status roi_recon_solve_tiled(roi_recon_t h, int tile, int margin, const roi_solve_params* params, float* out) {
