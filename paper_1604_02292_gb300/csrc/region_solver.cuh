@@ -417,14 +417,24 @@ __device__ __forceinline__ void phase_b_s(const Ctx& C, const Team& T, int pass,
             const int c = cc[al];
             int K = cb[al] + lj0 * c - li * cs[al];
             const float* srow = st + al * SBB;
+            // two pixels of the run per packed (f32x2) operation: the same fused multiply-adds
+            // as one pixel at a time
 #pragma unroll
-            for (int p = 0; p < RUNB; ++p) {
-                const int kl = chk(K >> 23, 0, SBB - 1, CHK_REGION_GATHER);
-                const float mf = frac_int<23>(K);
-                const float w0 = fma_sat(mf, niws, 1.f);
-                const float w1 = fma_sat(mf, iws, omiw);
-                acc[p] = fmaf(w0, srow[kl], fmaf(w1, srow[kl + 1], acc[p]));
-                K += c;
+            for (int p = 0; p < RUNB; p += 2) {
+                const int K1 = K + c;
+                const int kl0 = chk(K >> 23, 0, SBB - 1, CHK_REGION_GATHER);
+                const int kl1 = chk(K1 >> 23, 0, SBB - 1, CHK_REGION_GATHER);
+                const float2 bits = make_float2(__uint_as_float(0x4B000000u | ((unsigned)K & 0x7FFFFFu)),
+                                                __uint_as_float(0x4B000000u | ((unsigned)K1 & 0x7FFFFFu)));
+                const float2 mf = __fadd2_rn(bits, make_float2(-8388608.0f, -8388608.0f));
+                const float2 w0 = make_float2(fma_sat(mf.x, niws, 1.f), fma_sat(mf.y, niws, 1.f));
+                const float2 w1 = make_float2(fma_sat(mf.x, iws, omiw), fma_sat(mf.y, iws, omiw));
+                const float2 s0 = make_float2(srow[kl0], srow[kl1]);
+                const float2 s1 = make_float2(srow[kl0 + 1], srow[kl1 + 1]);
+                const float2 r = __ffma2_rn(w0, s0, __ffma2_rn(w1, s1, make_float2(acc[p], acc[p + 1])));
+                acc[p] = r.x;
+                acc[p + 1] = r.y;
+                K = K1 + c;
             }
         }
     };
