@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(BPT, 1) k_batch(BatchArgs B) {
     bufs.xa_base = B.slot_xa + slot * B.pad_cap;
     bufs.xaT_base = B.slot_xaT + slot * B.pad_cap;
     bufs.fgp = B.slot_fgp ? B.slot_fgp + slot * 5 * B.img_cap : nullptr;
+    bufs.part = nullptr;
     for (;;) {
         __syncthreads();
         if (tid == 0) s_roi = atomicAdd(B.queue, 1);

@@ -42,6 +42,7 @@ __global__ void __launch_bounds__(BPT, 1) k_batch_team(BatchArgs B) {
         s_bufs.xa_base = B.slot_xa + slot * B.pad_cap;
         s_bufs.xaT_base = B.slot_xaT + slot * B.pad_cap;
         s_bufs.fgp = B.slot_fgp ? B.slot_fgp + slot * 5 * B.img_cap : nullptr;
+        s_bufs.part = B.slot_part ? B.slot_part + slot * B.part_cap : nullptr;
     }
     __syncthreads();
     unsigned parity = 0;

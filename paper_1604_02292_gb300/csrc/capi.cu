@@ -102,6 +102,7 @@ struct BatchBufs {
     DevBufT<int> queue;
     DevBufT<unsigned> bars;
     DevBuf pp, u, sig, x, vx, vy, tau, xa, xaT, fgp;
+    DevBuf part;  // per-band ray partial sums of a band-streamed box on a team of every block
 };
 
 }  // namespace
@@ -1590,10 +1591,17 @@ roi_status solve_batch_impl(roi_recon* h, int n, const roi_region* regions, cons
     roi::BatchRoi* prois = reinterpret_cast<roi::BatchRoi*>(h->pin + tab_bytes);
     int* pord = reinterpret_cast<int*>(h->pin + tab_bytes + roi_bytes);
     size_t ooff = 0;
+    size_t part_cap = 0;  // a team of every block: phase A of band-streamed boxes by row band
     for (int i = 0; i < n; ++i) {
         const Rect box = boxes[i];
         int nr = 0;
         const int wl = roi::plan_region_table(h->N, na, h->nd, h->angles.data(), box, ptab + (size_t)i * na, &nr);
+        if (team_req < 0 && team > 1 && roi::stage_mode(box.w, box.h, h->esz) == 1 &&
+            (size_t)na * ((strides[i] + 31) / 32) > (size_t)32 * team) {  // as the solver's test
+            const int br = roi::band_rows(box.w, box.h, h->esz), nch = (strides[i] + 31) / 32;
+            part_cap = std::max(part_cap, ((size_t)(box.h + br - 1) / br * nr + (size_t)(box.w + br - 1) / br * (na - nr)) *
+                                              nch * 32);
+        }
         const roi_solve_params& P = params[i];
         roi::BatchRoi& R = prois[i];
         R = roi::BatchRoi{};
@@ -1637,6 +1645,7 @@ roi_status solve_batch_impl(roi_recon* h, int n, const roi_region* regions, cons
     CU(h, cudaMemcpyAsync(bb.rois.p, prois, roi_bytes, cudaMemcpyHostToDevice, h->st));
     CU(h, cudaMemcpyAsync(bb.order.p, pord, ord_bytes, cudaMemcpyHostToDevice, h->st));
     CU(h, cudaEventRecord(h->pin_free, h->st));
+    if (part_cap) CU(h, bb.part.ensure(part_cap * slots));
     // ---- all solves, exterior steps included, in one persistent launch
     roi::BatchArgs B{};
     B.rois = bb.rois.p;
@@ -1656,6 +1665,8 @@ roi_status solve_batch_impl(roi_recon* h, int n, const roi_region* regions, cons
     B.slot_xaT = bb.xaT.p;
     B.pad_cap = pad_cap;
     B.slot_fgp = need_fgp ? bb.fgp.p : nullptr;
+    B.slot_part = part_cap ? bb.part.p : nullptr;
+    B.part_cap = part_cap;
     B.err = h->d_err;
     B.wait_ns = h->opt_wait_ns;
     B.team = team > 1 ? team : 1;

@@ -851,6 +851,111 @@ __device__ __forceinline__ bool phase_a_banded(const Ctx& C, const Team& T, int 
     return true;
 }
 
+// Band-streamed phase A of a large team (a lone box on every block), decomposed by row band:
+// the branch's (band, 32 units) items are split among the branch's blocks in band order, so
+// a block stages the one or two bands of its items once and every warp takes a unit; each
+// ray's partial over a band -- the same operations as a band of phase_a_banded -- goes to
+// C.b.part, and after a team barrier one warp per unit adds the partials of the bands the ray
+// crosses in band order and applies the update: the same bits as phase_a_banded.  Every block
+// of the team calls this once per iteration (with its own branch).  false: a wait gave up.
+template <bool SOLO, int DT>
+__device__ __noinline__ bool phase_a_rowband(const Ctx& C, Team& T, int row, const void* img_base_v, int ld,
+                                             float* smem_f, uint64_t* mbar, unsigned& parity) {
+    using TS = typename Stor<DT>::T;
+    constexpr unsigned ES = sizeof(TS);
+    const TS* img_base = static_cast<const TS*>(img_base_v);
+    TS* smem = reinterpret_cast<TS*>(smem_f);
+    const BatchRoi& R = *C.R;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int M = row ? R.ny : R.nx, Mm = row ? R.nx : R.ny;
+    const int BR = band_rows(R.nx, R.ny, ES);
+    const int nb = (M + BR - 1) / BR;
+    const int band_floats = BR * ld;
+    const float halfM = 0.5f * (float)(M - 1);
+    const int total_r = R.nrow * C.nchunk, total_c = (R.na - R.nrow) * C.nchunk;
+    const int total = row ? total_r : total_c;
+    const int ustart = row ? 0 : total_r;
+    float* P = C.b.part + (row ? 0 : (size_t)((R.ny + BR - 1) / BR) * total_r * 32);
+    // ---- partials: items (band, 32 units), band-major, in contiguous ranges per block
+    const int nchk = (total + 31) / 32;
+    const long items = (long)nb * nchk;
+    const long it0 = items * C.amember / C.asize, it1 = items * (C.amember + 1) / C.asize;
+    int cur = -1;
+    for (long it = it0; it < it1; ++it) {
+        const int b = (int)(it / nchk), ch = (int)(it - (long)b * nchk);
+        if (b != cur) {
+            __syncthreads();  // the buffer's previous band is read
+            if (threadIdx.x == 0) {
+                const int rows = min(BR, M - b * BR);
+                bulk_load(smem, img_base + (size_t)b * band_floats, ES * rows * ld, &mbar[0]);
+            }
+            if (!mbar_wait(&mbar[0], parity & 1u, T.wait_ns, T.err)) return false;
+            parity ^= 1u;
+            cur = b;
+        }
+        const int u = ch * 32 + warp;
+        if (u >= total) continue;
+        const int unit = ustart + u;
+        const int a = unit / C.nchunk;
+        const int k = (unit - a * C.nchunk) * 32 + lane;
+        const AngleRec& r = R.rec[a];
+        float part = 0.f;
+        if (k < r.width) {
+            int mlo, mhi;
+            const ff Ak = ray_span(r, k, M, Mm, mlo, mhi);
+            const int m0 = max(mlo, b * BR), m1 = min(mhi, (b + 1) * BR);
+            if (m0 < m1) {
+                int j0;
+                int q = split_fixed22(ff_add(Ak, ff_mul_f((float)m0 - halfM, r.slope)), j0);
+                const int step = r.slope_q22;
+                const TS* rp = smem + (m0 - b * BR) * ld + kPad + j0;
+                const int jlo = -kPad - j0, jhi = ld - 1 - kPad - j0;
+                float s0 = 0.f, s1 = 0.f;
+#pragma unroll 4
+                for (int m = m0; m < m1; ++m, rp += ld, q += step) {
+                    const int j = chk(q >> 22, jlo, jhi, CHK_REGION_BAND);
+                    const float mf = frac_int<22>(q);
+                    const float v0 = to_f32<DT>(rp[j]), v1 = to_f32<DT>(rp[j + 1]);
+                    s0 += v0;
+                    s1 = fmaf(mf, v1 - v0, s1);
+                }
+                part = fmaf(s1, 2.384185791015625e-07f, s0);
+            }
+        }
+        P[((size_t)b * total + u) * 32 + lane] = part;
+    }
+    if (!team_sync<SOLO>(T)) return false;  // every band's partials are in
+    // ---- one warp per unit: the bands the ray crosses, in order, then the update
+    for (int u = C.amember * 32 + warp; u < total; u += C.asize * 32) {
+        const int unit = ustart + u;
+        const int a = unit / C.nchunk;
+        const int k = (unit - a * C.nchunk) * 32 + lane;
+        const AngleRec& r = R.rec[a];
+        if (k >= r.width) continue;
+        int mlo, mhi;
+        ray_span(r, k, M, Mm, mlo, mhi);
+        float sum = 0.f, cmp = 0.f;
+        for (int b = 0; b < nb; ++b) {
+            const int m0 = max(mlo, b * BR), m1 = min(mhi, (b + 1) * BR);
+            if (m0 < m1) neu_add(sum, cmp, __ldcg(P + ((size_t)b * total + u) * 32 + lane));
+        }
+        ff tot = ff_mul_f(r.inv_w, two_sum(sum, cmp));
+        const float acc = tot.hi + tot.lo;
+        const size_t o = (size_t)a * R.stride + k;
+        if (R.reg == 0) {
+            float res = C.b.pp[o] - acc;
+            if (R.weighting) res *= C.b.sig[o];
+            C.b.u[o] = res;
+        } else if (R.reg >= 2) {
+            C.b.u[o] = -R.alpha * acc;
+        } else {
+            const float sg = C.b.sig[o];
+            C.b.u[o] = (C.b.u[o] + sg * (acc - C.b.pp[o])) / (1.f + 0.5f * sg);
+        }
+    }
+    return true;
+}
+
 // CP gradient dual on this thread's pixels: v = proj_{|v| <= lambda}(v + sigma_v grad xbar).
 template <int DT>
 __device__ __forceinline__ void dual_grad(const Ctx& C) {
@@ -1130,11 +1235,20 @@ __device__ __forceinline__ bool solve_region(const BatchRoi& R, const RegionBufs
             }
         } else if (C.stage == 1) {
             if (R.reg == 1) dual_grad<DT>(C);
-            for (int row = 1; row >= 0; --row) {
-                if (C.arow >= 0 && row != C.arow) continue;
-                if (!phase_a_banded<SOLO, DT>(C, TA, row, row ? bufs.xa_base : bufs.xaT_base, row ? C.lda : C.ldaT,
-                                              smem, mbar, parity))
+            // a large team whose blocks would take more units than warps (the per-32-unit
+            // schedule would stream the image more than once): by row band, the same bits.
+            // The test is the same in every block of the team (the path adds a team barrier).
+            if (!SOLO && C.b.part && C.arow >= 0 && R.na * C.nchunk > BNW * T.size) {
+                if (!phase_a_rowband<SOLO, DT>(C, T, C.arow, C.arow ? bufs.xa_base : bufs.xaT_base,
+                                               C.arow ? C.lda : C.ldaT, smem, mbar, parity))
                     return false;
+            } else {
+                for (int row = 1; row >= 0; --row) {
+                    if (C.arow >= 0 && row != C.arow) continue;
+                    if (!phase_a_banded<SOLO, DT>(C, TA, row, row ? bufs.xa_base : bufs.xaT_base,
+                                                  row ? C.lda : C.ldaT, smem, mbar, parity))
+                        return false;
+                }
             }
         } else {
             if (R.reg == 1) dual_grad<DT>(C);

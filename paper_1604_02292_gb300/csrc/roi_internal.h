@@ -409,6 +409,8 @@ struct BatchArgs {
     float* slot_xaT;
     size_t pad_cap;
     float* slot_fgp;       // 5 img_cap per slot when a region uses reg = 3, else null
+    float* slot_part;      // per-band ray partial sums of a lone box's team (row-band phase A), else null
+    size_t part_cap;
     int* err;
     unsigned long long wait_ns;
     int team;              // blocks per region: 1, or > 1 for a cooperative launch of teams
@@ -428,6 +430,8 @@ struct RegionBufs {
     void* xa_base;         // storage dt of the region (float, bfloat16 or half)
     void* xaT_base;
     float* fgp;            // reg = 3: FGP state, 5 box arrays (v_x, v_y, r_x, r_y, x)
+    float* part;           // a band-streamed box on a large team: [band][unit][32] partial ray sums
+                           // per branch (rows first), else null (see phase_a_rowband)
 };
 
 // ---- serving: one cooperative launch whose blocks take requests from rings in

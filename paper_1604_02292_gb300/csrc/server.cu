@@ -383,6 +383,7 @@ void publish(roi_server* s, int pi, Req* r, size_t slot) {
     B.xa_base = base + r->lay.xa;
     B.xaT_base = base + r->lay.xaT;
     B.fgp = r->prm.reg >= ROI_FILTER_TV ? reinterpret_cast<float*>(base + r->lay.fgp) : nullptr;
+    B.part = nullptr;
     hdr.seq = (unsigned long long)r->ticket + 1ull;
     std::memcpy(sp, &hdr, sizeof hdr);
     std::memcpy(sp + roi::serve_slot_header_bytes, r->rec.data(), sizeof(AngleRec) * r->rec.size());
