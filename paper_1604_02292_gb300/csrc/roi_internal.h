@@ -472,6 +472,10 @@ struct ServeArgs {
     // testing only: > 0 barrier participants per team that never arrive; < 0 the team
     // leaders stay away (members' mailbox waits run out)
     int absent;
+    // solo launches (one team of every block): per-band ray partial sums for the row-band
+    // phase A of band-streamed boxes, when the request's fit in solo_part_cap floats
+    float* solo_part;
+    size_t solo_part_cap;
 };
 size_t serve_smem_bytes();
 int serve_max_blocks(int device);  // co-resident blocks of the serving kernel

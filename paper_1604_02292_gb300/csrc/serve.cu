@@ -164,7 +164,20 @@ __global__ void __launch_bounds__(BPT, 1) k_serve(const ServeArgs A) {
         const unsigned char* rp = sp + serve_slot_header_bytes;
         for (int w = tid; w < rec_words; w += BPT)
             reinterpret_cast<unsigned*>(myrec)[w] = ld_relaxed_sys_u32(rp + 4 * (size_t)w);
-        if (tid == 0) s_slot.roi.rec = myrec;
+        if (tid == 0) {
+            s_slot.roi.rec = myrec;
+            // a solo launch (one team of every block): the row-band phase A of a band-streamed
+            // box uses the solo partial-sum buffer when the box's partials fit (same bits)
+            s_slot.bufs.part = nullptr;
+            const BatchRoi& R = s_slot.roi;
+            const int es = dt_size(R.dt);
+            if (A.solo_part && s_team.size > 1 && s_team.size == (int)gridDim.x && stage_mode(R.nx, R.ny, es) == 1) {
+                const int br = band_rows(R.nx, R.ny, es);
+                const size_t need = ((size_t)((R.ny + br - 1) / br) * R.nrow + (size_t)((R.nx + br - 1) / br) *
+                                     (R.na - R.nrow)) * ((R.stride + 31) / 32) * 32;
+                if (need <= A.solo_part_cap) s_slot.bufs.part = A.solo_part;
+            }
+        }
         __syncthreads();
         // one code path for both pools (a single block is a team of one at run time)
         const bool ok = rs::solve_region_dt<false>(s_slot.roi, s_slot.bufs, s_team, smem, s_mbar, parity, &s_cnt);

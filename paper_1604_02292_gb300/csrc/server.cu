@@ -174,6 +174,8 @@ struct roi_server {
     unsigned* mseq_d = nullptr;
     long long* mval_d = nullptr;
     AngleRec* rec_slots_d = nullptr;
+    float* solo_part_d = nullptr;  // row-band partial sums of solo launches (see ensure_rings)
+    size_t solo_part_cap = 0;      // floats
     size_t ctl_reset_bytes = 0;  // bars + mail words, zeroed at each launch
     unsigned* ctl_reset_d = nullptr;
     // page-locked memory
@@ -277,6 +279,26 @@ roi_status ensure_rings(roi_server* s) {
     }
     if (!s->rec_slots_d)
         SCU(s, roi::dev_malloc((void**)&s->rec_slots_d, sizeof(AngleRec) * (size_t)s->max_na * s->blocks));
+    if (!s->solo_part_d) {
+        // the largest square box of each geometry whose images are band-streamed, its row-band
+        // partials (a box's window is below 1.5 side + 8 bins), at most 64 MB: larger boxes
+        // keep the per-32-unit phase A (the kernel checks each request's own size)
+        size_t need = 0;
+        for (const roi::SinoView& v : s->sinos) {
+            const int es = roi::dt_size(v.dt);
+            for (int side = std::min(v.N, 4096); side >= 1; --side)
+                if (roi::stage_mode(side, side, es) == 1) {
+                    const int br = roi::band_rows(side, side, es);
+                    need = std::max(need, (size_t)((side + br - 1) / br) * v.na * ((side * 3 / 2 + 8 + 31) / 32) * 32);
+                    break;
+                }
+        }
+        need = std::min<size_t>(need, (size_t)16 << 20);
+        if (need) {
+            SCU(s, roi::dev_malloc((void**)&s->solo_part_d, sizeof(float) * need));
+            s->solo_part_cap = need;
+        }
+    }
     s->rings_ready = true;
     return ROI_OK;
 }
@@ -502,6 +524,8 @@ roi_status launch(roi_server* s) {
     A.err = s->err_d;
     A.wait_ns = s->opt_wait_ns;
     A.absent = s->opt_absent;
+    A.solo_part = s->mode == 1 ? s->solo_part_d : nullptr;
+    A.solo_part_cap = s->solo_part_cap;
     cudaError_t e = roi::launch_serve(A, s->blocks, s->st);
     if (e != cudaSuccess) return scuda(s, e, "serving kernel launch");
     SCU(s, cudaEventRecord(s->ev_end, s->st));
@@ -594,6 +618,7 @@ void free_all(roi_server* s) {
     if (s->arena_d) cudaFree(s->arena_d);
     if (s->dctl) cudaFree(s->dctl);
     if (s->rec_slots_d) cudaFree(s->rec_slots_d);
+    if (s->solo_part_d) cudaFree(s->solo_part_d);
     if (s->out_h) cudaFreeHost(s->out_h);
     if (s->ctl_h) cudaFreeHost(s->ctl_h);
     if (s->ring_alloc) cudaFreeHost(s->ring_alloc);
