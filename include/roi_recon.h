@@ -502,7 +502,9 @@ typedef struct {
 
 /* Creates a server on the current device (it owns a non-blocking stream).  cfg may be
  * NULL (defaults).  ROI_EINVAL for bad sizes, ROI_ENOMEM when the budgets cannot be
- * allocated. */
+ * allocated.  Besides the two budgets, the first submit allocates the rings, a per-block
+ * copy of a request's angle table, and up to 64 MB of per-band partial sums that solo
+ * launches use for band-streamed boxes. */
 roi_status roi_server_create(const roi_server_config* cfg, roi_server_t* out);
 
 /* Registers the resident sinogram and FBP image of handle h (fbp done; ROI_ESTATE
